@@ -1,0 +1,211 @@
+/*
+ * henry.h -- C ABI of the GB300 (sm_103a) solver for the stochastic Henry
+ * problem and its multilevel Monte Carlo (MLMC) level statistics.
+ *
+ * Method (arxiv 2403.17018):
+ *   section 2.1, Eqs. 1-5: density-driven Darcy flow coupled to salt
+ *     transport, rho(c) = rho0 + (rho1 - rho0) c, D_tensor = phi D I;
+ *     boundary conditions of the Henry problem (seawater on the right,
+ *     freshwater inflow on the left, no flow top and bottom);
+ *   section 2.3: implicit Euler with r = T / tau steps, Newton on the
+ *     coupled (p, c) system, geometric multigrid V-cycles for the linear
+ *     solves, Gaussian elimination on the coarsest grid;
+ *   section 3, Eqs. EgL/A, Def. of Y_l and V_l: MLMC telescoping estimator
+ *     built from level pairs (g_l, g_{l-1}) that share one random input xi.
+ * The discretisation is cell-centred finite volumes with harmonic face K and
+ * phi, arithmetic face density, full upwinding of the advected rho and rho c.
+ *
+ * Conventions (all entry points):
+ *   - Return HENRY_OK (0) or a negative HENRY_E_* code; no exception crosses
+ *     the ABI. henry_strerror() names the code; henry_last_error() gives a
+ *     message for the last failing call on this host thread.
+ *   - Pointers marked "device" are CUDA device pointers owned by the caller
+ *     (the Python binding passes torch tensors). "host" pointers are plain
+ *     host memory. Arrays are C-contiguous FP64 unless stated otherwise.
+ *   - Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default
+ *     stream) and is asynchronous unless the entry point says otherwise.
+ *   - Per-sample failures (Newton iteration cap, non-finite values) are
+ *     reported in status[] and do not fail the call.
+ *   - A context is not thread-safe. Calls for different levels may run
+ *     concurrently on different streams; two calls that use the same
+ *     level's workspace must not overlap (fine level l and coarse level l-1
+ *     of a pair have separate workspaces).
+ */
+#ifndef HENRY_H
+#define HENRY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define HENRY_OK 0
+#define HENRY_E_INVALID (-1)     /* bad argument (NULL, size, level, config)  */
+#define HENRY_E_CUDA (-2)        /* a CUDA runtime call failed                */
+#define HENRY_E_NOMEM (-3)       /* device allocation failed                  */
+#define HENRY_E_TIMEOUT (-4)     /* a bounded device wait gave up             */
+#define HENRY_E_UNSUPPORTED (-5) /* grid cannot be coarsened to <= 32 cells  */
+
+/* ---- per-sample status bits (status[] outputs) ------------------------- */
+#define HENRY_S_OK 0
+#define HENRY_S_MAXIT 1          /* some time step hit newton_maxit          */
+#define HENRY_S_NONFINITE 2      /* a residual norm became NaN or Inf        */
+#define HENRY_S_BADINPUT 4       /* xi was not finite                        */
+
+/* ---- quantities of interest (q[] outputs, HENRY_NQ per sample) --------- */
+#define HENRY_NQ 6
+/* 0  Q_S   = int c rho dx                    (section 4, Eq. integral_s)
+ * 1  M     = int phi rho c dx                (stored salt mass, Eq. 2)
+ * 2  toe   = int c (Lx - x) dx               (salt-wedge penetration)
+ * 3..5     c at (1.40,0.05), (1.65,0.25), (1.90,0.50): the paper's points
+ *          3, 9 and 15 of Eq. 12points shifted into y in [0,1]; bilinear
+ *          interpolation of cell values clamped to the outer cell centres. */
+
+#define HENRY_PREC_FP64 0        /* multigrid in FP64                        */
+#define HENRY_PREC_FP32_MG 1     /* FP32 V-cycles inside FP64 defect correction */
+
+#define HENRY_LOOP_HOST 0        /* host checks convergence once per iteration */
+#define HENRY_LOOP_GRAPH 1       /* one CUDA graph per time step with a device-
+                                    side while loop over Newton iterations   */
+
+typedef struct henry_config {
+  /* physics (Table 1; g from Eq. 3; q0 = 6.6e-2 kg/s / rho0) */
+  double rho0, rho1, mu, g, D, K0, phi0, q0;
+  double Lx, Ly;       /* domain [0,Lx] x [0,Ly], y upward                  */
+  double T;            /* final time [s]                                    */
+  /* level hierarchy: level l has nx0*2^l x ny0*2^l cells, nt0*2^l steps    */
+  int nx0, ny0, nt0, nlevels;
+  int n_xi;            /* 3 or 6 random variables                           */
+  /* solver */
+  int precision;       /* HENRY_PREC_*                                      */
+  int loop_mode;       /* HENRY_LOOP_*                                      */
+  double newton_rtol;  /* stop when ||R|| <= max(rtol ||R(u^{n-1})||, atol) */
+  double newton_atol;  /*   (scaled RMS residual, units of c per step)      */
+  int newton_maxit;    /* iteration cap per step -> HENRY_S_MAXIT           */
+  int nu1, nu2;        /* red-black block Gauss-Seidel sweeps pre / post    */
+  int vcycles;         /* V-cycles per defect-correction iteration          */
+  int reserved[8];
+} henry_config;
+
+typedef struct henry_ctx henry_ctx; /* opaque: owns device workspaces */
+
+/* Running per-QoI statistics of one MLMC level: count, mean and sum of
+ * squared deviations (M2) of g_l and of g_l - g_{l-1} (g_{-1} = 0). */
+typedef struct henry_level_stats {
+  int64_t n;
+  double mean_f[HENRY_NQ], m2_f[HENRY_NQ];
+  double mean_d[HENRY_NQ], m2_d[HENRY_NQ];
+} henry_level_stats;
+
+/* Fill *cfg with the default configuration: Table 1 physics (rho1 =
+ * 1024.99, D = 18.8571e-6, K0 = 1.020408e-9, phi0 = 0.35, mu = 1e-3,
+ * g = 9.8), q0 = 6.6e-5 m/s, [0,2]x[0,1], T = 43200 s, 32x16 cells and 24
+ * steps on level 0, 2 levels, 3 random variables, FP64 multigrid, rtol
+ * 1e-10, atol 1e-12, maxit 30, V(2,2), 1 V-cycle per iteration. */
+int henry_default_config(henry_config* cfg);
+
+/* Validate *cfg and create a context for levels 0..cfg->nlevels-1.
+ * Device workspaces are allocated lazily, per (level, role), on the first
+ * call that needs them and grown when a larger batch arrives; growing
+ * synchronises the device. The device current at creation is used.
+ * Errors: HENRY_E_INVALID, HENRY_E_UNSUPPORTED (a level's grid does not
+ * coarsen to at most 32 cells with an even nx on every multigrid level). */
+int henry_create_levels(const henry_config* cfg, henry_ctx** out);
+
+/* Free the context and its device memory (synchronises the device). */
+void henry_destroy(henry_ctx* ctx);
+
+/* Batched deterministic solves of one level (section 2.3): for each of the
+ * B samples, the random fields from xi (and the optional per-cell log-K
+ * perturbation), then r_l implicit Euler steps from c = 0, then the QoIs.
+ *   xi      device [B][n_xi]
+ *   logk    device [B][ny_l][nx_l] added to log K, or NULL
+ *   q       device [B][HENRY_NQ] out
+ *   c_out   device [B][ny_l][nx_l] out (c at T), or NULL
+ *   p_out   device [B][ny_l][nx_l] out (p at T), or NULL
+ *   status  device int [B] out (HENRY_S_* bits)
+ *   iters   device int [B] out (total defect-correction iterations), or NULL
+ * B may be 0 (no work). Errors: HENRY_E_INVALID, HENRY_E_CUDA, HENRY_E_NOMEM. */
+int henry_solve(henry_ctx* ctx, int level, const double* xi, const double* logk, int B,
+                double* q, double* c_out, double* p_out, int* status, int* iters,
+                void* stream);
+
+/* MLMC level pair (Eq. A): the same xi drives a level-l solve and a
+ * level-(l-1) solve. At level 0 only the fine solve runs and q_coarse,
+ * c_coarse must be NULL.
+ *   q_fine, q_coarse   device [B][HENRY_NQ] out
+ *   c_fine             device [B][ny_l][nx_l] out, or NULL
+ *   c_coarse           device [B][ny_{l-1}][nx_{l-1}] out, or NULL
+ *   status             device int [B] out, OR of both solves' bits
+ * The coarse result is bitwise equal to henry_solve at level l-1 on the same
+ * xi. Errors as henry_solve. */
+int henry_sample_pairs(henry_ctx* ctx, int level, const double* xi, int B,
+                       double* q_fine, double* q_coarse, double* c_fine, double* c_coarse,
+                       int* status, void* stream);
+
+/* Merge one batch into the running statistics of a level (Def. of Y_l and
+ * V_l; V_l = m2_d / (n - 1)). Samples with status != 0 are skipped.
+ * Welford per thread in sample order, then a fixed pairwise Chan merge tree
+ * on the device (deterministic for a given B), then a Chan merge into
+ * *inout on the host. Synchronous: returns when the batch is merged.
+ *   q_fine    device [B][HENRY_NQ]
+ *   q_coarse  device [B][HENRY_NQ] or NULL (level 0: g_{-1} = 0)
+ *   status    device int [B] or NULL (all samples valid)
+ *   inout     host, running state updated in place */
+int mlmc_level_stats(henry_ctx* ctx, int level, const double* q_fine, const double* q_coarse,
+                     int B, const int* status, henry_level_stats* inout, void* stream);
+
+/* Per-cell running statistics of the c field of one level (section 4, Test
+ * A1): for every cell of the level-l grid, Welford over the batch in sample
+ * order of g = c_l and of d = c_l - P0 c_{l-1}, P0 the piecewise-constant
+ * transfer from the level-(l-1) grid. Samples with status != 0 are skipped.
+ *   c_fine    device [B][ny_l][nx_l];  c_coarse device [B][ny_{l-1}][nx_{l-1}] or NULL
+ *   n         device int64 [ny_l*nx_l]  running count (all cells equal)
+ *   mean_f, m2_f, mean_d, m2_d  device [ny_l][nx_l], updated in place */
+int mlmc_field_stats(henry_ctx* ctx, int level, const double* c_fine, const double* c_coarse,
+                     int B, const int* status, int64_t* n, double* mean_f, double* m2_f,
+                     double* mean_d, double* m2_d, void* stream);
+
+/* Evaluate the FP64 finite-volume residual of one implicit Euler step and,
+ * optionally, its exact Jacobian, for B states on an nx x ny grid (Eqs.
+ * 1-5 integrated over each cell). Context-free; for tests and tools.
+ *   phi, K          device [B][ny][nx] cell porosity and permeability
+ *   qin             device [B][ny] left-side inflow velocity per row [m/s]
+ *   p, c, c_old     device [B][ny][nx]
+ *   R               device [B][2][ny][nx] out: R_p then R_c
+ *   J               device [B][20][ny][nx] out or NULL: per cell the 2x2
+ *                   blocks (row = equation p|c, column = variable p|c,
+ *                   stored pp, pc, cp, cc) of d R_P / d u_Q for
+ *                   Q = P, W, E, S, N (in that order); blocks of missing
+ *                   neighbours are zero.
+ * Errors: HENRY_E_INVALID, HENRY_E_CUDA. */
+int henry_residual_jacobian(const henry_config* cfg, int nx, int ny, double tau, int B,
+                            const double* phi, const double* K, const double* qin,
+                            const double* p, const double* c, const double* c_old,
+                            double* R, double* J, void* stream);
+
+/* Random fields of the level-l grid for B samples (cell centres):
+ *   phi = phi0 (1 + 0.1 xi1 cos(pi x/2) sin(pi y) [+ 0.05 xi4 cos(pi x) sin(2 pi y)])
+ *   K   = K0 exp(0.5 xi2 sin(pi x/2) cos(pi y) [+ 0.05 xi5 sin(pi x) cos(2 pi y)] + logk)
+ *   qin = q0 (1 + 0.1 xi3 [+ 0.05 xi6 cos(pi y)])
+ * (the bracketed terms when n_xi = 6). Outputs device [B][ny][nx] and
+ * [B][ny]. logk may be NULL. */
+int henry_fields(henry_ctx* ctx, int level, const double* xi, const double* logk, int B,
+                 double* phi, double* K, double* qin, void* stream);
+
+/* Grid of level l: *nx, *ny, *nt (steps), *n_mg (multigrid levels). */
+int henry_level_info(const henry_ctx* ctx, int level, int* nx, int* ny, int* nt, int* n_mg);
+
+/* Device kernel launches issued by this context since creation (counts
+ * every launch, including those replayed inside CUDA graphs). */
+int64_t henry_launch_count(const henry_ctx* ctx);
+
+const char* henry_strerror(int code);
+const char* henry_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HENRY_H */

@@ -1,0 +1,273 @@
+"""ctypes binding of libhenry (include/henry.h): argument marshalling only.
+
+Every computation runs in the CUDA library; torch supplies device memory and
+streams. There is no CPU fallback: if libhenry.so cannot be loaded, calls
+raise. Names follow the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libhenry.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "henry.h")
+
+NQ = 6
+QOI_NAMES = ("Q_S", "salt_mass", "toe", "c_x3", "c_x9", "c_x15")
+PREC_FP64 = 0
+PREC_FP32_MG = 1
+LOOP_HOST = 0
+LOOP_GRAPH = 1
+S_MAXIT, S_NONFINITE, S_BADINPUT = 1, 2, 4
+ERRORS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "out of device memory",
+          -4: "device wait timed out", -5: "unsupported grid"}
+
+
+class HenryError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class HenryConfig(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("rho0", "rho1", "mu", "g", "D", "K0", "phi0", "q0", "Lx", "Ly", "T")] + \
+               [(n, ctypes.c_int) for n in ("nx0", "ny0", "nt0", "nlevels", "n_xi", "precision",
+                                             "loop_mode")] + \
+               [("newton_rtol", ctypes.c_double), ("newton_atol", ctypes.c_double),
+                ("newton_maxit", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+                ("vcycles", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
+
+
+class LevelStats(ctypes.Structure):
+    """Running per-QoI statistics of one MLMC level (henry_level_stats)."""
+    _fields_ = [("n", ctypes.c_int64), ("mean_f", ctypes.c_double * NQ),
+                ("m2_f", ctypes.c_double * NQ), ("mean_d", ctypes.c_double * NQ),
+                ("m2_d", ctypes.c_double * NQ)]
+
+    def numpy(self):
+        n = self.n
+        den = max(n - 1, 1)
+        return {"n": n, "mean_f": np.array(self.mean_f[:]), "var_f": np.array(self.m2_f[:]) / den,
+                "mean_d": np.array(self.mean_d[:]), "var_d": np.array(self.m2_d[:]) / den}
+
+
+_lib = None
+
+
+def load():
+    """Load libhenry.so (built by paper_2403_17018_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run paper_2403_17018_gb300.build.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    cfgp = ctypes.POINTER(HenryConfig)
+    sig = {
+        "henry_default_config": (I, [cfgp]),
+        "henry_create_levels": (I, [cfgp, ctypes.POINTER(P)]),
+        "henry_destroy": (None, [P]),
+        "henry_solve": (I, [P, I, V, V, I, V, V, V, V, V, V]),
+        "henry_sample_pairs": (I, [P, I, V, I, V, V, V, V, V, V]),
+        "mlmc_level_stats": (I, [P, I, V, V, I, V, ctypes.POINTER(LevelStats), V]),
+        "mlmc_field_stats": (I, [P, I, V, V, I, V, V, V, V, V, V, V]),
+        "henry_residual_jacobian": (I, [cfgp, I, I, D, I, V, V, V, V, V, V, V, V, V]),
+        "henry_fields": (I, [P, I, V, V, I, V, V, V, V]),
+        "henry_level_info": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                                 ctypes.POINTER(I)]),
+        "henry_launch_count": (ctypes.c_int64, [P]),
+        "henry_strerror": (ctypes.c_char_p, [I]),
+        "henry_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def declared_symbols() -> list[str]:
+    """Entry points declared in include/henry.h."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|int64_t|const char\*)\s+(\w+)\s*\(", text, re.M)))
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise HenryError(rc, load().henry_last_error().decode())
+
+
+def default_config(**kw) -> HenryConfig:
+    cfg = HenryConfig()
+    _check(load().henry_default_config(ctypes.byref(cfg)))
+    for k, v in kw.items():
+        if not hasattr(cfg, k):
+            raise KeyError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+def _ptr(t, dtype=None, shape=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (or NULL for None)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class LevelInfo:
+    nx: int
+    ny: int
+    nt: int
+    n_mg: int
+
+
+class Context:
+    """A henry_ctx: levels 0..cfg.nlevels-1 and their device workspaces."""
+
+    def __init__(self, cfg: HenryConfig):
+        self.lib = load()
+        self.cfg = cfg
+        h = ctypes.c_void_p()
+        _check(self.lib.henry_create_levels(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if self._h:
+            self.lib.henry_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def level_info(self, level: int) -> LevelInfo:
+        v = [ctypes.c_int() for _ in range(4)]
+        _check(self.lib.henry_level_info(self._h, level, *[ctypes.byref(x) for x in v]))
+        return LevelInfo(*[x.value for x in v])
+
+    def launch_count(self) -> int:
+        return int(self.lib.henry_launch_count(self._h))
+
+    def solve(self, level, xi, logk=None, want_c=False, want_p=False, want_iters=False,
+              stream=None):
+        """henry_solve: returns dict(q [B,NQ], status [B], c, p, iters as asked)."""
+        import torch
+        B = xi.shape[0]
+        li = self.level_info(level)
+        dev = xi.device
+        q = torch.empty((B, NQ), dtype=torch.float64, device=dev)
+        st = torch.empty((B,), dtype=torch.int32, device=dev)
+        c = torch.empty((B, li.ny, li.nx), dtype=torch.float64, device=dev) if want_c else None
+        p = torch.empty((B, li.ny, li.nx), dtype=torch.float64, device=dev) if want_p else None
+        it = torch.empty((B,), dtype=torch.int32, device=dev) if want_iters else None
+        _check(self.lib.henry_solve(
+            self._h, level, _ptr(xi, torch.float64, (B, self.cfg.n_xi), "xi"),
+            _ptr(logk, torch.float64, (B, li.ny, li.nx), "logk"), B, _ptr(q), _ptr(c), _ptr(p),
+            _ptr(st), _ptr(it), _stream(stream)))
+        return {"q": q, "status": st, "c": c, "p": p, "iters": it}
+
+    def sample_pairs(self, level, xi, want_c=False, stream=None):
+        """henry_sample_pairs: (q_fine, q_coarse or None, c_fine, c_coarse, status)."""
+        import torch
+        B = xi.shape[0]
+        dev = xi.device
+        li = self.level_info(level)
+        qf = torch.empty((B, NQ), dtype=torch.float64, device=dev)
+        qc = torch.empty((B, NQ), dtype=torch.float64, device=dev) if level > 0 else None
+        cf = torch.empty((B, li.ny, li.nx), dtype=torch.float64, device=dev) if want_c else None
+        cc = None
+        if want_c and level > 0:
+            lc = self.level_info(level - 1)
+            cc = torch.empty((B, lc.ny, lc.nx), dtype=torch.float64, device=dev)
+        st = torch.empty((B,), dtype=torch.int32, device=dev)
+        _check(self.lib.henry_sample_pairs(
+            self._h, level, _ptr(xi, torch.float64, (B, self.cfg.n_xi), "xi"), B, _ptr(qf),
+            _ptr(qc), _ptr(cf), _ptr(cc), _ptr(st), _stream(stream)))
+        return qf, qc, cf, cc, st
+
+    def level_stats(self, level, q_fine, q_coarse, status, stats: LevelStats, stream=None):
+        """mlmc_level_stats (synchronous): merges the batch into `stats`."""
+        import torch
+        B = q_fine.shape[0]
+        _check(self.lib.mlmc_level_stats(
+            self._h, level, _ptr(q_fine, torch.float64, (B, NQ), "q_fine"),
+            _ptr(q_coarse, torch.float64, (B, NQ), "q_coarse"), B,
+            _ptr(status, torch.int32, (B,), "status"), ctypes.byref(stats), _stream(stream)))
+        return stats
+
+    def field_stats(self, level, c_fine, c_coarse, status, acc: dict, stream=None):
+        """mlmc_field_stats: acc holds device tensors n, mean_f, m2_f, mean_d, m2_d."""
+        import torch
+        B = c_fine.shape[0]
+        _check(self.lib.mlmc_field_stats(
+            self._h, level, _ptr(c_fine, torch.float64, None, "c_fine"),
+            _ptr(c_coarse, torch.float64, None, "c_coarse"), B,
+            _ptr(status, torch.int32, (B,), "status"), _ptr(acc["n"], torch.int64),
+            _ptr(acc["mean_f"], torch.float64), _ptr(acc["m2_f"], torch.float64),
+            _ptr(acc["mean_d"], torch.float64), _ptr(acc["m2_d"], torch.float64),
+            _stream(stream)))
+        return acc
+
+    def fields(self, level, xi, logk=None, stream=None):
+        import torch
+        B = xi.shape[0]
+        li = self.level_info(level)
+        dev = xi.device
+        phi = torch.empty((B, li.ny, li.nx), dtype=torch.float64, device=dev)
+        K = torch.empty_like(phi)
+        qin = torch.empty((B, li.ny), dtype=torch.float64, device=dev)
+        _check(self.lib.henry_fields(self._h, level, _ptr(xi, torch.float64, (B, self.cfg.n_xi), "xi"),
+                                     _ptr(logk, torch.float64, (B, li.ny, li.nx), "logk"), B,
+                                     _ptr(phi), _ptr(K), _ptr(qin), _stream(stream)))
+        return phi, K, qin
+
+
+def new_field_accumulator(ny, nx, device="cuda"):
+    import torch
+    z = lambda: torch.zeros((ny, nx), dtype=torch.float64, device=device)
+    return {"n": torch.zeros((ny, nx), dtype=torch.int64, device=device), "mean_f": z(),
+            "m2_f": z(), "mean_d": z(), "m2_d": z()}
+
+
+def residual_jacobian(cfg: HenryConfig, tau, phi, K, qin, p, c, c_old, want_J=True, stream=None):
+    """henry_residual_jacobian: R [B,2,ny,nx] and J [B,20,ny,nx] (or None)."""
+    import torch
+    B, ny, nx = p.shape
+    R = torch.empty((B, 2, ny, nx), dtype=torch.float64, device=p.device)
+    J = torch.empty((B, 20, ny, nx), dtype=torch.float64, device=p.device) if want_J else None
+    f64 = torch.float64
+    _check(load().henry_residual_jacobian(
+        ctypes.byref(cfg), nx, ny, float(tau), B, _ptr(phi, f64, (B, ny, nx), "phi"),
+        _ptr(K, f64, (B, ny, nx), "K"), _ptr(qin, f64, (B, ny), "qin"), _ptr(p, f64, None, "p"),
+        _ptr(c, f64, (B, ny, nx), "c"), _ptr(c_old, f64, (B, ny, nx), "c_old"), _ptr(R), _ptr(J),
+        _stream(stream)))
+    return R, J

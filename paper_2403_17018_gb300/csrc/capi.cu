@@ -1,0 +1,308 @@
+// C ABI of libhenry (declarations and documentation in include/henry.h).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/henry.h"
+#include "solver.h"
+
+namespace henry {
+cudaError_t launch_level_stats(unsigned long long* ctr, int B, const double* qf, const double* qc,
+                               const int* status, double* out, cudaStream_t s);
+cudaError_t launch_field_stats(unsigned long long* ctr, int nx, int ny, int B, const double* cf,
+                               const double* cc, const int* status, int64_t* n, double* mean_f,
+                               double* m2_f, double* mean_d, double* m2_d, cudaStream_t s);
+cudaError_t launch_residual_jacobian(const Phys& P, const Geom& G, double tau, int B,
+                                     const double* phi, const double* K, const double* qin,
+                                     const double* p, const double* c, const double* c_old,
+                                     double* R, double* J, double* scratch, cudaStream_t s);
+}  // namespace henry
+
+using henry::Solver;
+
+struct henry_ctx {
+  henry_config cfg;
+  int device = 0;
+  // solvers per level: [0] fine role, [1] coarse role (level l-1 of a pair)
+  std::vector<std::unique_ptr<Solver>> role[2];
+  double* stats_dev = nullptr;         // 1 + 4*NQ doubles
+  double* stats_host = nullptr;        // pinned
+  unsigned long long* ctr = nullptr;   // launches outside the solvers
+};
+
+namespace {
+
+int fail(int code, const std::string& msg) {
+  henry::set_last_error(msg);
+  return code;
+}
+
+#define CKR(call)                                                                   \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return fail(e_ == cudaErrorMemoryAllocation ? HENRY_E_NOMEM : HENRY_E_CUDA,   \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));              \
+  } while (0)
+
+int level_dims(const henry_config& c, int level, int* nx, int* ny, int* nt) {
+  if (level < 0 || level >= c.nlevels) return HENRY_E_INVALID;
+  *nx = c.nx0 << level;
+  *ny = c.ny0 << level;
+  *nt = c.nt0 << level;
+  return HENRY_OK;
+}
+
+Solver* get_solver(henry_ctx* ctx, int level, int role) {
+  auto& v = ctx->role[role];
+  if (!v[level]) {
+    int nx, ny, nt;
+    level_dims(ctx->cfg, level, &nx, &ny, &nt);
+    v[level].reset(new Solver(ctx->cfg, nx, ny, nt));
+  }
+  return v[level].get();
+}
+
+int validate(const henry_config* c) {
+  if (!c) return fail(HENRY_E_INVALID, "config is NULL");
+  if (c->nlevels < 1 || c->nlevels > 12) return fail(HENRY_E_INVALID, "nlevels must be in 1..12");
+  if (c->nx0 < 2 || c->ny0 < 2 || c->nt0 < 1) return fail(HENRY_E_INVALID, "bad level-0 grid");
+  if (c->n_xi != 3 && c->n_xi != 6) return fail(HENRY_E_INVALID, "n_xi must be 3 or 6");
+  if (c->precision != HENRY_PREC_FP64 && c->precision != HENRY_PREC_FP32_MG)
+    return fail(HENRY_E_INVALID, "bad precision");
+  if (c->loop_mode != HENRY_LOOP_HOST && c->loop_mode != HENRY_LOOP_GRAPH)
+    return fail(HENRY_E_INVALID, "bad loop_mode");
+  if (!(c->T > 0) || !(c->Lx > 0) || !(c->Ly > 0) || !(c->mu > 0) || !(c->K0 > 0) ||
+      !(c->phi0 > 0) || !(c->D >= 0))
+    return fail(HENRY_E_INVALID, "non-positive physical parameter");
+  if (c->newton_maxit < 0 || c->nu1 < 0 || c->nu2 < 0 || c->vcycles < 1)
+    return fail(HENRY_E_INVALID, "bad solver parameter");
+  for (int l = 0; l < c->nlevels; ++l) {
+    std::vector<henry::Geom> g;
+    if (!henry::build_hierarchy(c->nx0 << l, c->ny0 << l, c->Lx, c->Ly, g))
+      return fail(HENRY_E_UNSUPPORTED, "level " + std::to_string(l) +
+                                           " does not coarsen to <= 32 cells with even nx");
+  }
+  return HENRY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int henry_default_config(henry_config* c) {
+  if (!c) return fail(HENRY_E_INVALID, "config is NULL");
+  *c = henry_config{};
+  c->rho0 = 1000.0;
+  c->rho1 = 1024.99;
+  c->mu = 1e-3;
+  c->g = 9.8;
+  c->D = 18.8571e-6;
+  c->K0 = 1.020408e-9;
+  c->phi0 = 0.35;
+  c->q0 = 6.6e-5;
+  c->Lx = 2.0;
+  c->Ly = 1.0;
+  c->T = 43200.0;
+  c->nx0 = 32;
+  c->ny0 = 16;
+  c->nt0 = 24;
+  c->nlevels = 2;
+  c->n_xi = 3;
+  c->precision = HENRY_PREC_FP64;
+  c->loop_mode = HENRY_LOOP_GRAPH;
+  c->newton_rtol = 1e-10;
+  c->newton_atol = 1e-12;
+  c->newton_maxit = 30;
+  c->nu1 = 2;
+  c->nu2 = 2;
+  c->vcycles = 1;
+  return HENRY_OK;
+}
+
+int henry_create_levels(const henry_config* cfg, henry_ctx** out) {
+  if (!out) return fail(HENRY_E_INVALID, "out is NULL");
+  *out = nullptr;
+  int rc = validate(cfg);
+  if (rc) return rc;
+  henry_ctx* ctx = new (std::nothrow) henry_ctx;
+  if (!ctx) return fail(HENRY_E_NOMEM, "host allocation failed");
+  ctx->cfg = *cfg;
+  ctx->role[0].resize(cfg->nlevels);
+  ctx->role[1].resize(cfg->nlevels);
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->stats_dev, sizeof(double) * (1 + 4 * HENRY_NQ) + 64);
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&ctx->stats_host, sizeof(double) * (1 + 4 * HENRY_NQ), 0);
+  if (e == cudaSuccess) {
+    ctx->ctr = (unsigned long long*)((char*)ctx->stats_dev + sizeof(double) * (1 + 4 * HENRY_NQ) + 32);
+    e = cudaMemset(ctx->ctr, 0, sizeof(unsigned long long));
+  }
+  if (e != cudaSuccess) {
+    henry_destroy(ctx);
+    return fail(HENRY_E_CUDA, std::string("context set-up: ") + cudaGetErrorString(e));
+  }
+  *out = ctx;
+  return HENRY_OK;
+}
+
+void henry_destroy(henry_ctx* ctx) {
+  if (!ctx) return;
+  cudaDeviceSynchronize();
+  for (auto& v : ctx->role) v.clear();
+  if (ctx->stats_dev) cudaFree(ctx->stats_dev);
+  if (ctx->stats_host) cudaFreeHost(ctx->stats_host);
+  delete ctx;
+}
+
+int henry_level_info(const henry_ctx* ctx, int level, int* nx, int* ny, int* nt, int* n_mg) {
+  if (!ctx || !nx || !ny || !nt || !n_mg) return fail(HENRY_E_INVALID, "NULL argument");
+  if (level_dims(ctx->cfg, level, nx, ny, nt)) return fail(HENRY_E_INVALID, "bad level");
+  std::vector<henry::Geom> g;
+  henry::build_hierarchy(*nx, *ny, ctx->cfg.Lx, ctx->cfg.Ly, g);
+  *n_mg = (int)g.size();
+  return HENRY_OK;
+}
+
+int henry_solve(henry_ctx* ctx, int level, const double* xi, const double* logk, int B, double* q,
+                double* c_out, double* p_out, int* status, int* iters, void* stream) {
+  if (!ctx) return fail(HENRY_E_INVALID, "ctx is NULL");
+  if (level < 0 || level >= ctx->cfg.nlevels) return fail(HENRY_E_INVALID, "bad level");
+  if (B < 0) return fail(HENRY_E_INVALID, "B < 0");
+  if (B == 0) return HENRY_OK;
+  if (!xi || !q || !status) return fail(HENRY_E_INVALID, "xi, q and status are required");
+  CKR(cudaSetDevice(ctx->device));
+  return get_solver(ctx, level, 0)->run(xi, logk, B, q, c_out, p_out, status, iters, 0,
+                                        (cudaStream_t)stream);
+}
+
+int henry_sample_pairs(henry_ctx* ctx, int level, const double* xi, int B, double* q_fine,
+                       double* q_coarse, double* c_fine, double* c_coarse, int* status,
+                       void* stream) {
+  if (!ctx) return fail(HENRY_E_INVALID, "ctx is NULL");
+  if (level < 0 || level >= ctx->cfg.nlevels) return fail(HENRY_E_INVALID, "bad level");
+  if (B < 0) return fail(HENRY_E_INVALID, "B < 0");
+  if (level == 0 && (q_coarse || c_coarse))
+    return fail(HENRY_E_INVALID, "level 0 has no coarse solve: q_coarse and c_coarse must be NULL");
+  if (level > 0 && !q_coarse) return fail(HENRY_E_INVALID, "q_coarse is required for level > 0");
+  if (B == 0) return HENRY_OK;
+  if (!xi || !q_fine || !status) return fail(HENRY_E_INVALID, "xi, q_fine and status are required");
+  CKR(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = get_solver(ctx, level, 0)->run(xi, nullptr, B, q_fine, c_fine, nullptr, status, nullptr,
+                                          0, s);
+  if (rc || level == 0) return rc;
+  return get_solver(ctx, level - 1, 1)->run(xi, nullptr, B, q_coarse, c_coarse, nullptr, status,
+                                            nullptr, 1, s);
+}
+
+int henry_fields(henry_ctx* ctx, int level, const double* xi, const double* logk, int B,
+                 double* phi, double* K, double* qin, void* stream) {
+  if (!ctx) return fail(HENRY_E_INVALID, "ctx is NULL");
+  if (level < 0 || level >= ctx->cfg.nlevels) return fail(HENRY_E_INVALID, "bad level");
+  if (B < 0) return fail(HENRY_E_INVALID, "B < 0");
+  if (B == 0) return HENRY_OK;
+  if (!xi || !phi || !K || !qin) return fail(HENRY_E_INVALID, "NULL argument");
+  CKR(cudaSetDevice(ctx->device));
+  return get_solver(ctx, level, 0)->fields(xi, logk, B, phi, K, qin, (cudaStream_t)stream);
+}
+
+int mlmc_level_stats(henry_ctx* ctx, int level, const double* q_fine, const double* q_coarse,
+                     int B, const int* status, henry_level_stats* inout, void* stream) {
+  if (!ctx || !inout) return fail(HENRY_E_INVALID, "NULL argument");
+  if (level < 0 || level >= ctx->cfg.nlevels) return fail(HENRY_E_INVALID, "bad level");
+  if (B < 0) return fail(HENRY_E_INVALID, "B < 0");
+  if (B == 0) return HENRY_OK;
+  if (!q_fine) return fail(HENRY_E_INVALID, "q_fine is NULL");
+  if (level == 0 && q_coarse) return fail(HENRY_E_INVALID, "level 0 takes no q_coarse");
+  CKR(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  CKR(henry::launch_level_stats(ctx->ctr, B, q_fine, q_coarse, status, ctx->stats_dev, s));
+  CKR(cudaMemcpyAsync(ctx->stats_host, ctx->stats_dev, sizeof(double) * (1 + 4 * HENRY_NQ),
+                      cudaMemcpyDeviceToHost, s));
+  CKR(cudaStreamSynchronize(s));
+  const double* o = ctx->stats_host;
+  const double nb = o[0];
+  if (nb == 0.0) return HENRY_OK;
+  const double na = (double)inout->n;
+  const double n = na + nb;
+  for (int k = 0; k < HENRY_NQ; ++k) {
+    double d = o[1 + k] - inout->mean_f[k];
+    inout->mean_f[k] += d * (nb / n);
+    inout->m2_f[k] += o[1 + HENRY_NQ + k] + d * d * (na * nb / n);
+    d = o[1 + 2 * HENRY_NQ + k] - inout->mean_d[k];
+    inout->mean_d[k] += d * (nb / n);
+    inout->m2_d[k] += o[1 + 3 * HENRY_NQ + k] + d * d * (na * nb / n);
+  }
+  inout->n += (int64_t)nb;
+  return HENRY_OK;
+}
+
+int mlmc_field_stats(henry_ctx* ctx, int level, const double* c_fine, const double* c_coarse, int B,
+                     const int* status, int64_t* n, double* mean_f, double* m2_f, double* mean_d,
+                     double* m2_d, void* stream) {
+  if (!ctx) return fail(HENRY_E_INVALID, "ctx is NULL");
+  if (level < 0 || level >= ctx->cfg.nlevels) return fail(HENRY_E_INVALID, "bad level");
+  if (B < 0) return fail(HENRY_E_INVALID, "B < 0");
+  if (level == 0 && c_coarse) return fail(HENRY_E_INVALID, "level 0 takes no c_coarse");
+  if (B == 0) return HENRY_OK;
+  if (!c_fine || !n || !mean_f || !m2_f || !mean_d || !m2_d)
+    return fail(HENRY_E_INVALID, "NULL argument");
+  CKR(cudaSetDevice(ctx->device));
+  const int nx = ctx->cfg.nx0 << level, ny = ctx->cfg.ny0 << level;
+  CKR(henry::launch_field_stats(ctx->ctr, nx, ny, B, c_fine, c_coarse, status, n, mean_f, m2_f,
+                                mean_d, m2_d, (cudaStream_t)stream));
+  return HENRY_OK;
+}
+
+int henry_residual_jacobian(const henry_config* cfg, int nx, int ny, double tau, int B,
+                            const double* phi, const double* K, const double* qin, const double* p,
+                            const double* c, const double* c_old, double* R, double* J,
+                            void* stream) {
+  if (!cfg) return fail(HENRY_E_INVALID, "config is NULL");
+  if (nx < 2 || ny < 1 || B < 0 || !(tau > 0)) return fail(HENRY_E_INVALID, "bad sizes");
+  if (B == 0) return HENRY_OK;
+  if (!phi || !K || !qin || !p || !c || !c_old || !R) return fail(HENRY_E_INVALID, "NULL argument");
+  henry::Phys P{cfg->rho0, cfg->rho1 - cfg->rho0, cfg->mu, cfg->g, cfg->D, cfg->K0, cfg->phi0,
+                cfg->q0, cfg->Lx, cfg->Ly};
+  henry::Geom G{nx, ny, cfg->Lx / nx, cfg->Ly / ny};
+  cudaStream_t s = (cudaStream_t)stream;
+  double* scratch = nullptr;
+  CKR(cudaMallocAsync((void**)&scratch, sizeof(double) * 4 * (size_t)B * nx * ny, s));
+  cudaError_t e = henry::launch_residual_jacobian(P, G, tau, B, phi, K, qin, p, c, c_old, R, J,
+                                                  scratch, s);
+  cudaError_t e2 = cudaFreeAsync(scratch, s);
+  CKR(e);
+  CKR(e2);
+  return HENRY_OK;
+}
+
+int64_t henry_launch_count(const henry_ctx* ctx) {
+  if (!ctx) return -1;
+  unsigned long long total = 0, v = 0;
+  cudaDeviceSynchronize();
+  if (ctx->ctr && cudaMemcpy(&v, ctx->ctr, sizeof(v), cudaMemcpyDeviceToHost) == cudaSuccess) total += v;
+  for (const auto& r : ctx->role)
+    for (const auto& s : r)
+      if (s) total += s->launches();
+  return (int64_t)total;
+}
+
+const char* henry_strerror(int code) {
+  switch (code) {
+    case HENRY_OK: return "ok";
+    case HENRY_E_INVALID: return "invalid argument";
+    case HENRY_E_CUDA: return "CUDA error";
+    case HENRY_E_NOMEM: return "out of device memory";
+    case HENRY_E_TIMEOUT: return "device wait timed out";
+    case HENRY_E_UNSUPPORTED: return "unsupported grid";
+    default: return "unknown error";
+  }
+}
+
+const char* henry_last_error(void) { return henry::last_error_cstr(); }
+
+}  // extern "C"

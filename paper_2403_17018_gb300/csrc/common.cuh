@@ -1,0 +1,36 @@
+// Constants and helpers shared by all kernels of libhenry.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace henry {
+
+constexpr int kNQ = 6;
+constexpr int kStatusMaxit = 1;
+constexpr int kStatusNonfinite = 2;
+constexpr int kStatusBadInput = 4;
+constexpr int kBlock = 256;
+constexpr int kMaxCoarseUnknowns = 64;
+
+#define HENRY_COUNT_LAUNCH(ctr)                                                        \
+  do {                                                                                 \
+    if (ctr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)                 \
+      atomicAdd((unsigned long long*)(ctr), 1ULL);                                     \
+  } while (0)
+
+// Block sum of a double, result valid in thread 0. Fixed order.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
+  return s;
+}
+
+}  // namespace henry

@@ -1,0 +1,239 @@
+// Device-side discretisation of the Henry problem (arxiv 2403.17018,
+// section 2.1, Eqs. 1-5; section 2.3 implicit Euler).
+//
+// Cell-centred finite volumes on [0,Lx] x [0,Ly] (y upward). For the face
+// between a lower cell L (west or south) and an upper cell U (east or north)
+// with unit vector e from L to U, area A and centre distance d:
+//   q     = -(K_f/mu) [ (p_U - p_L)/d + rho_bar g e_y ]         (Eq. 3)
+//   F_m   = A q rho_up                                          (Eq. 1 flux)
+//   F_s   = A [ q (rho c)_up - rho_bar phi_f D (c_U - c_L)/d ]  (Eq. 2 flux, Eq. 5)
+// K_f, phi_f harmonic means, rho_bar arithmetic mean of rho(c) (Eq. 4),
+// upwind from L when q >= 0, else from U. Both cells evaluate a face with the
+// same canonical orientation and the same operations, so the two residual
+// contributions cancel exactly in floating point.
+// Boundaries: left x=0 prescribed mass inflow rho0 q_in(y), no advected salt,
+// diffusive Dirichlet c=0 at hx/2; right x=Lx Dirichlet p = rho1 g (Ly - y)
+// at hx/2, advected values upwinded with c=1 on inflow, diffusive Dirichlet
+// c=1 at hx/2; top and bottom no flux.
+// Accumulation per cell: V phi (rho - rho_old)/tau and V phi (rho c -
+// rho_old c_old)/tau.
+//
+// Face constants are precomputed once per solve (the fields do not change in
+// time): tx = A_x K_f / (mu hx), dx = A_x phi_f D / hx for the east face of a
+// cell, ty, dy likewise for its north face. This keeps divisions out of the
+// per-iteration FP64 work.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace henry {
+
+struct Phys {
+  double rho0, drho, mu, g, D, K0, phi0, q0, Lx, Ly;
+  double rho1() const { return rho0 + drho; }
+};
+
+struct Geom {
+  int nx, ny;        // cells
+  double hx, hy;     // cell sizes
+  __host__ __device__ int ncell() const { return nx * ny; }
+  __host__ __device__ int half() const { return (nx * ny) >> 1; }
+};
+
+// Colour-split position of cell (i, j) inside one plane: red cells
+// ((i + j) even) first, then black, each in row-major order of (j, i/2).
+// Requires nx even.
+__device__ __forceinline__ int cs_pos(int i, int j, int nx, int half) {
+  return (((i + j) & 1) ? half : 0) + j * (nx >> 1) + (i >> 1);
+}
+
+// Per-face flux and its derivatives with respect to (p, c) of L and U.
+template <typename JT>
+struct FaceD {
+  JT mLp, mLc, mUp, mUc;   // d F_m / d (p_L, c_L, p_U, c_U)
+  JT sLp, sLc, sUp, sUc;   // d F_s / d (p_L, c_L, p_U, c_U)
+};
+
+// Interior face. t = A K_f/(mu d), dco = A phi_f D / d, gd = g e_y d.
+template <typename JT, bool WANT_J>
+__device__ __forceinline__ void face_flux(const Phys& P, double pL, double cL, double pU, double cU,
+                                          double t, double dco, double gd,
+                                          double& Fm, double& Fs, FaceD<JT>& J) {
+  const double rL = P.rho0 + P.drho * cL;
+  const double rU = P.rho0 + P.drho * cU;
+  const double rbar = 0.5 * (rL + rU);
+  const double q = -t * ((pU - pL) + rbar * gd);
+  const bool up = q >= 0.0;
+  const double rup = up ? rL : rU;
+  const double rcup = up ? rL * cL : rU * cU;
+  const double dc = cU - cL;
+  Fm = q * rup;
+  Fs = q * rcup - dco * rbar * dc;
+  if (WANT_J) {
+    const JT t_ = (JT)t, q_ = (JT)q, dr = (JT)P.drho;
+    const JT s_ = -t_ * (JT)gd * (JT)0.5 * dr;       // dq/dc_L = dq/dc_U
+    const JT rup_ = (JT)rup, rcup_ = (JT)rcup, dco_ = (JT)dco;
+    const JT diffc = -dco_ * (JT)0.5 * dr * (JT)dc;   // d(-dco rbar dc)/dc from rbar
+    const JT drb = dco_ * (JT)rbar;
+    J.mLp = t_ * rup_;
+    J.mUp = -t_ * rup_;
+    J.mLc = s_ * rup_ + (up ? q_ * dr : (JT)0);
+    J.mUc = s_ * rup_ + (up ? (JT)0 : q_ * dr);
+    J.sLp = t_ * rcup_;
+    J.sUp = -t_ * rcup_;
+    J.sLc = s_ * rcup_ + (up ? q_ * ((JT)rL + dr * (JT)cL) : (JT)0) + diffc + drb;
+    J.sUc = s_ * rcup_ + (up ? (JT)0 : q_ * ((JT)rU + dr * (JT)cU)) + diffc - drb;
+  }
+}
+
+// Inputs of one cell's residual/Jacobian evaluation, gathered by the caller.
+struct CellIn {
+  double p, c, c_old, phi, K;       // own values (K used on the right side only)
+  double pW, cW, pE, cE, pS, cS, pN, cN;
+  double tW, dW, tE, dE, tS, dS, tN, dN;   // face constants (valid where the face exists)
+  double qin;                        // left inflow velocity of this row (i == 0)
+  bool hasW, hasE, hasS, hasN;       // interior faces
+  double y;                          // cell-centre y (right boundary pressure)
+};
+
+// Residual (FP64) and, optionally, the 20 Jacobian entries of one cell:
+// J[0..3] = dR_P/du_P, J[4..7] W, J[8..11] E, J[12..15] S, J[16..19] N;
+// each block (pp, pc, cp, cc), row = equation, column = variable.
+template <typename JT, bool WANT_J>
+__device__ __forceinline__ void cell_residual(const Phys& P, const Geom& G, double tau,
+                                              const CellIn& in, double& Rp, double& Rc, JT* J) {
+  const double V = G.hx * G.hy;
+  const double vt = V * in.phi / tau;
+  const double rho = P.rho0 + P.drho * in.c;
+  const double rho_o = P.rho0 + P.drho * in.c_old;
+  Rp = vt * (rho - rho_o);
+  Rc = vt * (rho * in.c - rho_o * in.c_old);
+  if (WANT_J) {
+#pragma unroll
+    for (int m = 0; m < 20; ++m) J[m] = (JT)0;
+    J[1] = (JT)(vt * P.drho);
+    J[3] = (JT)(vt * (rho + P.drho * in.c));
+  }
+  FaceD<JT> d;
+  double Fm, Fs;
+  const double gdy = P.g * G.hy;
+  // west face: L = W, U = P; contributes -F to P
+  if (in.hasW) {
+    face_flux<JT, WANT_J>(P, in.pW, in.cW, in.p, in.c, in.tW, in.dW, 0.0, Fm, Fs, d);
+    Rp -= Fm;
+    Rc -= Fs;
+    if (WANT_J) {
+      J[0] -= d.mUp; J[1] -= d.mUc; J[2] -= d.sUp; J[3] -= d.sUc;
+      J[4] = -d.mLp; J[5] = -d.mLc; J[6] = -d.sLp; J[7] = -d.sLc;
+    }
+  } else {
+    // left side: fixed freshwater mass inflow, diffusion to c = 0 at hx/2
+    const double A = G.hy;
+    const double dco = 2.0 * A * in.phi * P.D / G.hx;
+    const double rb = 0.5 * (rho + P.rho0);
+    Rp += -A * P.rho0 * in.qin;
+    Rc += dco * rb * in.c;
+    if (WANT_J) J[3] += (JT)(dco * (0.5 * P.drho * in.c + rb));
+  }
+  // east face: L = P, U = E; contributes +F to P
+  if (in.hasE) {
+    face_flux<JT, WANT_J>(P, in.p, in.c, in.pE, in.cE, in.tE, in.dE, 0.0, Fm, Fs, d);
+    Rp += Fm;
+    Rc += Fs;
+    if (WANT_J) {
+      J[0] += d.mLp; J[1] += d.mLc; J[2] += d.sLp; J[3] += d.sLc;
+      J[8] = d.mUp; J[9] = d.mUc; J[10] = d.sUp; J[11] = d.sUc;
+    }
+  } else {
+    // right side: hydrostatic seawater, Dirichlet at hx/2
+    const double A = G.hy;
+    const double rho1 = P.rho0 + P.drho;
+    const double tR = 2.0 * A * in.K / (P.mu * G.hx);
+    const double dco = 2.0 * A * in.phi * P.D / G.hx;
+    const double pb = rho1 * P.g * (P.Ly - in.y);
+    const double q = -tR * (pb - in.p);
+    const bool up = q >= 0.0;
+    const double rup = up ? rho : rho1;
+    const double rcup = up ? rho * in.c : rho1;
+    const double rb = 0.5 * (rho + rho1);
+    Rp += q * rup;
+    Rc += q * rcup - dco * rb * (1.0 - in.c);
+    if (WANT_J) {
+      J[0] += (JT)(tR * rup);
+      J[1] += (JT)(up ? q * P.drho : 0.0);
+      J[2] += (JT)(tR * rcup);
+      J[3] += (JT)((up ? q * (rho + P.drho * in.c) : 0.0)
+                   - dco * 0.5 * P.drho * (1.0 - in.c) + dco * rb);
+    }
+  }
+  // south face: L = S, U = P (e = +y); contributes -F
+  if (in.hasS) {
+    face_flux<JT, WANT_J>(P, in.pS, in.cS, in.p, in.c, in.tS, in.dS, gdy, Fm, Fs, d);
+    Rp -= Fm;
+    Rc -= Fs;
+    if (WANT_J) {
+      J[0] -= d.mUp; J[1] -= d.mUc; J[2] -= d.sUp; J[3] -= d.sUc;
+      J[12] = -d.mLp; J[13] = -d.mLc; J[14] = -d.sLp; J[15] = -d.sLc;
+    }
+  }
+  // north face: L = P, U = N; contributes +F
+  if (in.hasN) {
+    face_flux<JT, WANT_J>(P, in.p, in.c, in.pN, in.cN, in.tN, in.dN, gdy, Fm, Fs, d);
+    Rp += Fm;
+    Rc += Fs;
+    if (WANT_J) {
+      J[0] += d.mLp; J[1] += d.mLc; J[2] += d.sLp; J[3] += d.sLc;
+      J[16] = d.mUp; J[17] = d.mUc; J[18] = d.sUp; J[19] = d.sUc;
+    }
+  }
+}
+
+// Gather the stencil of cell (i, j) from natural-layout arrays of one sample.
+// tx/dx hold east-face constants, ty/dy north-face constants.
+__device__ __forceinline__ void gather_cell(const Geom& G, int i, int j, const double* __restrict__ p,
+                                            const double* __restrict__ c, const double* __restrict__ phi,
+                                            const double* __restrict__ K, const double* __restrict__ tx,
+                                            const double* __restrict__ dx, const double* __restrict__ ty,
+                                            const double* __restrict__ dy, CellIn& in) {
+  const int nx = G.nx;
+  const int id = j * nx + i;
+  in.p = p[id];
+  in.c = c[id];
+  in.phi = phi[id];
+  in.hasW = i > 0;
+  in.hasE = i < nx - 1;
+  in.hasS = j > 0;
+  in.hasN = j < G.ny - 1;
+  in.K = in.hasE ? 0.0 : K[id];
+  in.y = (j + 0.5) * G.hy;
+  if (in.hasW) { in.pW = p[id - 1]; in.cW = c[id - 1]; in.tW = tx[id - 1]; in.dW = dx[id - 1]; }
+  if (in.hasE) { in.pE = p[id + 1]; in.cE = c[id + 1]; in.tE = tx[id]; in.dE = dx[id]; }
+  if (in.hasS) { in.pS = p[id - nx]; in.cS = c[id - nx]; in.tS = ty[id - nx]; in.dS = dy[id - nx]; }
+  if (in.hasN) { in.pN = p[id + nx]; in.cN = c[id + nx]; in.tN = ty[id]; in.dN = dy[id]; }
+}
+
+// Face constants of cell (i, j): east face (if any) and north face (if any).
+__device__ __forceinline__ void face_constants(const Phys& P, const Geom& G, int i, int j,
+                                               const double* __restrict__ phi,
+                                               const double* __restrict__ K, double& tx, double& dx,
+                                               double& ty, double& dy) {
+  const int id = j * G.nx + i;
+  tx = dx = ty = dy = 0.0;
+  if (i < G.nx - 1) {
+    const double k1 = K[id], k2 = K[id + 1], f1 = phi[id], f2 = phi[id + 1];
+    const double Kf = 2.0 * k1 * k2 / (k1 + k2);
+    const double ff = 2.0 * f1 * f2 / (f1 + f2);
+    tx = G.hy * Kf / (P.mu * G.hx);
+    dx = G.hy * ff * P.D / G.hx;
+  }
+  if (j < G.ny - 1) {
+    const double k1 = K[id], k2 = K[id + G.nx], f1 = phi[id], f2 = phi[id + G.nx];
+    const double Kf = 2.0 * k1 * k2 / (k1 + k2);
+    const double ff = 2.0 * f1 * f2 / (f1 + f2);
+    ty = G.hx * Kf / (P.mu * G.hy);
+    dy = G.hx * ff * P.D / G.hy;
+  }
+}
+
+}  // namespace henry

@@ -1,0 +1,631 @@
+// Batched kernels of the Henry solver. Every kernel works on B independent
+// samples at once; per-sample arrays are contiguous blocks ([B][...]).
+// Multigrid vectors and matrices use the colour-split plane layout of
+// cs_pos() so that each red-black half-sweep streams one contiguous half of
+// every plane. FP64 state (p, c) uses the natural row-major layout.
+//
+// Samples whose `active` flag is 0 (converged in this time step, or failed)
+// are skipped by every per-iteration kernel, so a sample's result does not
+// depend on which other samples share its batch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "henry_device.cuh"
+
+namespace henry {
+
+// ---------------------------------------------------------------------------
+// set-up kernels (once per solve)
+// ---------------------------------------------------------------------------
+
+// Random fields at cell centres (workload stand-in for the paper's Eq.
+// poro_2levels; see henry.h for the formulas) and the inflow per row.
+__global__ void k_fields(unsigned long long* ctr, Phys P, Geom G, int B, int n_xi,
+                         const double* __restrict__ xi, const double* __restrict__ logk,
+                         double* __restrict__ phi, double* __restrict__ K, double* __restrict__ qin,
+                         int* __restrict__ status) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int64_t n = (int64_t)B * G.ncell();
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int b = (int)(idx / G.ncell());
+  const int cell = (int)(idx - (int64_t)b * G.ncell());
+  const int j = cell / G.nx, i = cell - j * G.nx;
+  const double x = (i + 0.5) * G.hx, y = (j + 0.5) * G.hy;
+  const double* z = xi + (int64_t)b * n_xi;
+  const double pi = 3.14159265358979323846;
+  double a = 0.1 * z[0] * cos(0.5 * pi * x) * sin(pi * y);
+  double e = 0.5 * z[1] * sin(0.5 * pi * x) * cos(pi * y);
+  double qf = 1.0 + 0.1 * z[2];
+  if (n_xi >= 6) {
+    a += 0.05 * z[3] * cos(pi * x) * sin(2.0 * pi * y);
+    e += 0.05 * z[4] * sin(pi * x) * cos(2.0 * pi * y);
+    qf += 0.05 * z[5] * cos(pi * y);
+  }
+  if (logk) e += logk[idx];
+  phi[idx] = P.phi0 * (1.0 + a);
+  K[idx] = P.K0 * exp(e);
+  if (i == 0) qin[(int64_t)b * G.ny + j] = P.q0 * qf;
+  if (cell == 0) {
+    bool ok = true;
+    for (int k = 0; k < n_xi; ++k) ok = ok && isfinite(z[k]);
+    status[b] = ok ? 0 : kStatusBadInput;
+  }
+}
+
+// Coarse-grid fields for the rediscretised multigrid operators: arithmetic
+// mean of the four children.
+__global__ void k_coarsen_fields(unsigned long long* ctr, Geom Gf, Geom Gc, int B,
+                                 const double* __restrict__ phif, const double* __restrict__ Kf,
+                                 double* __restrict__ phic, double* __restrict__ Kc) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int64_t n = (int64_t)B * Gc.ncell();
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int b = (int)(idx / Gc.ncell());
+  const int cell = (int)(idx - (int64_t)b * Gc.ncell());
+  const int J = cell / Gc.nx, I = cell - J * Gc.nx;
+  const int64_t f0 = (int64_t)b * Gf.ncell() + (2 * J) * Gf.nx + 2 * I;
+  phic[idx] = 0.25 * (phif[f0] + phif[f0 + 1] + phif[f0 + Gf.nx] + phif[f0 + Gf.nx + 1]);
+  Kc[idx] = 0.25 * (Kf[f0] + Kf[f0 + 1] + Kf[f0 + Gf.nx] + Kf[f0 + Gf.nx + 1]);
+}
+
+__global__ void k_face_consts(unsigned long long* ctr, Phys P, Geom G, int B,
+                              const double* __restrict__ phi, const double* __restrict__ K,
+                              double* __restrict__ tx, double* __restrict__ dx,
+                              double* __restrict__ ty, double* __restrict__ dy) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int64_t n = (int64_t)B * G.ncell();
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int b = (int)(idx / G.ncell());
+  const int cell = (int)(idx - (int64_t)b * G.ncell());
+  const int j = cell / G.nx, i = cell - j * G.nx;
+  const int64_t o = (int64_t)b * G.ncell();
+  face_constants(P, G, i, j, phi + o, K + o, tx[idx], dx[idx], ty[idx], dy[idx]);
+}
+
+// Initial state c = 0; the Newton guess for p is seawater hydrostatics.
+__global__ void k_init_state(unsigned long long* ctr, Phys P, Geom G, int B, double* __restrict__ p,
+                             double* __restrict__ c, int* __restrict__ iters) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int64_t n = (int64_t)B * G.ncell();
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int b = (int)(idx / G.ncell());
+  const int cell = (int)(idx - (int64_t)b * G.ncell());
+  const int j = cell / G.nx;
+  const double y = (j + 0.5) * G.hy;
+  p[idx] = (P.rho0 + P.drho) * P.g * (P.Ly - y);
+  c[idx] = 0.0;
+  if (cell == 0) iters[b] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// per time step
+// ---------------------------------------------------------------------------
+__global__ void k_begin_step(unsigned long long* ctr, Geom G, int B, const double* __restrict__ c,
+                             double* __restrict__ c_old, const int* __restrict__ status,
+                             int* __restrict__ active, int* __restrict__ it_step) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int64_t n = (int64_t)B * G.ncell();
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  c_old[idx] = c[idx];
+  const int b = (int)(idx / G.ncell());
+  if (idx - (int64_t)b * G.ncell() == 0) {
+    active[b] = (status[b] & (kStatusNonfinite | kStatusBadInput)) ? 0 : 1;
+    it_step[b] = 0;
+  }
+}
+
+// FP64 residual of the finest grid and its Jacobian in the multigrid type T.
+// Writes b = -R and x = 0 (colour-split), J (colour-split planes), and one
+// partial sum of R_p^2 + R_c^2 per block. grid = (chunks per sample, B).
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+k_resjac(unsigned long long* ctr, Phys P, Geom G, double tau, int B,
+         const double* __restrict__ p, const double* __restrict__ c,
+         const double* __restrict__ c_old, const double* __restrict__ phi,
+         const double* __restrict__ K, const double* __restrict__ tx,
+         const double* __restrict__ dx, const double* __restrict__ ty,
+         const double* __restrict__ dy, const double* __restrict__ qin,
+         const int* __restrict__ active, T* __restrict__ J, T* __restrict__ bvec,
+         T* __restrict__ xvec, double* __restrict__ partial) {
+  HENRY_COUNT_LAUNCH(ctr);
+  __shared__ double sh[kBlock / 32];
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  const int ncell = G.ncell(), half = G.half();
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (cell < ncell) {
+    const int j = cell / G.nx, i = cell - j * G.nx;
+    const int64_t o = (int64_t)b * ncell;
+    CellIn in;
+    gather_cell(G, i, j, p + o, c + o, phi + o, K + o, tx + o, dx + o, ty + o, dy + o, in);
+    in.c_old = c_old[o + cell];
+    in.qin = qin[(int64_t)b * G.ny + j];
+    double Rp, Rc;
+    T Jc[20];
+    cell_residual<T, true>(P, G, tau, in, Rp, Rc, Jc);
+    const int cs = cs_pos(i, j, G.nx, half);
+    const int64_t ob = (int64_t)b * 2 * ncell;
+    bvec[ob + cs] = (T)(-Rp);
+    bvec[ob + ncell + cs] = (T)(-Rc);
+    xvec[ob + cs] = (T)0;
+    xvec[ob + ncell + cs] = (T)0;
+    T* Jb = J + (int64_t)b * 20 * ncell + cs;
+#pragma unroll
+    for (int m = 0; m < 20; ++m) Jb[(int64_t)m * ncell] = Jc[m];
+    v = Rp * Rp + Rc * Rc;
+  }
+  const double s = block_sum(v, sh);
+  if (threadIdx.x == 0) partial[(int64_t)b * gridDim.x + blockIdx.x] = s;
+}
+
+// Per-sample convergence decision after k_resjac. One block; warp w handles
+// samples w, w + nwarps, ... Sums the partials in a fixed order, scales the
+// RMS residual to units of c per step, updates active / status / counters
+// and the number of still-active samples.
+__global__ void k_check(unsigned long long* ctr, int B, int nchunk, int ncell,
+                        const double* __restrict__ partial, double scale, double rtol,
+                        double atol, int maxit, int* __restrict__ active,
+                        int* __restrict__ it_step, double* __restrict__ res0,
+                        double* __restrict__ res_last, int* __restrict__ status,
+                        int* __restrict__ iters, int* __restrict__ n_active) {
+  HENRY_COUNT_LAUNCH(ctr);
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  int mine = 0;
+  for (int b = w; b < B; b += nw) {
+    if (!active[b]) continue;
+    double s = 0.0;
+    for (int k = l; k < nchunk; k += 32) s += partial[(int64_t)b * nchunk + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (l == 0) {
+      const double r = sqrt(s / ncell) * scale;
+      const int it = it_step[b];
+      if (it == 0) res0[b] = r;
+      res_last[b] = r;
+      if (!isfinite(r)) {
+        status[b] |= kStatusNonfinite;
+        active[b] = 0;
+      } else if (r <= fmax(rtol * res0[b], atol)) {
+        active[b] = 0;
+      } else if (it >= maxit) {
+        status[b] |= kStatusMaxit;
+        active[b] = 0;
+      } else {
+        it_step[b] = it + 1;
+        iters[b] += 1;
+        ++mine;
+      }
+    }
+  }
+  if (l == 0 && mine) atomicAdd(&cnt, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) *n_active = cnt;
+}
+
+// Average the state of level k onto level k-1 (rediscretisation of the
+// multigrid operators at the current Newton iterate).
+__global__ void k_restrict_state(unsigned long long* ctr, Geom Gf, Geom Gc, int B,
+                                 const int* __restrict__ active, const double* __restrict__ pf,
+                                 const double* __restrict__ cf, double* __restrict__ pc,
+                                 double* __restrict__ cc) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int64_t n = (int64_t)B * Gc.ncell();
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int b = (int)(idx / Gc.ncell());
+  if (!active[b]) return;
+  const int cell = (int)(idx - (int64_t)b * Gc.ncell());
+  const int J = cell / Gc.nx, I = cell - J * Gc.nx;
+  const int64_t f0 = (int64_t)b * Gf.ncell() + (2 * J) * Gf.nx + 2 * I;
+  pc[idx] = 0.25 * (pf[f0] + pf[f0 + 1] + pf[f0 + Gf.nx] + pf[f0 + Gf.nx + 1]);
+  cc[idx] = 0.25 * (cf[f0] + cf[f0 + 1] + cf[f0 + Gf.nx] + cf[f0 + Gf.nx + 1]);
+}
+
+// Jacobian of a coarse multigrid level from its own state and fields.
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+k_jac(unsigned long long* ctr, Phys P, Geom G, double tau, int B, const int* __restrict__ active,
+      const double* __restrict__ p, const double* __restrict__ c, const double* __restrict__ phi,
+      const double* __restrict__ K, const double* __restrict__ tx, const double* __restrict__ dx,
+      const double* __restrict__ ty, const double* __restrict__ dy, T* __restrict__ J) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int ncell = G.ncell();
+  const int64_t n = (int64_t)B * ncell;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int b = (int)(idx / ncell);
+  if (!active[b]) return;
+  const int cell = (int)(idx - (int64_t)b * ncell);
+  const int j = cell / G.nx, i = cell - j * G.nx;
+  const int64_t o = (int64_t)b * ncell;
+  CellIn in;
+  gather_cell(G, i, j, p + o, c + o, phi + o, K + o, tx + o, dx + o, ty + o, dy + o, in);
+  in.c_old = in.c;
+  in.qin = 0.0;
+  double Rp, Rc;
+  T Jc[20];
+  cell_residual<T, true>(P, G, tau, in, Rp, Rc, Jc);
+  T* Jb = J + (int64_t)b * 20 * ncell + cs_pos(i, j, G.nx, G.half());
+#pragma unroll
+  for (int m = 0; m < 20; ++m) Jb[(int64_t)m * ncell] = Jc[m];
+}
+
+// Dense LU with partial pivoting of the coarsest system, one block per
+// sample (Gaussian elimination, section 2.3). Unknown order 2*cell + var,
+// cell natural. Computed in FP64 whatever T is.
+template <typename T>
+__global__ void k_coarse_lu(unsigned long long* ctr, Geom G, int B, const int* __restrict__ active,
+                            const T* __restrict__ J, double* __restrict__ LU, int* __restrict__ piv) {
+  HENRY_COUNT_LAUNCH(ctr);
+  __shared__ double A[kMaxCoarseUnknowns][kMaxCoarseUnknowns + 1];
+  __shared__ int pr;
+  const int b = blockIdx.x;
+  if (!active[b]) return;
+  const int nc = G.ncell(), n = 2 * nc, half = G.half();
+  const T* Jb = J + (int64_t)b * 20 * nc;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e / n][e % n] = 0.0;
+  __syncthreads();
+  for (int cell = threadIdx.x; cell < nc; cell += blockDim.x) {
+    const int j = cell / G.nx, i = cell - j * G.nx;
+    const int cs = cs_pos(i, j, G.nx, half);
+    const int nb[5] = {cell, i > 0 ? cell - 1 : -1, i < G.nx - 1 ? cell + 1 : -1,
+                       j > 0 ? cell - G.nx : -1, j < G.ny - 1 ? cell + G.nx : -1};
+    for (int q = 0; q < 5; ++q) {
+      if (nb[q] < 0) continue;
+      for (int e = 0; e < 2; ++e)
+        for (int v = 0; v < 2; ++v)
+          A[2 * cell + e][2 * nb[q] + v] = (double)Jb[(int64_t)(4 * q + 2 * e + v) * nc + cs];
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      int best = k;
+      double bv = fabs(A[k][k]);
+      for (int r = k + 1; r < n; ++r)
+        if (fabs(A[r][k]) > bv) { bv = fabs(A[r][k]); best = r; }
+      pr = best;
+      piv[(int64_t)b * kMaxCoarseUnknowns + k] = best;
+    }
+    __syncthreads();
+    const int r = pr;
+    if (r != k)
+      for (int col = threadIdx.x; col < n; col += blockDim.x) {
+        const double t = A[k][col];
+        A[k][col] = A[r][col];
+        A[r][col] = t;
+      }
+    __syncthreads();
+    const double d = A[k][k];
+    for (int row = k + 1 + threadIdx.x; row < n; row += blockDim.x) A[row][k] = d != 0.0 ? A[row][k] / d : 0.0;
+    __syncthreads();
+    for (int row = k + 1 + threadIdx.x; row < n; row += blockDim.x) {
+      const double m = A[row][k];
+      for (int col = k + 1; col < n; ++col) A[row][col] -= m * A[k][col];
+    }
+    __syncthreads();
+  }
+  double* L = LU + (int64_t)b * kMaxCoarseUnknowns * kMaxCoarseUnknowns;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) L[e] = A[e / n][e % n];
+}
+
+// Solve with the stored LU, one warp per sample; rows spread over lanes.
+template <typename T>
+__global__ void k_coarse_solve(unsigned long long* ctr, Geom G, int B, const int* __restrict__ active,
+                               const double* __restrict__ LU, const int* __restrict__ piv,
+                               const T* __restrict__ bvec, T* __restrict__ xvec) {
+  HENRY_COUNT_LAUNCH(ctr);
+  __shared__ double ysh[kBlock / 32][kMaxCoarseUnknowns];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int b = blockIdx.x * (blockDim.x >> 5) + w;
+  if (b >= B || !active[b]) return;
+  const int nc = G.ncell(), n = 2 * nc, half = G.half();
+  double* y = ysh[w];
+  const int64_t ob = (int64_t)b * 2 * nc;
+  for (int u = l; u < n; u += 32) {
+    const int cell = u >> 1, v = u & 1;
+    const int j = cell / G.nx, i = cell - j * G.nx;
+    y[u] = (double)bvec[ob + v * nc + cs_pos(i, j, G.nx, half)];
+  }
+  __syncwarp();
+  const int* pv = piv + (int64_t)b * kMaxCoarseUnknowns;
+  if (l == 0)
+    for (int k = 0; k < n; ++k) {
+      const int r = pv[k];
+      if (r != k) { const double t = y[k]; y[k] = y[r]; y[r] = t; }
+    }
+  __syncwarp();
+  const double* A = LU + (int64_t)b * kMaxCoarseUnknowns * kMaxCoarseUnknowns;
+  for (int k = 0; k < n; ++k) {  // forward, unit lower
+    const double yk = y[k];
+    __syncwarp();
+    for (int r = k + 1 + l; r < n; r += 32) y[r] -= A[r * n + k] * yk;
+    __syncwarp();
+  }
+  for (int k = n - 1; k >= 0; --k) {  // backward
+    if (l == 0) y[k] = y[k] / A[k * n + k];
+    __syncwarp();
+    const double yk = y[k];
+    for (int r = l; r < k; r += 32) y[r] -= A[r * n + k] * yk;
+    __syncwarp();
+  }
+  for (int u = l; u < n; u += 32) {
+    const int cell = u >> 1, v = u & 1;
+    const int j = cell / G.nx, i = cell - j * G.nx;
+    xvec[ob + v * nc + cs_pos(i, j, G.nx, half)] = (T)y[u];
+  }
+}
+
+// One red (colour 0) or black (colour 1) half-sweep of point-block
+// Gauss-Seidel: x_P = D_P^{-1} (b_P - sum_Q A_PQ x_Q), 2x2 blocks.
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+k_smooth(unsigned long long* ctr, Geom G, int B, int colour, const int* __restrict__ active,
+         const T* __restrict__ J, const T* __restrict__ bvec, T* __restrict__ xvec) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int half = G.half(), ncell = G.ncell(), hx2 = G.nx >> 1;
+  const int64_t n = (int64_t)B * half;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int b = (int)(idx / half);
+  if (!active[b]) return;
+  const int pos = (int)(idx - (int64_t)b * half);
+  const int j = pos / hx2, k = pos - j * hx2;
+  const int i = 2 * k + ((j + colour) & 1);
+  const int own = colour * half + pos;
+  const int oth = (1 - colour) * half;
+  const T* Jb = J + (int64_t)b * 20 * ncell + own;
+  const int64_t ob = (int64_t)b * 2 * ncell;
+  const T* xp = xvec + ob + oth;
+  const T* xc = xvec + ob + ncell + oth;
+  T rp = bvec[ob + own], rc = bvec[ob + ncell + own];
+  if (i > 0) {
+    const int q = j * hx2 + ((i - 1) >> 1);
+    const T vp = xp[q], vc = xc[q];
+    rp -= Jb[4 * (int64_t)ncell] * vp + Jb[5 * (int64_t)ncell] * vc;
+    rc -= Jb[6 * (int64_t)ncell] * vp + Jb[7 * (int64_t)ncell] * vc;
+  }
+  if (i < G.nx - 1) {
+    const int q = j * hx2 + ((i + 1) >> 1);
+    const T vp = xp[q], vc = xc[q];
+    rp -= Jb[8 * (int64_t)ncell] * vp + Jb[9 * (int64_t)ncell] * vc;
+    rc -= Jb[10 * (int64_t)ncell] * vp + Jb[11 * (int64_t)ncell] * vc;
+  }
+  if (j > 0) {
+    const int q = (j - 1) * hx2 + (i >> 1);
+    const T vp = xp[q], vc = xc[q];
+    rp -= Jb[12 * (int64_t)ncell] * vp + Jb[13 * (int64_t)ncell] * vc;
+    rc -= Jb[14 * (int64_t)ncell] * vp + Jb[15 * (int64_t)ncell] * vc;
+  }
+  if (j < G.ny - 1) {
+    const int q = (j + 1) * hx2 + (i >> 1);
+    const T vp = xp[q], vc = xc[q];
+    rp -= Jb[16 * (int64_t)ncell] * vp + Jb[17 * (int64_t)ncell] * vc;
+    rc -= Jb[18 * (int64_t)ncell] * vp + Jb[19 * (int64_t)ncell] * vc;
+  }
+  const T a = Jb[0], bb = Jb[(int64_t)ncell], cc = Jb[2 * (int64_t)ncell], d = Jb[3 * (int64_t)ncell];
+  const T inv = (T)1 / (a * d - bb * cc);
+  xvec[ob + own] = (d * rp - bb * rc) * inv;
+  xvec[ob + ncell + own] = (a * rc - cc * rp) * inv;
+}
+
+// A x at cell (i, j) of one sample, colour-split arrays.
+template <typename T>
+__device__ __forceinline__ void apply_cell(const Geom& G, int i, int j, const T* __restrict__ Jb,
+                                           const T* __restrict__ x, T& ap, T& ac) {
+  const int ncell = G.ncell(), half = G.half(), nx = G.nx;
+  const int cs = cs_pos(i, j, nx, half);
+  const T* Jc = Jb + cs;
+  const T* xp = x;
+  const T* xc = x + ncell;
+  T vp = xp[cs], vc = xc[cs];
+  ap = Jc[0] * vp + Jc[ncell] * vc;
+  ac = Jc[2 * ncell] * vp + Jc[3 * ncell] * vc;
+  if (i > 0) {
+    const int q = cs_pos(i - 1, j, nx, half);
+    vp = xp[q]; vc = xc[q];
+    ap += Jc[4 * ncell] * vp + Jc[5 * ncell] * vc;
+    ac += Jc[6 * ncell] * vp + Jc[7 * ncell] * vc;
+  }
+  if (i < nx - 1) {
+    const int q = cs_pos(i + 1, j, nx, half);
+    vp = xp[q]; vc = xc[q];
+    ap += Jc[8 * ncell] * vp + Jc[9 * ncell] * vc;
+    ac += Jc[10 * ncell] * vp + Jc[11 * ncell] * vc;
+  }
+  if (j > 0) {
+    const int q = cs_pos(i, j - 1, nx, half);
+    vp = xp[q]; vc = xc[q];
+    ap += Jc[12 * ncell] * vp + Jc[13 * ncell] * vc;
+    ac += Jc[14 * ncell] * vp + Jc[15 * ncell] * vc;
+  }
+  if (j < G.ny - 1) {
+    const int q = cs_pos(i, j + 1, nx, half);
+    vp = xp[q]; vc = xc[q];
+    ap += Jc[16 * ncell] * vp + Jc[17 * ncell] * vc;
+    ac += Jc[18 * ncell] * vp + Jc[19 * ncell] * vc;
+  }
+}
+
+// r = b - A x on level k, summed over the four children of each coarse
+// cell (finite-volume restriction) into b_{k-1}; x_{k-1} = 0.
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+k_resid_restrict(unsigned long long* ctr, Geom Gf, Geom Gc, int B, const int* __restrict__ active,
+                 const T* __restrict__ Jf, const T* __restrict__ bf, const T* __restrict__ xf,
+                 T* __restrict__ bc, T* __restrict__ xc) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int ncc = Gc.ncell();
+  const int64_t n = (int64_t)B * ncc;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int b = (int)(idx / ncc);
+  if (!active[b]) return;
+  const int cell = (int)(idx - (int64_t)b * ncc);
+  const int J = cell / Gc.nx, I = cell - J * Gc.nx;
+  const int ncf = Gf.ncell(), hf = Gf.half();
+  const T* Jb = Jf + (int64_t)b * 20 * ncf;
+  const T* bb = bf + (int64_t)b * 2 * ncf;
+  const T* xb = xf + (int64_t)b * 2 * ncf;
+  T sp = 0, sc = 0;
+#pragma unroll
+  for (int c4 = 0; c4 < 4; ++c4) {
+    const int i = 2 * I + (c4 & 1), j = 2 * J + (c4 >> 1);
+    T ap, ac;
+    apply_cell(Gf, i, j, Jb, xb, ap, ac);
+    const int cs = cs_pos(i, j, Gf.nx, hf);
+    sp += bb[cs] - ap;
+    sc += bb[ncf + cs] - ac;
+  }
+  const int csc = cs_pos(I, J, Gc.nx, Gc.half());
+  const int64_t oc = (int64_t)b * 2 * ncc;
+  bc[oc + csc] = sp;
+  bc[oc + ncc + csc] = sc;
+  xc[oc + csc] = (T)0;
+  xc[oc + ncc + csc] = (T)0;
+}
+
+// x_k += P x_{k-1}: cell-centred bilinear interpolation (weights 9/16,
+// 3/16, 3/16, 1/16), constant extrapolation at the domain boundary.
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+k_prolong(unsigned long long* ctr, Geom Gc, Geom Gf, int B, const int* __restrict__ active,
+          const T* __restrict__ xc, T* __restrict__ xf) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int ncf = Gf.ncell();
+  const int64_t n = (int64_t)B * ncf;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int b = (int)(idx / ncf);
+  if (!active[b]) return;
+  const int cell = (int)(idx - (int64_t)b * ncf);
+  const int j = cell / Gf.nx, i = cell - j * Gf.nx;
+  const int I = i >> 1, J = j >> 1;
+  int I2 = I + ((i & 1) ? 1 : -1), J2 = J + ((j & 1) ? 1 : -1);
+  I2 = I2 < 0 ? 0 : (I2 >= Gc.nx ? Gc.nx - 1 : I2);
+  J2 = J2 < 0 ? 0 : (J2 >= Gc.ny ? Gc.ny - 1 : J2);
+  const int ncc = Gc.ncell(), hc = Gc.half();
+  const T* xb = xc + (int64_t)b * 2 * ncc;
+  const int a0 = cs_pos(I, J, Gc.nx, hc), a1 = cs_pos(I2, J, Gc.nx, hc);
+  const int a2 = cs_pos(I, J2, Gc.nx, hc), a3 = cs_pos(I2, J2, Gc.nx, hc);
+  const T w0 = (T)0.5625, w1 = (T)0.1875, w3 = (T)0.0625;
+  const T vp = w0 * xb[a0] + w1 * (xb[a1] + xb[a2]) + w3 * xb[a3];
+  const T vc = w0 * xb[ncc + a0] + w1 * (xb[ncc + a1] + xb[ncc + a2]) + w3 * xb[ncc + a3];
+  const int cs = cs_pos(i, j, Gf.nx, Gf.half());
+  T* xo = xf + (int64_t)b * 2 * ncf;
+  xo[cs] += vp;
+  xo[ncf + cs] += vc;
+}
+
+// Defect-correction update of the FP64 state: u += x (finest level).
+template <typename T>
+__global__ void k_update(unsigned long long* ctr, Geom G, int B, const int* __restrict__ active,
+                         const T* __restrict__ xvec, double* __restrict__ p, double* __restrict__ c) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int ncell = G.ncell();
+  const int64_t n = (int64_t)B * ncell;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int b = (int)(idx / ncell);
+  if (!active[b]) return;
+  const int cell = (int)(idx - (int64_t)b * ncell);
+  const int j = cell / G.nx, i = cell - j * G.nx;
+  const int cs = cs_pos(i, j, G.nx, G.half());
+  const int64_t ob = (int64_t)b * 2 * ncell;
+  p[idx] += (double)xvec[ob + cs];
+  c[idx] += (double)xvec[ob + ncell + cs];
+}
+
+// ---------------------------------------------------------------------------
+// quantities of interest (section 4): one block per sample
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double bilinear(const Geom& G, const double* c, double x, double y) {
+  const double fx = x / G.hx - 0.5, fy = y / G.hy - 0.5;
+  int i0 = (int)floor(fx), j0 = (int)floor(fy);
+  i0 = i0 < 0 ? 0 : (i0 > G.nx - 2 ? G.nx - 2 : i0);
+  j0 = j0 < 0 ? 0 : (j0 > G.ny - 2 ? G.ny - 2 : j0);
+  const double tx = fmin(fmax(fx - i0, 0.0), 1.0), ty = fmin(fmax(fy - j0, 0.0), 1.0);
+  const int id = j0 * G.nx + i0;
+  return (1 - tx) * (1 - ty) * c[id] + tx * (1 - ty) * c[id + 1] + (1 - tx) * ty * c[id + G.nx] +
+         tx * ty * c[id + G.nx + 1];
+}
+
+__global__ void __launch_bounds__(kBlock)
+k_qoi(unsigned long long* ctr, Phys P, Geom G, int B, const double* __restrict__ p,
+      const double* __restrict__ c, const double* __restrict__ phi, double* __restrict__ q,
+      double* __restrict__ c_out, double* __restrict__ p_out) {
+  HENRY_COUNT_LAUNCH(ctr);
+  __shared__ double sh[kBlock / 32];
+  const int b = blockIdx.x;
+  const int ncell = G.ncell();
+  const int64_t o = (int64_t)b * ncell;
+  double s0 = 0, s1 = 0, s2 = 0;
+  for (int cell = threadIdx.x; cell < ncell; cell += blockDim.x) {
+    const double cv = c[o + cell];
+    const double rho = P.rho0 + P.drho * cv;
+    const int j = cell / G.nx, i = cell - j * G.nx;
+    const double x = (i + 0.5) * G.hx;
+    s0 += cv * rho;
+    s1 += phi[o + cell] * rho * cv;
+    s2 += cv * (P.Lx - x);
+    if (c_out) c_out[o + cell] = cv;
+    if (p_out) p_out[o + cell] = p[o + cell];
+  }
+  const double V = G.hx * G.hy;
+  s0 = block_sum(s0, sh);
+  s1 = block_sum(s1, sh);
+  s2 = block_sum(s2, sh);
+  if (threadIdx.x == 0) {
+    double* qb = q + (int64_t)b * kNQ;
+    qb[0] = s0 * V;
+    qb[1] = s1 * V;
+    qb[2] = s2 * V;
+    qb[3] = bilinear(G, c + o, 1.40, 0.05);
+    qb[4] = bilinear(G, c + o, 1.65, 0.25);
+    qb[5] = bilinear(G, c + o, 1.90, 0.50);
+  }
+}
+
+// Residual and Jacobian in natural layout (FP64), for parity tests.
+__global__ void k_residual_jacobian_natural(unsigned long long* ctr, Phys P, Geom G, double tau, int B,
+                                            const double* __restrict__ p, const double* __restrict__ c,
+                                            const double* __restrict__ c_old, const double* __restrict__ phi,
+                                            const double* __restrict__ K, const double* __restrict__ tx,
+                                            const double* __restrict__ dx, const double* __restrict__ ty,
+                                            const double* __restrict__ dy, const double* __restrict__ qin,
+                                            double* __restrict__ R, double* __restrict__ Jout) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int ncell = G.ncell();
+  const int64_t n = (int64_t)B * ncell;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int b = (int)(idx / ncell);
+  const int cell = (int)(idx - (int64_t)b * ncell);
+  const int j = cell / G.nx, i = cell - j * G.nx;
+  const int64_t o = (int64_t)b * ncell;
+  CellIn in;
+  gather_cell(G, i, j, p + o, c + o, phi + o, K + o, tx + o, dx + o, ty + o, dy + o, in);
+  in.c_old = c_old[idx];
+  in.qin = qin[(int64_t)b * G.ny + j];
+  double Rp, Rc, Jc[20];
+  cell_residual<double, true>(P, G, tau, in, Rp, Rc, Jc);
+  R[(int64_t)b * 2 * ncell + cell] = Rp;
+  R[(int64_t)b * 2 * ncell + ncell + cell] = Rc;
+  if (Jout)
+    for (int m = 0; m < 20; ++m) Jout[(int64_t)b * 20 * ncell + (int64_t)m * ncell + cell] = Jc[m];
+}
+
+}  // namespace henry

@@ -1,0 +1,411 @@
+// Host orchestration of the batched Henry solve (see solver.h).
+#include "solver.h"
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "kernels.cuh"
+
+namespace henry {
+
+namespace {
+thread_local std::string g_last_error;
+
+inline int grid1(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
+
+size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Check a CUDA call; on failure record the message and return HENRY_E_CUDA.
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      set_last_error(std::string(#call) + ": " + cudaGetErrorString(e_));          \
+      return e_ == cudaErrorMemoryAllocation ? HENRY_E_NOMEM : HENRY_E_CUDA;      \
+    }                                                                              \
+  } while (0)
+
+// Convergence check; in graph mode also drives the while node.
+__global__ void k_check_cond(unsigned long long* ctr, int B, int nchunk, int ncell,
+                             const double* __restrict__ partial, double scale, double rtol,
+                             double atol, int maxit, int* __restrict__ active,
+                             int* __restrict__ it_step, double* __restrict__ res0,
+                             double* __restrict__ res_last, int* __restrict__ status,
+                             int* __restrict__ iters, int* __restrict__ n_active,
+                             cudaGraphConditionalHandle h) {
+  // same body as k_check, then set the loop condition from the count
+  HENRY_COUNT_LAUNCH(ctr);
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  int mine = 0;
+  for (int b = w; b < B; b += nw) {
+    if (!active[b]) continue;
+    double s = 0.0;
+    for (int k = l; k < nchunk; k += 32) s += partial[(int64_t)b * nchunk + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (l == 0) {
+      const double r = sqrt(s / ncell) * scale;
+      const int it = it_step[b];
+      if (it == 0) res0[b] = r;
+      res_last[b] = r;
+      if (!isfinite(r)) {
+        status[b] |= kStatusNonfinite;
+        active[b] = 0;
+      } else if (r <= fmax(rtol * res0[b], atol)) {
+        active[b] = 0;
+      } else if (it >= maxit) {
+        status[b] |= kStatusMaxit;
+        active[b] = 0;
+      } else {
+        it_step[b] = it + 1;
+        iters[b] += 1;
+        ++mine;
+      }
+    }
+  }
+  if (l == 0 && mine) atomicAdd(&cnt, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *n_active = cnt;
+    cudaGraphSetConditional(h, cnt > 0 ? 1u : 0u);
+  }
+}
+
+__global__ void k_copy_int(unsigned long long* ctr, int n, const int* __restrict__ src,
+                           int* __restrict__ dst, int do_or) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = do_or ? (dst[i] | src[i]) : src[i];
+}
+}  // namespace
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+const char* last_error_cstr() { return g_last_error.c_str(); }
+
+bool build_hierarchy(int nx, int ny, double Lx, double Ly, std::vector<Geom>& out) {
+  std::vector<Geom> fine_to_coarse;
+  int x = nx, y = ny;
+  fine_to_coarse.push_back(Geom{x, y, Lx / x, Ly / y});
+  while (x % 4 == 0 && y % 2 == 0 && (x / 2) * (y / 2) >= 8) {
+    x /= 2;
+    y /= 2;
+    fine_to_coarse.push_back(Geom{x, y, Lx / x, Ly / y});
+  }
+  if (x % 2 != 0 || x * y > 32) return false;
+  out.assign(fine_to_coarse.rbegin(), fine_to_coarse.rend());
+  return true;
+}
+
+Solver::Solver(const henry_config& cfg, int nx, int ny, int nt) : cfg_(cfg), nt_(nt) {
+  phys_ = Phys{cfg.rho0, cfg.rho1 - cfg.rho0, cfg.mu, cfg.g, cfg.D, cfg.K0, cfg.phi0, cfg.q0,
+               cfg.Lx, cfg.Ly};
+  tau_ = cfg.T / nt;
+  tsize_ = cfg.precision == HENRY_PREC_FP32_MG ? sizeof(float) : sizeof(double);
+  build_hierarchy(nx, ny, cfg.Lx, cfg.Ly, geoms_);
+  levels_.resize(geoms_.size());
+  for (size_t k = 0; k < geoms_.size(); ++k) levels_[k].g = geoms_[k];
+  nchunk_ = (geoms_.back().ncell() + kBlock - 1) / kBlock;
+}
+
+Solver::~Solver() { free_all(); }
+
+void Solver::free_all() {
+  if (step_exec_) cudaGraphExecDestroy(step_exec_);
+  if (step_graph_) cudaGraphDestroy(step_graph_);
+  step_exec_ = nullptr;
+  step_graph_ = nullptr;
+  graph_B_ = -1;
+  if (arena_) cudaFree(arena_);
+  if (n_active_host_) cudaFreeHost(n_active_host_);
+  arena_ = nullptr;
+  n_active_host_ = nullptr;
+  cap_ = 0;
+}
+
+unsigned long long Solver::launches() const {
+  unsigned long long v = 0;
+  if (counter_) cudaMemcpy(&v, counter_, sizeof(v), cudaMemcpyDeviceToHost);
+  return v;
+}
+
+int Solver::ensure(int B, cudaStream_t s) {
+  if (B <= cap_) return HENRY_OK;
+  unsigned long long count = 0;
+  if (counter_) CK(cudaMemcpy(&count, counter_, sizeof(count), cudaMemcpyDeviceToHost));
+  CK(cudaDeviceSynchronize());
+  free_all();
+  const size_t Bz = (size_t)B;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+  struct Off { size_t J, b, x, p, c, phi, K, tx, dx, ty, dy; };
+  std::vector<Off> lo(levels_.size());
+  for (size_t k = 0; k < levels_.size(); ++k) {
+    const size_t n = (size_t)levels_[k].g.ncell() * Bz;
+    lo[k].J = take(20 * n * tsize_);
+    lo[k].b = take(2 * n * tsize_);
+    lo[k].x = take(2 * n * tsize_);
+    lo[k].p = take(n * 8);
+    lo[k].c = take(n * 8);
+    lo[k].phi = take(n * 8);
+    lo[k].K = take(n * 8);
+    lo[k].tx = take(n * 8);
+    lo[k].dx = take(n * 8);
+    lo[k].ty = take(n * 8);
+    lo[k].dy = take(n * 8);
+  }
+  const Geom& F = levels_.back().g;
+  const size_t o_cold = take((size_t)F.ncell() * Bz * 8);
+  const size_t o_qin = take((size_t)F.ny * Bz * 8);
+  const size_t o_part = take((size_t)nchunk_ * Bz * 8);
+  const size_t o_res0 = take(Bz * 8);
+  const size_t o_resl = take(Bz * 8);
+  const size_t o_lu = take(Bz * kMaxCoarseUnknowns * kMaxCoarseUnknowns * 8);
+  const size_t o_piv = take(Bz * kMaxCoarseUnknowns * 4);
+  const size_t o_act = take(Bz * 4);
+  const size_t o_its = take(Bz * 4);
+  const size_t o_st = take(Bz * 4);
+  const size_t o_it = take(Bz * 4);
+  const size_t o_na = take(4);
+  const size_t o_ctr = take(8);
+  CK(cudaMalloc(&arena_, off));
+  CK(cudaHostAlloc((void**)&n_active_host_, sizeof(int), cudaHostAllocDefault));
+  char* a = (char*)arena_;
+  for (size_t k = 0; k < levels_.size(); ++k) {
+    MGLevel& L = levels_[k];
+    L.J = a + lo[k].J;
+    L.b = a + lo[k].b;
+    L.x = a + lo[k].x;
+    L.p = (double*)(a + lo[k].p);
+    L.c = (double*)(a + lo[k].c);
+    L.phi = (double*)(a + lo[k].phi);
+    L.K = (double*)(a + lo[k].K);
+    L.tx = (double*)(a + lo[k].tx);
+    L.dx = (double*)(a + lo[k].dx);
+    L.ty = (double*)(a + lo[k].ty);
+    L.dy = (double*)(a + lo[k].dy);
+  }
+  c_old_ = (double*)(a + o_cold);
+  qin_ = (double*)(a + o_qin);
+  partial_ = (double*)(a + o_part);
+  res0_ = (double*)(a + o_res0);
+  res_last_ = (double*)(a + o_resl);
+  lu_ = (double*)(a + o_lu);
+  piv_ = (int*)(a + o_piv);
+  active_ = (int*)(a + o_act);
+  it_step_ = (int*)(a + o_its);
+  status_w_ = (int*)(a + o_st);
+  iters_w_ = (int*)(a + o_it);
+  n_active_ = (int*)(a + o_na);
+  counter_ = (unsigned long long*)(a + o_ctr);
+  CK(cudaMemset(arena_, 0, off));
+  CK(cudaMemcpy(counter_, &count, sizeof(count), cudaMemcpyHostToDevice));
+  cap_ = B;
+  (void)s;
+  return HENRY_OK;
+}
+
+template <typename T>
+void Solver::enqueue_vcycle(int k, int B, cudaStream_t s) {
+  MGLevel& L = levels_[k];
+  const Geom& G = L.g;
+  if (k == 0) {
+    k_coarse_solve<T><<<(B + 7) / 8, kBlock, 0, s>>>(counter_, G, B, active_, lu_, piv_,
+                                                     (const T*)L.b, (T*)L.x);
+    return;
+  }
+  const int gs = grid1((int64_t)B * G.half());
+  for (int sw = 0; sw < cfg_.nu1; ++sw)
+    for (int col = 0; col < 2; ++col)
+      k_smooth<T><<<gs, kBlock, 0, s>>>(counter_, G, B, col, active_, (const T*)L.J,
+                                       (const T*)L.b, (T*)L.x);
+  MGLevel& C = levels_[k - 1];
+  k_resid_restrict<T><<<grid1((int64_t)B * C.g.ncell()), kBlock, 0, s>>>(
+      counter_, G, C.g, B, active_, (const T*)L.J, (const T*)L.b, (const T*)L.x, (T*)C.b,
+      (T*)C.x);
+  enqueue_vcycle<T>(k - 1, B, s);
+  k_prolong<T><<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(counter_, C.g, G, B, active_,
+                                                                (const T*)C.x, (T*)L.x);
+  for (int sw = 0; sw < cfg_.nu2; ++sw)
+    for (int col = 0; col < 2; ++col)
+      k_smooth<T><<<gs, kBlock, 0, s>>>(counter_, G, B, col, active_, (const T*)L.J,
+                                       (const T*)L.b, (T*)L.x);
+}
+
+// Multigrid operators at the current iterate, V-cycles, state update.
+template <typename T>
+void Solver::enqueue_iteration(int B, cudaStream_t s) {
+  const int nl = (int)levels_.size();
+  for (int k = nl - 1; k >= 1; --k) {
+    MGLevel& F = levels_[k];
+    MGLevel& C = levels_[k - 1];
+    k_restrict_state<<<grid1((int64_t)B * C.g.ncell()), kBlock, 0, s>>>(
+        counter_, F.g, C.g, B, active_, F.p, F.c, C.p, C.c);
+    k_jac<T><<<grid1((int64_t)B * C.g.ncell()), kBlock, 0, s>>>(
+        counter_, phys_, C.g, tau_, B, active_, C.p, C.c, C.phi, C.K, C.tx, C.dx, C.ty, C.dy,
+        (T*)C.J);
+  }
+  k_coarse_lu<T><<<B, 64, 0, s>>>(counter_, levels_[0].g, B, active_, (const T*)levels_[0].J,
+                                  lu_, piv_);
+  for (int v = 0; v < cfg_.vcycles; ++v) enqueue_vcycle<T>(nl - 1, B, s);
+  MGLevel& F = levels_.back();
+  k_update<T><<<grid1((int64_t)B * F.g.ncell()), kBlock, 0, s>>>(counter_, F.g, B, active_,
+                                                                 (const T*)F.x, F.p, F.c);
+}
+
+template <typename T>
+void Solver::enqueue_resjac_check(int B, cudaStream_t s, bool set_cond) {
+  MGLevel& F = levels_.back();
+  const Geom& G = F.g;
+  k_resjac<T><<<dim3(nchunk_, B), kBlock, 0, s>>>(counter_, phys_, G, tau_, B, F.p, F.c, c_old_,
+                                                  F.phi, F.K, F.tx, F.dx, F.ty, F.dy, qin_,
+                                                  active_, (T*)F.J, (T*)F.b, (T*)F.x, partial_);
+  // residual scaled to units of c per step: RMS(R) * tau / (V phi0 rho0)
+  const double scale = tau_ / (G.hx * G.hy * cfg_.phi0 * cfg_.rho0);
+  if (set_cond)
+    k_check_cond<<<1, 1024, 0, s>>>(counter_, B, nchunk_, G.ncell(), partial_, scale,
+                                    cfg_.newton_rtol, cfg_.newton_atol, cfg_.newton_maxit,
+                                    active_, it_step_, res0_, res_last_, status_w_, iters_w_,
+                                    n_active_, (cudaGraphConditionalHandle)cond_handle_);
+  else
+    k_check<<<1, 1024, 0, s>>>(counter_, B, nchunk_, G.ncell(), partial_, scale,
+                               cfg_.newton_rtol, cfg_.newton_atol, cfg_.newton_maxit, active_,
+                               it_step_, res0_, res_last_, status_w_, iters_w_, n_active_);
+}
+
+// One implicit Euler step as a CUDA graph: begin, residual + check, then a
+// device-side while loop over defect-correction iterations.
+template <typename T>
+int Solver::step_graph(int B, cudaStream_t s) {
+  if (graph_B_ != B) {
+    if (step_exec_) cudaGraphExecDestroy(step_exec_);
+    if (step_graph_) cudaGraphDestroy(step_graph_);
+    step_exec_ = nullptr;
+    step_graph_ = nullptr;
+    cudaStream_t cs, bs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    CK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+    cond_handle_ = (unsigned long long)h;
+    CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    MGLevel& F = levels_.back();
+    k_begin_step<<<grid1((int64_t)B * F.g.ncell()), kBlock, 0, cs>>>(
+        counter_, F.g, B, F.c, c_old_, status_w_, active_, it_step_);
+    enqueue_resjac_check<T>(B, cs, true);
+    cudaStreamCaptureStatus st;
+    cudaGraph_t cg;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(cs, &st, nullptr, &cg, &deps, nullptr, &nd));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wn;
+    CK(cudaGraphAddNode(&wn, cg, deps, nullptr, nd, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(cs, &wn, nullptr, 1, cudaStreamSetCaptureDependencies));
+    CK(cudaStreamEndCapture(cs, &g));
+    CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    enqueue_iteration<T>(B, bs);
+    enqueue_resjac_check<T>(B, bs, true);
+    CK(cudaStreamEndCapture(bs, &body));
+    CK(cudaGraphInstantiate(&step_exec_, g, 0));
+    step_graph_ = g;
+    graph_B_ = B;
+    cudaStreamDestroy(cs);
+    cudaStreamDestroy(bs);
+  }
+  CK(cudaGraphLaunch(step_exec_, s));
+  return HENRY_OK;
+}
+
+int Solver::fields(const double* xi, const double* logk, int B, double* phi, double* K,
+                   double* qin, cudaStream_t s) {
+  if (B == 0) return HENRY_OK;
+  int rc = ensure(B, s);
+  if (rc) return rc;
+  const Geom& G = levels_.back().g;
+  k_fields<<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(counter_, phys_, G, B, cfg_.n_xi, xi,
+                                                            logk, phi, K, qin, status_w_);
+  CK(cudaGetLastError());
+  return HENRY_OK;
+}
+
+template <typename T>
+int Solver::run_t(const double* xi, const double* logk, int B, double* q, double* c_out,
+                  double* p_out, int* status, int* iters, int status_or, cudaStream_t s) {
+  const int nl = (int)levels_.size();
+  MGLevel& F = levels_.back();
+  const Geom& G = F.g;
+  k_fields<<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(counter_, phys_, G, B, cfg_.n_xi, xi,
+                                                            logk, F.phi, F.K, qin_, status_w_);
+  for (int k = nl - 1; k >= 1; --k)
+    k_coarsen_fields<<<grid1((int64_t)B * levels_[k - 1].g.ncell()), kBlock, 0, s>>>(
+        counter_, levels_[k].g, levels_[k - 1].g, B, levels_[k].phi, levels_[k].K,
+        levels_[k - 1].phi, levels_[k - 1].K);
+  for (int k = 0; k < nl; ++k) {
+    MGLevel& L = levels_[k];
+    k_face_consts<<<grid1((int64_t)B * L.g.ncell()), kBlock, 0, s>>>(
+        counter_, phys_, L.g, B, L.phi, L.K, L.tx, L.dx, L.ty, L.dy);
+  }
+  k_init_state<<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(counter_, phys_, G, B, F.p, F.c,
+                                                                iters_w_);
+  CK(cudaGetLastError());
+  for (int n = 0; n < nt_; ++n) {
+    if (cfg_.loop_mode == HENRY_LOOP_GRAPH) {
+      int rc = step_graph<T>(B, s);
+      if (rc) return rc;
+      continue;
+    }
+    k_begin_step<<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(counter_, G, B, F.c, c_old_,
+                                                                  status_w_, active_, it_step_);
+    for (;;) {
+      enqueue_resjac_check<T>(B, s, false);
+      CK(cudaMemcpyAsync(n_active_host_, n_active_, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (*n_active_host_ == 0) break;
+      enqueue_iteration<T>(B, s);
+    }
+  }
+  k_qoi<<<B, kBlock, 0, s>>>(counter_, phys_, G, B, F.p, F.c, F.phi, q, c_out, p_out);
+  k_copy_int<<<grid1(B), kBlock, 0, s>>>(counter_, B, status_w_, status, status_or);
+  if (iters) k_copy_int<<<grid1(B), kBlock, 0, s>>>(counter_, B, iters_w_, iters, 0);
+  CK(cudaGetLastError());
+  return HENRY_OK;
+}
+
+int Solver::run(const double* xi, const double* logk, int B, double* q, double* c_out,
+                double* p_out, int* status, int* iters, int status_or, cudaStream_t s) {
+  if (B == 0) return HENRY_OK;
+  int rc = ensure(B, s);
+  if (rc) return rc;
+  if (tsize_ == sizeof(float))
+    return run_t<float>(xi, logk, B, q, c_out, p_out, status, iters, status_or, s);
+  return run_t<double>(xi, logk, B, q, c_out, p_out, status, iters, status_or, s);
+}
+
+cudaError_t launch_residual_jacobian(const Phys& P, const Geom& G, double tau, int B,
+                                     const double* phi, const double* K, const double* qin,
+                                     const double* p, const double* c, const double* c_old,
+                                     double* R, double* J, double* scratch, cudaStream_t s) {
+  const int64_t n = (int64_t)B * G.ncell();
+  const int grid = (int)((n + kBlock - 1) / kBlock);
+  double* tx = scratch;
+  double* dx = scratch + n;
+  double* ty = scratch + 2 * n;
+  double* dy = scratch + 3 * n;
+  k_face_consts<<<grid, kBlock, 0, s>>>(nullptr, P, G, B, phi, K, tx, dx, ty, dy);
+  k_residual_jacobian_natural<<<grid, kBlock, 0, s>>>(nullptr, P, G, tau, B, p, c, c_old, phi, K,
+                                                      tx, dx, ty, dy, qin, R, J);
+  return cudaGetLastError();
+}
+
+}  // namespace henry

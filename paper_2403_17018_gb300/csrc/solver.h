@@ -1,0 +1,104 @@
+// Host-side solver of one grid level of the Henry problem (one "role" of an
+// MLMC level pair). Owns the device workspace of its batch and issues the
+// kernels of the time loop: per implicit Euler step, Newton defect
+// correction with geometric-multigrid V-cycles (arxiv 2403.17018, section
+// 2.3).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/henry.h"
+#include "henry_device.cuh"
+
+namespace henry {
+
+struct MGLevel {
+  Geom g;
+  void* J = nullptr;     // T [B][20][ncell], colour-split planes
+  void* b = nullptr;     // T [B][2][ncell]
+  void* x = nullptr;     // T [B][2][ncell]
+  double* p = nullptr;   // state at this level (finest: the solver's p)
+  double* c = nullptr;
+  double* phi = nullptr;
+  double* K = nullptr;
+  double* tx = nullptr;  // face constants
+  double* dx = nullptr;
+  double* ty = nullptr;
+  double* dy = nullptr;
+};
+
+// Build the multigrid hierarchy of an nx x ny grid: halve while nx is a
+// multiple of 4, ny is even and the coarse grid keeps at least 8 cells.
+// Returns false if the coarsest grid has more than 32 cells or an odd nx.
+bool build_hierarchy(int nx, int ny, double Lx, double Ly, std::vector<Geom>& out);
+
+class Solver {
+ public:
+  Solver(const henry_config& cfg, int nx, int ny, int nt);
+  ~Solver();
+  Solver(const Solver&) = delete;
+  Solver& operator=(const Solver&) = delete;
+
+  // Batched solve; see henry_solve in henry.h. status_or != 0 ORs the
+  // per-sample status into `status` instead of overwriting it.
+  int run(const double* xi, const double* logk, int B, double* q, double* c_out, double* p_out,
+          int* status, int* iters, int status_or, cudaStream_t s);
+  // Fields only (henry_fields).
+  int fields(const double* xi, const double* logk, int B, double* phi, double* K, double* qin,
+             cudaStream_t s);
+
+  const Geom& fine() const { return levels_.back().g; }
+  int nt() const { return nt_; }
+  int n_mg() const { return (int)levels_.size(); }
+  unsigned long long launches() const;
+
+ private:
+  template <typename T> int run_t(const double* xi, const double* logk, int B, double* q,
+                                  double* c_out, double* p_out, int* status, int* iters,
+                                  int status_or, cudaStream_t s);
+  template <typename T> void enqueue_iteration(int B, cudaStream_t s);
+  template <typename T> void enqueue_vcycle(int k, int B, cudaStream_t s);
+  template <typename T> void enqueue_resjac_check(int B, cudaStream_t s, bool set_cond);
+  template <typename T> int step_graph(int B, cudaStream_t s);
+  int ensure(int B, cudaStream_t s);
+  void free_all();
+
+  henry_config cfg_;
+  Phys phys_;
+  int nt_;
+  double tau_;
+  size_t tsize_;              // sizeof(T) of the multigrid arrays
+  std::vector<Geom> geoms_;   // 0 = coarsest
+  std::vector<MGLevel> levels_;
+  int cap_ = 0;               // allocated batch capacity
+  void* arena_ = nullptr;
+  // finest-level / per-sample arrays
+  double* c_old_ = nullptr;
+  double* qin_ = nullptr;
+  double* partial_ = nullptr;
+  double* res0_ = nullptr;
+  double* res_last_ = nullptr;
+  double* lu_ = nullptr;
+  int* piv_ = nullptr;
+  int* active_ = nullptr;
+  int* it_step_ = nullptr;
+  int* status_w_ = nullptr;
+  int* iters_w_ = nullptr;
+  int* n_active_ = nullptr;     // device
+  int* n_active_host_ = nullptr;  // pinned
+  unsigned long long* counter_ = nullptr;  // device launch counter
+  int nchunk_ = 0;
+  // CUDA graph of one time step (HENRY_LOOP_GRAPH), rebuilt when B changes
+  cudaGraphExec_t step_exec_ = nullptr;
+  cudaGraph_t step_graph_ = nullptr;
+  int graph_B_ = -1;
+  unsigned long long cond_handle_ = 0;
+};
+
+void set_last_error(const std::string& msg);
+const char* last_error_cstr();
+
+}  // namespace henry

@@ -1,0 +1,243 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: residual and Jacobian entries to 1e-12 (relative to the flux
+scale of the grid); solutions to max|dc| <= 1e-9 and max|dp|/max|p| <= 1e-9
+(the parity bar for FP64 and for FP32 multigrid inside FP64 defect
+correction, whose converged solution is fixed by the FP64 residual).
+"""
+import numpy as np
+import pytest
+
+from oracle import henry as H
+from oracle import mlmc as M
+from paper_2403_17018_gb300 import binding as hb
+from paper_2403_17018_gb300.inputs import logk_perturbation, xi_batch
+
+from gpu_helpers import oracle_grid, oracle_physics, oracle_solve, tight_config, xi_cuda
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+C_TOL = 1e-9
+P_TOL = 1e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    hb.load()
+
+
+def _oracle_jacobian_blocks(J, nx, ny):
+    """Oracle sparse Jacobian -> [20, ny, nx] in the C ABI's block layout."""
+    J = J.tocsr()
+    out = np.zeros((20, ny, nx))
+    for j in range(ny):
+        for i in range(nx):
+            P = j * nx + i
+            nbs = [P, P - 1 if i > 0 else -1, P + 1 if i < nx - 1 else -1,
+                   P - nx if j > 0 else -1, P + nx if j < ny - 1 else -1]
+            for q, Q in enumerate(nbs):
+                if Q < 0:
+                    continue
+                for e in range(2):
+                    for v in range(2):
+                        out[4 * q + 2 * e + v, j, i] = J[2 * P + e, 2 * Q + v]
+    return out
+
+
+@pytest.mark.parametrize("nx,ny", [(32, 16), (24, 6), (10, 4)])
+def test_residual_and_jacobian_match_oracle(nx, ny):
+    cfg = hb.default_config()
+    ph = oracle_physics(cfg)
+    g = H.Grid(nx=nx, ny=ny, nt=1, T=1800.0)
+    B = 3
+    rng = np.random.default_rng(nx * 100 + ny)
+    xis = xi_batch(0, 40, B)
+    lk = logk_perturbation(ny, nx, B)
+    phi, K, qin, p, c, c_old = [], [], [], [], [], []
+    for b in range(B):
+        f = H.fields(g, ph, xis[b], lk[b])
+        phi.append(f.phi); K.append(f.K); qin.append(f.qin)
+        c.append(np.clip(rng.random((ny, nx)), 0, 1))
+        c_old.append(np.clip(c[-1] + 0.1 * rng.standard_normal((ny, nx)), 0, 1))
+        p.append(H.hydrostatic_guess(g, ph) + 40 * rng.standard_normal((ny, nx)))
+    cuda = lambda a: torch.from_numpy(np.ascontiguousarray(np.array(a))).cuda()
+    R, J = hb.residual_jacobian(cfg, g.tau, cuda(phi), cuda(K), cuda(qin), cuda(p), cuda(c),
+                                cuda(c_old))
+    R, J = R.cpu().numpy(), J.cpu().numpy()
+    for b in range(B):
+        f = H.Fields(phi=phi[b], K=K[b], qin=qin[b])
+        Rp, Rc = H.residual(g, ph, f, p[b], c[b], c_old[b])
+        Fx = H.face_fluxes(g, ph, f, p[b], c[b])
+        scale = max(np.max(np.abs(Fx["mass_y"])), np.max(np.abs(Fx["mass_x"])), np.max(np.abs(Rp)))
+        assert np.max(np.abs(R[b, 0] - Rp)) <= 1e-12 * scale
+        assert np.max(np.abs(R[b, 1] - Rc)) <= 1e-12 * scale
+        Jo = _oracle_jacobian_blocks(H.jacobian(g, ph, f, p[b], c[b], c_old[b]), nx, ny)
+        for m in range(20):
+            sc = max(np.max(np.abs(Jo[m])), 1e-300)
+            assert np.max(np.abs(J[b, m] - Jo[m])) <= 1e-11 * sc, (b, m)
+
+
+@pytest.mark.parametrize("n_xi", [3, 6])
+def test_fields_match_oracle(n_xi):
+    cfg = hb.default_config(n_xi=n_xi, nlevels=2)
+    ctx = hb.Context(cfg)
+    ph = oracle_physics(cfg)
+    for level in (0, 1):
+        B = 4
+        xi = xi_cuda(level, 0, B, n_xi)
+        g = oracle_grid(cfg, level)
+        lk = torch.from_numpy(logk_perturbation(g.ny, g.nx, B)).cuda()
+        phi, K, qin = ctx.fields(level, xi, lk)
+        for b in range(B):
+            f = H.fields(g, ph, xi[b].cpu().numpy(), lk[b].cpu().numpy())
+            assert np.allclose(phi[b].cpu().numpy(), f.phi, rtol=1e-14, atol=0)
+            assert np.allclose(K[b].cpu().numpy(), f.K, rtol=1e-13, atol=0)
+            assert np.allclose(qin[b].cpu().numpy(), f.qin, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("precision,loop", [(hb.PREC_FP64, hb.LOOP_HOST),
+                                            (hb.PREC_FP64, hb.LOOP_GRAPH),
+                                            (hb.PREC_FP32_MG, hb.LOOP_GRAPH)])
+def test_level0_solve_matches_oracle(precision, loop):
+    cfg = tight_config(precision=precision, loop_mode=loop)
+    ctx = hb.Context(cfg)
+    B = 3
+    xi = xi_cuda(0, 0, B)
+    out = ctx.solve(0, xi, want_c=True, want_p=True, want_iters=True)
+    assert out["status"].cpu().numpy().tolist() == [0] * B
+    for b in range(B):
+        p_o, c_o, q_o = oracle_solve(cfg, 0, xi[b].cpu().numpy())
+        c_g = out["c"][b].cpu().numpy()
+        p_g = out["p"][b].cpu().numpy()
+        assert np.max(np.abs(c_g - c_o)) <= C_TOL
+        assert np.max(np.abs(p_g - p_o)) <= P_TOL * np.max(np.abs(p_o))
+        q_g = out["q"][b].cpu().numpy()
+        assert np.allclose(q_g, q_o, rtol=1e-9, atol=1e-9)
+
+
+def test_graph_loop_is_bitwise_equal_to_host_loop():
+    res = []
+    for loop in (hb.LOOP_HOST, hb.LOOP_GRAPH):
+        ctx = hb.Context(tight_config(loop_mode=loop))
+        out = ctx.solve(0, xi_cuda(0, 3, 4), want_c=True, want_iters=True)
+        res.append(out)
+    assert torch.equal(res[0]["c"], res[1]["c"])
+    assert torch.equal(res[0]["q"], res[1]["q"])
+    assert torch.equal(res[0]["iters"], res[1]["iters"])
+
+
+def test_sample_result_does_not_depend_on_batch():
+    ctx = hb.Context(tight_config())
+    xi = xi_cuda(0, 0, 7)
+    full = ctx.solve(0, xi, want_c=True)
+    part = ctx.solve(0, xi[2:5].contiguous(), want_c=True)
+    assert torch.equal(full["c"][2:5], part["c"])
+    assert torch.equal(full["q"][2:5], part["q"])
+
+
+def test_pair_coarse_is_bitwise_the_level_below():
+    ctx = hb.Context(tight_config(nlevels=2))
+    xi = xi_cuda(1, 0, 3)
+    qf, qc, cf, cc, st = ctx.sample_pairs(1, xi, want_c=True)
+    below = ctx.solve(0, xi, want_c=True)
+    fine = ctx.solve(1, xi, want_c=True)
+    assert st.cpu().numpy().tolist() == [0, 0, 0]
+    assert torch.equal(qc, below["q"]) and torch.equal(cc, below["c"])
+    assert torch.equal(qf, fine["q"]) and torch.equal(cf, fine["c"])
+
+
+@pytest.mark.parametrize("precision", [hb.PREC_FP64, hb.PREC_FP32_MG])
+def test_level1_pairs_match_oracle(precision):
+    cfg = tight_config(nlevels=2, precision=precision)
+    ctx = hb.Context(cfg)
+    xi = xi_cuda(1, 0, 2)
+    qf, qc, cf, cc, st = ctx.sample_pairs(1, xi, want_c=True)
+    assert st.cpu().numpy().tolist() == [0, 0]
+    for b in range(2):
+        _, c1, q1 = oracle_solve(cfg, 1, xi[b].cpu().numpy())
+        _, c0, q0 = oracle_solve(cfg, 0, xi[b].cpu().numpy())
+        assert np.max(np.abs(cf[b].cpu().numpy() - c1)) <= C_TOL
+        assert np.max(np.abs(cc[b].cpu().numpy() - c0)) <= C_TOL
+        assert np.allclose(qf[b].cpu().numpy(), q1, rtol=1e-9, atol=1e-9)
+        assert np.allclose(qc[b].cpu().numpy(), q0, rtol=1e-9, atol=1e-9)
+
+
+def test_ragged_grid_matches_oracle():
+    """24x12 cells (coarsest multigrid grid 6x3, odd ny), 5 steps: blocks of
+    256 threads end mid-sample and mid-row."""
+    cfg = tight_config(nx0=24, ny0=12, nt0=5, T=5 * 1800.0, nlevels=1)
+    ctx = hb.Context(cfg)
+    assert ctx.level_info(0).n_mg == 3
+    xi = xi_cuda(0, 9, 5)
+    out = ctx.solve(0, xi, want_c=True, want_p=True)
+    for b in range(5):
+        p_o, c_o, q_o = oracle_solve(cfg, 0, xi[b].cpu().numpy())
+        assert np.max(np.abs(out["c"][b].cpu().numpy() - c_o)) <= C_TOL
+        assert np.max(np.abs(out["p"][b].cpu().numpy() - p_o)) <= P_TOL * np.max(np.abs(p_o))
+
+
+def test_level_stats_match_two_pass():
+    ctx = hb.Context(hb.default_config(nlevels=2))
+    rng = np.random.default_rng(5)
+    qf = rng.standard_normal((300, hb.NQ)) * 3 + 10
+    qc = qf + 0.01 * rng.standard_normal(qf.shape)
+    st = np.zeros(300, dtype=np.int32)
+    st[[4, 77]] = 1
+    S = hb.LevelStats()
+    for a, b in ((0, 129), (129, 300)):
+        ctx.level_stats(1, torch.from_numpy(qf[a:b]).cuda(), torch.from_numpy(qc[a:b]).cuda(),
+                        torch.from_numpy(st[a:b]).cuda(), S)
+    keep = st == 0
+    ref = M.level_stats(qf[keep], qc[keep])
+    got = S.numpy()
+    assert got["n"] == keep.sum()
+    for k in ("mean_f", "var_f", "mean_d", "var_d"):
+        assert np.allclose(got[k], ref[k], rtol=1e-12, atol=0), k
+
+
+def test_field_stats_match_two_pass():
+    ctx = hb.Context(hb.default_config(nlevels=2))
+    li1, li0 = ctx.level_info(1), ctx.level_info(0)
+    rng = np.random.default_rng(6)
+    cf = rng.random((40, li1.ny, li1.nx))
+    cc = rng.random((40, li0.ny, li0.nx))
+    st = np.zeros(40, dtype=np.int32)
+    acc = hb.new_field_accumulator(li1.ny, li1.nx)
+    for a, b in ((0, 17), (17, 40)):
+        ctx.field_stats(1, torch.from_numpy(cf[a:b]).cuda(), torch.from_numpy(cc[a:b]).cuda(),
+                        torch.from_numpy(st[a:b]).cuda(), acc)
+    d = cf - H.prolong_constant(cc.transpose(1, 2, 0)).transpose(2, 0, 1)
+    assert int(acc["n"][0, 0]) == 40
+    assert np.allclose(acc["mean_f"].cpu().numpy(), cf.mean(0), rtol=1e-13, atol=1e-15)
+    assert np.allclose(acc["m2_f"].cpu().numpy() / 39, cf.var(0, ddof=1), rtol=1e-11, atol=1e-15)
+    assert np.allclose(acc["mean_d"].cpu().numpy(), d.mean(0), rtol=1e-12, atol=1e-15)
+    assert np.allclose(acc["m2_d"].cpu().numpy() / 39, d.var(0, ddof=1), rtol=1e-11, atol=1e-15)
+
+
+def test_bad_input_and_iteration_cap_are_reported_per_sample():
+    ctx = hb.Context(hb.default_config(nlevels=1, newton_maxit=30))
+    xi = xi_cuda(0, 0, 3)
+    xi[1, 0] = float("nan")
+    out = ctx.solve(0, xi)
+    st = out["status"].cpu().numpy()
+    assert st[1] & hb.S_BADINPUT and st[0] == 0 and st[2] == 0
+    ref = hb.Context(hb.default_config(nlevels=1)).solve(0, xi[[0, 2]].contiguous())
+    assert torch.equal(out["q"][[0, 2]], ref["q"])
+    capped = hb.Context(hb.default_config(nlevels=1, newton_maxit=1)).solve(0, xi_cuda(0, 0, 2))
+    assert np.all(capped["status"].cpu().numpy() & hb.S_MAXIT)
+
+
+def test_invalid_arguments_are_rejected():
+    ctx = hb.Context(hb.default_config(nlevels=2))
+    with pytest.raises(hb.HenryError) as e:
+        ctx.solve(5, xi_cuda(0, 0, 2))
+    assert e.value.code == -1
+    with pytest.raises(ValueError):
+        ctx.solve(0, xi_cuda(0, 0, 2).float())
+    with pytest.raises(hb.HenryError):
+        hb.Context(hb.default_config(nx0=30, ny0=15))   # 15 rows cannot be coarsened
+    empty = ctx.solve(0, xi_cuda(0, 0, 0))
+    assert empty["q"].shape == (0, hb.NQ)
