@@ -198,6 +198,21 @@ int henry_fields(henry_ctx* ctx, int level, const double* xi, const double* logk
 /* Grid of level l: *nx, *ny, *nt (steps), *n_mg (multigrid levels). */
 int henry_level_info(const henry_ctx* ctx, int level, int* nx, int* ny, int* nt, int* n_mg);
 
+/* Diagnostics: copy an internal array of the solver that serves `level`
+ * (role 0: fine solves and level-l halves of pairs; role 1: the level-(l-1)
+ * halves of pairs, addressed by their own level l-1) for multigrid level
+ * mg_level (0 = coarsest). what: 0 J [B][20][ncell] (colour-split planes),
+ * 1 b, 2 x ([B][2][ncell], colour-split), 3 p, 4 c, 5 phi, 6 K ([B][ncell],
+ * natural), 7..10 face constants tx, dx, ty, dy, 11..12 face fluxes of the
+ * linearisation point qx (east faces; the right side in the last column),
+ * qy (north faces). Element size is 4 bytes
+ * for J, b, x with FP32 multigrid, else 8. Copies min(bytes, size) bytes
+ * to the device or host pointer dst and synchronises the device.
+ * Errors: HENRY_E_INVALID if the solver does not exist yet or an index is
+ * out of range. */
+int henry_debug_copy(henry_ctx* ctx, int level, int role, int mg_level, int what, void* dst,
+                     int64_t bytes);
+
 /* Device kernel launches issued by this context since creation (counts
  * every launch, including those replayed inside CUDA graphs). */
 int64_t henry_launch_count(const henry_ctx* ctx);

@@ -86,6 +86,7 @@ def load():
         "henry_level_info": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                                  ctypes.POINTER(I)]),
         "henry_launch_count": (ctypes.c_int64, [P]),
+        "henry_debug_copy": (I, [P, I, I, I, I, V, ctypes.c_int64]),
         "henry_strerror": (ctypes.c_char_p, [I]),
         "henry_last_error": (ctypes.c_char_p, []),
     }
@@ -173,6 +174,13 @@ class Context:
         v = [ctypes.c_int() for _ in range(4)]
         _check(self.lib.henry_level_info(self._h, level, *[ctypes.byref(x) for x in v]))
         return LevelInfo(*[x.value for x in v])
+
+    def debug_copy(self, level, role, mg_level, what, nbytes):
+        """henry_debug_copy into a host numpy byte buffer."""
+        buf = np.zeros(nbytes, dtype=np.uint8)
+        _check(self.lib.henry_debug_copy(self._h, level, role, mg_level, what,
+                                         buf.ctypes.data_as(ctypes.c_void_p), nbytes))
+        return buf
 
     def launch_count(self) -> int:
         return int(self.lib.henry_launch_count(self._h))

@@ -271,12 +271,24 @@ int henry_residual_jacobian(const henry_config* cfg, int nx, int ny, double tau,
   henry::Geom G{nx, ny, cfg->Lx / nx, cfg->Ly / ny};
   cudaStream_t s = (cudaStream_t)stream;
   double* scratch = nullptr;
-  CKR(cudaMallocAsync((void**)&scratch, sizeof(double) * 4 * (size_t)B * nx * ny, s));
+  CKR(cudaMallocAsync((void**)&scratch, sizeof(double) * 5 * (size_t)B * nx * ny, s));
   cudaError_t e = henry::launch_residual_jacobian(P, G, tau, B, phi, K, qin, p, c, c_old, R, J,
                                                   scratch, s);
   cudaError_t e2 = cudaFreeAsync(scratch, s);
   CKR(e);
   CKR(e2);
+  return HENRY_OK;
+}
+
+int henry_debug_copy(henry_ctx* ctx, int level, int role, int mg_level, int what, void* dst,
+                     int64_t bytes) {
+  if (!ctx || level < 0 || level >= ctx->cfg.nlevels || role < 0 || role > 1)
+    return fail(HENRY_E_INVALID, "bad context, level or role");
+  const auto& s = ctx->role[role][level];
+  if (!s) return fail(HENRY_E_INVALID, "no solver has run for this level and role");
+  CKR(cudaSetDevice(ctx->device));
+  int rc = s->debug_copy(mg_level, what, dst, bytes);
+  if (rc) return fail(rc, "debug_copy: bad index, empty workspace or copy failure");
   return HENRY_OK;
 }
 

@@ -18,6 +18,15 @@
 // Accumulation per cell: V phi (rho - rho_old)/tau and V phi (rho c -
 // rho_old c_old)/tau.
 //
+// Pressure unknown: the kernels carry the reduced pressure
+//   p' = p - rho0 g (Ly - y)
+// (the fresh-water hydrostatic part removed), so the gravity term of a
+// vertical face becomes (rho_bar - rho0) g d = 0.5 (rho1 - rho0)(c_L + c_U) g d
+// and the Dirichlet value on the right side (rho1 - rho0) g (Ly - y). This
+// is the same discrete equation as with p, but without the cancellation of
+// two ~rho0 g d terms in every vertical face flux, which lowers the rounding
+// floor of the FP64 residual by about (rho0 / (rho1 - rho0)) = 40x.
+//
 // Face constants are precomputed once per solve (the fields do not change in
 // time): tx = A_x K_f / (mu hx), dx = A_x phi_f D / hx for the east face of a
 // cell, ty, dy likewise for its north face. This keeps divisions out of the
@@ -56,14 +65,17 @@ struct FaceD {
 };
 
 // Interior face. t = A K_f/(mu d), dco = A phi_f D / d, gd = g e_y d.
-template <typename JT, bool WANT_J>
+// q is the area-weighted face flux A q.n: computed from p unless Q_GIVEN, in
+// which case the caller supplies it (coarse multigrid levels linearise about
+// the restricted fine-level flux field) and the pressures are not used.
+template <typename JT, bool WANT_J, bool Q_GIVEN>
 __device__ __forceinline__ void face_flux(const Phys& P, double pL, double cL, double pU, double cU,
-                                          double t, double dco, double gd,
+                                          double t, double dco, double gd, double& q,
                                           double& Fm, double& Fs, FaceD<JT>& J) {
   const double rL = P.rho0 + P.drho * cL;
   const double rU = P.rho0 + P.drho * cU;
   const double rbar = 0.5 * (rL + rU);
-  const double q = -t * ((pU - pL) + rbar * gd);
+  if (!Q_GIVEN) q = -t * ((pU - pL) + (0.5 * P.drho) * (cL + cU) * gd);
   const bool up = q >= 0.0;
   const double rup = up ? rL : rU;
   const double rcup = up ? rL * cL : rU * cU;
@@ -93,6 +105,8 @@ struct CellIn {
   double pW, cW, pE, cE, pS, cS, pN, cN;
   double tW, dW, tE, dE, tS, dS, tN, dN;   // face constants (valid where the face exists)
   double qin;                        // left inflow velocity of this row (i == 0)
+  double qW, qE, qS, qN;             // face fluxes A q.n (qE: right side when i == nx-1);
+                                     // outputs, or inputs when Q_GIVEN
   bool hasW, hasE, hasS, hasN;       // interior faces
   double y;                          // cell-centre y (right boundary pressure)
 };
@@ -100,9 +114,9 @@ struct CellIn {
 // Residual (FP64) and, optionally, the 20 Jacobian entries of one cell:
 // J[0..3] = dR_P/du_P, J[4..7] W, J[8..11] E, J[12..15] S, J[16..19] N;
 // each block (pp, pc, cp, cc), row = equation, column = variable.
-template <typename JT, bool WANT_J>
+template <typename JT, bool WANT_J, bool Q_GIVEN = false>
 __device__ __forceinline__ void cell_residual(const Phys& P, const Geom& G, double tau,
-                                              const CellIn& in, double& Rp, double& Rc, JT* J) {
+                                              CellIn& in, double& Rp, double& Rc, JT* J) {
   const double V = G.hx * G.hy;
   const double vt = V * in.phi / tau;
   const double rho = P.rho0 + P.drho * in.c;
@@ -120,7 +134,7 @@ __device__ __forceinline__ void cell_residual(const Phys& P, const Geom& G, doub
   const double gdy = P.g * G.hy;
   // west face: L = W, U = P; contributes -F to P
   if (in.hasW) {
-    face_flux<JT, WANT_J>(P, in.pW, in.cW, in.p, in.c, in.tW, in.dW, 0.0, Fm, Fs, d);
+    face_flux<JT, WANT_J, Q_GIVEN>(P, in.pW, in.cW, in.p, in.c, in.tW, in.dW, 0.0, in.qW, Fm, Fs, d);
     Rp -= Fm;
     Rc -= Fs;
     if (WANT_J) {
@@ -138,7 +152,7 @@ __device__ __forceinline__ void cell_residual(const Phys& P, const Geom& G, doub
   }
   // east face: L = P, U = E; contributes +F to P
   if (in.hasE) {
-    face_flux<JT, WANT_J>(P, in.p, in.c, in.pE, in.cE, in.tE, in.dE, 0.0, Fm, Fs, d);
+    face_flux<JT, WANT_J, Q_GIVEN>(P, in.p, in.c, in.pE, in.cE, in.tE, in.dE, 0.0, in.qE, Fm, Fs, d);
     Rp += Fm;
     Rc += Fs;
     if (WANT_J) {
@@ -151,8 +165,9 @@ __device__ __forceinline__ void cell_residual(const Phys& P, const Geom& G, doub
     const double rho1 = P.rho0 + P.drho;
     const double tR = 2.0 * A * in.K / (P.mu * G.hx);
     const double dco = 2.0 * A * in.phi * P.D / G.hx;
-    const double pb = rho1 * P.g * (P.Ly - in.y);
-    const double q = -tR * (pb - in.p);
+    const double pb = P.drho * P.g * (P.Ly - in.y);   // reduced pressure
+    if (!Q_GIVEN) in.qE = -tR * (pb - in.p);
+    const double q = in.qE;
     const bool up = q >= 0.0;
     const double rup = up ? rho : rho1;
     const double rcup = up ? rho * in.c : rho1;
@@ -169,7 +184,7 @@ __device__ __forceinline__ void cell_residual(const Phys& P, const Geom& G, doub
   }
   // south face: L = S, U = P (e = +y); contributes -F
   if (in.hasS) {
-    face_flux<JT, WANT_J>(P, in.pS, in.cS, in.p, in.c, in.tS, in.dS, gdy, Fm, Fs, d);
+    face_flux<JT, WANT_J, Q_GIVEN>(P, in.pS, in.cS, in.p, in.c, in.tS, in.dS, gdy, in.qS, Fm, Fs, d);
     Rp -= Fm;
     Rc -= Fs;
     if (WANT_J) {
@@ -179,7 +194,7 @@ __device__ __forceinline__ void cell_residual(const Phys& P, const Geom& G, doub
   }
   // north face: L = P, U = N; contributes +F
   if (in.hasN) {
-    face_flux<JT, WANT_J>(P, in.p, in.c, in.pN, in.cN, in.tN, in.dN, gdy, Fm, Fs, d);
+    face_flux<JT, WANT_J, Q_GIVEN>(P, in.p, in.c, in.pN, in.cN, in.tN, in.dN, gdy, in.qN, Fm, Fs, d);
     Rp += Fm;
     Rc += Fs;
     if (WANT_J) {

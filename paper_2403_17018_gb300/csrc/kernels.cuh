@@ -89,7 +89,8 @@ __global__ void k_face_consts(unsigned long long* ctr, Phys P, Geom G, int B,
   face_constants(P, G, i, j, phi + o, K + o, tx[idx], dx[idx], ty[idx], dy[idx]);
 }
 
-// Initial state c = 0; the Newton guess for p is seawater hydrostatics.
+// Initial state c = 0; the Newton guess for p is seawater hydrostatics,
+// stored as the reduced pressure p' = p - rho0 g (Ly - y).
 __global__ void k_init_state(unsigned long long* ctr, Phys P, Geom G, int B, double* __restrict__ p,
                              double* __restrict__ c, int* __restrict__ iters) {
   HENRY_COUNT_LAUNCH(ctr);
@@ -100,7 +101,7 @@ __global__ void k_init_state(unsigned long long* ctr, Phys P, Geom G, int B, dou
   const int cell = (int)(idx - (int64_t)b * G.ncell());
   const int j = cell / G.nx;
   const double y = (j + 0.5) * G.hy;
-  p[idx] = (P.rho0 + P.drho) * P.g * (P.Ly - y);
+  p[idx] = P.drho * P.g * (P.Ly - y);
   c[idx] = 0.0;
   if (cell == 0) iters[b] = 0;
 }
@@ -135,7 +136,8 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double tau, int B,
          const double* __restrict__ dx, const double* __restrict__ ty,
          const double* __restrict__ dy, const double* __restrict__ qin,
          const int* __restrict__ active, T* __restrict__ J, T* __restrict__ bvec,
-         T* __restrict__ xvec, double* __restrict__ partial) {
+         T* __restrict__ xvec, double* __restrict__ partial, double* __restrict__ qx,
+         double* __restrict__ qy) {
   HENRY_COUNT_LAUNCH(ctr);
   __shared__ double sh[kBlock / 32];
   const int b = blockIdx.y;
@@ -162,6 +164,8 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double tau, int B,
     T* Jb = J + (int64_t)b * 20 * ncell + cs;
 #pragma unroll
     for (int m = 0; m < 20; ++m) Jb[(int64_t)m * ncell] = Jc[m];
+    qx[o + cell] = in.qE;
+    qy[o + cell] = in.hasN ? in.qN : 0.0;
     v = Rp * Rp + Rc * Rc;
   }
   const double s = block_sum(v, sh);
@@ -215,12 +219,17 @@ __global__ void k_check(unsigned long long* ctr, int B, int nchunk, int ncell,
   if (threadIdx.x == 0) *n_active = cnt;
 }
 
-// Average the state of level k onto level k-1 (rediscretisation of the
-// multigrid operators at the current Newton iterate).
+// Linearisation point of level k-1 from level k: c averaged over the four
+// children, face fluxes summed over the two fine faces that make up each
+// coarse face (east faces of the right children, north faces of the top
+// children; at the right side these are the boundary fluxes). Linearising
+// every level about the same flux field keeps the upwind decisions of the
+// coarse operators consistent with the finest one.
 __global__ void k_restrict_state(unsigned long long* ctr, Geom Gf, Geom Gc, int B,
-                                 const int* __restrict__ active, const double* __restrict__ pf,
-                                 const double* __restrict__ cf, double* __restrict__ pc,
-                                 double* __restrict__ cc) {
+                                 const int* __restrict__ active, const double* __restrict__ cf,
+                                 const double* __restrict__ qxf, const double* __restrict__ qyf,
+                                 double* __restrict__ cc, double* __restrict__ qxc,
+                                 double* __restrict__ qyc) {
   HENRY_COUNT_LAUNCH(ctr);
   const int64_t n = (int64_t)B * Gc.ncell();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -229,9 +238,11 @@ __global__ void k_restrict_state(unsigned long long* ctr, Geom Gf, Geom Gc, int 
   if (!active[b]) return;
   const int cell = (int)(idx - (int64_t)b * Gc.ncell());
   const int J = cell / Gc.nx, I = cell - J * Gc.nx;
-  const int64_t f0 = (int64_t)b * Gf.ncell() + (2 * J) * Gf.nx + 2 * I;
-  pc[idx] = 0.25 * (pf[f0] + pf[f0 + 1] + pf[f0 + Gf.nx] + pf[f0 + Gf.nx + 1]);
-  cc[idx] = 0.25 * (cf[f0] + cf[f0 + 1] + cf[f0 + Gf.nx] + cf[f0 + Gf.nx + 1]);
+  const int nx = Gf.nx;
+  const int64_t f0 = (int64_t)b * Gf.ncell() + (2 * J) * nx + 2 * I;
+  cc[idx] = 0.25 * (cf[f0] + cf[f0 + 1] + cf[f0 + nx] + cf[f0 + nx + 1]);
+  qxc[idx] = qxf[f0 + 1] + qxf[f0 + nx + 1];
+  qyc[idx] = qyf[f0 + nx] + qyf[f0 + nx + 1];
 }
 
 // Jacobian of a coarse multigrid level from its own state and fields.
@@ -240,7 +251,8 @@ __global__ void __launch_bounds__(kBlock)
 k_jac(unsigned long long* ctr, Phys P, Geom G, double tau, int B, const int* __restrict__ active,
       const double* __restrict__ p, const double* __restrict__ c, const double* __restrict__ phi,
       const double* __restrict__ K, const double* __restrict__ tx, const double* __restrict__ dx,
-      const double* __restrict__ ty, const double* __restrict__ dy, T* __restrict__ J) {
+      const double* __restrict__ ty, const double* __restrict__ dy, const double* __restrict__ qx,
+      const double* __restrict__ qy, T* __restrict__ J) {
   HENRY_COUNT_LAUNCH(ctr);
   const int ncell = G.ncell();
   const int64_t n = (int64_t)B * ncell;
@@ -255,9 +267,14 @@ k_jac(unsigned long long* ctr, Phys P, Geom G, double tau, int B, const int* __r
   gather_cell(G, i, j, p + o, c + o, phi + o, K + o, tx + o, dx + o, ty + o, dy + o, in);
   in.c_old = in.c;
   in.qin = 0.0;
+  const int id = cell;
+  in.qE = qx[o + id];
+  in.qN = in.hasN ? qy[o + id] : 0.0;
+  in.qW = in.hasW ? qx[o + id - 1] : 0.0;
+  in.qS = in.hasS ? qy[o + id - G.nx] : 0.0;
   double Rp, Rc;
   T Jc[20];
-  cell_residual<T, true>(P, G, tau, in, Rp, Rc, Jc);
+  cell_residual<T, true, true>(P, G, tau, in, Rp, Rc, Jc);
   T* Jb = J + (int64_t)b * 20 * ncell + cs_pos(i, j, G.nx, G.half());
 #pragma unroll
   for (int m = 0; m < 20; ++m) Jb[(int64_t)m * ncell] = Jc[m];
@@ -582,7 +599,7 @@ k_qoi(unsigned long long* ctr, Phys P, Geom G, int B, const double* __restrict__
     s1 += phi[o + cell] * rho * cv;
     s2 += cv * (P.Lx - x);
     if (c_out) c_out[o + cell] = cv;
-    if (p_out) p_out[o + cell] = p[o + cell];
+    if (p_out) p_out[o + cell] = p[o + cell] + P.rho0 * P.g * (P.Ly - (j + 0.5) * G.hy);
   }
   const double V = G.hx * G.hy;
   s0 = block_sum(s0, sh);
@@ -597,6 +614,17 @@ k_qoi(unsigned long long* ctr, Phys P, Geom G, int B, const double* __restrict__
     qb[4] = bilinear(G, c + o, 1.65, 0.25);
     qb[5] = bilinear(G, c + o, 1.90, 0.50);
   }
+}
+
+// p -> p' = p - rho0 g (Ly - y) for the natural-layout entry point.
+__global__ void k_reduce_pressure(Phys P, Geom G, int B, const double* __restrict__ p,
+                                  double* __restrict__ pr) {
+  const int64_t n = (int64_t)B * G.ncell();
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int cell = (int)(idx % G.ncell());
+  const int j = cell / G.nx;
+  pr[idx] = p[idx] - P.rho0 * P.g * (P.Ly - (j + 0.5) * G.hy);
 }
 
 // Residual and Jacobian in natural layout (FP64), for parity tests.

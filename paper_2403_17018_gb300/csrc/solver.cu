@@ -132,6 +132,21 @@ unsigned long long Solver::launches() const {
   return v;
 }
 
+int Solver::debug_copy(int mg_level, int what, void* dst, int64_t bytes) const {
+  if (mg_level < 0 || mg_level >= (int)levels_.size() || what < 0 || what > 12 || !dst || bytes < 0)
+    return HENRY_E_INVALID;
+  if (cap_ == 0) return HENRY_E_INVALID;
+  const MGLevel& L = levels_[mg_level];
+  const size_t n = (size_t)L.g.ncell() * cap_;
+  const void* src[13] = {L.J, L.b, L.x, L.p, L.c, L.phi, L.K, L.tx, L.dx, L.ty, L.dy, L.qx, L.qy};
+  const size_t size[13] = {20 * n * tsize_, 2 * n * tsize_, 2 * n * tsize_, n * 8, n * 8,
+                           n * 8, n * 8, n * 8, n * 8, n * 8, n * 8, n * 8, n * 8};
+  const size_t nb = (size_t)bytes < size[what] ? (size_t)bytes : size[what];
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(dst, src[what], nb, cudaMemcpyDefault));
+  return HENRY_OK;
+}
+
 int Solver::ensure(int B, cudaStream_t s) {
   if (B <= cap_) return HENRY_OK;
   unsigned long long count = 0;
@@ -141,7 +156,7 @@ int Solver::ensure(int B, cudaStream_t s) {
   const size_t Bz = (size_t)B;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
-  struct Off { size_t J, b, x, p, c, phi, K, tx, dx, ty, dy; };
+  struct Off { size_t J, b, x, p, c, phi, K, tx, dx, ty, dy, qx, qy; };
   std::vector<Off> lo(levels_.size());
   for (size_t k = 0; k < levels_.size(); ++k) {
     const size_t n = (size_t)levels_[k].g.ncell() * Bz;
@@ -156,6 +171,8 @@ int Solver::ensure(int B, cudaStream_t s) {
     lo[k].dx = take(n * 8);
     lo[k].ty = take(n * 8);
     lo[k].dy = take(n * 8);
+    lo[k].qx = take(n * 8);
+    lo[k].qy = take(n * 8);
   }
   const Geom& F = levels_.back().g;
   const size_t o_cold = take((size_t)F.ncell() * Bz * 8);
@@ -187,6 +204,8 @@ int Solver::ensure(int B, cudaStream_t s) {
     L.dx = (double*)(a + lo[k].dx);
     L.ty = (double*)(a + lo[k].ty);
     L.dy = (double*)(a + lo[k].dy);
+    L.qx = (double*)(a + lo[k].qx);
+    L.qy = (double*)(a + lo[k].qy);
   }
   c_old_ = (double*)(a + o_cold);
   qin_ = (double*)(a + o_qin);
@@ -243,10 +262,10 @@ void Solver::enqueue_iteration(int B, cudaStream_t s) {
     MGLevel& F = levels_[k];
     MGLevel& C = levels_[k - 1];
     k_restrict_state<<<grid1((int64_t)B * C.g.ncell()), kBlock, 0, s>>>(
-        counter_, F.g, C.g, B, active_, F.p, F.c, C.p, C.c);
+        counter_, F.g, C.g, B, active_, F.c, F.qx, F.qy, C.c, C.qx, C.qy);
     k_jac<T><<<grid1((int64_t)B * C.g.ncell()), kBlock, 0, s>>>(
         counter_, phys_, C.g, tau_, B, active_, C.p, C.c, C.phi, C.K, C.tx, C.dx, C.ty, C.dy,
-        (T*)C.J);
+        C.qx, C.qy, (T*)C.J);
   }
   k_coarse_lu<T><<<B, 64, 0, s>>>(counter_, levels_[0].g, B, active_, (const T*)levels_[0].J,
                                   lu_, piv_);
@@ -262,7 +281,8 @@ void Solver::enqueue_resjac_check(int B, cudaStream_t s, bool set_cond) {
   const Geom& G = F.g;
   k_resjac<T><<<dim3(nchunk_, B), kBlock, 0, s>>>(counter_, phys_, G, tau_, B, F.p, F.c, c_old_,
                                                   F.phi, F.K, F.tx, F.dx, F.ty, F.dy, qin_,
-                                                  active_, (T*)F.J, (T*)F.b, (T*)F.x, partial_);
+                                                  active_, (T*)F.J, (T*)F.b, (T*)F.x, partial_,
+                                                  F.qx, F.qy);
   // residual scaled to units of c per step: RMS(R) * tau / (V phi0 rho0)
   const double scale = tau_ / (G.hx * G.hy * cfg_.phi0 * cfg_.rho0);
   if (set_cond)
@@ -402,8 +422,10 @@ cudaError_t launch_residual_jacobian(const Phys& P, const Geom& G, double tau, i
   double* dx = scratch + n;
   double* ty = scratch + 2 * n;
   double* dy = scratch + 3 * n;
+  double* pr = scratch + 4 * n;
   k_face_consts<<<grid, kBlock, 0, s>>>(nullptr, P, G, B, phi, K, tx, dx, ty, dy);
-  k_residual_jacobian_natural<<<grid, kBlock, 0, s>>>(nullptr, P, G, tau, B, p, c, c_old, phi, K,
+  k_reduce_pressure<<<grid, kBlock, 0, s>>>(P, G, B, p, pr);
+  k_residual_jacobian_natural<<<grid, kBlock, 0, s>>>(nullptr, P, G, tau, B, pr, c, c_old, phi, K,
                                                       tx, dx, ty, dy, qin, R, J);
   return cudaGetLastError();
 }

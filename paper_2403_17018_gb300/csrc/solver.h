@@ -28,6 +28,8 @@ struct MGLevel {
   double* dx = nullptr;
   double* ty = nullptr;
   double* dy = nullptr;
+  double* qx = nullptr;  // face fluxes of the linearisation point (east / right side)
+  double* qy = nullptr;  // (north faces)
 };
 
 // Build the multigrid hierarchy of an nx x ny grid: halve while nx is a
@@ -54,6 +56,8 @@ class Solver {
   int nt() const { return nt_; }
   int n_mg() const { return (int)levels_.size(); }
   unsigned long long launches() const;
+  // Copy an internal array (see henry_debug_copy); returns HENRY_* code.
+  int debug_copy(int mg_level, int what, void* dst, int64_t bytes) const;
 
  private:
   template <typename T> int run_t(const double* xi, const double* logk, int B, double* q,
