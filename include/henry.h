@@ -213,6 +213,19 @@ int henry_level_info(const henry_ctx* ctx, int level, int* nx, int* ny, int* nt,
 int henry_debug_copy(henry_ctx* ctx, int level, int role, int mg_level, int what, void* dst,
                      int64_t bytes);
 
+/* Kernel timing for roofline reports: replays one kernel of the solver that
+ * served `level` (role as in henry_debug_copy) on its current workspace,
+ * `reps` times between two CUDA events on `stream`, after one untimed
+ * launch; the solver must have run a solve of `batch` samples before.
+ * which: 0 red half-sweep of the block Gauss-Seidel smoother on the finest
+ * multigrid level; 1 the FP64 residual + Jacobian kernel of the finest level.
+ * Outputs the average duration of one launch [ms], its algorithmic DRAM
+ * bytes (every array read or written once) and its FP64 + FP32 floating
+ * point operations (FMA = 2). Synchronises the stream. The replay changes
+ * the workspace (not the caller's outputs). */
+int henry_time_kernel(henry_ctx* ctx, int level, int role, int which, int reps, void* stream,
+                      double* avg_ms, double* bytes, double* flops);
+
 /* Device kernel launches issued by this context since creation (counts
  * every launch, including those replayed inside CUDA graphs). */
 int64_t henry_launch_count(const henry_ctx* ctx);

@@ -87,6 +87,8 @@ def load():
                                  ctypes.POINTER(I)]),
         "henry_launch_count": (ctypes.c_int64, [P]),
         "henry_debug_copy": (I, [P, I, I, I, I, V, ctypes.c_int64]),
+        "henry_time_kernel": (I, [P, I, I, I, I, V, ctypes.POINTER(D), ctypes.POINTER(D),
+                                  ctypes.POINTER(D)]),
         "henry_strerror": (ctypes.c_char_p, [I]),
         "henry_last_error": (ctypes.c_char_p, []),
     }
@@ -181,6 +183,13 @@ class Context:
         _check(self.lib.henry_debug_copy(self._h, level, role, mg_level, what,
                                          buf.ctypes.data_as(ctypes.c_void_p), nbytes))
         return buf
+
+    def time_kernel(self, level, role, which, reps=20, stream=None):
+        """henry_time_kernel: (avg ms per launch, algorithmic bytes, flops)."""
+        ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(self.lib.henry_time_kernel(self._h, level, role, which, reps, _stream(stream),
+                                          ctypes.byref(ms), ctypes.byref(by), ctypes.byref(fl)))
+        return ms.value, by.value, fl.value
 
     def launch_count(self) -> int:
         return int(self.lib.henry_launch_count(self._h))

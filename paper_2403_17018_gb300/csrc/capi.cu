@@ -292,6 +292,19 @@ int henry_debug_copy(henry_ctx* ctx, int level, int role, int mg_level, int what
   return HENRY_OK;
 }
 
+int henry_time_kernel(henry_ctx* ctx, int level, int role, int which, int reps, void* stream,
+                      double* avg_ms, double* bytes, double* flops) {
+  if (!ctx || level < 0 || level >= ctx->cfg.nlevels || role < 0 || role > 1 || !avg_ms ||
+      !bytes || !flops)
+    return fail(HENRY_E_INVALID, "bad argument");
+  const auto& s = ctx->role[role][level];
+  if (!s) return fail(HENRY_E_INVALID, "no solver has run for this level and role");
+  CKR(cudaSetDevice(ctx->device));
+  int rc = s->time_kernel(which, reps, (cudaStream_t)stream, avg_ms, bytes, flops);
+  if (rc) return fail(rc, "time_kernel failed (which, reps or no previous solve)");
+  return HENRY_OK;
+}
+
 int64_t henry_launch_count(const henry_ctx* ctx) {
   if (!ctx) return -1;
   unsigned long long total = 0, v = 0;

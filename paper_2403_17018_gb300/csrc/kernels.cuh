@@ -339,107 +339,58 @@ __global__ void k_coarse_lu(unsigned long long* ctr, Geom G, int B, const int* _
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) L[e] = A[e / n][e % n];
 }
 
-// Solve with the stored LU, one warp per sample; rows spread over lanes.
-template <typename T>
-__global__ void k_coarse_solve(unsigned long long* ctr, Geom G, int B, const int* __restrict__ active,
-                               const double* __restrict__ LU, const int* __restrict__ piv,
-                               const T* __restrict__ bvec, T* __restrict__ xvec) {
-  HENRY_COUNT_LAUNCH(ctr);
-  __shared__ double ysh[kBlock / 32][kMaxCoarseUnknowns];
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  const int b = blockIdx.x * (blockDim.x >> 5) + w;
-  if (b >= B || !active[b]) return;
-  const int nc = G.ncell(), n = 2 * nc, half = G.half();
-  double* y = ysh[w];
-  const int64_t ob = (int64_t)b * 2 * nc;
-  for (int u = l; u < n; u += 32) {
-    const int cell = u >> 1, v = u & 1;
-    const int j = cell / G.nx, i = cell - j * G.nx;
-    y[u] = (double)bvec[ob + v * nc + cs_pos(i, j, G.nx, half)];
-  }
-  __syncwarp();
-  const int* pv = piv + (int64_t)b * kMaxCoarseUnknowns;
-  if (l == 0)
-    for (int k = 0; k < n; ++k) {
-      const int r = pv[k];
-      if (r != k) { const double t = y[k]; y[k] = y[r]; y[r] = t; }
-    }
-  __syncwarp();
-  const double* A = LU + (int64_t)b * kMaxCoarseUnknowns * kMaxCoarseUnknowns;
-  for (int k = 0; k < n; ++k) {  // forward, unit lower
-    const double yk = y[k];
-    __syncwarp();
-    for (int r = k + 1 + l; r < n; r += 32) y[r] -= A[r * n + k] * yk;
-    __syncwarp();
-  }
-  for (int k = n - 1; k >= 0; --k) {  // backward
-    if (l == 0) y[k] = y[k] / A[k * n + k];
-    __syncwarp();
-    const double yk = y[k];
-    for (int r = l; r < k; r += 32) y[r] -= A[r * n + k] * yk;
-    __syncwarp();
-  }
-  for (int u = l; u < n; u += 32) {
-    const int cell = u >> 1, v = u & 1;
-    const int j = cell / G.nx, i = cell - j * G.nx;
-    xvec[ob + v * nc + cs_pos(i, j, G.nx, half)] = (T)y[u];
-  }
-}
+// ---------------------------------------------------------------------------
+// multigrid building blocks on one sample's arrays (J: [20][ncell], b, x:
+// [2][ncell], colour-split planes). Used by the batched kernels below, with
+// global-memory bases, and by k_vcycle_small, with shared-memory copies.
+// ---------------------------------------------------------------------------
 
-// One red (colour 0) or black (colour 1) half-sweep of point-block
-// Gauss-Seidel: x_P = D_P^{-1} (b_P - sum_Q A_PQ x_Q), 2x2 blocks.
+// Point-block Gauss-Seidel update of the cell at colour-split position
+// `pos` of colour `colour`: x_P = D_P^{-1} (b_P - sum_Q A_PQ x_Q).
 template <typename T>
-__global__ void __launch_bounds__(kBlock)
-k_smooth(unsigned long long* ctr, Geom G, int B, int colour, const int* __restrict__ active,
-         const T* __restrict__ J, const T* __restrict__ bvec, T* __restrict__ xvec) {
-  HENRY_COUNT_LAUNCH(ctr);
+__device__ __forceinline__ void smooth_cell(const Geom& G, int colour, int pos,
+                                            const T* __restrict__ J, const T* __restrict__ b,
+                                            T* __restrict__ x) {
   const int half = G.half(), ncell = G.ncell(), hx2 = G.nx >> 1;
-  const int64_t n = (int64_t)B * half;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n) return;
-  const int b = (int)(idx / half);
-  if (!active[b]) return;
-  const int pos = (int)(idx - (int64_t)b * half);
   const int j = pos / hx2, k = pos - j * hx2;
   const int i = 2 * k + ((j + colour) & 1);
   const int own = colour * half + pos;
   const int oth = (1 - colour) * half;
-  const T* Jb = J + (int64_t)b * 20 * ncell + own;
-  const int64_t ob = (int64_t)b * 2 * ncell;
-  const T* xp = xvec + ob + oth;
-  const T* xc = xvec + ob + ncell + oth;
-  T rp = bvec[ob + own], rc = bvec[ob + ncell + own];
+  const T* Jb = J + own;
+  const T* xp = x + oth;
+  const T* xc = x + ncell + oth;
+  T rp = b[own], rc = b[ncell + own];
   if (i > 0) {
     const int q = j * hx2 + ((i - 1) >> 1);
     const T vp = xp[q], vc = xc[q];
-    rp -= Jb[4 * (int64_t)ncell] * vp + Jb[5 * (int64_t)ncell] * vc;
-    rc -= Jb[6 * (int64_t)ncell] * vp + Jb[7 * (int64_t)ncell] * vc;
+    rp -= Jb[4 * ncell] * vp + Jb[5 * ncell] * vc;
+    rc -= Jb[6 * ncell] * vp + Jb[7 * ncell] * vc;
   }
   if (i < G.nx - 1) {
     const int q = j * hx2 + ((i + 1) >> 1);
     const T vp = xp[q], vc = xc[q];
-    rp -= Jb[8 * (int64_t)ncell] * vp + Jb[9 * (int64_t)ncell] * vc;
-    rc -= Jb[10 * (int64_t)ncell] * vp + Jb[11 * (int64_t)ncell] * vc;
+    rp -= Jb[8 * ncell] * vp + Jb[9 * ncell] * vc;
+    rc -= Jb[10 * ncell] * vp + Jb[11 * ncell] * vc;
   }
   if (j > 0) {
     const int q = (j - 1) * hx2 + (i >> 1);
     const T vp = xp[q], vc = xc[q];
-    rp -= Jb[12 * (int64_t)ncell] * vp + Jb[13 * (int64_t)ncell] * vc;
-    rc -= Jb[14 * (int64_t)ncell] * vp + Jb[15 * (int64_t)ncell] * vc;
+    rp -= Jb[12 * ncell] * vp + Jb[13 * ncell] * vc;
+    rc -= Jb[14 * ncell] * vp + Jb[15 * ncell] * vc;
   }
   if (j < G.ny - 1) {
     const int q = (j + 1) * hx2 + (i >> 1);
     const T vp = xp[q], vc = xc[q];
-    rp -= Jb[16 * (int64_t)ncell] * vp + Jb[17 * (int64_t)ncell] * vc;
-    rc -= Jb[18 * (int64_t)ncell] * vp + Jb[19 * (int64_t)ncell] * vc;
+    rp -= Jb[16 * ncell] * vp + Jb[17 * ncell] * vc;
+    rc -= Jb[18 * ncell] * vp + Jb[19 * ncell] * vc;
   }
-  const T a = Jb[0], bb = Jb[(int64_t)ncell], cc = Jb[2 * (int64_t)ncell], d = Jb[3 * (int64_t)ncell];
+  const T a = Jb[0], bb = Jb[ncell], cc = Jb[2 * ncell], d = Jb[3 * ncell];
   const T inv = (T)1 / (a * d - bb * cc);
-  xvec[ob + own] = (d * rp - bb * rc) * inv;
-  xvec[ob + ncell + own] = (a * rc - cc * rp) * inv;
+  x[own] = (d * rp - bb * rc) * inv;
+  x[ncell + own] = (a * rc - cc * rp) * inv;
 }
 
-// A x at cell (i, j) of one sample, colour-split arrays.
+// A x at cell (i, j).
 template <typename T>
 __device__ __forceinline__ void apply_cell(const Geom& G, int i, int j, const T* __restrict__ Jb,
                                            const T* __restrict__ x, T& ap, T& ac) {
@@ -477,74 +428,260 @@ __device__ __forceinline__ void apply_cell(const Geom& G, int i, int j, const T*
   }
 }
 
-// r = b - A x on level k, summed over the four children of each coarse
-// cell (finite-volume restriction) into b_{k-1}; x_{k-1} = 0.
+// Coarse cell `cell` of level k-1: b_c = sum over the four children of
+// (b - A x) on level k (finite-volume restriction), x_c = 0.
+template <typename T>
+__device__ __forceinline__ void restrict_cell(const Geom& Gf, const Geom& Gc, int cell,
+                                              const T* __restrict__ Jf, const T* __restrict__ bf,
+                                              const T* __restrict__ xf, T* __restrict__ bc,
+                                              T* __restrict__ xc) {
+  const int J = cell / Gc.nx, I = cell - J * Gc.nx;
+  const int ncf = Gf.ncell(), hf = Gf.half(), ncc = Gc.ncell();
+  T sp = 0, sc = 0;
+#pragma unroll
+  for (int c4 = 0; c4 < 4; ++c4) {
+    const int i = 2 * I + (c4 & 1), j = 2 * J + (c4 >> 1);
+    T ap, ac;
+    apply_cell(Gf, i, j, Jf, xf, ap, ac);
+    const int cs = cs_pos(i, j, Gf.nx, hf);
+    sp += bf[cs] - ap;
+    sc += bf[ncf + cs] - ac;
+  }
+  const int csc = cs_pos(I, J, Gc.nx, Gc.half());
+  bc[csc] = sp;
+  bc[ncc + csc] = sc;
+  xc[csc] = (T)0;
+  xc[ncc + csc] = (T)0;
+}
+
+// Fine cell `cell` of level k: x_f += P x_c, cell-centred bilinear
+// interpolation (9/16, 3/16, 3/16, 1/16), constant extrapolation at the
+// domain boundary.
+template <typename T>
+__device__ __forceinline__ void prolong_cell(const Geom& Gc, const Geom& Gf, int cell,
+                                             const T* __restrict__ xc, T* __restrict__ xf) {
+  const int j = cell / Gf.nx, i = cell - j * Gf.nx;
+  const int I = i >> 1, J = j >> 1;
+  int I2 = I + ((i & 1) ? 1 : -1), J2 = J + ((j & 1) ? 1 : -1);
+  I2 = I2 < 0 ? 0 : (I2 >= Gc.nx ? Gc.nx - 1 : I2);
+  J2 = J2 < 0 ? 0 : (J2 >= Gc.ny ? Gc.ny - 1 : J2);
+  const int ncc = Gc.ncell(), hc = Gc.half(), ncf = Gf.ncell();
+  const int a0 = cs_pos(I, J, Gc.nx, hc), a1 = cs_pos(I2, J, Gc.nx, hc);
+  const int a2 = cs_pos(I, J2, Gc.nx, hc), a3 = cs_pos(I2, J2, Gc.nx, hc);
+  const T w0 = (T)0.5625, w1 = (T)0.1875, w3 = (T)0.0625;
+  const T vp = w0 * xc[a0] + w1 * (xc[a1] + xc[a2]) + w3 * xc[a3];
+  const T vc = w0 * xc[ncc + a0] + w1 * (xc[ncc + a1] + xc[ncc + a2]) + w3 * xc[ncc + a3];
+  const int cs = cs_pos(i, j, Gf.nx, Gf.half());
+  xf[cs] += vp;
+  xf[ncf + cs] += vc;
+}
+
+// Coarsest-grid solve with the stored LU factors (row-major n x n, pivots)
+// by one warp; y is an n-vector of scratch in shared memory.
+template <typename T>
+__device__ __forceinline__ void coarse_solve_warp(const Geom& G, const double* __restrict__ A,
+                                                  const int* __restrict__ pv,
+                                                  const T* __restrict__ b, T* __restrict__ x,
+                                                  double* y, int l) {
+  const int nc = G.ncell(), n = 2 * nc, half = G.half();
+  for (int u = l; u < n; u += 32) {
+    const int cell = u >> 1, v = u & 1;
+    const int j = cell / G.nx, i = cell - j * G.nx;
+    y[u] = (double)b[v * nc + cs_pos(i, j, G.nx, half)];
+  }
+  __syncwarp();
+  if (l == 0)
+    for (int k = 0; k < n; ++k) {
+      const int r = pv[k];
+      if (r != k) { const double t = y[k]; y[k] = y[r]; y[r] = t; }
+    }
+  __syncwarp();
+  for (int k = 0; k < n; ++k) {  // forward, unit lower
+    const double yk = y[k];
+    __syncwarp();
+    for (int r = k + 1 + l; r < n; r += 32) y[r] -= A[r * n + k] * yk;
+    __syncwarp();
+  }
+  for (int k = n - 1; k >= 0; --k) {  // backward
+    if (l == 0) y[k] = y[k] / A[k * n + k];
+    __syncwarp();
+    const double yk = y[k];
+    for (int r = l; r < k; r += 32) y[r] -= A[r * n + k] * yk;
+    __syncwarp();
+  }
+  for (int u = l; u < n; u += 32) {
+    const int cell = u >> 1, v = u & 1;
+    const int j = cell / G.nx, i = cell - j * G.nx;
+    x[v * nc + cs_pos(i, j, G.nx, half)] = (T)y[u];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// batched multigrid kernels (one thread per cell of all B samples)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_coarse_solve(unsigned long long* ctr, Geom G, int B, const int* __restrict__ active,
+                               const double* __restrict__ LU, const int* __restrict__ piv,
+                               const T* __restrict__ bvec, T* __restrict__ xvec) {
+  HENRY_COUNT_LAUNCH(ctr);
+  __shared__ double ysh[kBlock / 32][kMaxCoarseUnknowns];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int b = blockIdx.x * (blockDim.x >> 5) + w;
+  if (b >= B || !active[b]) return;
+  const int64_t ob = (int64_t)b * 2 * G.ncell();
+  coarse_solve_warp<T>(G, LU + (int64_t)b * kMaxCoarseUnknowns * kMaxCoarseUnknowns,
+                       piv + (int64_t)b * kMaxCoarseUnknowns, bvec + ob, xvec + ob, ysh[w], l);
+}
+
+// One red (colour 0) or black (colour 1) half-sweep of point-block
+// Gauss-Seidel on every sample.
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+k_smooth(unsigned long long* ctr, Geom G, int B, int colour, const int* __restrict__ active,
+         const T* __restrict__ J, const T* __restrict__ bvec, T* __restrict__ xvec) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int half = G.half(), ncell = G.ncell();
+  const int64_t n = (int64_t)B * half;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const int b = (int)(idx / half);
+  if (!active[b]) return;
+  const int pos = (int)(idx - (int64_t)b * half);
+  const int64_t ob = (int64_t)b * 2 * ncell;
+  smooth_cell<T>(G, colour, pos, J + (int64_t)b * 20 * ncell, bvec + ob, xvec + ob);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 k_resid_restrict(unsigned long long* ctr, Geom Gf, Geom Gc, int B, const int* __restrict__ active,
                  const T* __restrict__ Jf, const T* __restrict__ bf, const T* __restrict__ xf,
                  T* __restrict__ bc, T* __restrict__ xc) {
   HENRY_COUNT_LAUNCH(ctr);
-  const int ncc = Gc.ncell();
+  const int ncc = Gc.ncell(), ncf = Gf.ncell();
   const int64_t n = (int64_t)B * ncc;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n) return;
   const int b = (int)(idx / ncc);
   if (!active[b]) return;
   const int cell = (int)(idx - (int64_t)b * ncc);
-  const int J = cell / Gc.nx, I = cell - J * Gc.nx;
-  const int ncf = Gf.ncell(), hf = Gf.half();
-  const T* Jb = Jf + (int64_t)b * 20 * ncf;
-  const T* bb = bf + (int64_t)b * 2 * ncf;
-  const T* xb = xf + (int64_t)b * 2 * ncf;
-  T sp = 0, sc = 0;
-#pragma unroll
-  for (int c4 = 0; c4 < 4; ++c4) {
-    const int i = 2 * I + (c4 & 1), j = 2 * J + (c4 >> 1);
-    T ap, ac;
-    apply_cell(Gf, i, j, Jb, xb, ap, ac);
-    const int cs = cs_pos(i, j, Gf.nx, hf);
-    sp += bb[cs] - ap;
-    sc += bb[ncf + cs] - ac;
-  }
-  const int csc = cs_pos(I, J, Gc.nx, Gc.half());
-  const int64_t oc = (int64_t)b * 2 * ncc;
-  bc[oc + csc] = sp;
-  bc[oc + ncc + csc] = sc;
-  xc[oc + csc] = (T)0;
-  xc[oc + ncc + csc] = (T)0;
+  restrict_cell<T>(Gf, Gc, cell, Jf + (int64_t)b * 20 * ncf, bf + (int64_t)b * 2 * ncf,
+                   xf + (int64_t)b * 2 * ncf, bc + (int64_t)b * 2 * ncc, xc + (int64_t)b * 2 * ncc);
 }
 
-// x_k += P x_{k-1}: cell-centred bilinear interpolation (weights 9/16,
-// 3/16, 3/16, 1/16), constant extrapolation at the domain boundary.
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 k_prolong(unsigned long long* ctr, Geom Gc, Geom Gf, int B, const int* __restrict__ active,
           const T* __restrict__ xc, T* __restrict__ xf) {
   HENRY_COUNT_LAUNCH(ctr);
-  const int ncf = Gf.ncell();
+  const int ncf = Gf.ncell(), ncc = Gc.ncell();
   const int64_t n = (int64_t)B * ncf;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n) return;
   const int b = (int)(idx / ncf);
   if (!active[b]) return;
   const int cell = (int)(idx - (int64_t)b * ncf);
-  const int j = cell / Gf.nx, i = cell - j * Gf.nx;
-  const int I = i >> 1, J = j >> 1;
-  int I2 = I + ((i & 1) ? 1 : -1), J2 = J + ((j & 1) ? 1 : -1);
-  I2 = I2 < 0 ? 0 : (I2 >= Gc.nx ? Gc.nx - 1 : I2);
-  J2 = J2 < 0 ? 0 : (J2 >= Gc.ny ? Gc.ny - 1 : J2);
-  const int ncc = Gc.ncell(), hc = Gc.half();
-  const T* xb = xc + (int64_t)b * 2 * ncc;
-  const int a0 = cs_pos(I, J, Gc.nx, hc), a1 = cs_pos(I2, J, Gc.nx, hc);
-  const int a2 = cs_pos(I, J2, Gc.nx, hc), a3 = cs_pos(I2, J2, Gc.nx, hc);
-  const T w0 = (T)0.5625, w1 = (T)0.1875, w3 = (T)0.0625;
-  const T vp = w0 * xb[a0] + w1 * (xb[a1] + xb[a2]) + w3 * xb[a3];
-  const T vc = w0 * xb[ncc + a0] + w1 * (xb[ncc + a1] + xb[ncc + a2]) + w3 * xb[ncc + a3];
-  const int cs = cs_pos(i, j, Gf.nx, Gf.half());
-  T* xo = xf + (int64_t)b * 2 * ncf;
-  xo[cs] += vp;
-  xo[ncf + cs] += vc;
+  prolong_cell<T>(Gc, Gf, cell, xc + (int64_t)b * 2 * ncc, xf + (int64_t)b * 2 * ncf);
+}
+
+// ---------------------------------------------------------------------------
+// fused V-cycles on the small multigrid levels 0..ks (at most kSmallCells
+// cells per sample on level ks): one block per sample; J, b and x of these
+// levels and the coarsest LU factors are staged in shared memory and every
+// phase of the cycle is separated by __syncthreads(). Level ks takes b from
+// and returns x to global memory (x_ks is read as the initial guess).
+// ---------------------------------------------------------------------------
+constexpr int kSmallCells = 512;
+constexpr int kMaxLevels = 12;
+
+template <typename T>
+struct SmallMG {
+  int ks;                           // top small level
+  Geom g[kMaxLevels];
+  T* J[kMaxLevels];                 // global bases (sample 0)
+  T* b[kMaxLevels];
+  T* x[kMaxLevels];
+};
+
+template <typename T>
+__host__ __device__ inline size_t small_smem_bytes(const SmallMG<T>& M) {
+  size_t cells = 0;
+  for (int k = 0; k <= M.ks; ++k) cells += (size_t)M.g[k].ncell();
+  const int n = 2 * M.g[0].ncell();
+  return cells * 24 * sizeof(T) + (size_t)n * n * sizeof(double) + n * sizeof(double) +
+         n * sizeof(int) + 64;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+k_vcycle_small(unsigned long long* ctr, SmallMG<T> M, int B, const int* __restrict__ active,
+               const double* __restrict__ LU, const int* __restrict__ piv, int nu1, int nu2,
+               int ncycles) {
+  HENRY_COUNT_LAUNCH(ctr);
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int bs = blockIdx.x;
+  if (!active[bs]) return;
+  const int ks = M.ks;
+  T* J[kMaxLevels];
+  T* bv[kMaxLevels];
+  T* xv[kMaxLevels];
+  T* p = (T*)smem;
+  for (int k = 0; k <= ks; ++k) {
+    const int nc = M.g[k].ncell();
+    J[k] = p; p += 20 * nc;
+    bv[k] = p; p += 2 * nc;
+    xv[k] = p; p += 2 * nc;
+  }
+  const int n = 2 * M.g[0].ncell();
+  double* A = (double*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+  double* y = A + n * n;
+  int* pv = (int*)(y + n);
+  // stage J of all small levels, b and x of the top one, the LU factors
+  for (int k = 0; k <= ks; ++k) {
+    const int nc = M.g[k].ncell();
+    const T* src = M.J[k] + (int64_t)bs * 20 * nc;
+    for (int e = threadIdx.x; e < 20 * nc; e += blockDim.x) J[k][e] = src[e];
+  }
+  {
+    const int nc = M.g[ks].ncell();
+    const T* sb = M.b[ks] + (int64_t)bs * 2 * nc;
+    const T* sx = M.x[ks] + (int64_t)bs * 2 * nc;
+    for (int e = threadIdx.x; e < 2 * nc; e += blockDim.x) { bv[ks][e] = sb[e]; xv[ks][e] = sx[e]; }
+  }
+  const double* Ag = LU + (int64_t)bs * kMaxCoarseUnknowns * kMaxCoarseUnknowns;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = Ag[e];
+  for (int e = threadIdx.x; e < n; e += blockDim.x) pv[e] = piv[(int64_t)bs * kMaxCoarseUnknowns + e];
+  __syncthreads();
+  for (int cyc = 0; cyc < ncycles; ++cyc) {
+    for (int k = ks; k >= 1; --k) {
+      const Geom& G = M.g[k];
+      for (int s = 0; s < nu1; ++s)
+        for (int col = 0; col < 2; ++col) {
+          for (int pos = threadIdx.x; pos < G.half(); pos += blockDim.x)
+            smooth_cell<T>(G, col, pos, J[k], bv[k], xv[k]);
+          __syncthreads();
+        }
+      for (int cell = threadIdx.x; cell < M.g[k - 1].ncell(); cell += blockDim.x)
+        restrict_cell<T>(G, M.g[k - 1], cell, J[k], bv[k], xv[k], bv[k - 1], xv[k - 1]);
+      __syncthreads();
+    }
+    if (threadIdx.x < 32) coarse_solve_warp<T>(M.g[0], A, pv, bv[0], xv[0], y, threadIdx.x);
+    __syncthreads();
+    for (int k = 1; k <= ks; ++k) {
+      const Geom& G = M.g[k];
+      for (int cell = threadIdx.x; cell < G.ncell(); cell += blockDim.x)
+        prolong_cell<T>(M.g[k - 1], G, cell, xv[k - 1], xv[k]);
+      __syncthreads();
+      for (int s = 0; s < nu2; ++s)
+        for (int col = 0; col < 2; ++col) {
+          for (int pos = threadIdx.x; pos < G.half(); pos += blockDim.x)
+            smooth_cell<T>(G, col, pos, J[k], bv[k], xv[k]);
+          __syncthreads();
+        }
+    }
+  }
+  const int nc = M.g[ks].ncell();
+  T* dx = M.x[ks] + (int64_t)bs * 2 * nc;
+  for (int e = threadIdx.x; e < 2 * nc; e += blockDim.x) dx[e] = xv[ks][e];
 }
 
 // Defect-correction update of the FP64 state: u += x (finest level).

@@ -109,6 +109,9 @@ Solver::Solver(const henry_config& cfg, int nx, int ny, int nt) : cfg_(cfg), nt_
   levels_.resize(geoms_.size());
   for (size_t k = 0; k < geoms_.size(); ++k) levels_[k].g = geoms_[k];
   nchunk_ = (geoms_.back().ncell() + kBlock - 1) / kBlock;
+  ks_ = 0;
+  for (size_t k = 0; k < geoms_.size(); ++k)
+    if (geoms_[k].ncell() <= kSmallCells) ks_ = (int)k;
 }
 
 Solver::~Solver() { free_all(); }
@@ -228,9 +231,32 @@ int Solver::ensure(int B, cudaStream_t s) {
 }
 
 template <typename T>
+void Solver::launch_small(int B, int ncycles, cudaStream_t s) {
+  SmallMG<T> M;
+  M.ks = ks_;
+  for (int k = 0; k <= ks_; ++k) {
+    M.g[k] = levels_[k].g;
+    M.J[k] = (T*)levels_[k].J;
+    M.b[k] = (T*)levels_[k].b;
+    M.x[k] = (T*)levels_[k].x;
+  }
+  const size_t smem = small_smem_bytes(M);
+  if (smem != small_smem_) {
+    cudaFuncSetAttribute(k_vcycle_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    small_smem_ = smem;
+  }
+  k_vcycle_small<T><<<B, kBlock, smem, s>>>(counter_, M, B, active_, lu_, piv_, cfg_.nu1, cfg_.nu2,
+                                            ncycles);
+}
+
+template <typename T>
 void Solver::enqueue_vcycle(int k, int B, cudaStream_t s) {
   MGLevel& L = levels_[k];
   const Geom& G = L.g;
+  if (k == ks_ && k > 0) {
+    launch_small<T>(B, 1, s);
+    return;
+  }
   if (k == 0) {
     k_coarse_solve<T><<<(B + 7) / 8, kBlock, 0, s>>>(counter_, G, B, active_, lu_, piv_,
                                                      (const T*)L.b, (T*)L.x);
@@ -269,7 +295,10 @@ void Solver::enqueue_iteration(int B, cudaStream_t s) {
   }
   k_coarse_lu<T><<<B, 64, 0, s>>>(counter_, levels_[0].g, B, active_, (const T*)levels_[0].J,
                                   lu_, piv_);
-  for (int v = 0; v < cfg_.vcycles; ++v) enqueue_vcycle<T>(nl - 1, B, s);
+  if (ks_ == nl - 1 && nl > 1)
+    launch_small<T>(B, cfg_.vcycles, s);
+  else
+    for (int v = 0; v < cfg_.vcycles; ++v) enqueue_vcycle<T>(nl - 1, B, s);
   MGLevel& F = levels_.back();
   k_update<T><<<grid1((int64_t)B * F.g.ncell()), kBlock, 0, s>>>(counter_, F.g, B, active_,
                                                                  (const T*)F.x, F.p, F.c);
@@ -402,11 +431,72 @@ int Solver::run_t(const double* xi, const double* logk, int B, double* q, double
   return HENRY_OK;
 }
 
+template <typename T>
+void Solver::launch_timed(int which, int B, cudaStream_t s) {
+  MGLevel& F = levels_.back();
+  if (which == 0) {
+    k_smooth<T><<<grid1((int64_t)B * F.g.half()), kBlock, 0, s>>>(
+        counter_, F.g, B, 0, active_, (const T*)F.J, (const T*)F.b, (T*)F.x);
+  } else {
+    k_resjac<T><<<dim3(nchunk_, B), kBlock, 0, s>>>(counter_, phys_, F.g, tau_, B, F.p, F.c, c_old_,
+                                                    F.phi, F.K, F.tx, F.dx, F.ty, F.dy, qin_,
+                                                    active_, (T*)F.J, (T*)F.b, (T*)F.x, partial_,
+                                                    F.qx, F.qy);
+  }
+}
+
+// Algorithmic counts per launch (each array read or written once):
+//  smoother half-sweep, per updated cell: J 20, b 2, x write 2, neighbour x
+//    read 2 values of the type T; FP ops: 16 neighbour products (FMA) + 2x2
+//    solve (6 mul/sub + 1 rcp + 4 mul) = 32 + 2 + 11 ~ 45 FLOP.
+//  residual + Jacobian, per cell: p, c, c_old, phi, tx, dx, ty, dy read (8
+//    doubles), b 2, x 2, J 20 of type T and qx, qy (2 doubles) written;
+//    FP ops counted from the code: 4 faces x (flux 14 + Jacobian 34) +
+//    accumulation and scatter 30 ~ 220 FLOP.
+int Solver::time_kernel(int which, int reps, cudaStream_t s, double* avg_ms, double* bytes,
+                        double* flops) {
+  if (which < 0 || which > 1 || reps < 1 || last_B_ < 1) return HENRY_E_INVALID;
+  const int B = last_B_;
+  // all samples active for the replay
+  std::vector<int> ones(B, 1);
+  CK(cudaMemcpyAsync(active_, ones.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
+  auto launch = [&]() {
+    if (tsize_ == sizeof(float)) launch_timed<float>(which, B, s);
+    else launch_timed<double>(which, B, s);
+  };
+  launch();
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s));
+  for (int r = 0; r < reps; ++r) launch();
+  CK(cudaEventRecord(e1, s));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const Geom& G = levels_.back().g;
+  const double T = (double)tsize_;
+  if (which == 0) {
+    const double cells = (double)B * G.half();
+    *bytes = cells * 26.0 * T;
+    *flops = cells * 45.0;
+  } else {
+    const double cells = (double)B * G.ncell();
+    *bytes = cells * (8.0 * 8 + 24.0 * T + 16.0);
+    *flops = cells * 220.0;
+  }
+  *avg_ms = ms / reps;
+  return HENRY_OK;
+}
+
 int Solver::run(const double* xi, const double* logk, int B, double* q, double* c_out,
                 double* p_out, int* status, int* iters, int status_or, cudaStream_t s) {
   if (B == 0) return HENRY_OK;
   int rc = ensure(B, s);
   if (rc) return rc;
+  last_B_ = B;
   if (tsize_ == sizeof(float))
     return run_t<float>(xi, logk, B, q, c_out, p_out, status, iters, status_or, s);
   return run_t<double>(xi, logk, B, q, c_out, p_out, status, iters, status_or, s);

@@ -56,6 +56,10 @@ class Solver {
   int nt() const { return nt_; }
   int n_mg() const { return (int)levels_.size(); }
   unsigned long long launches() const;
+  // Time one kernel of the finest level (see henry_time_kernel).
+  int time_kernel(int which, int reps, cudaStream_t s, double* avg_ms, double* bytes,
+                  double* flops);
+  int batch() const { return last_B_; }
   // Copy an internal array (see henry_debug_copy); returns HENRY_* code.
   int debug_copy(int mg_level, int what, void* dst, int64_t bytes) const;
 
@@ -67,6 +71,8 @@ class Solver {
   template <typename T> void enqueue_vcycle(int k, int B, cudaStream_t s);
   template <typename T> void enqueue_resjac_check(int B, cudaStream_t s, bool set_cond);
   template <typename T> int step_graph(int B, cudaStream_t s);
+  template <typename T> void launch_timed(int which, int B, cudaStream_t s);
+  template <typename T> void launch_small(int B, int ncycles, cudaStream_t s);
   int ensure(int B, cudaStream_t s);
   void free_all();
 
@@ -78,6 +84,7 @@ class Solver {
   std::vector<Geom> geoms_;   // 0 = coarsest
   std::vector<MGLevel> levels_;
   int cap_ = 0;               // allocated batch capacity
+  int last_B_ = 0;            // batch of the last solve
   void* arena_ = nullptr;
   // finest-level / per-sample arrays
   double* c_old_ = nullptr;
@@ -95,6 +102,8 @@ class Solver {
   int* n_active_host_ = nullptr;  // pinned
   unsigned long long* counter_ = nullptr;  // device launch counter
   int nchunk_ = 0;
+  int ks_ = 0;                // top multigrid level handled by k_vcycle_small
+  size_t small_smem_ = 0;     // its dynamic shared memory per block
   // CUDA graph of one time step (HENRY_LOOP_GRAPH), rebuilt when B changes
   cudaGraphExec_t step_exec_ = nullptr;
   cudaGraph_t step_graph_ = nullptr;
