@@ -33,4 +33,21 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return s;
 }
 
+// Tiling of the face-based residual kernel (see k_resjac).
+struct ResTile {
+  int TX, GR, R;    // columns per tile, row groups per block, rows per thread
+  int ntx, nty;     // tiles per sample in x and y
+};
+
+__host__ inline ResTile make_res_tile(int nx, int ny) {
+  ResTile t;
+  t.TX = nx < kBlock ? nx : kBlock;
+  t.GR = kBlock / t.TX;
+  int rows = (ny + t.GR - 1) / t.GR;        // rows per thread if one tile covered all
+  t.R = rows < 8 ? rows : 8;
+  t.ntx = (nx + t.TX - 1) / t.TX;
+  t.nty = (ny + t.GR * t.R - 1) / (t.GR * t.R);
+  return t;
+}
+
 }  // namespace henry

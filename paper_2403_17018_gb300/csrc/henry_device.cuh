@@ -99,6 +99,29 @@ __device__ __forceinline__ void face_flux(const Phys& P, double pL, double cL, d
   }
 }
 
+// Right side (x = Lx, outward +x): flux from P to the seawater boundary and
+// its derivatives with respect to (p_P, c_P). tR = 2 A K_P / (mu hx),
+// dco = 2 A phi_P D / hx, pb = reduced Dirichlet pressure.
+template <typename JT, bool WANT_J, bool Q_GIVEN>
+__device__ __forceinline__ void right_face(const Phys& P, double p, double c, double tR, double dco,
+                                           double pb, double& q, double& Fm, double& Fs, JT* jd) {
+  const double rho = P.rho0 + P.drho * c;
+  const double rho1 = P.rho0 + P.drho;
+  if (!Q_GIVEN) q = -tR * (pb - p);
+  const bool up = q >= 0.0;
+  const double rup = up ? rho : rho1;
+  const double rcup = up ? rho * c : rho1;
+  const double rb = 0.5 * (rho + rho1);
+  Fm = q * rup;
+  Fs = q * rcup - dco * rb * (1.0 - c);
+  if (WANT_J) {
+    jd[0] = (JT)(tR * rup);
+    jd[1] = (JT)(up ? q * P.drho : 0.0);
+    jd[2] = (JT)(tR * rcup);
+    jd[3] = (JT)((up ? q * (rho + P.drho * c) : 0.0) - dco * 0.5 * P.drho * (1.0 - c) + dco * rb);
+  }
+}
+
 // Inputs of one cell's residual/Jacobian evaluation, gathered by the caller.
 struct CellIn {
   double p, c, c_old, phi, K;       // own values (K used on the right side only)

@@ -124,12 +124,22 @@ __global__ void k_begin_step(unsigned long long* ctr, Geom G, int B, const doubl
   }
 }
 
-// FP64 residual of the finest grid and its Jacobian in the multigrid type T.
-// Writes b = -R and x = 0 (colour-split), J (colour-split planes), and one
-// partial sum of R_p^2 + R_c^2 per block. grid = (chunks per sample, B).
-template <typename T>
+// FP64 residual of the finest grid and its Jacobian in the multigrid type T,
+// face by face. Tiling: a block covers TX columns x (GR * R) rows of one
+// sample; thread t takes column t % TX and walks R rows of row group t / TX.
+// Per cell the thread evaluates its east and north faces only: the west
+// face comes from the left neighbour thread through shared memory (or is
+// evaluated again at a tile edge) and the south face is the north face of
+// the previous row, kept in registers (evaluated once per column at the
+// bottom of a row group). Each face is evaluated with the canonical
+// orientation, so both cells see bitwise the same flux.
+// MG layout (NATURAL = false): writes b = -R, x = 0, J (colour-split), the
+// face fluxes qx (east / right side) and qy (north), one partial sum of
+// R_p^2 + R_c^2 per block. NATURAL = true: writes R [B][2][ncell] and J
+// [B][20][ncell] in natural cell order (FP64), for tests.
+template <typename T, bool NATURAL>
 __global__ void __launch_bounds__(kBlock)
-k_resjac(unsigned long long* ctr, Phys P, Geom G, double tau, int B,
+k_resjac(unsigned long long* ctr, Phys P, Geom G, double tau, int B, ResTile tl,
          const double* __restrict__ p, const double* __restrict__ c,
          const double* __restrict__ c_old, const double* __restrict__ phi,
          const double* __restrict__ K, const double* __restrict__ tx,
@@ -139,57 +149,186 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double tau, int B,
          T* __restrict__ xvec, double* __restrict__ partial, double* __restrict__ qx,
          double* __restrict__ qy) {
   HENRY_COUNT_LAUNCH(ctr);
-  __shared__ double sh[kBlock / 32];
+  __shared__ double shF[2][kBlock];
+  __shared__ T shD[8][kBlock];
+  __shared__ double shr[kBlock / 32];
   const int b = blockIdx.y;
-  if (!active[b]) return;
-  const int ncell = G.ncell(), half = G.half();
-  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!NATURAL && !active[b]) return;
+  const int nx = G.nx, ny = G.ny, ncell = G.ncell(), half = G.half();
+  const int t = threadIdx.x;
+  const int col = t % tl.TX, rg = t / tl.TX;
+  const int bx = blockIdx.x % tl.ntx, by = blockIdx.x / tl.ntx;
+  const int i = bx * tl.TX + col;
+  const int j0 = by * tl.GR * tl.R + rg * tl.R;
+  const bool thr = rg < tl.GR && i < nx;
+  const int64_t o = (int64_t)b * ncell;
+  const double* pb_ = p + o;
+  const double* cb_ = c + o;
+  const double V = G.hx * G.hy;
+  const double gdy = P.g * G.hy;
+  const double A = G.hy;
+  const double dcoL = 2.0 * A * P.D / G.hx;      // times phi_P
+  const double tRf = 2.0 * A / (P.mu * G.hx);    // times K_P
   double v = 0.0;
-  if (cell < ncell) {
-    const int j = cell / G.nx, i = cell - j * G.nx;
-    const int64_t o = (int64_t)b * ncell;
-    CellIn in;
-    gather_cell(G, i, j, p + o, c + o, phi + o, K + o, tx + o, dx + o, ty + o, dy + o, in);
-    in.c_old = c_old[o + cell];
-    in.qin = qin[(int64_t)b * G.ny + j];
-    double Rp, Rc;
-    T Jc[20];
-    cell_residual<T, true>(P, G, tau, in, Rp, Rc, Jc);
-    const int cs = cs_pos(i, j, G.nx, half);
-    const int64_t ob = (int64_t)b * 2 * ncell;
-    bvec[ob + cs] = (T)(-Rp);
-    bvec[ob + ncell + cs] = (T)(-Rc);
-    xvec[ob + cs] = (T)0;
-    xvec[ob + ncell + cs] = (T)0;
-    T* Jb = J + (int64_t)b * 20 * ncell + cs;
-#pragma unroll
-    for (int m = 0; m < 20; ++m) Jb[(int64_t)m * ncell] = Jc[m];
-    qx[o + cell] = in.qE;
-    qy[o + cell] = in.hasN ? in.qN : 0.0;
-    v = Rp * Rp + Rc * Rc;
+  // south face of the first row (halo), as L = S, U = P
+  double FmS = 0.0, FsS = 0.0;
+  FaceD<T> dS;
+  double pP = 0.0, cP = 0.0;
+  if (thr && j0 < ny) {
+    pP = pb_[j0 * nx + i];
+    cP = cb_[j0 * nx + i];
+    if (j0 > 0) {
+      const int id = (j0 - 1) * nx + i;
+      double q;
+      face_flux<T, true, false>(P, pb_[id], cb_[id], pP, cP, ty[o + id], dy[o + id], gdy, q, FmS,
+                                FsS, dS);
+    }
   }
-  const double s = block_sum(v, sh);
-  if (threadIdx.x == 0) partial[(int64_t)b * gridDim.x + blockIdx.x] = s;
+  for (int r = 0; r < tl.R; ++r) {
+    const int j = j0 + r;
+    const bool cv = thr && j < ny;
+    const int id = j * nx + i;
+    double FmE = 0.0, FsE = 0.0, qE = 0.0;
+    FaceD<T> dE;
+    T dR[4];   // right side derivatives (dF/du_P)
+    double phiP = 0.0, pN = 0.0, cN = 0.0;
+    if (cv) {
+      phiP = phi[o + id];
+      if (i < nx - 1) {
+        face_flux<T, true, false>(P, pP, cP, pb_[id + 1], cb_[id + 1], tx[o + id], dx[o + id], 0.0,
+                                  qE, FmE, FsE, dE);
+      } else {
+        const double pbd = P.drho * P.g * (P.Ly - (j + 0.5) * G.hy);
+        right_face<T, true, false>(P, pP, cP, tRf * K[o + id], dcoL * phiP, pbd, qE, FmE, FsE, dR);
+      }
+      shF[0][t] = FmE;
+      shF[1][t] = FsE;
+      shD[0][t] = dE.mLp; shD[1][t] = dE.mLc; shD[2][t] = dE.mUp; shD[3][t] = dE.mUc;
+      shD[4][t] = dE.sLp; shD[5][t] = dE.sLc; shD[6][t] = dE.sUp; shD[7][t] = dE.sUc;
+    }
+    __syncthreads();
+    if (cv) {
+      // west face (L = W, U = P)
+      double FmW = 0.0, FsW = 0.0;
+      FaceD<T> dW;
+      if (i > 0) {
+        if (col > 0) {
+          FmW = shF[0][t - 1];
+          FsW = shF[1][t - 1];
+          dW.mLp = shD[0][t - 1]; dW.mLc = shD[1][t - 1]; dW.mUp = shD[2][t - 1]; dW.mUc = shD[3][t - 1];
+          dW.sLp = shD[4][t - 1]; dW.sLc = shD[5][t - 1]; dW.sUp = shD[6][t - 1]; dW.sUc = shD[7][t - 1];
+        } else {
+          double q;
+          face_flux<T, true, false>(P, pb_[id - 1], cb_[id - 1], pP, cP, tx[o + id - 1],
+                                    dx[o + id - 1], 0.0, q, FmW, FsW, dW);
+        }
+      }
+      // north face (L = P, U = N)
+      double FmN = 0.0, FsN = 0.0, qN = 0.0;
+      FaceD<T> dN;
+      if (j < ny - 1) {
+        pN = pb_[id + nx];
+        cN = cb_[id + nx];
+        face_flux<T, true, false>(P, pP, cP, pN, cN, ty[o + id], dy[o + id], gdy, qN, FmN, FsN, dN);
+      }
+      // accumulation
+      const double vt = V * phiP / tau;
+      const double rho = P.rho0 + P.drho * cP;
+      const double cO = c_old[o + id];
+      const double rho_o = P.rho0 + P.drho * cO;
+      double Rp = vt * (rho - rho_o) + FmE + FmN - FmW - FmS;
+      double Rc = vt * (rho * cP - rho_o * cO) + FsE + FsN - FsW - FsS;
+      T Jc[20];
+#pragma unroll
+      for (int m = 0; m < 20; ++m) Jc[m] = (T)0;
+      Jc[1] = (T)(vt * P.drho);
+      Jc[3] = (T)(vt * (rho + P.drho * cP));
+      if (i > 0) {
+        Jc[0] -= dW.mUp; Jc[1] -= dW.mUc; Jc[2] -= dW.sUp; Jc[3] -= dW.sUc;
+        Jc[4] = -dW.mLp; Jc[5] = -dW.mLc; Jc[6] = -dW.sLp; Jc[7] = -dW.sLc;
+      } else {
+        // left side: fixed freshwater inflow, diffusion to c = 0 at hx/2
+        const double dco = dcoL * phiP;
+        const double rb = 0.5 * (rho + P.rho0);
+        Rp += -A * P.rho0 * qin[(int64_t)b * ny + j];
+        Rc += dco * rb * cP;
+        Jc[3] += (T)(dco * (0.5 * P.drho * cP + rb));
+      }
+      if (i < nx - 1) {
+        Jc[0] += dE.mLp; Jc[1] += dE.mLc; Jc[2] += dE.sLp; Jc[3] += dE.sLc;
+        Jc[8] = dE.mUp; Jc[9] = dE.mUc; Jc[10] = dE.sUp; Jc[11] = dE.sUc;
+      } else {
+        Jc[0] += dR[0]; Jc[1] += dR[1]; Jc[2] += dR[2]; Jc[3] += dR[3];
+      }
+      if (j > 0) {
+        Jc[0] -= dS.mUp; Jc[1] -= dS.mUc; Jc[2] -= dS.sUp; Jc[3] -= dS.sUc;
+        Jc[12] = -dS.mLp; Jc[13] = -dS.mLc; Jc[14] = -dS.sLp; Jc[15] = -dS.sLc;
+      }
+      if (j < ny - 1) {
+        Jc[0] += dN.mLp; Jc[1] += dN.mLc; Jc[2] += dN.sLp; Jc[3] += dN.sLc;
+        Jc[16] = dN.mUp; Jc[17] = dN.mUc; Jc[18] = dN.sUp; Jc[19] = dN.sUc;
+      }
+      if (NATURAL) {
+        double* Rn = (double*)bvec + (int64_t)b * 2 * ncell;
+        Rn[id] = Rp;
+        Rn[ncell + id] = Rc;
+        if (J) {
+          T* Jn = J + (int64_t)b * 20 * ncell + id;
+#pragma unroll
+          for (int m = 0; m < 20; ++m) Jn[(int64_t)m * ncell] = Jc[m];
+        }
+      } else {
+        const int cs = cs_pos(i, j, nx, half);
+        const int64_t ob = (int64_t)b * 2 * ncell;
+        bvec[ob + cs] = (T)(-Rp);
+        bvec[ob + ncell + cs] = (T)(-Rc);
+        xvec[ob + cs] = (T)0;
+        xvec[ob + ncell + cs] = (T)0;
+        T* Jb = J + (int64_t)b * 20 * ncell + cs;
+#pragma unroll
+        for (int m = 0; m < 20; ++m) Jb[(int64_t)m * ncell] = Jc[m];
+        qx[o + id] = qE;
+        qy[o + id] = qN;
+      }
+      v += Rp * Rp + Rc * Rc;
+      // the north face is the next row's south face
+      FmS = FmN;
+      FsS = FsN;
+      dS = dN;
+      pP = pN;
+      cP = cN;
+    }
+    __syncthreads();
+  }
+  if (!NATURAL) {
+    const double s = block_sum(v, shr);
+    if (threadIdx.x == 0) partial[(int64_t)b * gridDim.x + blockIdx.x] = s;
+  }
 }
 
-// Per-sample convergence decision after k_resjac. One block; warp w handles
-// samples w, w + nwarps, ... Sums the partials in a fixed order, scales the
-// RMS residual to units of c per step, updates active / status / counters
-// and the number of still-active samples.
+// Per-sample convergence decision after k_resjac, one warp per sample:
+// sums the sample's partials in a fixed order, scales the RMS residual to
+// units of c per step, updates active / status / counters. Blocks add their
+// count of still-active samples to acc[0]; the last block to finish
+// (acc[1] counts finished blocks) publishes the total to *n_active, resets
+// acc for the next launch and, when SET_COND, sets the while-loop condition
+// of the enclosing CUDA graph.
+template <bool SET_COND>
 __global__ void k_check(unsigned long long* ctr, int B, int nchunk, int ncell,
                         const double* __restrict__ partial, double scale, double rtol,
                         double atol, int maxit, int* __restrict__ active,
                         int* __restrict__ it_step, double* __restrict__ res0,
                         double* __restrict__ res_last, int* __restrict__ status,
-                        int* __restrict__ iters, int* __restrict__ n_active) {
+                        int* __restrict__ iters, int* __restrict__ n_active,
+                        unsigned int* __restrict__ acc, cudaGraphConditionalHandle h) {
   HENRY_COUNT_LAUNCH(ctr);
   __shared__ int cnt;
+  __shared__ bool last;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-  int mine = 0;
-  for (int b = w; b < B; b += nw) {
-    if (!active[b]) continue;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int b = blockIdx.x * (blockDim.x >> 5) + w;
+  if (b < B && active[b]) {
     double s = 0.0;
     for (int k = l; k < nchunk; k += 32) s += partial[(int64_t)b * nchunk + k];
 #pragma unroll
@@ -210,13 +349,24 @@ __global__ void k_check(unsigned long long* ctr, int B, int nchunk, int ncell,
       } else {
         it_step[b] = it + 1;
         iters[b] += 1;
-        ++mine;
+        atomicAdd(&cnt, 1);
       }
     }
   }
-  if (l == 0 && mine) atomicAdd(&cnt, mine);
   __syncthreads();
-  if (threadIdx.x == 0) *n_active = cnt;
+  if (threadIdx.x == 0) {
+    if (cnt) atomicAdd(&acc[0], (unsigned int)cnt);
+    __threadfence();
+    last = atomicAdd(&acc[1], 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int total = atomicExch(&acc[0], 0u);
+    acc[1] = 0u;
+    *n_active = (int)total;
+    if (SET_COND) cudaGraphSetConditional(h, total > 0 ? 1u : 0u);
+  }
 }
 
 // Linearisation point of level k-1 from level k: c averaged over the four
@@ -280,22 +430,24 @@ k_jac(unsigned long long* ctr, Phys P, Geom G, double tau, int B, const int* __r
   for (int m = 0; m < 20; ++m) Jb[(int64_t)m * ncell] = Jc[m];
 }
 
-// Dense LU with partial pivoting of the coarsest system, one block per
-// sample (Gaussian elimination, section 2.3). Unknown order 2*cell + var,
-// cell natural. Computed in FP64 whatever T is.
+// Dense LU with partial pivoting of the coarsest system (Gaussian
+// elimination, section 2.3), one warp per sample, rows spread over lanes.
+// Unknown order 2*cell + var, cell natural. FP64 whatever T is. Shared
+// memory: warps_per_block * n * (n + 1) doubles (dynamic).
 template <typename T>
 __global__ void k_coarse_lu(unsigned long long* ctr, Geom G, int B, const int* __restrict__ active,
                             const T* __restrict__ J, double* __restrict__ LU, int* __restrict__ piv) {
   HENRY_COUNT_LAUNCH(ctr);
-  __shared__ double A[kMaxCoarseUnknowns][kMaxCoarseUnknowns + 1];
-  __shared__ int pr;
-  const int b = blockIdx.x;
-  if (!active[b]) return;
-  const int nc = G.ncell(), n = 2 * nc, half = G.half();
+  extern __shared__ double lu_sh[];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int b = blockIdx.x * (blockDim.x >> 5) + w;
+  if (b >= B || !active[b]) return;
+  const int nc = G.ncell(), n = 2 * nc, half = G.half(), ld = n + 1;
+  double* A = lu_sh + (size_t)w * n * ld;
   const T* Jb = J + (int64_t)b * 20 * nc;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e / n][e % n] = 0.0;
-  __syncthreads();
-  for (int cell = threadIdx.x; cell < nc; cell += blockDim.x) {
+  for (int e = l; e < n * ld; e += 32) A[e] = 0.0;
+  __syncwarp();
+  for (int cell = l; cell < nc; cell += 32) {
     const int j = cell / G.nx, i = cell - j * G.nx;
     const int cs = cs_pos(i, j, G.nx, half);
     const int nb[5] = {cell, i > 0 ? cell - 1 : -1, i < G.nx - 1 ? cell + 1 : -1,
@@ -304,39 +456,44 @@ __global__ void k_coarse_lu(unsigned long long* ctr, Geom G, int B, const int* _
       if (nb[q] < 0) continue;
       for (int e = 0; e < 2; ++e)
         for (int v = 0; v < 2; ++v)
-          A[2 * cell + e][2 * nb[q] + v] = (double)Jb[(int64_t)(4 * q + 2 * e + v) * nc + cs];
+          A[(2 * cell + e) * ld + 2 * nb[q] + v] = (double)Jb[(int64_t)(4 * q + 2 * e + v) * nc + cs];
     }
   }
-  __syncthreads();
+  __syncwarp();
+  int* pv = piv + (int64_t)b * kMaxCoarseUnknowns;
   for (int k = 0; k < n; ++k) {
-    if (threadIdx.x == 0) {
-      int best = k;
-      double bv = fabs(A[k][k]);
-      for (int r = k + 1; r < n; ++r)
-        if (fabs(A[r][k]) > bv) { bv = fabs(A[r][k]); best = r; }
-      pr = best;
-      piv[(int64_t)b * kMaxCoarseUnknowns + k] = best;
+    // pivot: largest |A[r][k]|, r >= k, lowest index on ties
+    double bv = -1.0;
+    int br = k;
+    for (int r = k + l; r < n; r += 32) {
+      const double v = fabs(A[r * ld + k]);
+      if (v > bv) { bv = v; br = r; }
     }
-    __syncthreads();
-    const int r = pr;
-    if (r != k)
-      for (int col = threadIdx.x; col < n; col += blockDim.x) {
-        const double t = A[k][col];
-        A[k][col] = A[r][col];
-        A[r][col] = t;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+      const int orr = __shfl_down_sync(0xffffffffu, br, o);
+      if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
+    }
+    br = __shfl_sync(0xffffffffu, br, 0);
+    if (l == 0) pv[k] = br;
+    if (br != k)
+      for (int col = l; col < n; col += 32) {
+        const double t = A[k * ld + col];
+        A[k * ld + col] = A[br * ld + col];
+        A[br * ld + col] = t;
       }
-    __syncthreads();
-    const double d = A[k][k];
-    for (int row = k + 1 + threadIdx.x; row < n; row += blockDim.x) A[row][k] = d != 0.0 ? A[row][k] / d : 0.0;
-    __syncthreads();
-    for (int row = k + 1 + threadIdx.x; row < n; row += blockDim.x) {
-      const double m = A[row][k];
-      for (int col = k + 1; col < n; ++col) A[row][col] -= m * A[k][col];
+    __syncwarp();
+    const double d = A[k * ld + k];
+    for (int row = k + 1 + l; row < n; row += 32) {
+      const double m = d != 0.0 ? A[row * ld + k] / d : 0.0;
+      A[row * ld + k] = m;
+      for (int col = k + 1; col < n; ++col) A[row * ld + col] -= m * A[k * ld + col];
     }
-    __syncthreads();
+    __syncwarp();
   }
   double* L = LU + (int64_t)b * kMaxCoarseUnknowns * kMaxCoarseUnknowns;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) L[e] = A[e / n][e % n];
+  for (int e = l; e < n * n; e += 32) L[e] = A[(e / n) * ld + (e % n)];
 }
 
 // ---------------------------------------------------------------------------
@@ -762,35 +919,6 @@ __global__ void k_reduce_pressure(Phys P, Geom G, int B, const double* __restric
   const int cell = (int)(idx % G.ncell());
   const int j = cell / G.nx;
   pr[idx] = p[idx] - P.rho0 * P.g * (P.Ly - (j + 0.5) * G.hy);
-}
-
-// Residual and Jacobian in natural layout (FP64), for parity tests.
-__global__ void k_residual_jacobian_natural(unsigned long long* ctr, Phys P, Geom G, double tau, int B,
-                                            const double* __restrict__ p, const double* __restrict__ c,
-                                            const double* __restrict__ c_old, const double* __restrict__ phi,
-                                            const double* __restrict__ K, const double* __restrict__ tx,
-                                            const double* __restrict__ dx, const double* __restrict__ ty,
-                                            const double* __restrict__ dy, const double* __restrict__ qin,
-                                            double* __restrict__ R, double* __restrict__ Jout) {
-  HENRY_COUNT_LAUNCH(ctr);
-  const int ncell = G.ncell();
-  const int64_t n = (int64_t)B * ncell;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n) return;
-  const int b = (int)(idx / ncell);
-  const int cell = (int)(idx - (int64_t)b * ncell);
-  const int j = cell / G.nx, i = cell - j * G.nx;
-  const int64_t o = (int64_t)b * ncell;
-  CellIn in;
-  gather_cell(G, i, j, p + o, c + o, phi + o, K + o, tx + o, dx + o, ty + o, dy + o, in);
-  in.c_old = c_old[idx];
-  in.qin = qin[(int64_t)b * G.ny + j];
-  double Rp, Rc, Jc[20];
-  cell_residual<double, true>(P, G, tau, in, Rp, Rc, Jc);
-  R[(int64_t)b * 2 * ncell + cell] = Rp;
-  R[(int64_t)b * 2 * ncell + ncell + cell] = Rc;
-  if (Jout)
-    for (int m = 0; m < 20; ++m) Jout[(int64_t)b * 20 * ncell + (int64_t)m * ncell + cell] = Jc[m];
 }
 
 }  // namespace henry

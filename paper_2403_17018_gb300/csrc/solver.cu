@@ -26,55 +26,6 @@ size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
     }                                                                              \
   } while (0)
 
-// Convergence check; in graph mode also drives the while node.
-__global__ void k_check_cond(unsigned long long* ctr, int B, int nchunk, int ncell,
-                             const double* __restrict__ partial, double scale, double rtol,
-                             double atol, int maxit, int* __restrict__ active,
-                             int* __restrict__ it_step, double* __restrict__ res0,
-                             double* __restrict__ res_last, int* __restrict__ status,
-                             int* __restrict__ iters, int* __restrict__ n_active,
-                             cudaGraphConditionalHandle h) {
-  // same body as k_check, then set the loop condition from the count
-  HENRY_COUNT_LAUNCH(ctr);
-  __shared__ int cnt;
-  if (threadIdx.x == 0) cnt = 0;
-  __syncthreads();
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-  int mine = 0;
-  for (int b = w; b < B; b += nw) {
-    if (!active[b]) continue;
-    double s = 0.0;
-    for (int k = l; k < nchunk; k += 32) s += partial[(int64_t)b * nchunk + k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (l == 0) {
-      const double r = sqrt(s / ncell) * scale;
-      const int it = it_step[b];
-      if (it == 0) res0[b] = r;
-      res_last[b] = r;
-      if (!isfinite(r)) {
-        status[b] |= kStatusNonfinite;
-        active[b] = 0;
-      } else if (r <= fmax(rtol * res0[b], atol)) {
-        active[b] = 0;
-      } else if (it >= maxit) {
-        status[b] |= kStatusMaxit;
-        active[b] = 0;
-      } else {
-        it_step[b] = it + 1;
-        iters[b] += 1;
-        ++mine;
-      }
-    }
-  }
-  if (l == 0 && mine) atomicAdd(&cnt, mine);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    *n_active = cnt;
-    cudaGraphSetConditional(h, cnt > 0 ? 1u : 0u);
-  }
-}
-
 __global__ void k_copy_int(unsigned long long* ctr, int n, const int* __restrict__ src,
                            int* __restrict__ dst, int do_or) {
   HENRY_COUNT_LAUNCH(ctr);
@@ -108,7 +59,8 @@ Solver::Solver(const henry_config& cfg, int nx, int ny, int nt) : cfg_(cfg), nt_
   build_hierarchy(nx, ny, cfg.Lx, cfg.Ly, geoms_);
   levels_.resize(geoms_.size());
   for (size_t k = 0; k < geoms_.size(); ++k) levels_[k].g = geoms_[k];
-  nchunk_ = (geoms_.back().ncell() + kBlock - 1) / kBlock;
+  tile_ = make_res_tile(geoms_.back().nx, geoms_.back().ny);
+  nchunk_ = tile_.ntx * tile_.nty;
   ks_ = 0;
   for (size_t k = 0; k < geoms_.size(); ++k)
     if (geoms_[k].ncell() <= kSmallCells) ks_ = (int)k;
@@ -190,6 +142,7 @@ int Solver::ensure(int B, cudaStream_t s) {
   const size_t o_st = take(Bz * 4);
   const size_t o_it = take(Bz * 4);
   const size_t o_na = take(4);
+  const size_t o_acc = take(8);
   const size_t o_ctr = take(8);
   CK(cudaMalloc(&arena_, off));
   CK(cudaHostAlloc((void**)&n_active_host_, sizeof(int), cudaHostAllocDefault));
@@ -222,6 +175,7 @@ int Solver::ensure(int B, cudaStream_t s) {
   status_w_ = (int*)(a + o_st);
   iters_w_ = (int*)(a + o_it);
   n_active_ = (int*)(a + o_na);
+  check_acc_ = (unsigned int*)(a + o_acc);
   counter_ = (unsigned long long*)(a + o_ctr);
   CK(cudaMemset(arena_, 0, off));
   CK(cudaMemcpy(counter_, &count, sizeof(count), cudaMemcpyHostToDevice));
@@ -293,8 +247,14 @@ void Solver::enqueue_iteration(int B, cudaStream_t s) {
         counter_, phys_, C.g, tau_, B, active_, C.p, C.c, C.phi, C.K, C.tx, C.dx, C.ty, C.dy,
         C.qx, C.qy, (T*)C.J);
   }
-  k_coarse_lu<T><<<B, 64, 0, s>>>(counter_, levels_[0].g, B, active_, (const T*)levels_[0].J,
-                                  lu_, piv_);
+  {
+    const int n = 2 * levels_[0].g.ncell();
+    const size_t per_warp = (size_t)n * (n + 1) * sizeof(double);
+    int wpb = (int)(40960 / per_warp);
+    wpb = wpb < 1 ? 1 : (wpb > 8 ? 8 : wpb);
+    k_coarse_lu<T><<<(B + wpb - 1) / wpb, 32 * wpb, per_warp * wpb, s>>>(
+        counter_, levels_[0].g, B, active_, (const T*)levels_[0].J, lu_, piv_);
+  }
   if (ks_ == nl - 1 && nl > 1)
     launch_small<T>(B, cfg_.vcycles, s);
   else
@@ -308,21 +268,23 @@ template <typename T>
 void Solver::enqueue_resjac_check(int B, cudaStream_t s, bool set_cond) {
   MGLevel& F = levels_.back();
   const Geom& G = F.g;
-  k_resjac<T><<<dim3(nchunk_, B), kBlock, 0, s>>>(counter_, phys_, G, tau_, B, F.p, F.c, c_old_,
-                                                  F.phi, F.K, F.tx, F.dx, F.ty, F.dy, qin_,
-                                                  active_, (T*)F.J, (T*)F.b, (T*)F.x, partial_,
-                                                  F.qx, F.qy);
+  k_resjac<T, false><<<dim3(nchunk_, B), kBlock, 0, s>>>(
+      counter_, phys_, G, tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx, F.ty, F.dy, qin_,
+      active_, (T*)F.J, (T*)F.b, (T*)F.x, partial_, F.qx, F.qy);
   // residual scaled to units of c per step: RMS(R) * tau / (V phi0 rho0)
   const double scale = tau_ / (G.hx * G.hy * cfg_.phi0 * cfg_.rho0);
+  const int gb = (B + 7) / 8;
   if (set_cond)
-    k_check_cond<<<1, 1024, 0, s>>>(counter_, B, nchunk_, G.ncell(), partial_, scale,
-                                    cfg_.newton_rtol, cfg_.newton_atol, cfg_.newton_maxit,
-                                    active_, it_step_, res0_, res_last_, status_w_, iters_w_,
-                                    n_active_, (cudaGraphConditionalHandle)cond_handle_);
+    k_check<true><<<gb, kBlock, 0, s>>>(counter_, B, nchunk_, G.ncell(), partial_, scale,
+                                        cfg_.newton_rtol, cfg_.newton_atol, cfg_.newton_maxit,
+                                        active_, it_step_, res0_, res_last_, status_w_, iters_w_,
+                                        n_active_, check_acc_,
+                                        (cudaGraphConditionalHandle)cond_handle_);
   else
-    k_check<<<1, 1024, 0, s>>>(counter_, B, nchunk_, G.ncell(), partial_, scale,
-                               cfg_.newton_rtol, cfg_.newton_atol, cfg_.newton_maxit, active_,
-                               it_step_, res0_, res_last_, status_w_, iters_w_, n_active_);
+    k_check<false><<<gb, kBlock, 0, s>>>(counter_, B, nchunk_, G.ncell(), partial_, scale,
+                                         cfg_.newton_rtol, cfg_.newton_atol, cfg_.newton_maxit,
+                                         active_, it_step_, res0_, res_last_, status_w_, iters_w_,
+                                         n_active_, check_acc_, 0);
 }
 
 // One implicit Euler step as a CUDA graph: begin, residual + check, then a
@@ -438,10 +400,9 @@ void Solver::launch_timed(int which, int B, cudaStream_t s) {
     k_smooth<T><<<grid1((int64_t)B * F.g.half()), kBlock, 0, s>>>(
         counter_, F.g, B, 0, active_, (const T*)F.J, (const T*)F.b, (T*)F.x);
   } else {
-    k_resjac<T><<<dim3(nchunk_, B), kBlock, 0, s>>>(counter_, phys_, F.g, tau_, B, F.p, F.c, c_old_,
-                                                    F.phi, F.K, F.tx, F.dx, F.ty, F.dy, qin_,
-                                                    active_, (T*)F.J, (T*)F.b, (T*)F.x, partial_,
-                                                    F.qx, F.qy);
+    k_resjac<T, false><<<dim3(nchunk_, B), kBlock, 0, s>>>(
+        counter_, phys_, F.g, tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx, F.ty, F.dy,
+        qin_, active_, (T*)F.J, (T*)F.b, (T*)F.x, partial_, F.qx, F.qy);
   }
 }
 
@@ -451,8 +412,10 @@ void Solver::launch_timed(int which, int B, cudaStream_t s) {
 //    solve (6 mul/sub + 1 rcp + 4 mul) = 32 + 2 + 11 ~ 45 FLOP.
 //  residual + Jacobian, per cell: p, c, c_old, phi, tx, dx, ty, dy read (8
 //    doubles), b 2, x 2, J 20 of type T and qx, qy (2 doubles) written;
-//    FP ops counted from the code: 4 faces x (flux 14 + Jacobian 34) +
-//    accumulation and scatter 30 ~ 220 FLOP.
+//    FP ops counted from the face-based code: 2 faces x 15 (flux) + 16
+//    (accumulation, sums, norm) = 46 FP64 operations, plus the Jacobian,
+//    2 faces x 30 + 24 = 84 operations in the multigrid type (FP64 or
+//    FP32). The figure reported is the FP64 count: 46 + (84 if T = double).
 int Solver::time_kernel(int which, int reps, cudaStream_t s, double* avg_ms, double* bytes,
                         double* flops) {
   if (which < 0 || which > 1 || reps < 1 || last_B_ < 1) return HENRY_E_INVALID;
@@ -485,7 +448,7 @@ int Solver::time_kernel(int which, int reps, cudaStream_t s, double* avg_ms, dou
   } else {
     const double cells = (double)B * G.ncell();
     *bytes = cells * (8.0 * 8 + 24.0 * T + 16.0);
-    *flops = cells * 220.0;
+    *flops = cells * (46.0 + (tsize_ == sizeof(double) ? 84.0 : 0.0));
   }
   *avg_ms = ms / reps;
   return HENRY_OK;
@@ -515,8 +478,10 @@ cudaError_t launch_residual_jacobian(const Phys& P, const Geom& G, double tau, i
   double* pr = scratch + 4 * n;
   k_face_consts<<<grid, kBlock, 0, s>>>(nullptr, P, G, B, phi, K, tx, dx, ty, dy);
   k_reduce_pressure<<<grid, kBlock, 0, s>>>(P, G, B, p, pr);
-  k_residual_jacobian_natural<<<grid, kBlock, 0, s>>>(nullptr, P, G, tau, B, pr, c, c_old, phi, K,
-                                                      tx, dx, ty, dy, qin, R, J);
+  const ResTile tl = make_res_tile(G.nx, G.ny);
+  k_resjac<double, true><<<dim3(tl.ntx * tl.nty, B), kBlock, 0, s>>>(
+      nullptr, P, G, tau, B, tl, pr, c, c_old, phi, K, tx, dx, ty, dy, qin, nullptr, J, R, nullptr,
+      nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
 

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/henry.h"
+#include "common.cuh"
 #include "henry_device.cuh"
 
 namespace henry {
@@ -99,9 +100,11 @@ class Solver {
   int* status_w_ = nullptr;
   int* iters_w_ = nullptr;
   int* n_active_ = nullptr;     // device
+  unsigned int* check_acc_ = nullptr;  // k_check's block count / active count (2 words)
   int* n_active_host_ = nullptr;  // pinned
   unsigned long long* counter_ = nullptr;  // device launch counter
-  int nchunk_ = 0;
+  int nchunk_ = 0;            // residual blocks per sample
+  ResTile tile_{};            // tiling of the residual kernel
   int ks_ = 0;                // top multigrid level handled by k_vcycle_small
   size_t small_smem_ = 0;     // its dynamic shared memory per block
   // CUDA graph of one time step (HENRY_LOOP_GRAPH), rebuilt when B changes
