@@ -186,6 +186,30 @@ int henry_residual_jacobian(const henry_config* cfg, int nx, int ny, double tau,
                             const double* p, const double* c, const double* c_old,
                             double* R, double* J, void* stream);
 
+/* henry_residual_jacobian without any device allocation. The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory during the call -- code running inside a CUDA stream
+ * capture or a graph that must not contain allocation nodes, processes whose
+ * device memory is entirely owned by another allocator (a framework's
+ * caching pool or a fixed memory budget), and latency-critical loops where
+ * an allocation could synchronise or fail. Arguments, layouts, outputs and
+ * errors are those of henry_residual_jacobian; the caller still provides
+ * every input and output buffer.
+ * Scratch: 5 doubles per cell and sample in a file-scope device array of
+ * 2^20 doubles (8 MiB), held by every GPU that loads the library until the
+ * process exits; B * nx * ny above 209715 cells is rejected with
+ * HENRY_E_INVALID. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture. Every call shares the array and it keeps
+ * the last call's contents; each call writes every scratch element it reads
+ * before reading it, so nothing needs to start at zero. Calls that overlap
+ * on the GPU (on different streams, or from different host threads) race on
+ * the array and must be serialised by the caller. */
+int henry_residual_jacobian_noalloc(const henry_config* cfg, int nx, int ny, double tau, int B,
+                                    const double* phi, const double* K, const double* qin,
+                                    const double* p, const double* c, const double* c_old,
+                                    double* R, double* J, void* stream);
+
 /* Random fields of the level-l grid for B samples (cell centres):
  *   phi = phi0 (1 + 0.1 xi1 cos(pi x/2) sin(pi y) [+ 0.05 xi4 cos(pi x) sin(2 pi y)])
  *   K   = K0 exp(0.5 xi2 sin(pi x/2) cos(pi y) [+ 0.05 xi5 sin(pi x) cos(2 pi y)] + logk)

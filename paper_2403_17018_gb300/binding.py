@@ -82,6 +82,7 @@ def load():
         "mlmc_level_stats": (I, [P, I, V, V, I, V, ctypes.POINTER(LevelStats), V]),
         "mlmc_field_stats": (I, [P, I, V, V, I, V, V, V, V, V, V, V]),
         "henry_residual_jacobian": (I, [cfgp, I, I, D, I, V, V, V, V, V, V, V, V, V]),
+        "henry_residual_jacobian_noalloc": (I, [cfgp, I, I, D, I, V, V, V, V, V, V, V, V, V]),
         "henry_fields": (I, [P, I, V, V, I, V, V, V, V]),
         "henry_level_info": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                                  ctypes.POINTER(I)]),
@@ -275,14 +276,17 @@ def new_field_accumulator(ny, nx, device="cuda"):
             "m2_f": z(), "mean_d": z(), "m2_d": z()}
 
 
-def residual_jacobian(cfg: HenryConfig, tau, phi, K, qin, p, c, c_old, want_J=True, stream=None):
-    """henry_residual_jacobian: R [B,2,ny,nx] and J [B,20,ny,nx] (or None)."""
+def residual_jacobian(cfg: HenryConfig, tau, phi, K, qin, p, c, c_old, want_J=True, stream=None,
+                      noalloc=False):
+    """henry_residual_jacobian (or, with noalloc=True, the entry point that
+    allocates no device memory): R [B,2,ny,nx] and J [B,20,ny,nx] (or None)."""
     import torch
     B, ny, nx = p.shape
     R = torch.empty((B, 2, ny, nx), dtype=torch.float64, device=p.device)
     J = torch.empty((B, 20, ny, nx), dtype=torch.float64, device=p.device) if want_J else None
     f64 = torch.float64
-    _check(load().henry_residual_jacobian(
+    fn = load().henry_residual_jacobian_noalloc if noalloc else load().henry_residual_jacobian
+    _check(fn(
         ctypes.byref(cfg), nx, ny, float(tau), B, _ptr(phi, f64, (B, ny, nx), "phi"),
         _ptr(K, f64, (B, ny, nx), "K"), _ptr(qin, f64, (B, ny), "qin"), _ptr(p, f64, None, "p"),
         _ptr(c, f64, (B, ny, nx), "c"), _ptr(c_old, f64, (B, ny, nx), "c_old"), _ptr(R), _ptr(J),
