@@ -1,0 +1,255 @@
+"""Adaptive multilevel Monte Carlo driver (arxiv 2403.17018, section 3).
+
+The estimator of E[g_L] is the telescoping sum Y = sum_l Y_l (Eqs. EgL, A),
+Y_l the mean of g_l - g_{l-1} over m_l independent level pairs (g_{-1} = 0),
+with Var Y = sum_l V_l / m_l (Eq. goal_variance). For a target root mean
+square error eps the variance budget is eps^2 / 2 (Eq. var_error) and the
+cost-optimal sample numbers are
+
+    m_l = 2 eps^-2 sqrt(V_l / s_l) sum_i sqrt(V_i s_i)          (Eq. M_ell)
+
+with V_l the variance of g_l - g_{l-1} and s_l the cost of one pair. Here
+s_l is the measured GPU time per pair of the last batch of level l and
+V_l the largest variance over the selected QoIs. The driver starts from a
+pilot, recomputes m_l from the running statistics, draws the missing
+samples, and stops when no level needs more. The bias is estimated from
+the finest correction, |E Y_L| / (2^alpha - 1), with alpha fitted to
+log2 |E Y_l| (the build refines by 2 per level; the paper fits in log_4).
+
+Samples are drawn by a sampler object; GpuSampler runs level pairs through
+the C ABI (henry_sample_pairs + mlmc_level_stats). Sample i of level l
+always gets the same xi, so a run is reproducible and can be resumed from
+its saved state. Under torch.distributed each rank draws a disjoint slice
+of every batch and the per-level statistics are merged with Chan's formula.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+NQ = 6
+
+
+@dataclass
+class LevelState:
+    """Running statistics of one level: count, means and M2 (sum of squared
+    deviations) of g_l and of g_l - g_{l-1}, cost in seconds and pairs."""
+    n: int = 0
+    mean_f: np.ndarray = field(default_factory=lambda: np.zeros(NQ))
+    m2_f: np.ndarray = field(default_factory=lambda: np.zeros(NQ))
+    mean_d: np.ndarray = field(default_factory=lambda: np.zeros(NQ))
+    m2_d: np.ndarray = field(default_factory=lambda: np.zeros(NQ))
+    seconds: float = 0.0
+    timed_pairs: int = 0
+    failed: int = 0
+    drawn: int = 0           # next sample index of this level's stream
+
+    def var_d(self):
+        return self.m2_d / (self.n - 1) if self.n > 1 else np.full(NQ, np.inf)
+
+    def var_f(self):
+        return self.m2_f / (self.n - 1) if self.n > 1 else np.full(NQ, np.inf)
+
+    def to_json(self):
+        return {k: (v.tolist() if isinstance(v, np.ndarray) else v) for k, v in self.__dict__.items()}
+
+    @staticmethod
+    def from_json(d):
+        s = LevelState()
+        for k, v in d.items():
+            setattr(s, k, np.array(v) if isinstance(v, list) else v)
+        return s
+
+
+def chan_merge(a: LevelState, n_b: int, mean_f, m2_f, mean_d, m2_d) -> None:
+    """Merge a batch's statistics into `a` (Chan, Golub and LeVeque)."""
+    if n_b == 0:
+        return
+    n = a.n + n_b
+    for mean, m2, mb, m2b in ((a.mean_f, a.m2_f, mean_f, m2_f), (a.mean_d, a.m2_d, mean_d, m2_d)):
+        d = np.asarray(mb) - mean
+        m2 += np.asarray(m2b) + d * d * (a.n * n_b / n)
+        mean += d * (n_b / n)
+    a.n = n
+
+
+def allocate(V, s, eps, var_budget_fraction=0.5):
+    """Eq. M_ell: m_l = eps^-2 / f sqrt(V_l/s_l) sum_i sqrt(V_i s_i), rounded up."""
+    V = np.asarray(V, dtype=np.float64)
+    s = np.asarray(s, dtype=np.float64)
+    total = float(np.sum(np.sqrt(V * s)))
+    m = np.sqrt(V / s) * total / (var_budget_fraction * eps * eps)
+    return np.ceil(m * (1 - 1e-12)).astype(np.int64)
+
+
+def fit_alpha(means):
+    """Weak rate alpha from |E Y_l| ~ 2^(-alpha l), l >= 1 (least squares)."""
+    l = np.arange(1, len(means))
+    y = np.abs(np.asarray(means[1:], dtype=np.float64))
+    ok = y > 0
+    if ok.sum() < 2:
+        return 1.0
+    A = np.vstack([-l[ok], np.ones(ok.sum())]).T
+    (alpha, _), *_ = np.linalg.lstsq(A, np.log2(y[ok]), rcond=None)
+    return float(max(alpha, 0.5))
+
+
+class GpuSampler:
+    """Level pairs on the GPU through the C ABI; statistics merged on device."""
+
+    def __init__(self, cfg, rank=0, world=1):
+        import torch
+        from paper_2403_17018_gb300 import binding as hb
+        self.torch = torch
+        self.hb = hb
+        self.ctx = hb.Context(cfg)
+        self.n_xi = cfg.n_xi
+        self.rank, self.world = rank, world
+
+    def batch(self, level, first, count):
+        """Run pairs first..first+count-1 of `level` (this rank's slice);
+        returns (n, mean_f, m2_f, mean_d, m2_d, seconds, failed)."""
+        from paper_2403_17018_gb300.inputs import xi_batch
+        torch = self.torch
+        lo = first + (count * self.rank) // self.world
+        hi = first + (count * (self.rank + 1)) // self.world
+        if hi <= lo:
+            return 0, np.zeros(NQ), np.zeros(NQ), np.zeros(NQ), np.zeros(NQ), 0.0, 0
+        xi = torch.from_numpy(xi_batch(level, lo, hi - lo, n_xi=self.n_xi)).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        qf, qc, _, _, st = self.ctx.sample_pairs(level, xi)
+        S = self.hb.LevelStats()
+        self.ctx.level_stats(level, qf, qc, st, S)
+        dt = time.perf_counter() - t0
+        failed = int((st != 0).sum().item())
+        return (S.n, np.array(S.mean_f[:]), np.array(S.m2_f[:]), np.array(S.mean_d[:]),
+                np.array(S.m2_d[:]), dt, failed)
+
+
+def _merge_ranks(levels, dist):
+    """Chan-merge every rank's per-level statistics (a few hundred bytes)."""
+    if dist is None:
+        return levels
+    gathered = [None] * dist.get_world_size()
+    dist.all_gather_object(gathered, [s.to_json() for s in levels])
+    merged = []
+    for l in range(len(levels)):
+        m = LevelState(drawn=levels[l].drawn)
+        for r in gathered:
+            s = LevelState.from_json(r[l])
+            chan_merge(m, s.n, s.mean_f, s.m2_f, s.mean_d, s.m2_d)
+            m.seconds = max(m.seconds, s.seconds)
+            m.timed_pairs = max(m.timed_pairs, s.timed_pairs)
+            m.failed += s.failed
+        merged.append(m)
+    return merged
+
+
+def run(sampler, L, eps, qois=(3, 4, 5), pilot=None, max_batch=None, var_budget_fraction=0.5,
+        max_rounds=20, log=None, dist=None, state=None):
+    """Adaptive MLMC on levels 0..L to RMSE eps for the QoIs `qois`.
+
+    Returns a dict with the estimate per QoI, Var Y, the bias estimate, the
+    RMSE estimate, samples and cost per level and the wall time. `state`
+    (from a previous result's "state") resumes a run."""
+    pilot = pilot or [max(16, 512 >> (2 * l)) for l in range(L + 1)]
+    max_batch = max_batch or [max(32, 16384 >> (2 * l)) for l in range(L + 1)]
+    local = [LevelState() for _ in range(L + 1)] if state is None else \
+        [LevelState.from_json(d) for d in state]
+    target = [max(pilot[l], local[l].n) for l in range(L + 1)]
+    t_start = time.perf_counter()
+    rounds = 0
+    qs = list(qois)
+    levels = _merge_ranks(local, dist)
+    while True:
+        for l in range(L + 1):
+            need = target[l] - levels[l].n
+            while need > 0:
+                cnt = min(need, max_batch[l])
+                n, mf, m2f, md, m2d, dt, failed = sampler.batch(l, local[l].drawn, cnt)
+                chan_merge(local[l], n, mf, m2f, md, m2d)
+                local[l].drawn += cnt
+                local[l].seconds = dt
+                local[l].timed_pairs = cnt
+                local[l].failed += failed
+                need -= cnt
+        levels = _merge_ranks(local, dist)
+        V = np.array([[lv.var_d()[q] for q in qs] for lv in levels])          # [L+1, nq]
+        s = np.array([max(lv.seconds, 1e-9) / max(lv.timed_pairs, 1) for lv in levels])
+        m = np.max(np.stack([allocate(V[:, k], s, eps, var_budget_fraction)
+                             for k in range(len(qs))]), axis=0)
+        rounds += 1
+        if log:
+            log({"round": rounds, "n": [lv.n for lv in levels], "m": m.tolist(),
+                 "V": V.max(axis=1).tolist(), "s": s.tolist()})
+        if all(m[l] <= levels[l].n for l in range(L + 1)) or rounds >= max_rounds:
+            break
+        target = [int(max(levels[l].n, m[l])) for l in range(L + 1)]
+    wall = time.perf_counter() - t_start
+    n = np.array([lv.n for lv in levels], dtype=np.float64)
+    Y = np.sum([lv.mean_d for lv in levels], axis=0)
+    varY = np.sum([lv.var_d() / max(lv.n, 1) for lv in levels], axis=0)
+    alphas = [fit_alpha([lv.mean_d[q] for lv in levels]) if L >= 2 else 1.0 for q in range(NQ)]
+    bias = np.array([abs(levels[L].mean_d[q]) / (2.0 ** alphas[q] - 1.0) if L >= 1 else 0.0
+                     for q in range(NQ)])
+    rmse = np.sqrt(varY + bias ** 2)
+    return {"levels": L + 1, "eps": eps, "qois": qs, "estimate": Y.tolist(),
+            "var_Y": varY.tolist(), "bias": bias.tolist(), "alpha": alphas,
+            "rmse": rmse.tolist(), "rmse_sampling": np.sqrt(varY).tolist(),
+            "n": n.astype(int).tolist(), "V_l": [lv.var_d().tolist() for lv in levels],
+            "mean_l": [lv.mean_d.tolist() for lv in levels],
+            "seconds_per_pair": [max(lv.seconds, 1e-9) / max(lv.timed_pairs, 1) for lv in levels],
+            "failed": int(sum(lv.failed for lv in levels)), "rounds": rounds, "wall_s": wall,
+            "state": [lv.to_json() for lv in local]}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--levels", type=int, default=6)
+    ap.add_argument("--eps", type=float, default=1e-3)
+    ap.add_argument("--n-xi", type=int, default=6)
+    ap.add_argument("--precision", choices=["fp64", "fp32mg"], default="fp32mg")
+    ap.add_argument("--vcycles", type=int, default=2)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args(argv)
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2403_17018_gb300 import binding as hb
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    cfg = hb.default_config(nlevels=a.levels, n_xi=a.n_xi, vcycles=a.vcycles,
+                            precision=hb.PREC_FP64 if a.precision == "fp64" else hb.PREC_FP32_MG)
+    sampler = GpuSampler(cfg, rank, world)
+    log = (lambda d: print(json.dumps(d), flush=True)) if rank == 0 else None
+    res = run(sampler, a.levels - 1, a.eps, log=log, dist=dist)
+    res.update({"precision": a.precision, "n_gpus": world})
+    if rank == 0:
+        out = {k: v for k, v in res.items() if k != "state"}
+        print(json.dumps(out))
+        if a.out:
+            with open(a.out, "w") as fh:
+                json.dump(res, fh)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
