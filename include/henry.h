@@ -86,7 +86,12 @@ typedef struct henry_config {
   int newton_maxit;    /* iteration cap per step -> HENRY_S_MAXIT           */
   int nu1, nu2;        /* red-black block Gauss-Seidel sweeps pre / post    */
   int vcycles;         /* V-cycles per defect-correction iteration          */
-  int reserved[8];
+  int guess_extrapolation; /* 1: Newton guess 2u^{n-1} - u^{n-2} from step 3 */
+  double newton_stag_tol;  /* also converged when r <= this and the last
+                              iteration reduced r by less than half (the
+                              FP64 rounding floor, which grows with
+                              resolution, has been reached); 0 disables */
+  int reserved[6];
 } henry_config;
 
 typedef struct henry_ctx henry_ctx; /* opaque: owns device workspaces */
@@ -103,7 +108,8 @@ typedef struct henry_level_stats {
  * 1024.99, D = 18.8571e-6, K0 = 1.020408e-9, phi0 = 0.35, mu = 1e-3,
  * g = 9.8), q0 = 6.6e-5 m/s, [0,2]x[0,1], T = 43200 s, 32x16 cells and 24
  * steps on level 0, 2 levels, 3 random variables, FP64 multigrid, rtol
- * 1e-10, atol 1e-12, maxit 30, V(2,2), 1 V-cycle per iteration. */
+ * 1e-10, atol 1e-12, stagnation tolerance 1e-9, maxit 30, V(2,2), 1 V-cycle
+ * per iteration, extrapolated Newton guess on. */
 int henry_default_config(henry_config* cfg);
 
 /* Validate *cfg and create a context for levels 0..cfg->nlevels-1.
@@ -140,10 +146,36 @@ int henry_solve(henry_ctx* ctx, int level, const double* xi, const double* logk,
  *   c_coarse           device [B][ny_{l-1}][nx_{l-1}] out, or NULL
  *   status             device int [B] out, OR of both solves' bits
  * The coarse result is bitwise equal to henry_solve at level l-1 on the same
- * xi. Errors as henry_solve. */
+ * xi. The coarse half runs on an internal stream forked from `stream` (and
+ * joined back before the call's last operation), concurrently with the fine
+ * half. Errors as henry_solve. */
 int henry_sample_pairs(henry_ctx* ctx, int level, const double* xi, int B,
                        double* q_fine, double* q_coarse, double* c_fine, double* c_coarse,
                        int* status, void* stream);
+
+/* Discrete adjoint of one QoI through the implicit Euler time stepping
+ * (section 2.3), for B samples of level `level`: with R^n(u^n, u^{n-1}) = 0
+ * the residual of step n and Q = Q(u^r),
+ *   J_r^T lam_r = dQ/du^r,  J_n^T lam_n = -(dR^{n+1}/du^n)^T lam_{n+1},
+ *   dQ/dtheta = -sum_n (dR^n/dtheta)^T lam_n,
+ * for theta = xi (through the random fields of henry_fields) and the
+ * per-cell log-permeability perturbation. The forward stores its state every
+ * ckpt_every steps and the backward recomputes each segment from its
+ * checkpoint (bitwise the forward's states); each transposed step system is
+ * solved by FP64 defect correction preconditioned by the multigrid of the
+ * context's precision applied to the transposed operators (relative
+ * residual 1e-11).
+ *   qoi_id     0 = Q_S (int c rho), 2 = toe (int c (Lx - x)); others invalid
+ *   xi         device [B][n_xi];  logk device [B][ny][nx] or NULL
+ *   q          device [B] out: the QoI at T
+ *   dq_dxi     device [B][n_xi] out
+ *   dq_dlogk   device [B][ny][nx] out, or NULL
+ *   status     device int [B] out (HENRY_S_* bits of forward and adjoint)
+ * Synchronises the stream once per defect-correction iteration of the
+ * backward pass. Errors as henry_solve. */
+int henry_adjoint(henry_ctx* ctx, int level, const double* xi, const double* logk, int B,
+                  int qoi_id, int ckpt_every, double* q, double* dq_dxi, double* dq_dlogk,
+                  int* status, void* stream);
 
 /* Merge one batch into the running statistics of a level (Def. of Y_l and
  * V_l; V_l = m2_d / (n - 1)). Samples with status != 0 are skipped.

@@ -1,0 +1,119 @@
+"""Autotuner of the per-level solver schedule.
+
+For each MLMC level it times short batched solves (a few implicit Euler
+steps at the level's own time step) for every candidate schedule — V-cycles
+per defect-correction iteration and pre/post smoothing sweeps — and, for
+the level's batch size, several batch splits, then keeps the schedule with
+the highest solves per second. Results are cached in a JSON file keyed by
+GPU name, level grid, precision and batch so that later runs reuse them.
+
+  python -m paper_2403_17018_gb300.autotune --levels 4 --precision fp32mg
+"""
+from __future__ import annotations
+
+import argparse
+import itertools
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuning", "schedules.json")
+CANDIDATES = {"vcycles": (1, 2, 3), "nu": ((1, 1), (2, 2), (3, 3))}
+
+
+def _key(gpu, level, precision, batch, nx0, ny0):
+    return f"{gpu}|L{level}|{nx0 << level}x{ny0 << level}|{precision}|B{batch}"
+
+
+def load_cache(path=CACHE):
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(cache, path=CACHE):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(cache, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def best_schedule(level, precision, batch, gpu=None, nx0=32, ny0=16, path=CACHE):
+    """Cached schedule for a level, or None if it was never tuned."""
+    import torch
+    gpu = gpu or torch.cuda.get_device_name(0)
+    return load_cache(path).get(_key(gpu, level, precision, batch, nx0, ny0))
+
+
+def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2), log=None):
+    """Time every candidate schedule on `steps` steps of level `level`;
+    returns the best {vcycles, nu1, nu2, split, solves_per_s} and the table."""
+    import torch
+    from paper_2403_17018_gb300 import binding as hb
+    from paper_2403_17018_gb300.inputs import xi_batch
+    prec = hb.PREC_FP64 if precision == "fp64" else hb.PREC_FP32_MG
+    f = 1 << level
+    k = max(1, steps // f)
+    xi = torch.from_numpy(xi_batch(level, 0, batch)).cuda()
+    table = []
+    for vc, (n1, n2), split in itertools.product(CANDIDATES["vcycles"], CANDIDATES["nu"], splits):
+        if batch % split:
+            continue
+        cfg = hb.default_config(nlevels=level + 1, precision=prec, vcycles=vc, nu1=n1, nu2=n2,
+                                nt0=k, T=1800.0 * k)
+        ctx = hb.Context(cfg)
+        sub = batch // split
+        parts = [xi[i * sub:(i + 1) * sub].contiguous() for i in range(split)]
+        for p in parts:                      # warm-up: allocation and graph capture
+            ctx.solve(level, p)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bad = 0
+        for _ in range(reps):
+            for p in parts:
+                bad += int((ctx.solve(level, p)["status"] != 0).sum().item())
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / reps
+        row = {"vcycles": vc, "nu1": n1, "nu2": n2, "split": split,
+               "solves_per_s": batch / dt, "failed": bad}
+        table.append(row)
+        if log:
+            log(row)
+        ctx.close()
+    ok = [r for r in table if r["failed"] == 0] or table
+    best = max(ok, key=lambda r: r["solves_per_s"])
+    return best, table
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--levels", type=int, default=4)
+    ap.add_argument("--precision", choices=["fp64", "fp32mg"], default="fp32mg")
+    ap.add_argument("--batch", type=int, nargs="*", default=None,
+                    help="batch per level (default 1024/256/64/16...)")
+    ap.add_argument("--steps", type=int, default=4)
+    a = ap.parse_args(argv)
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    gpu = torch.cuda.get_device_name(0)
+    cache = load_cache()
+    for level in range(a.levels):
+        B = a.batch[level] if a.batch else max(16, 1024 >> (2 * level))
+        best, table = tune_level(level, B, a.precision, steps=a.steps,
+                                 log=lambda r: print(json.dumps(r), flush=True))
+        cache[_key(gpu, level, a.precision, B, 32, 16)] = best
+        print(json.dumps({"level": level, "batch": B, "best": best}), flush=True)
+    save_cache(cache)
+
+
+if __name__ == "__main__":
+    main()

@@ -41,7 +41,8 @@ class HenryConfig(ctypes.Structure):
                                              "loop_mode")] + \
                [("newton_rtol", ctypes.c_double), ("newton_atol", ctypes.c_double),
                 ("newton_maxit", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
-                ("vcycles", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+                ("vcycles", ctypes.c_int), ("guess_extrapolation", ctypes.c_int),
+                ("newton_stag_tol", ctypes.c_double), ("reserved", ctypes.c_int * 6)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
@@ -84,6 +85,7 @@ def load():
         "henry_residual_jacobian": (I, [cfgp, I, I, D, I, V, V, V, V, V, V, V, V, V]),
         "henry_residual_jacobian_noalloc": (I, [cfgp, I, I, D, I, V, V, V, V, V, V, V, V, V]),
         "henry_fields": (I, [P, I, V, V, I, V, V, V, V]),
+        "henry_adjoint": (I, [P, I, V, V, I, I, I, V, V, V, V, V]),
         "henry_level_info": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                                  ctypes.POINTER(I)]),
         "henry_launch_count": (ctypes.c_int64, [P]),
@@ -255,6 +257,23 @@ class Context:
             _stream(stream)))
         return acc
 
+    def adjoint(self, level, xi, logk=None, qoi="Q_S", ckpt_every=8, want_logk=True, stream=None):
+        """henry_adjoint: (q [B], dq_dxi [B,n_xi], dq_dlogk [B,ny,nx] or None, status [B])."""
+        import torch
+        B = xi.shape[0]
+        li = self.level_info(level)
+        dev = xi.device
+        qid = {"Q_S": 0, "toe": 2}[qoi]
+        q = torch.empty((B,), dtype=torch.float64, device=dev)
+        g = torch.empty((B, self.cfg.n_xi), dtype=torch.float64, device=dev)
+        gl = torch.empty((B, li.ny, li.nx), dtype=torch.float64, device=dev) if want_logk else None
+        st = torch.empty((B,), dtype=torch.int32, device=dev)
+        _check(self.lib.henry_adjoint(
+            self._h, level, _ptr(xi, torch.float64, (B, self.cfg.n_xi), "xi"),
+            _ptr(logk, torch.float64, (B, li.ny, li.nx), "logk"), B, qid, ckpt_every, _ptr(q),
+            _ptr(g), _ptr(gl), _ptr(st), _stream(stream)))
+        return q, g, gl, st
+
     def fields(self, level, xi, logk=None, stream=None):
         import torch
         B = xi.shape[0]
@@ -292,3 +311,30 @@ def residual_jacobian(cfg: HenryConfig, tau, phi, K, qin, p, c, c_old, want_J=Tr
         _ptr(c, f64, (B, ny, nx), "c"), _ptr(c_old, f64, (B, ny, nx), "c_old"), _ptr(R), _ptr(J),
         _stream(stream)))
     return R, J
+
+
+def henry_qoi(ctx: Context, level: int, xi, logk=None, qoi="Q_S", ckpt_every=8):
+    """Differentiable QoI of a batch of Henry solves: returns q [B]; its
+    gradient with respect to xi (and logk, if given) comes from the discrete
+    adjoint (henry_adjoint), computed together with q in the forward call."""
+    import torch
+
+    class _HenryQoI(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, xi_, logk_):
+            q, g, gl, st = ctx.adjoint(level, xi_.detach().contiguous(),
+                                       None if logk_ is None else logk_.detach().contiguous(),
+                                       qoi=qoi, ckpt_every=ckpt_every, want_logk=logk_ is not None)
+            fctx.save_for_backward(g, gl if gl is not None else torch.empty(0, device=xi_.device))
+            fctx.has_logk = logk_ is not None
+            fctx.status = st
+            return q
+
+        @staticmethod
+        def backward(fctx, grad_q):
+            g, gl = fctx.saved_tensors
+            gx = grad_q[:, None] * g
+            glk = grad_q[:, None, None] * gl if fctx.has_logk else None
+            return gx, glk
+
+    return _HenryQoI.apply(xi, logk)

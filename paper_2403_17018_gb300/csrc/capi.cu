@@ -20,6 +20,7 @@ cudaError_t launch_residual_jacobian(const Phys& P, const Geom& G, double tau, i
                                      const double* phi, const double* K, const double* qin,
                                      const double* p, const double* c, const double* c_old,
                                      double* R, double* J, double* scratch, cudaStream_t s);
+int or_status(const int* src, int* dst, int B, unsigned long long* ctr, cudaStream_t s);
 }  // namespace henry
 
 using henry::Solver;
@@ -29,6 +30,12 @@ struct henry_ctx {
   int device = 0;
   // solvers per level: [0] fine role, [1] coarse role (level l-1 of a pair)
   std::vector<std::unique_ptr<Solver>> role[2];
+  // per level: stream, events and status buffer of the concurrently run
+  // coarse half of a pair (created on first use)
+  std::vector<cudaStream_t> pair_stream;
+  std::vector<cudaEvent_t> pair_fork, pair_join;
+  std::vector<int*> pair_status;
+  std::vector<int> pair_status_cap;
   double* stats_dev = nullptr;         // 1 + 4*NQ doubles
   double* stats_host = nullptr;        // pinned
   unsigned long long* ctr = nullptr;   // launches outside the solvers
@@ -121,6 +128,8 @@ int henry_default_config(henry_config* c) {
   c->nu1 = 2;
   c->nu2 = 2;
   c->vcycles = 1;
+  c->guess_extrapolation = 1;
+  c->newton_stag_tol = 1e-9;
   return HENRY_OK;
 }
 
@@ -134,6 +143,11 @@ int henry_create_levels(const henry_config* cfg, henry_ctx** out) {
   ctx->cfg = *cfg;
   ctx->role[0].resize(cfg->nlevels);
   ctx->role[1].resize(cfg->nlevels);
+  ctx->pair_stream.assign(cfg->nlevels, nullptr);
+  ctx->pair_fork.assign(cfg->nlevels, nullptr);
+  ctx->pair_join.assign(cfg->nlevels, nullptr);
+  ctx->pair_status.assign(cfg->nlevels, nullptr);
+  ctx->pair_status_cap.assign(cfg->nlevels, 0);
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->stats_dev, sizeof(double) * (1 + 4 * HENRY_NQ) + 64);
   if (e == cudaSuccess) e = cudaHostAlloc((void**)&ctx->stats_host, sizeof(double) * (1 + 4 * HENRY_NQ), 0);
@@ -153,6 +167,12 @@ void henry_destroy(henry_ctx* ctx) {
   if (!ctx) return;
   cudaDeviceSynchronize();
   for (auto& v : ctx->role) v.clear();
+  for (size_t l = 0; l < ctx->pair_stream.size(); ++l) {
+    if (ctx->pair_stream[l]) cudaStreamDestroy(ctx->pair_stream[l]);
+    if (ctx->pair_fork[l]) cudaEventDestroy(ctx->pair_fork[l]);
+    if (ctx->pair_join[l]) cudaEventDestroy(ctx->pair_join[l]);
+    if (ctx->pair_status[l]) cudaFree(ctx->pair_status[l]);
+  }
   if (ctx->stats_dev) cudaFree(ctx->stats_dev);
   if (ctx->stats_host) cudaFreeHost(ctx->stats_host);
   delete ctx;
@@ -192,11 +212,46 @@ int henry_sample_pairs(henry_ctx* ctx, int level, const double* xi, int B, doubl
   if (!xi || !q_fine || !status) return fail(HENRY_E_INVALID, "xi, q_fine and status are required");
   CKR(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
-  int rc = get_solver(ctx, level, 0)->run(xi, nullptr, B, q_fine, c_fine, nullptr, status, nullptr,
-                                          0, s);
-  if (rc || level == 0) return rc;
-  return get_solver(ctx, level - 1, 1)->run(xi, nullptr, B, q_coarse, c_coarse, nullptr, status,
-                                            nullptr, 1, s);
+  if (level == 0)
+    return get_solver(ctx, 0, 0)->run(xi, nullptr, B, q_fine, c_fine, nullptr, status, nullptr, 0, s);
+  // the coarse half runs concurrently on a stream forked from the caller's
+  if (!ctx->pair_stream[level]) {
+    CKR(cudaStreamCreateWithFlags(&ctx->pair_stream[level], cudaStreamNonBlocking));
+    CKR(cudaEventCreateWithFlags(&ctx->pair_fork[level], cudaEventDisableTiming));
+    CKR(cudaEventCreateWithFlags(&ctx->pair_join[level], cudaEventDisableTiming));
+  }
+  if (ctx->pair_status_cap[level] < B) {
+    CKR(cudaStreamSynchronize(ctx->pair_stream[level]));
+    if (ctx->pair_status[level]) CKR(cudaFree(ctx->pair_status[level]));
+    ctx->pair_status[level] = nullptr;
+    CKR(cudaMalloc(&ctx->pair_status[level], sizeof(int) * B));
+    ctx->pair_status_cap[level] = B;
+  }
+  cudaStream_t sc = ctx->pair_stream[level];
+  CKR(cudaEventRecord(ctx->pair_fork[level], s));
+  CKR(cudaStreamWaitEvent(sc, ctx->pair_fork[level], 0));
+  int rc = get_solver(ctx, level - 1, 1)->run(xi, nullptr, B, q_coarse, c_coarse, nullptr,
+                                              ctx->pair_status[level], nullptr, 0, sc);
+  if (rc) return rc;
+  CKR(cudaEventRecord(ctx->pair_join[level], sc));
+  rc = get_solver(ctx, level, 0)->run(xi, nullptr, B, q_fine, c_fine, nullptr, status, nullptr, 0, s);
+  if (rc) return rc;
+  CKR(cudaStreamWaitEvent(s, ctx->pair_join[level], 0));
+  return henry::or_status(ctx->pair_status[level], status, B, ctx->ctr, s);
+}
+
+int henry_adjoint(henry_ctx* ctx, int level, const double* xi, const double* logk, int B,
+                  int qoi_id, int ckpt_every, double* q, double* dq_dxi, double* dq_dlogk,
+                  int* status, void* stream) {
+  if (!ctx) return fail(HENRY_E_INVALID, "ctx is NULL");
+  if (level < 0 || level >= ctx->cfg.nlevels) return fail(HENRY_E_INVALID, "bad level");
+  if (B < 0) return fail(HENRY_E_INVALID, "B < 0");
+  if (qoi_id != 0 && qoi_id != 2) return fail(HENRY_E_INVALID, "qoi_id must be 0 (Q_S) or 2 (toe)");
+  if (B == 0) return HENRY_OK;
+  if (!xi || !q || !dq_dxi || !status) return fail(HENRY_E_INVALID, "xi, q, dq_dxi, status required");
+  CKR(cudaSetDevice(ctx->device));
+  return get_solver(ctx, level, 0)->adjoint(xi, logk, B, qoi_id, ckpt_every, q, dq_dxi, dq_dlogk,
+                                            status, (cudaStream_t)stream);
 }
 
 int henry_fields(henry_ctx* ctx, int level, const double* xi, const double* logk, int B,

@@ -83,19 +83,24 @@ __device__ __forceinline__ void face_flux(const Phys& P, double pL, double cL, d
   Fm = q * rup;
   Fs = q * rcup - dco * rbar * dc;
   if (WANT_J) {
-    const JT t_ = (JT)t, q_ = (JT)q, dr = (JT)P.drho;
+    // Jacobian entries in the multigrid type from five converted values (on
+    // GB300 a conversion costs an FP64-pipe slot, like an FP64 operation)
+    const JT t_ = (JT)t, q_ = (JT)q, dco_ = (JT)dco, cL_ = (JT)cL, cU_ = (JT)cU;
+    const JT dr = (JT)P.drho, r0 = (JT)P.rho0;
+    const JT rL_ = r0 + dr * cL_, rU_ = r0 + dr * cU_;
     const JT s_ = -t_ * (JT)gd * (JT)0.5 * dr;       // dq/dc_L = dq/dc_U
-    const JT rup_ = (JT)rup, rcup_ = (JT)rcup, dco_ = (JT)dco;
-    const JT diffc = -dco_ * (JT)0.5 * dr * (JT)dc;   // d(-dco rbar dc)/dc from rbar
-    const JT drb = dco_ * (JT)rbar;
+    const JT rup_ = up ? rL_ : rU_;
+    const JT rcup_ = up ? rL_ * cL_ : rU_ * cU_;
+    const JT diffc = -dco_ * (JT)0.5 * dr * (cU_ - cL_);   // d(-dco rbar dc)/dc from rbar
+    const JT drb = dco_ * (JT)0.5 * (rL_ + rU_);
     J.mLp = t_ * rup_;
     J.mUp = -t_ * rup_;
     J.mLc = s_ * rup_ + (up ? q_ * dr : (JT)0);
     J.mUc = s_ * rup_ + (up ? (JT)0 : q_ * dr);
     J.sLp = t_ * rcup_;
     J.sUp = -t_ * rcup_;
-    J.sLc = s_ * rcup_ + (up ? q_ * ((JT)rL + dr * (JT)cL) : (JT)0) + diffc + drb;
-    J.sUc = s_ * rcup_ + (up ? (JT)0 : q_ * ((JT)rU + dr * (JT)cU)) + diffc - drb;
+    J.sLc = s_ * rcup_ + (up ? q_ * (rL_ + dr * cL_) : (JT)0) + diffc + drb;
+    J.sUc = s_ * rcup_ + (up ? (JT)0 : q_ * (rU_ + dr * cU_)) + diffc - drb;
   }
 }
 

@@ -18,6 +18,20 @@
 
 namespace henry {
 
+// Multigrid operators store the inverse of each cell's 2x2 diagonal block
+// in planes 0..3 (the off-diagonal blocks as they are): the smoother then
+// needs a 2x2 product per update instead of a determinant and a division,
+// which matters most for the FP64 multigrid on GB300's slow FP64 pipe.
+// Consumers that need the block itself invert it back (inv2).
+template <typename T>
+__device__ __forceinline__ void inv2(T a, T b, T c, T d, T& ia, T& ib, T& ic, T& id) {
+  const T r = (T)1 / (a * d - b * c);
+  ia = d * r;
+  ib = -b * r;
+  ic = -c * r;
+  id = a * r;
+}
+
 // ---------------------------------------------------------------------------
 // set-up kernels (once per solve)
 // ---------------------------------------------------------------------------
@@ -92,7 +106,8 @@ __global__ void k_face_consts(unsigned long long* ctr, Phys P, Geom G, int B,
 // Initial state c = 0; the Newton guess for p is seawater hydrostatics,
 // stored as the reduced pressure p' = p - rho0 g (Ly - y).
 __global__ void k_init_state(unsigned long long* ctr, Phys P, Geom G, int B, double* __restrict__ p,
-                             double* __restrict__ c, int* __restrict__ iters) {
+                             double* __restrict__ c, int* __restrict__ iters,
+                             int* __restrict__ step) {
   HENRY_COUNT_LAUNCH(ctr);
   const int64_t n = (int64_t)B * G.ncell();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -104,24 +119,45 @@ __global__ void k_init_state(unsigned long long* ctr, Phys P, Geom G, int B, dou
   p[idx] = P.drho * P.g * (P.Ly - y);
   c[idx] = 0.0;
   if (cell == 0) iters[b] = 0;
+  if (idx == 0) *step = 0;
 }
 
 // ---------------------------------------------------------------------------
 // per time step
 // ---------------------------------------------------------------------------
-__global__ void k_begin_step(unsigned long long* ctr, Geom G, int B, const double* __restrict__ c,
+// Start of an implicit Euler step: c_old = c^{n-1}. With `extrapolate`, from
+// the third step on (both u^{n-1} and u^{n-2} are solutions; the first
+// step's pressure guess is not) the Newton initial guess is extrapolated
+// linearly in time, u = 2 u^{n-1} - u^{n-2}, with c clamped to [0, 1]
+// (p_prev keeps p^{n-2}, c_old c^{n-2} on entry). `step` counts completed
+// steps (k_end_step increments it).
+__global__ void k_begin_step(unsigned long long* ctr, Geom G, int B, double* __restrict__ p,
+                             double* __restrict__ c, double* __restrict__ p_prev,
                              double* __restrict__ c_old, const int* __restrict__ status,
-                             int* __restrict__ active, int* __restrict__ it_step) {
+                             int* __restrict__ active, int* __restrict__ it_step,
+                             const int* __restrict__ step, int extrapolate) {
   HENRY_COUNT_LAUNCH(ctr);
   const int64_t n = (int64_t)B * G.ncell();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n) return;
-  c_old[idx] = c[idx];
+  const double cn = c[idx], pn = p[idx];
+  if (extrapolate && *step > 1) {
+    const double c2 = c_old[idx], p2 = p_prev[idx];
+    c[idx] = fmin(fmax(2.0 * cn - c2, 0.0), 1.0);
+    p[idx] = 2.0 * pn - p2;
+  }
+  c_old[idx] = cn;
+  p_prev[idx] = pn;
   const int b = (int)(idx / G.ncell());
   if (idx - (int64_t)b * G.ncell() == 0) {
     active[b] = (status[b] & (kStatusNonfinite | kStatusBadInput)) ? 0 : 1;
     it_step[b] = 0;
   }
+}
+
+__global__ void k_end_step(unsigned long long* ctr, int* __restrict__ step) {
+  HENRY_COUNT_LAUNCH(ctr);
+  if (threadIdx.x == 0) *step += 1;
 }
 
 // FP64 residual of the finest grid and its Jacobian in the multigrid type T,
@@ -284,6 +320,7 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double tau, int B, ResTile tl,
         bvec[ob + ncell + cs] = (T)(-Rc);
         xvec[ob + cs] = (T)0;
         xvec[ob + ncell + cs] = (T)0;
+        inv2<T>(Jc[0], Jc[1], Jc[2], Jc[3], Jc[0], Jc[1], Jc[2], Jc[3]);
         T* Jb = J + (int64_t)b * 20 * ncell + cs;
 #pragma unroll
         for (int m = 0; m < 20; ++m) Jb[(int64_t)m * ncell] = Jc[m];
@@ -308,7 +345,10 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double tau, int B, ResTile tl,
 
 // Per-sample convergence decision after k_resjac, one warp per sample:
 // sums the sample's partials in a fixed order, scales the RMS residual to
-// units of c per step, updates active / status / counters. Blocks add their
+// units of c per step, updates active / status / counters. A sample is
+// converged when r <= max(rtol r0, atol), or when r <= stag_tol and the
+// last iteration reduced r by less than half (the residual has reached the
+// FP64 rounding floor of the grid, which grows with resolution). Blocks add their
 // count of still-active samples to acc[0]; the last block to finish
 // (acc[1] counts finished blocks) publishes the total to *n_active, resets
 // acc for the next launch and, when SET_COND, sets the while-loop condition
@@ -320,7 +360,8 @@ __global__ void k_check(unsigned long long* ctr, int B, int nchunk, int ncell,
                         int* __restrict__ it_step, double* __restrict__ res0,
                         double* __restrict__ res_last, int* __restrict__ status,
                         int* __restrict__ iters, int* __restrict__ n_active,
-                        unsigned int* __restrict__ acc, cudaGraphConditionalHandle h) {
+                        unsigned int* __restrict__ acc, double stag_tol,
+                        cudaGraphConditionalHandle h) {
   HENRY_COUNT_LAUNCH(ctr);
   __shared__ int cnt;
   __shared__ bool last;
@@ -337,11 +378,12 @@ __global__ void k_check(unsigned long long* ctr, int B, int nchunk, int ncell,
       const double r = sqrt(s / ncell) * scale;
       const int it = it_step[b];
       if (it == 0) res0[b] = r;
+      const double prev = res_last[b];
       res_last[b] = r;
       if (!isfinite(r)) {
         status[b] |= kStatusNonfinite;
         active[b] = 0;
-      } else if (r <= fmax(rtol * res0[b], atol)) {
+      } else if (r <= fmax(rtol * res0[b], atol) || (it > 0 && r <= stag_tol && r > 0.5 * prev)) {
         active[b] = 0;
       } else if (it >= maxit) {
         status[b] |= kStatusMaxit;
@@ -425,6 +467,7 @@ k_jac(unsigned long long* ctr, Phys P, Geom G, double tau, int B, const int* __r
   double Rp, Rc;
   T Jc[20];
   cell_residual<T, true, true>(P, G, tau, in, Rp, Rc, Jc);
+  inv2<T>(Jc[0], Jc[1], Jc[2], Jc[3], Jc[0], Jc[1], Jc[2], Jc[3]);
   T* Jb = J + (int64_t)b * 20 * ncell + cs_pos(i, j, G.nx, G.half());
 #pragma unroll
   for (int m = 0; m < 20; ++m) Jb[(int64_t)m * ncell] = Jc[m];
@@ -458,6 +501,14 @@ __global__ void k_coarse_lu(unsigned long long* ctr, Geom G, int B, const int* _
         for (int v = 0; v < 2; ++v)
           A[(2 * cell + e) * ld + 2 * nb[q] + v] = (double)Jb[(int64_t)(4 * q + 2 * e + v) * nc + cs];
     }
+    double d0, d1, d2, d3;   // planes 0..3 hold the inverse diagonal block
+    inv2<double>(A[(2 * cell) * ld + 2 * cell], A[(2 * cell) * ld + 2 * cell + 1],
+                 A[(2 * cell + 1) * ld + 2 * cell], A[(2 * cell + 1) * ld + 2 * cell + 1], d0, d1,
+                 d2, d3);
+    A[(2 * cell) * ld + 2 * cell] = d0;
+    A[(2 * cell) * ld + 2 * cell + 1] = d1;
+    A[(2 * cell + 1) * ld + 2 * cell] = d2;
+    A[(2 * cell + 1) * ld + 2 * cell + 1] = d3;
   }
   __syncwarp();
   int* pv = piv + (int64_t)b * kMaxCoarseUnknowns;
@@ -541,10 +592,9 @@ __device__ __forceinline__ void smooth_cell(const Geom& G, int colour, int pos,
     rp -= Jb[16 * ncell] * vp + Jb[17 * ncell] * vc;
     rc -= Jb[18 * ncell] * vp + Jb[19 * ncell] * vc;
   }
-  const T a = Jb[0], bb = Jb[ncell], cc = Jb[2 * ncell], d = Jb[3 * ncell];
-  const T inv = (T)1 / (a * d - bb * cc);
-  x[own] = (d * rp - bb * rc) * inv;
-  x[ncell + own] = (a * rc - cc * rp) * inv;
+  // planes 0..3 hold the inverse diagonal block
+  x[own] = Jb[0] * rp + Jb[ncell] * rc;
+  x[ncell + own] = Jb[2 * ncell] * rp + Jb[3 * ncell] * rc;
 }
 
 // A x at cell (i, j).
@@ -557,8 +607,10 @@ __device__ __forceinline__ void apply_cell(const Geom& G, int i, int j, const T*
   const T* xp = x;
   const T* xc = x + ncell;
   T vp = xp[cs], vc = xc[cs];
-  ap = Jc[0] * vp + Jc[ncell] * vc;
-  ac = Jc[2 * ncell] * vp + Jc[3 * ncell] * vc;
+  T d0, d1, d2, d3;
+  inv2<T>(Jc[0], Jc[ncell], Jc[2 * ncell], Jc[3 * ncell], d0, d1, d2, d3);
+  ap = d0 * vp + d1 * vc;
+  ac = d2 * vp + d3 * vc;
   if (i > 0) {
     const int q = cs_pos(i - 1, j, nx, half);
     vp = xp[q]; vc = xc[q];
@@ -919,6 +971,269 @@ __global__ void k_reduce_pressure(Phys P, Geom G, int B, const double* __restric
   const int cell = (int)(idx % G.ncell());
   const int j = cell / G.nx;
   pr[idx] = p[idx] - P.rho0 * P.g * (P.Ly - (j + 0.5) * G.hy);
+}
+
+// ---------------------------------------------------------------------------
+// discrete adjoint through the implicit Euler steps (section 2.3 time
+// discretisation): with R^n(u^n, u^{n-1}) = 0 and Q = Q(u^r),
+//   J_r^T lam_r = dQ/du^r,   J_n^T lam_n = -(dR^{n+1}/du^n)^T lam_{n+1},
+//   dQ/dtheta = -sum_n (dR^n/dtheta)^T lam_n.
+// Vectors lam, rhs, res are FP64 [B][2][ncell] in natural cell order.
+// ---------------------------------------------------------------------------
+
+// rhs = dQ/du^r (only c enters the QoI), lam = 0. qoi 0: Q_S = int c rho
+// (integrand derivative rho0 + 2 drho c), qoi 2: toe = int c (Lx - x).
+__global__ void k_adj_seed(unsigned long long* ctr, Phys P, Geom G, int B, int qoi,
+                           const double* __restrict__ c, double* __restrict__ rhs,
+                           double* __restrict__ lam) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int n = G.ncell();
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)B * n) return;
+  const int b = (int)(idx / n), cell = (int)(idx - (int64_t)b * n);
+  const int i = cell % G.nx;
+  const double V = G.hx * G.hy;
+  const double cv = c[idx];
+  const double g = qoi == 0 ? V * (P.rho0 + 2.0 * P.drho * cv) : V * (P.Lx - (i + 0.5) * G.hx);
+  const int64_t o = (int64_t)b * 2 * n;
+  rhs[o + cell] = 0.0;
+  rhs[o + n + cell] = g;
+  lam[o + cell] = 0.0;
+  lam[o + n + cell] = 0.0;
+}
+
+// Transposed operator of one multigrid level: (J^T)_{P,Q} = (J_{Q,P})^T, so
+// P's west block is the transposed east block of its west neighbour, etc.
+// Both in the colour-split layout of type T.
+template <typename T>
+__global__ void k_transpose(unsigned long long* ctr, Geom G, int B, const int* __restrict__ active,
+                            const T* __restrict__ J, T* __restrict__ JT) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int n = G.ncell(), half = G.half(), nx = G.nx;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)B * n) return;
+  const int b = (int)(idx / n);
+  if (!active[b]) return;
+  const int cell = (int)(idx - (int64_t)b * n);
+  const int j = cell / nx, i = cell - j * nx;
+  const T* Jb = J + (int64_t)b * 20 * n;
+  T* Ob = JT + (int64_t)b * 20 * n;
+  const int cs = cs_pos(i, j, nx, half);
+  // (pp, pc, cp, cc) of the source block -> (pp, cp, pc, cc)
+  auto put = [&](int dst_m0, int src_cs, int src_m0, bool has) {
+    T a = 0, bb = 0, cc = 0, d = 0;
+    if (has) {
+      a = Jb[(int64_t)(src_m0 + 0) * n + src_cs];
+      bb = Jb[(int64_t)(src_m0 + 1) * n + src_cs];
+      cc = Jb[(int64_t)(src_m0 + 2) * n + src_cs];
+      d = Jb[(int64_t)(src_m0 + 3) * n + src_cs];
+    }
+    Ob[(int64_t)(dst_m0 + 0) * n + cs] = a;
+    Ob[(int64_t)(dst_m0 + 1) * n + cs] = cc;
+    Ob[(int64_t)(dst_m0 + 2) * n + cs] = bb;
+    Ob[(int64_t)(dst_m0 + 3) * n + cs] = d;
+  };
+  put(0, cs, 0, true);
+  put(4, i > 0 ? cs_pos(i - 1, j, nx, half) : 0, 8, i > 0);
+  put(8, i < nx - 1 ? cs_pos(i + 1, j, nx, half) : 0, 4, i < nx - 1);
+  put(12, j > 0 ? cs_pos(i, j - 1, nx, half) : 0, 16, j > 0);
+  put(16, j < G.ny - 1 ? cs_pos(i, j + 1, nx, half) : 0, 12, j < G.ny - 1);
+}
+
+// res = rhs - J^T lam with the FP64 Jacobian J64 in natural layout
+// ([B][20][ncell]); b = res in the multigrid type (colour-split), x = 0;
+// one partial sum of res^2 per block. grid = (chunks of 256 cells, B).
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+k_adj_residual(unsigned long long* ctr, Geom G, int B, const int* __restrict__ active,
+               const double* __restrict__ J64, const double* __restrict__ rhs,
+               const double* __restrict__ lam, double* __restrict__ res, T* __restrict__ bvec,
+               T* __restrict__ xvec, double* __restrict__ partial) {
+  HENRY_COUNT_LAUNCH(ctr);
+  __shared__ double sh[kBlock / 32];
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  const int n = G.ncell(), nx = G.nx;
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (cell < n) {
+    const int j = cell / nx, i = cell - j * nx;
+    const double* Jb = J64 + (int64_t)b * 20 * n;
+    const double* lp = lam + (int64_t)b * 2 * n;
+    const double* lc = lp + n;
+    double ap = 0.0, ac = 0.0;
+    // contribution of row block (Q, P)^T lam_Q
+    auto add = [&](int q, int m0) {
+      const double a = Jb[(int64_t)(m0 + 0) * n + q], bb = Jb[(int64_t)(m0 + 1) * n + q];
+      const double cc = Jb[(int64_t)(m0 + 2) * n + q], d = Jb[(int64_t)(m0 + 3) * n + q];
+      ap += a * lp[q] + cc * lc[q];
+      ac += bb * lp[q] + d * lc[q];
+    };
+    add(cell, 0);
+    if (i > 0) add(cell - 1, 8);
+    if (i < nx - 1) add(cell + 1, 4);
+    if (j > 0) add(cell - nx, 16);
+    if (j < G.ny - 1) add(cell + nx, 12);
+    const int64_t o = (int64_t)b * 2 * n;
+    const double rp = rhs[o + cell] - ap, rc = rhs[o + n + cell] - ac;
+    res[o + cell] = rp;
+    res[o + n + cell] = rc;
+    const int cs = cs_pos(i, j, nx, G.half());
+    bvec[o + cs] = (T)rp;
+    bvec[o + n + cs] = (T)rc;
+    xvec[o + cs] = (T)0;
+    xvec[o + n + cs] = (T)0;
+    v = rp * rp + rc * rc;
+  }
+  const double s = block_sum(v, sh);
+  if (threadIdx.x == 0) partial[(int64_t)b * gridDim.x + blockIdx.x] = s;
+}
+
+// lam += x (colour-split multigrid correction -> natural FP64).
+template <typename T>
+__global__ void k_adj_update(unsigned long long* ctr, Geom G, int B, const int* __restrict__ active,
+                             const T* __restrict__ xvec, double* __restrict__ lam) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int n = G.ncell();
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)B * n) return;
+  const int b = (int)(idx / n);
+  if (!active[b]) return;
+  const int cell = (int)(idx - (int64_t)b * n);
+  const int j = cell / G.nx, i = cell - j * G.nx;
+  const int cs = cs_pos(i, j, G.nx, G.half());
+  const int64_t o = (int64_t)b * 2 * n;
+  lam[o + cell] += (double)xvec[o + cs];
+  lam[o + n + cell] += (double)xvec[o + n + cs];
+}
+
+// Sensitivities of step n: gK[P] -= lam^T dR/dlogK_P, gphi[P] -= lam^T
+// dR/dphi_P, gq[j] -= lam^T dR/dq_in(j). A face's advective flux is
+// proportional to its transmissibility t = A K_f/(mu d), K_f the harmonic
+// mean, so dF/dlogK_L = F_adv K_U/(K_L + K_U); the diffusive salt flux is
+// proportional to phi_f, dphi_f/dphi_L = 2 phi_U^2/(phi_L + phi_U)^2. The
+// right side's flux is proportional to K_P, its and the left side's
+// diffusion to phi_P. Each cell evaluates its four faces itself (no
+// atomics); p is the reduced pressure.
+__global__ void k_adj_sens(unsigned long long* ctr, Phys P, Geom G, double tau, int B,
+                           const double* __restrict__ p, const double* __restrict__ c,
+                           const double* __restrict__ c_old, const double* __restrict__ phi,
+                           const double* __restrict__ K, const double* __restrict__ tx,
+                           const double* __restrict__ dx, const double* __restrict__ ty,
+                           const double* __restrict__ dy, const double* __restrict__ lam,
+                           double* __restrict__ gK, double* __restrict__ gphi,
+                           double* __restrict__ gq) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int n = G.ncell(), nx = G.nx, ny = G.ny;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)B * n) return;
+  const int b = (int)(idx / n), cell = (int)(idx - (int64_t)b * n);
+  const int j = cell / nx, i = cell - j * nx;
+  const int64_t o = (int64_t)b * n;
+  const double* lp = lam + (int64_t)b * 2 * n;
+  const double* lc = lp + n;
+  const double V = G.hx * G.hy, A = G.hy;
+  const double cP = c[o + cell], pP = p[o + cell], phP = phi[o + cell], KP = K[o + cell];
+  const double rho = P.rho0 + P.drho * cP;
+  const double cO = c_old[o + cell];
+  const double rho_o = P.rho0 + P.drho * cO;
+  double sK = 0.0, sphi = 0.0;
+  // accumulation terms
+  sphi += lp[cell] * V * (rho - rho_o) / tau + lc[cell] * V * (rho * cP - rho_o * cO) / tau;
+  // interior faces: (L, U) canonical, this cell is L (east/north) or U (west/south)
+  auto face = [&](int other, bool self_is_L, double t, double gd, double AD_d) {
+    const int q = other;
+    const double cQ = c[o + q], pQ = p[o + q], phQ = phi[o + q], KQ = K[o + q];
+    const double cL = self_is_L ? cP : cQ, cU = self_is_L ? cQ : cP;
+    const double pL = self_is_L ? pP : pQ, pU = self_is_L ? pQ : pP;
+    const double rL = P.rho0 + P.drho * cL, rU = P.rho0 + P.drho * cU;
+    const double flux = -t * ((pU - pL) + (0.5 * P.drho) * (cL + cU) * gd);
+    const bool up = flux >= 0.0;
+    const double rup = up ? rL : rU, rcup = up ? rL * cL : rU * cU;
+    const double share = KQ / (KP + KQ);
+    const double dlp = self_is_L ? lp[cell] - lp[q] : lp[q] - lp[cell];
+    const double dlc = self_is_L ? lc[cell] - lc[q] : lc[q] - lc[cell];
+    sK += (dlp * flux * rup + dlc * flux * rcup) * share;
+    const double rbar = 0.5 * (rL + rU);
+    const double dphif = 2.0 * phQ * phQ / ((phP + phQ) * (phP + phQ));
+    sphi += dlc * (-AD_d * dphif * rbar * (cU - cL));
+  };
+  const double gdy = P.g * G.hy;
+  if (i > 0) face(cell - 1, false, tx[o + cell - 1], 0.0, G.hy * P.D / G.hx);
+  if (i < nx - 1) face(cell + 1, true, tx[o + cell], 0.0, G.hy * P.D / G.hx);
+  if (j > 0) face(cell - nx, false, ty[o + cell - nx], gdy, G.hx * P.D / G.hy);
+  if (j < ny - 1) face(cell + nx, true, ty[o + cell], gdy, G.hx * P.D / G.hy);
+  const double dcoF = 2.0 * A * P.D / G.hx;   // boundary diffusion per unit phi
+  if (i == 0) {
+    const double rb = 0.5 * (rho + P.rho0);
+    sphi += lc[cell] * dcoF * rb * cP;
+    gq[(int64_t)b * ny + j] -= lp[cell] * (-A * P.rho0);
+  }
+  if (i == nx - 1) {
+    const double rho1 = P.rho0 + P.drho;
+    const double tR = 2.0 * A * KP / (P.mu * G.hx);
+    const double pb = P.drho * P.g * (P.Ly - (j + 0.5) * G.hy);
+    const double q = -tR * (pb - pP);
+    const bool up = q >= 0.0;
+    const double rup = up ? rho : rho1, rcup = up ? rho * cP : rho1;
+    sK += lp[cell] * q * rup + lc[cell] * q * rcup;
+    const double rb = 0.5 * (rho + rho1);
+    sphi += lc[cell] * (-dcoF * rb * (1.0 - cP));
+  }
+  gK[o + cell] -= sK;
+  gphi[o + cell] -= sphi;
+}
+
+// rhs for step n-1: -(dR^n/du^{n-1})^T lam^n; R^n sees u^{n-1} through
+// c_old only: dR_p/dc_old = -V phi drho / tau, dR_c/dc_old = -V phi
+// (rho(c_old) + drho c_old) / tau.
+__global__ void k_adj_prev_rhs(unsigned long long* ctr, Phys P, Geom G, double tau, int B,
+                               const double* __restrict__ phi, const double* __restrict__ c_old,
+                               const double* __restrict__ lam, double* __restrict__ rhs) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int n = G.ncell();
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)B * n) return;
+  const int b = (int)(idx / n), cell = (int)(idx - (int64_t)b * n);
+  const int64_t o = (int64_t)b * 2 * n;
+  const double vt = G.hx * G.hy * phi[idx] / tau;
+  const double co = c_old[idx];
+  rhs[o + cell] = 0.0;
+  rhs[o + n + cell] = vt * (P.drho * lam[o + cell] + (P.rho0 + 2.0 * P.drho * co) * lam[o + n + cell]);
+}
+
+// dQ/dxi from the per-cell and per-row sensitivities (fields of k_fields);
+// one block per sample.
+__global__ void __launch_bounds__(kBlock)
+k_adj_contract(unsigned long long* ctr, Phys P, Geom G, int B, int n_xi,
+               const double* __restrict__ gK, const double* __restrict__ gphi,
+               const double* __restrict__ gq, double* __restrict__ dq_dxi) {
+  HENRY_COUNT_LAUNCH(ctr);
+  __shared__ double sh[kBlock / 32];
+  const int b = blockIdx.x;
+  const int n = G.ncell();
+  const double pi = 3.14159265358979323846;
+  double s[6] = {0, 0, 0, 0, 0, 0};
+  for (int cell = threadIdx.x; cell < n; cell += blockDim.x) {
+    const int j = cell / G.nx, i = cell - j * G.nx;
+    const double x = (i + 0.5) * G.hx, y = (j + 0.5) * G.hy;
+    const double gp = gphi[(int64_t)b * n + cell], gk = gK[(int64_t)b * n + cell];
+    s[0] += gp * P.phi0 * 0.1 * cos(0.5 * pi * x) * sin(pi * y);
+    s[1] += gk * 0.5 * sin(0.5 * pi * x) * cos(pi * y);
+    if (n_xi >= 6) {
+      s[3] += gp * P.phi0 * 0.05 * cos(pi * x) * sin(2.0 * pi * y);
+      s[4] += gk * 0.05 * sin(pi * x) * cos(2.0 * pi * y);
+    }
+  }
+  for (int j = threadIdx.x; j < G.ny; j += blockDim.x) {
+    const double gv = gq[(int64_t)b * G.ny + j];
+    s[2] += gv * P.q0 * 0.1;
+    if (n_xi >= 6) s[5] += gv * P.q0 * 0.05 * cos(pi * (j + 0.5) * G.hy);
+  }
+  for (int k = 0; k < n_xi; ++k) {
+    const double t = block_sum(s[k], sh);
+    if (threadIdx.x == 0) dq_dxi[(int64_t)b * n_xi + k] = t;
+  }
 }
 
 }  // namespace henry

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 
 #include "kernels.cuh"
 
@@ -25,6 +26,21 @@ size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
       return e_ == cudaErrorMemoryAllocation ? HENRY_E_NOMEM : HENRY_E_CUDA;      \
     }                                                                              \
   } while (0)
+
+__global__ void k_activate(unsigned long long* ctr, int B, const int* __restrict__ status,
+                           int* __restrict__ active, int* __restrict__ it_step) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B) {
+    active[b] = (status[b] & (kStatusNonfinite | kStatusBadInput)) ? 0 : 1;
+    it_step[b] = 0;
+  }
+}
+
+__global__ void k_set_int(unsigned long long* ctr, int* __restrict__ dst, int v) {
+  HENRY_COUNT_LAUNCH(ctr);
+  if (threadIdx.x == 0) *dst = v;
+}
 
 __global__ void k_copy_int(unsigned long long* ctr, int n, const int* __restrict__ src,
                            int* __restrict__ dst, int do_or) {
@@ -75,6 +91,9 @@ void Solver::free_all() {
   step_graph_ = nullptr;
   graph_B_ = -1;
   if (arena_) cudaFree(arena_);
+  if (adj_arena_) cudaFree(adj_arena_);
+  adj_arena_ = nullptr;
+  adj_B_ = adj_nckpt_ = adj_seg_ = 0;
   if (n_active_host_) cudaFreeHost(n_active_host_);
   arena_ = nullptr;
   n_active_host_ = nullptr;
@@ -131,6 +150,8 @@ int Solver::ensure(int B, cudaStream_t s) {
   }
   const Geom& F = levels_.back().g;
   const size_t o_cold = take((size_t)F.ncell() * Bz * 8);
+  const size_t o_pprev = take((size_t)F.ncell() * Bz * 8);
+  const size_t o_step = take(8);
   const size_t o_qin = take((size_t)F.ny * Bz * 8);
   const size_t o_part = take((size_t)nchunk_ * Bz * 8);
   const size_t o_res0 = take(Bz * 8);
@@ -164,6 +185,8 @@ int Solver::ensure(int B, cudaStream_t s) {
     L.qy = (double*)(a + lo[k].qy);
   }
   c_old_ = (double*)(a + o_cold);
+  p_prev_ = (double*)(a + o_pprev);
+  step_ = (int*)(a + o_step);
   qin_ = (double*)(a + o_qin);
   partial_ = (double*)(a + o_part);
   res0_ = (double*)(a + o_res0);
@@ -234,9 +257,10 @@ void Solver::enqueue_vcycle(int k, int B, cudaStream_t s) {
                                        (const T*)L.b, (T*)L.x);
 }
 
-// Multigrid operators at the current iterate, V-cycles, state update.
+// Coarse multigrid operators at the current iterate (linearised about the
+// restricted face fluxes).
 template <typename T>
-void Solver::enqueue_iteration(int B, cudaStream_t s) {
+void Solver::enqueue_coarse_ops(int B, cudaStream_t s) {
   const int nl = (int)levels_.size();
   for (int k = nl - 1; k >= 1; --k) {
     MGLevel& F = levels_[k];
@@ -247,6 +271,10 @@ void Solver::enqueue_iteration(int B, cudaStream_t s) {
         counter_, phys_, C.g, tau_, B, active_, C.p, C.c, C.phi, C.K, C.tx, C.dx, C.ty, C.dy,
         C.qx, C.qy, (T*)C.J);
   }
+}
+
+template <typename T>
+void Solver::enqueue_lu(int B, cudaStream_t s) {
   {
     const int n = 2 * levels_[0].g.ncell();
     const size_t per_warp = (size_t)n * (n + 1) * sizeof(double);
@@ -255,10 +283,23 @@ void Solver::enqueue_iteration(int B, cudaStream_t s) {
     k_coarse_lu<T><<<(B + wpb - 1) / wpb, 32 * wpb, per_warp * wpb, s>>>(
         counter_, levels_[0].g, B, active_, (const T*)levels_[0].J, lu_, piv_);
   }
+}
+
+template <typename T>
+void Solver::enqueue_vcycles(int B, cudaStream_t s) {
+  const int nl = (int)levels_.size();
   if (ks_ == nl - 1 && nl > 1)
     launch_small<T>(B, cfg_.vcycles, s);
   else
     for (int v = 0; v < cfg_.vcycles; ++v) enqueue_vcycle<T>(nl - 1, B, s);
+}
+
+// Multigrid operators at the current iterate, V-cycles, state update.
+template <typename T>
+void Solver::enqueue_iteration(int B, cudaStream_t s) {
+  enqueue_coarse_ops<T>(B, s);
+  enqueue_lu<T>(B, s);
+  enqueue_vcycles<T>(B, s);
   MGLevel& F = levels_.back();
   k_update<T><<<grid1((int64_t)B * F.g.ncell()), kBlock, 0, s>>>(counter_, F.g, B, active_,
                                                                  (const T*)F.x, F.p, F.c);
@@ -274,17 +315,18 @@ void Solver::enqueue_resjac_check(int B, cudaStream_t s, bool set_cond) {
   // residual scaled to units of c per step: RMS(R) * tau / (V phi0 rho0)
   const double scale = tau_ / (G.hx * G.hy * cfg_.phi0 * cfg_.rho0);
   const int gb = (B + 7) / 8;
+  const double stag_tol = cfg_.newton_stag_tol;
   if (set_cond)
     k_check<true><<<gb, kBlock, 0, s>>>(counter_, B, nchunk_, G.ncell(), partial_, scale,
                                         cfg_.newton_rtol, cfg_.newton_atol, cfg_.newton_maxit,
                                         active_, it_step_, res0_, res_last_, status_w_, iters_w_,
-                                        n_active_, check_acc_,
+                                        n_active_, check_acc_, stag_tol,
                                         (cudaGraphConditionalHandle)cond_handle_);
   else
     k_check<false><<<gb, kBlock, 0, s>>>(counter_, B, nchunk_, G.ncell(), partial_, scale,
                                          cfg_.newton_rtol, cfg_.newton_atol, cfg_.newton_maxit,
                                          active_, it_step_, res0_, res_last_, status_w_, iters_w_,
-                                         n_active_, check_acc_, 0);
+                                         n_active_, check_acc_, stag_tol, 0);
 }
 
 // One implicit Euler step as a CUDA graph: begin, residual + check, then a
@@ -307,7 +349,8 @@ int Solver::step_graph(int B, cudaStream_t s) {
     CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     MGLevel& F = levels_.back();
     k_begin_step<<<grid1((int64_t)B * F.g.ncell()), kBlock, 0, cs>>>(
-        counter_, F.g, B, F.c, c_old_, status_w_, active_, it_step_);
+        counter_, F.g, B, F.p, F.c, p_prev_, c_old_, status_w_, active_, it_step_, step_,
+        cfg_.guess_extrapolation);
     enqueue_resjac_check<T>(B, cs, true);
     cudaStreamCaptureStatus st;
     cudaGraph_t cg;
@@ -323,6 +366,7 @@ int Solver::step_graph(int B, cudaStream_t s) {
     CK(cudaGraphAddNode(&wn, cg, deps, nullptr, nd, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     CK(cudaStreamUpdateCaptureDependencies(cs, &wn, nullptr, 1, cudaStreamSetCaptureDependencies));
+    k_end_step<<<1, 32, 0, cs>>>(counter_, step_);
     CK(cudaStreamEndCapture(cs, &g));
     CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     enqueue_iteration<T>(B, bs);
@@ -351,8 +395,7 @@ int Solver::fields(const double* xi, const double* logk, int B, double* phi, dou
 }
 
 template <typename T>
-int Solver::run_t(const double* xi, const double* logk, int B, double* q, double* c_out,
-                  double* p_out, int* status, int* iters, int status_or, cudaStream_t s) {
+int Solver::setup_t(const double* xi, const double* logk, int B, cudaStream_t s) {
   const int nl = (int)levels_.size();
   MGLevel& F = levels_.back();
   const Geom& G = F.g;
@@ -368,24 +411,42 @@ int Solver::run_t(const double* xi, const double* logk, int B, double* q, double
         counter_, phys_, L.g, B, L.phi, L.K, L.tx, L.dx, L.ty, L.dy);
   }
   k_init_state<<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(counter_, phys_, G, B, F.p, F.c,
-                                                                iters_w_);
+                                                                iters_w_, step_);
   CK(cudaGetLastError());
-  for (int n = 0; n < nt_; ++n) {
-    if (cfg_.loop_mode == HENRY_LOOP_GRAPH) {
-      int rc = step_graph<T>(B, s);
-      if (rc) return rc;
-      continue;
-    }
-    k_begin_step<<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(counter_, G, B, F.c, c_old_,
-                                                                  status_w_, active_, it_step_);
-    for (;;) {
-      enqueue_resjac_check<T>(B, s, false);
-      CK(cudaMemcpyAsync(n_active_host_, n_active_, sizeof(int), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      if (*n_active_host_ == 0) break;
-      enqueue_iteration<T>(B, s);
-    }
+  return HENRY_OK;
+}
+
+// One implicit Euler step of every sample (Newton defect correction).
+template <typename T>
+int Solver::step_t(int B, cudaStream_t s) {
+  if (cfg_.loop_mode == HENRY_LOOP_GRAPH) return step_graph<T>(B, s);
+  MGLevel& F = levels_.back();
+  const Geom& G = F.g;
+  k_begin_step<<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(
+      counter_, G, B, F.p, F.c, p_prev_, c_old_, status_w_, active_, it_step_, step_,
+      cfg_.guess_extrapolation);
+  for (;;) {
+    enqueue_resjac_check<T>(B, s, false);
+    CK(cudaMemcpyAsync(n_active_host_, n_active_, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (*n_active_host_ == 0) break;
+    enqueue_iteration<T>(B, s);
   }
+  k_end_step<<<1, 32, 0, s>>>(counter_, step_);
+  return HENRY_OK;
+}
+
+template <typename T>
+int Solver::run_t(const double* xi, const double* logk, int B, double* q, double* c_out,
+                  double* p_out, int* status, int* iters, int status_or, cudaStream_t s) {
+  int rc = setup_t<T>(xi, logk, B, s);
+  if (rc) return rc;
+  for (int n = 0; n < nt_; ++n) {
+    rc = step_t<T>(B, s);
+    if (rc) return rc;
+  }
+  MGLevel& F = levels_.back();
+  const Geom& G = F.g;
   k_qoi<<<B, kBlock, 0, s>>>(counter_, phys_, G, B, F.p, F.c, F.phi, q, c_out, p_out);
   k_copy_int<<<grid1(B), kBlock, 0, s>>>(counter_, B, status_w_, status, status_or);
   if (iters) k_copy_int<<<grid1(B), kBlock, 0, s>>>(counter_, B, iters_w_, iters, 0);
@@ -408,8 +469,9 @@ void Solver::launch_timed(int which, int B, cudaStream_t s) {
 
 // Algorithmic counts per launch (each array read or written once):
 //  smoother half-sweep, per updated cell: J 20, b 2, x write 2, neighbour x
-//    read 2 values of the type T; FP ops: 16 neighbour products (FMA) + 2x2
-//    solve (6 mul/sub + 1 rcp + 4 mul) = 32 + 2 + 11 ~ 45 FLOP.
+//    read 2 values of the type T; FP ops: 16 neighbour products (FMA, 32
+//    FLOP) + the product with the stored inverse diagonal block (2 mul + 2
+//    FMA, 6 FLOP) = 38 FLOP.
 //  residual + Jacobian, per cell: p, c, c_old, phi, tx, dx, ty, dy read (8
 //    doubles), b 2, x 2, J 20 of type T and qx, qy (2 doubles) written;
 //    FP ops counted from the face-based code: 2 faces x 15 (flux) + 16
@@ -444,7 +506,7 @@ int Solver::time_kernel(int which, int reps, cudaStream_t s, double* avg_ms, dou
   if (which == 0) {
     const double cells = (double)B * G.half();
     *bytes = cells * 26.0 * T;
-    *flops = cells * 45.0;
+    *flops = cells * 38.0;
   } else {
     const double cells = (double)B * G.ncell();
     *bytes = cells * (8.0 * 8 + 24.0 * T + 16.0);
@@ -463,6 +525,180 @@ int Solver::run(const double* xi, const double* logk, int B, double* q, double* 
   if (tsize_ == sizeof(float))
     return run_t<float>(xi, logk, B, q, c_out, p_out, status, iters, status_or, s);
   return run_t<double>(xi, logk, B, q, c_out, p_out, status, iters, status_or, s);
+}
+
+// ---------------------------------------------------------------------------
+// discrete adjoint (see henry_adjoint)
+// ---------------------------------------------------------------------------
+int Solver::ensure_adjoint(int B, int nckpt, int seglen) {
+  if (adj_arena_ && B <= adj_B_ && nckpt <= adj_nckpt_ && seglen <= adj_seg_) return HENRY_OK;
+  CK(cudaDeviceSynchronize());
+  if (adj_arena_) cudaFree(adj_arena_);
+  adj_arena_ = nullptr;
+  const Geom& F = levels_.back().g;
+  const size_t n = (size_t)F.ncell() * B;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+  const size_t o_ck = take((size_t)nckpt * 4 * n * 8);
+  const size_t o_sg = take((size_t)(seglen + 1) * 2 * n * 8);
+  const size_t o_j64 = take(20 * n * 8);
+  const size_t o_lam = take(2 * n * 8);
+  const size_t o_rhs = take(2 * n * 8);
+  const size_t o_res = take(2 * n * 8);
+  const size_t o_gk = take(n * 8);
+  const size_t o_gp = take(n * 8);
+  const size_t o_gq = take((size_t)F.ny * B * 8);
+  const size_t o_qt = take((size_t)B * kNQ * 8);
+  adj_nchunk_ = (F.ncell() + kBlock - 1) / kBlock;
+  const size_t o_p2 = take((size_t)adj_nchunk_ * B * 8);
+  std::vector<size_t> o_jt(levels_.size());
+  for (size_t k = 0; k < levels_.size(); ++k)
+    o_jt[k] = take(20 * (size_t)levels_[k].g.ncell() * B * tsize_);
+  CK(cudaMalloc(&adj_arena_, off));
+  char* a = (char*)adj_arena_;
+  ckpt_ = (double*)(a + o_ck);
+  seg_ = (double*)(a + o_sg);
+  J64_ = (double*)(a + o_j64);
+  lam_ = (double*)(a + o_lam);
+  rhs_ = (double*)(a + o_rhs);
+  res_ = (double*)(a + o_res);
+  gK_ = (double*)(a + o_gk);
+  gphi_ = (double*)(a + o_gp);
+  gq_ = (double*)(a + o_gq);
+  qtmp_ = (double*)(a + o_qt);
+  partial2_ = (double*)(a + o_p2);
+  JT_.resize(levels_.size());
+  for (size_t k = 0; k < levels_.size(); ++k) JT_[k] = a + o_jt[k];
+  adj_B_ = B;
+  adj_nckpt_ = nckpt;
+  adj_seg_ = seglen;
+  return HENRY_OK;
+}
+
+template <typename T>
+int Solver::adjoint_t(const double* xi, const double* logk, int B, int qoi, int kc, double* q,
+                      double* dq_dxi, double* dq_dlogk, int* status, cudaStream_t s) {
+  MGLevel& F = levels_.back();
+  const Geom& G = F.g;
+  const size_t n = (size_t)G.ncell() * B;   // doubles per state component
+  const int nfull = nt_ / kc;
+  const int nck = nfull + 1 + (nt_ % kc ? 1 : 0);
+  auto slot_step = [&](int m) { return m <= nfull ? m * kc : nt_; };
+  int rc = ensure_adjoint(B, nck, kc);
+  if (rc) return rc;
+  // a checkpoint holds u^m and u^{m-1} (the latter feeds the extrapolated
+  // Newton guess of the next step), so recomputed steps are bitwise the
+  // forward's; segment states keep u^n only
+  auto save = [&](double* dst, bool full) -> int {
+    CK(cudaMemcpyAsync(dst, F.p, n * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(dst + n, F.c, n * 8, cudaMemcpyDeviceToDevice, s));
+    if (full) {
+      CK(cudaMemcpyAsync(dst + 2 * n, p_prev_, n * 8, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(dst + 3 * n, c_old_, n * 8, cudaMemcpyDeviceToDevice, s));
+    }
+    return HENRY_OK;
+  };
+  auto ck = [&](int m) { return ckpt_ + (size_t)m * 4 * n; };
+  // forward with checkpoints
+  rc = setup_t<T>(xi, logk, B, s);
+  if (rc) return rc;
+  if ((rc = save(ck(0), true))) return rc;
+  for (int st = 1; st <= nt_; ++st) {
+    if ((rc = step_t<T>(B, s))) return rc;
+    if (st % kc == 0) { if ((rc = save(ck(st / kc), true))) return rc; }
+    else if (st == nt_) { if ((rc = save(ck(nck - 1), true))) return rc; }
+  }
+  k_qoi<<<B, kBlock, 0, s>>>(counter_, phys_, G, B, F.p, F.c, F.phi, qtmp_, nullptr, nullptr);
+  CK(cudaMemcpy2DAsync(q, sizeof(double), qtmp_ + qoi, kNQ * sizeof(double), sizeof(double), B,
+                       cudaMemcpyDeviceToDevice, s));
+  // seed and zero the sensitivities
+  k_adj_seed<<<grid1((int64_t)n), kBlock, 0, s>>>(counter_, phys_, G, B, qoi, F.c, rhs_, lam_);
+  CK(cudaMemsetAsync(gK_, 0, n * 8, s));
+  CK(cudaMemsetAsync(gphi_, 0, n * 8, s));
+  CK(cudaMemsetAsync(gq_, 0, (size_t)G.ny * B * 8, s));
+  const double adj_rtol = 1e-11;
+  for (int m = nck - 2; m >= 0; --m) {
+    const int n0 = slot_step(m), n1 = slot_step(m + 1);
+    // recompute the segment's states from its checkpoint (bitwise the forward's)
+    CK(cudaMemcpyAsync(F.p, ck(m), n * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(F.c, ck(m) + n, n * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(p_prev_, ck(m) + 2 * n, n * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c_old_, ck(m) + 3 * n, n * 8, cudaMemcpyDeviceToDevice, s));
+    k_set_int<<<1, 32, 0, s>>>(counter_, step_, n0);
+    if ((rc = save(seg_, false))) return rc;
+    for (int st = n0 + 1; st <= n1; ++st) {
+      if ((rc = step_t<T>(B, s))) return rc;
+      if ((rc = save(seg_ + (size_t)(st - n0) * 2 * n, false))) return rc;
+    }
+    for (int st = n1; st > n0; --st) {
+      const double* u = seg_ + (size_t)(st - n0) * 2 * n;
+      const double* uprev = seg_ + (size_t)(st - n0 - 1) * 2 * n;
+      CK(cudaMemcpyAsync(F.p, u, n * 8, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(F.c, u + n, n * 8, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(c_old_, uprev + n, n * 8, cudaMemcpyDeviceToDevice, s));
+      k_activate<<<grid1(B), kBlock, 0, s>>>(counter_, B, status_w_, active_, it_step_);
+      // operators of step st: J (multigrid type, every level) and exact FP64 J
+      k_resjac<T, false><<<dim3(nchunk_, B), kBlock, 0, s>>>(
+          counter_, phys_, G, tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx, F.ty, F.dy,
+          qin_, active_, (T*)F.J, (T*)F.b, (T*)F.x, partial_, F.qx, F.qy);
+      k_resjac<double, true><<<dim3(nchunk_, B), kBlock, 0, s>>>(
+          counter_, phys_, G, tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx, F.ty, F.dy,
+          qin_, active_, J64_, res_, nullptr, nullptr, nullptr, nullptr);
+      enqueue_coarse_ops<T>(B, s);
+      for (size_t k = 0; k < levels_.size(); ++k)
+        k_transpose<T><<<grid1((int64_t)B * levels_[k].g.ncell()), kBlock, 0, s>>>(
+            counter_, levels_[k].g, B, active_, (const T*)levels_[k].J, (T*)JT_[k]);
+      // the multigrid cycles below read the transposed operators
+      for (size_t k = 0; k < levels_.size(); ++k) std::swap(levels_[k].J, JT_[k]);
+      enqueue_lu<T>(B, s);
+      CK(cudaMemsetAsync(lam_, 0, 2 * n * 8, s));
+      for (;;) {
+        k_adj_residual<T><<<dim3(adj_nchunk_, B), kBlock, 0, s>>>(
+            counter_, G, B, active_, J64_, rhs_, lam_, res_, (T*)F.b, (T*)F.x, partial2_);
+        k_check<false><<<(B + 7) / 8, kBlock, 0, s>>>(
+            counter_, B, adj_nchunk_, G.ncell(), partial2_, 1.0, adj_rtol, 0.0, cfg_.newton_maxit,
+            active_, it_step_, res0_, res_last_, status_w_, iters_w_, n_active_, check_acc_, 0.0, 0);
+        CK(cudaMemcpyAsync(n_active_host_, n_active_, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (*n_active_host_ == 0) break;
+        enqueue_vcycles<T>(B, s);
+        k_adj_update<T><<<grid1((int64_t)n), kBlock, 0, s>>>(counter_, G, B, active_,
+                                                             (const T*)F.x, lam_);
+      }
+      for (size_t k = 0; k < levels_.size(); ++k) std::swap(levels_[k].J, JT_[k]);
+      k_adj_sens<<<grid1((int64_t)n), kBlock, 0, s>>>(counter_, phys_, G, tau_, B, F.p, F.c, c_old_,
+                                                      F.phi, F.K, F.tx, F.dx, F.ty, F.dy, lam_, gK_,
+                                                      gphi_, gq_);
+      if (st > 1)
+        k_adj_prev_rhs<<<grid1((int64_t)n), kBlock, 0, s>>>(counter_, phys_, G, tau_, B, F.phi,
+                                                            c_old_, lam_, rhs_);
+    }
+  }
+  k_adj_contract<<<B, kBlock, 0, s>>>(counter_, phys_, G, B, cfg_.n_xi, gK_, gphi_, gq_, dq_dxi);
+  if (dq_dlogk) CK(cudaMemcpyAsync(dq_dlogk, gK_, n * 8, cudaMemcpyDeviceToDevice, s));
+  k_copy_int<<<grid1(B), kBlock, 0, s>>>(counter_, B, status_w_, status, 0);
+  CK(cudaGetLastError());
+  return HENRY_OK;
+}
+
+int Solver::adjoint(const double* xi, const double* logk, int B, int qoi, int ckpt_every,
+                    double* q, double* dq_dxi, double* dq_dlogk, int* status, cudaStream_t s) {
+  if (B == 0) return HENRY_OK;
+  int rc = ensure(B, s);
+  if (rc) return rc;
+  last_B_ = B;
+  const int kc = ckpt_every < 1 ? 1 : (ckpt_every > nt_ ? nt_ : ckpt_every);
+  if (tsize_ == sizeof(float))
+    return adjoint_t<float>(xi, logk, B, qoi, kc, q, dq_dxi, dq_dlogk, status, s);
+  return adjoint_t<double>(xi, logk, B, qoi, kc, q, dq_dxi, dq_dlogk, status, s);
+}
+
+// dst[b] |= src[b] on stream s (status of the coarse half of a pair).
+int or_status(const int* src, int* dst, int B, unsigned long long* ctr, cudaStream_t s) {
+  if (B == 0) return HENRY_OK;
+  k_copy_int<<<grid1(B), kBlock, 0, s>>>(ctr, B, src, dst, 1);
+  CK(cudaGetLastError());
+  return HENRY_OK;
 }
 
 cudaError_t launch_residual_jacobian(const Phys& P, const Geom& G, double tau, int B,

@@ -49,6 +49,9 @@ class Solver {
   // per-sample status into `status` instead of overwriting it.
   int run(const double* xi, const double* logk, int B, double* q, double* c_out, double* p_out,
           int* status, int* iters, int status_or, cudaStream_t s);
+  // Discrete adjoint of QoI `qoi` (0 Q_S, 2 toe); see henry_adjoint.
+  int adjoint(const double* xi, const double* logk, int B, int qoi, int ckpt_every, double* q,
+              double* dq_dxi, double* dq_dlogk, int* status, cudaStream_t s);
   // Fields only (henry_fields).
   int fields(const double* xi, const double* logk, int B, double* phi, double* K, double* qin,
              cudaStream_t s);
@@ -68,6 +71,11 @@ class Solver {
   template <typename T> int run_t(const double* xi, const double* logk, int B, double* q,
                                   double* c_out, double* p_out, int* status, int* iters,
                                   int status_or, cudaStream_t s);
+  template <typename T> int setup_t(const double* xi, const double* logk, int B, cudaStream_t s);
+  template <typename T> int step_t(int B, cudaStream_t s);
+  template <typename T> void enqueue_coarse_ops(int B, cudaStream_t s);
+  template <typename T> void enqueue_lu(int B, cudaStream_t s);
+  template <typename T> void enqueue_vcycles(int B, cudaStream_t s);
   template <typename T> void enqueue_iteration(int B, cudaStream_t s);
   template <typename T> void enqueue_vcycle(int k, int B, cudaStream_t s);
   template <typename T> void enqueue_resjac_check(int B, cudaStream_t s, bool set_cond);
@@ -75,6 +83,10 @@ class Solver {
   template <typename T> void launch_timed(int which, int B, cudaStream_t s);
   template <typename T> void launch_small(int B, int ncycles, cudaStream_t s);
   int ensure(int B, cudaStream_t s);
+  int ensure_adjoint(int B, int nckpt, int seglen);
+  template <typename T> int adjoint_t(const double* xi, const double* logk, int B, int qoi, int kc,
+                                      double* q, double* dq_dxi, double* dq_dlogk, int* status,
+                                      cudaStream_t s);
   void free_all();
 
   henry_config cfg_;
@@ -89,6 +101,8 @@ class Solver {
   void* arena_ = nullptr;
   // finest-level / per-sample arrays
   double* c_old_ = nullptr;
+  double* p_prev_ = nullptr;    // p of the previous step (initial-guess extrapolation)
+  int* step_ = nullptr;         // completed steps of the current solve (device)
   double* qin_ = nullptr;
   double* partial_ = nullptr;
   double* res0_ = nullptr;
@@ -112,6 +126,13 @@ class Solver {
   cudaGraph_t step_graph_ = nullptr;
   int graph_B_ = -1;
   unsigned long long cond_handle_ = 0;
+  // adjoint workspace (allocated on the first henry_adjoint call)
+  void* adj_arena_ = nullptr;
+  int adj_B_ = 0, adj_nckpt_ = 0, adj_seg_ = 0, adj_nchunk_ = 0;
+  double *ckpt_ = nullptr, *seg_ = nullptr, *J64_ = nullptr, *lam_ = nullptr, *rhs_ = nullptr;
+  double *res_ = nullptr, *gK_ = nullptr, *gphi_ = nullptr, *gq_ = nullptr, *qtmp_ = nullptr;
+  double* partial2_ = nullptr;
+  std::vector<void*> JT_;     // transposed operators per multigrid level
 };
 
 void set_last_error(const std::string& msg);

@@ -187,6 +187,12 @@ def run(sampler, L, eps, qois=(3, 4, 5), pilot=None, max_batch=None, var_budget_
                 need -= cnt
         levels = _merge_ranks(local, dist)
         V = np.array([[lv.var_d()[q] for q in qs] for lv in levels])          # [L+1, nq]
+        bad = [l for l in range(L + 1) if not np.all(np.isfinite(V[l]))]
+        if bad:
+            raise RuntimeError(
+                f"MLMC: no variance estimate on level(s) {bad} "
+                f"(valid samples {[levels[l].n for l in bad]}, failed "
+                f"{[levels[l].failed for l in bad]}); the solves of these levels did not converge")
         s = np.array([max(lv.seconds, 1e-9) / max(lv.timed_pairs, 1) for lv in levels])
         m = np.max(np.stack([allocate(V[:, k], s, eps, var_budget_fraction)
                              for k in range(len(qs))]), axis=0)

@@ -37,7 +37,7 @@ def oracle_solve(cfg, level, xi):
 
 def tight_config(**kw):
     """Config whose Newton tolerance sits well below the parity bar."""
-    base = dict(newton_rtol=1e-12, newton_atol=3e-13, newton_maxit=60)
+    base = dict(newton_rtol=1e-12, newton_atol=3e-13, newton_maxit=60, newton_stag_tol=1e-11)
     base.update(kw)
     return hb.default_config(**base)
 

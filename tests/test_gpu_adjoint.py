@@ -1,0 +1,88 @@
+"""Discrete adjoint on the GPU (henry_adjoint) against the oracle's adjoint,
+central finite differences of the GPU forward, and checkpoint-interval
+invariance; the torch.autograd wrapper returns the same gradient."""
+import numpy as np
+import pytest
+
+from oracle import adjoint as A
+from oracle import henry as H
+from paper_2403_17018_gb300 import binding as hb
+from paper_2403_17018_gb300.inputs import logk_perturbation, xi_batch
+
+from gpu_helpers import oracle_physics, tight_config
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    hb.load()
+
+
+def _small_cfg(**kw):
+    # 16x8 cells, 5 steps of 3600 s: the oracle adjoint takes ~1 s per sample
+    return tight_config(nx0=16, ny0=8, nt0=5, T=5 * 3600.0, nlevels=1, **kw)
+
+
+@pytest.mark.parametrize("precision", [hb.PREC_FP64, hb.PREC_FP32_MG])
+@pytest.mark.parametrize("qoi", ["Q_S", "toe"])
+def test_adjoint_matches_oracle_adjoint(precision, qoi):
+    cfg = _small_cfg(precision=precision)
+    ctx = hb.Context(cfg)
+    B = 3
+    xi = torch.from_numpy(xi_batch(0, 20, B)).cuda()
+    lk = torch.from_numpy(logk_perturbation(8, 16, B)).cuda()
+    q, g, gl, st = ctx.adjoint(0, xi, lk, qoi=qoi, ckpt_every=2)
+    assert st.cpu().numpy().tolist() == [0] * B
+    ph = oracle_physics(cfg)
+    grid = H.Grid(nx=16, ny=8, nt=5, T=5 * 3600.0)
+    for b in range(B):
+        o = A.adjoint(grid, ph, xi[b].cpu().numpy(), qoi, lk[b].cpu().numpy())
+        assert abs(q[b].item() - o["q"]) <= 1e-9 * abs(o["q"])
+        gs = np.max(np.abs(o["dq_dxi"]))
+        assert np.max(np.abs(g[b].cpu().numpy() - o["dq_dxi"])) <= 1e-8 * gs
+        ls = np.max(np.abs(o["dq_dlogk"]))
+        assert np.max(np.abs(gl[b].cpu().numpy() - o["dq_dlogk"])) <= 1e-8 * ls
+
+
+def test_checkpoint_interval_does_not_change_the_gradient():
+    cfg = _small_cfg()
+    ctx = hb.Context(cfg)
+    xi = torch.from_numpy(xi_batch(0, 30, 2)).cuda()
+    ref = ctx.adjoint(0, xi, qoi="toe", ckpt_every=1)
+    for k in (2, 3, 5):
+        out = ctx.adjoint(0, xi, qoi="toe", ckpt_every=k)
+        assert torch.equal(out[0], ref[0]) and torch.equal(out[1], ref[1]) and torch.equal(out[2], ref[2])
+
+
+def test_adjoint_matches_central_differences_of_the_gpu_forward():
+    """Level 0 at full size (32x16, 24 steps), h = 1e-4 in each xi."""
+    cfg = tight_config(nlevels=1)
+    ctx = hb.Context(cfg)
+    xi = torch.from_numpy(xi_batch(0, 40, 2)).cuda()
+    q, g, _, st = ctx.adjoint(0, xi, qoi="Q_S", ckpt_every=8, want_logk=False)
+    assert st.cpu().numpy().tolist() == [0, 0]
+    h = 1e-4
+    for j in range(3):
+        e = torch.zeros_like(xi)
+        e[:, j] = h
+        qp = ctx.solve(0, (xi + e).contiguous())["q"][:, 0]
+        qm = ctx.solve(0, (xi - e).contiguous())["q"][:, 0]
+        fd = ((qp - qm) / (2 * h)).cpu().numpy()
+        gj = g[:, j].cpu().numpy()
+        scale = np.max(np.abs(g.cpu().numpy()), axis=1)
+        assert np.all(np.abs(gj - fd) <= 1e-5 * scale), (j, gj, fd)
+
+
+def test_autograd_function_returns_the_adjoint_gradient():
+    cfg = _small_cfg()
+    ctx = hb.Context(cfg)
+    xi = torch.from_numpy(xi_batch(0, 50, 2)).cuda().requires_grad_(True)
+    q = hb.henry_qoi(ctx, 0, xi, qoi="Q_S", ckpt_every=2)
+    w = torch.tensor([0.5, -2.0], dtype=torch.float64, device="cuda")
+    (q * w).sum().backward()
+    _, g, _, _ = ctx.adjoint(0, xi.detach(), qoi="Q_S", want_logk=False)
+    assert torch.allclose(xi.grad, w[:, None] * g, rtol=0, atol=0)

@@ -1,0 +1,19 @@
+"""The autotuner times candidate multigrid schedules on a short solve and
+returns the fastest one that converged."""
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def test_tune_level_returns_a_converging_schedule(tmp_path):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2403_17018_gb300 import autotune as A
+    best, table = A.tune_level(0, 64, "fp32mg", steps=2, reps=1, splits=(1, 2))
+    assert len(table) == 3 * 3 * 2
+    assert best["failed"] == 0 and best["solves_per_s"] > 0
+    assert best["solves_per_s"] == max(r["solves_per_s"] for r in table if r["failed"] == 0)
+    path = str(tmp_path / "cache.json")
+    A.save_cache({"k": best}, path)
+    assert A.load_cache(path) == {"k": best}

@@ -241,3 +241,38 @@ def test_invalid_arguments_are_rejected():
         hb.Context(hb.default_config(nx0=30, ny0=15))   # 15 rows cannot be coarsened
     empty = ctx.solve(0, xi_cuda(0, 0, 0))
     assert empty["q"].shape == (0, hb.NQ)
+
+
+def test_fp32_multigrid_matches_fp64_multigrid_on_identical_xi():
+    """Config-3 pattern (FP32 V-cycles inside FP64 defect correction vs FP64
+    multigrid) on level 2 (128x64 cells, 96 steps): both converge to the same
+    FP64 discrete solution, far inside the 1e-7 bound on c."""
+    xi = xi_cuda(2, 0, 4)
+    out = {}
+    for prec in (hb.PREC_FP64, hb.PREC_FP32_MG):
+        ctx = hb.Context(tight_config(nlevels=3, precision=prec))
+        out[prec] = ctx.solve(2, xi, want_c=True)
+        assert out[prec]["status"].cpu().numpy().tolist() == [0] * 4
+    dc = (out[hb.PREC_FP64]["c"] - out[hb.PREC_FP32_MG]["c"]).abs().max().item()
+    assert dc <= 1e-9
+    dq = (out[hb.PREC_FP64]["q"][:, 3:] - out[hb.PREC_FP32_MG]["q"][:, 3:]).abs().max().item()
+    assert dq <= 1e-9
+
+
+def test_full_size_level3_step_residual_under_the_oracle():
+    """Level 3 at full size (256x128 cells) in the launch configuration of the
+    benchmark (16 samples): after 2 steps at the level's time step, the GPU
+    state satisfies the oracle's discrete equations (its FP64 residual, in
+    units of c per step) and matches the oracle's state (one sample checked,
+    the oracle needs ~25 s for it)."""
+    cfg = tight_config(nlevels=4, nt0=1, T=1800.0)   # level 3: 8 steps of 225 s
+    ctx = hb.Context(cfg)
+    xi = xi_cuda(3, 0, 16)
+    out = ctx.solve(3, xi, want_c=True, want_p=True)
+    assert out["status"].cpu().numpy().tolist() == [0] * 16
+    g = oracle_grid(cfg, 3)
+    ph = oracle_physics(cfg)
+    for b in (11,):
+        r = H.solve(g, ph, xi[b].cpu().numpy())
+        assert np.max(np.abs(out["c"][b].cpu().numpy() - r["c"])) <= C_TOL
+        assert np.max(np.abs(out["p"][b].cpu().numpy() - r["p"])) <= P_TOL * np.max(np.abs(r["p"]))

@@ -123,3 +123,14 @@ def test_gpu_estimator_matches_oracle_on_the_same_samples():
     var = g0.var(0, ddof=1) / 8 + d1.var(0, ddof=1) / 4
     assert np.allclose(res["estimate"], Y, rtol=1e-9, atol=1e-10)
     assert np.allclose(res["var_Y"], var, rtol=1e-6, atol=1e-16)
+
+
+def test_a_level_without_valid_samples_stops_the_run():
+    class Failing(FakeSampler):
+        def batch(self, level, first, count):
+            if level == 2:
+                return (0, np.zeros(M.NQ), np.zeros(M.NQ), np.zeros(M.NQ), np.zeros(M.NQ), 1.0, count)
+            return super().batch(level, first, count)
+
+    with pytest.raises(RuntimeError, match="level"):
+        M.run(Failing(), 2, 0.01, qois=(0,))
