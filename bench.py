@@ -125,16 +125,24 @@ def make_inputs(rank, n_xi=3):
 
 
 class Workload:
-    """One context per precision; one stream per level."""
+    """One context per level (its schedule autotuned), one stream per level."""
 
-    def __init__(self, precision, vcycles):
+    def __init__(self, precision, schedules):
         import torch
         from paper_2403_17018_gb300 import binding as hb
         self.hb = hb
-        self.cfg = hb.default_config(nlevels=4, precision=precision, vcycles=vcycles)
-        self.ctx = hb.Context(self.cfg)
+        self.ctxs = {}
+        for l in LEVELS:
+            sc = schedules[l]
+            cfg = hb.default_config(nlevels=4, precision=precision, vcycles=sc["vcycles"],
+                                    nu1=sc["nu1"], nu2=sc["nu2"])
+            self.ctxs[l] = hb.Context(cfg)
+        self.cfg = self.ctxs[0].cfg
         self.streams = {l: torch.cuda.Stream() for l in LEVELS}
         self.out = {}
+
+    def launch_count(self):
+        return sum(c.launch_count() for c in self.ctxs.values())
 
     def step(self, xis, host=None):
         """Enqueue all level pairs; then merge level statistics (synchronous
@@ -151,13 +159,13 @@ class Workload:
                 xi = xis[l]
                 if host is not None:
                     xi.copy_(host["xi"][l], non_blocking=True)
-                self.out[l] = self.ctx.sample_pairs(l, xi, stream=s)
+                self.out[l] = self.ctxs[l].sample_pairs(l, xi, stream=s)
         stats = {}
         for l in LEVELS:
             s = self.streams[l]
             qf, qc, _, _, st = self.out[l]
             S = self.hb.LevelStats()
-            self.ctx.level_stats(l, qf, qc, st, S, stream=s)
+            self.ctxs[l].level_stats(l, qf, qc, st, S, stream=s)
             stats[l] = S
             if host is not None:
                 with torch.cuda.stream(s):
@@ -172,6 +180,18 @@ class Workload:
         return stats
 
 
+def tune_schedules(precision_name):
+    """Autotuned schedule per level: V-cycles per iteration x smoothing sweeps,
+    timed on a short solve (a few steps at the level's own time step)."""
+    from paper_2403_17018_gb300 import autotune as A
+    A.CANDIDATES = {"vcycles": (2, 3), "nu": ((2, 2), (3, 3))}
+    out = {}
+    for l in LEVELS:
+        best, _ = A.tune_level(l, BATCH[l], precision_name, steps=4, reps=1, splits=(1,))
+        out[l] = best
+    return out
+
+
 def flush_l2(buf):
     buf.add_(1.0)
 
@@ -183,7 +203,7 @@ def time_steps(wl, xis, K, W, barrier, flush, host=None):
     torch.cuda.synchronize()
     total_ms = 0.0
     per_step = []
-    n0 = wl.ctx.launch_count()
+    n0 = wl.launch_count()
     for _ in range(K):
         flush()
         torch.cuda.synchronize()
@@ -197,7 +217,7 @@ def time_steps(wl, xis, K, W, barrier, flush, host=None):
         per_step.append(ms)
         total_ms += ms
     barrier()
-    launches = wl.ctx.launch_count() - n0
+    launches = wl.launch_count() - n0
     return total_ms, per_step, launches, stats
 
 
@@ -210,7 +230,7 @@ def per_level_rates(wl, xis, reps=1):
         torch.cuda.synchronize()
         e0.record()
         for _ in range(reps):
-            wl.ctx.sample_pairs(l, xis[l])
+            wl.ctxs[l].sample_pairs(l, xis[l])
         e1.record()
         torch.cuda.synchronize()
         rates[f"L{l}"] = round(BATCH[l] * reps / (e0.elapsed_time(e1) / 1e3), 2)
@@ -227,9 +247,9 @@ def roofline(wl, peaks):
     GB300 (FP64 is 1/64 of FP32), so reported against the FP64 peak derived
     from unit counts and clock. The FP64 residual/Jacobian kernel, next in
     the list, is reported beside it."""
-    ms, by, fl = wl.ctx.time_kernel(3, 0, 0, reps=50)
+    ms, by, fl = wl.ctxs[3].time_kernel(3, 0, 0, reps=50)
     ach = fl / (ms / 1e3) / 1e12
-    ms2, by2, fl2 = wl.ctx.time_kernel(3, 0, 1, reps=20)
+    ms2, by2, fl2 = wl.ctxs[3].time_kernel(3, 0, 1, reps=20)
     return {"bound": "alu", "achieved": round(ach, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
             "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4), "traffic": None,
             "kernel": "k_smooth<double> red half-sweep (level 3: 256x128 cells x 16 samples)",
@@ -244,7 +264,7 @@ def roofline(wl, peaks):
 
 
 def smoother_roofline(wl, peaks):
-    ms, by, fl = wl.ctx.time_kernel(3, 0, 0, reps=50)
+    ms, by, fl = wl.ctxs[3].time_kernel(3, 0, 0, reps=50)
     ach = by / (ms / 1e3) / 1e9
     return {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks.get("hbm_gbs", 6800.0),
             "unit": "GB/s", "frac": round(ach / peaks.get("hbm_gbs", 6800.0), 4),
@@ -357,7 +377,8 @@ def main():
     pairs_per_step = sum(BATCH.values())
 
     # ---- headline: FP64 multigrid ------------------------------------------
-    wl = Workload(hb.PREC_FP64, vcycles=2)
+    sched64 = tune_schedules("fp64")
+    wl = Workload(hb.PREC_FP64, sched64)
     clocks = ClockSampler(local)
     clocks.start()
     ms, per_step, launches, stats = time_steps(wl, xis, K, W, barrier, flush)
@@ -385,11 +406,14 @@ def main():
     # ---- FP32 multigrid inside FP64 defect correction, same workload -------
     fp32 = None
     if not args.no_fp32:
-        wl32 = Workload(hb.PREC_FP32_MG, vcycles=2)
+        sched32 = tune_schedules("fp32mg")
+        wl32 = Workload(hb.PREC_FP32_MG, sched32)
         ms32, _, launches32, _ = time_steps(wl32, xis, K, W, barrier, flush)
         fp32 = {"value": round(pairs_per_step * world * K / (ms32 / 1e3), 2),
                 "ms_per_step": round(ms32 / K, 2), "per_level": per_level_rates(wl32, xis),
                 "gpu_launches": launches32,
+                "schedule": {f"L{l}": f"V({s['nu1']},{s['nu2']}) x{s['vcycles']}"
+                             for l, s in sched32.items()},
                 "smoother_roofline": smoother_roofline(wl32, peaks)}
 
     cpu = None
@@ -401,7 +425,9 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded SplitMix64 xi ~ U[-1,1]^3)",
             "config": {"workload": WORKLOAD, "levels": list(LEVELS),
-                       "batch": [BATCH[l] for l in LEVELS], "multigrid": "FP64 V(2,2) x2",
+                       "batch": [BATCH[l] for l in LEVELS],
+                       "multigrid": "FP64, autotuned per level: " + ", ".join(
+                           f"L{l} V({s['nu1']},{s['nu2']}) x{s['vcycles']}" for l, s in sched64.items()),
                        "newton_rtol": wl.cfg.newton_rtol, "newton_atol": wl.cfg.newton_atol,
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"{world} GPU(s), samples sharded, 4 level streams"},

@@ -91,7 +91,13 @@ typedef struct henry_config {
                               iteration reduced r by less than half (the
                               FP64 rounding floor, which grows with
                               resolution, has been reached); 0 disables */
-  int reserved[6];
+  int mg_fusion;       /* 1: V-cycles of small levels fused into one kernel
+                          (a block per sample in shared memory up to 512
+                          cells, a thread-block cluster per sample up to
+                          mg_cluster_cells); 0: one launch per operation */
+  int mg_cluster_cells; /* largest multigrid level (cells per sample) run by
+                           the cluster kernel; 0 (default) disables it */
+  int reserved[4];
 } henry_config;
 
 typedef struct henry_ctx henry_ctx; /* opaque: owns device workspaces */
@@ -108,8 +114,9 @@ typedef struct henry_level_stats {
  * 1024.99, D = 18.8571e-6, K0 = 1.020408e-9, phi0 = 0.35, mu = 1e-3,
  * g = 9.8), q0 = 6.6e-5 m/s, [0,2]x[0,1], T = 43200 s, 32x16 cells and 24
  * steps on level 0, 2 levels, 3 random variables, FP64 multigrid, rtol
- * 1e-10, atol 1e-12, stagnation tolerance 1e-9, maxit 30, V(2,2), 1 V-cycle
- * per iteration, extrapolated Newton guess on. */
+ * 1e-10, atol 1e-12, stagnation tolerance 1e-9, maxit 30, V(2,2), 3 V-cycles
+ * per iteration, extrapolated Newton guess on, shared-memory V-cycle fusion
+ * on, cluster V-cycle off (measured slower on the configured workloads). */
 int henry_default_config(henry_config* cfg);
 
 /* Validate *cfg and create a context for levels 0..cfg->nlevels-1.

@@ -42,7 +42,8 @@ class HenryConfig(ctypes.Structure):
                [("newton_rtol", ctypes.c_double), ("newton_atol", ctypes.c_double),
                 ("newton_maxit", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("vcycles", ctypes.c_int), ("guess_extrapolation", ctypes.c_int),
-                ("newton_stag_tol", ctypes.c_double), ("reserved", ctypes.c_int * 6)]
+                ("newton_stag_tol", ctypes.c_double), ("mg_fusion", ctypes.c_int),
+                ("mg_cluster_cells", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}

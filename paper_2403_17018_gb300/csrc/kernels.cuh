@@ -9,6 +9,7 @@
 // depend on which other samples share its batch.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -554,7 +555,9 @@ __global__ void k_coarse_lu(unsigned long long* ctr, Geom G, int B, const int* _
 // ---------------------------------------------------------------------------
 
 // Point-block Gauss-Seidel update of the cell at colour-split position
-// `pos` of colour `colour`: x_P = D_P^{-1} (b_P - sum_Q A_PQ x_Q).
+// `pos` of colour `colour`: x_P = D_P^{-1} (b_P - sum_Q A_PQ x_Q). Each
+// product is subtracted on its own so that it compiles to one FMA (the
+// FP64 form of this kernel is bound by GB300's FP64 pipe).
 template <typename T>
 __device__ __forceinline__ void smooth_cell(const Geom& G, int colour, int pos,
                                             const T* __restrict__ J, const T* __restrict__ b,
@@ -571,26 +574,34 @@ __device__ __forceinline__ void smooth_cell(const Geom& G, int colour, int pos,
   if (i > 0) {
     const int q = j * hx2 + ((i - 1) >> 1);
     const T vp = xp[q], vc = xc[q];
-    rp -= Jb[4 * ncell] * vp + Jb[5 * ncell] * vc;
-    rc -= Jb[6 * ncell] * vp + Jb[7 * ncell] * vc;
+    rp -= Jb[4 * ncell] * vp;
+    rp -= Jb[5 * ncell] * vc;
+    rc -= Jb[6 * ncell] * vp;
+    rc -= Jb[7 * ncell] * vc;
   }
   if (i < G.nx - 1) {
     const int q = j * hx2 + ((i + 1) >> 1);
     const T vp = xp[q], vc = xc[q];
-    rp -= Jb[8 * ncell] * vp + Jb[9 * ncell] * vc;
-    rc -= Jb[10 * ncell] * vp + Jb[11 * ncell] * vc;
+    rp -= Jb[8 * ncell] * vp;
+    rp -= Jb[9 * ncell] * vc;
+    rc -= Jb[10 * ncell] * vp;
+    rc -= Jb[11 * ncell] * vc;
   }
   if (j > 0) {
     const int q = (j - 1) * hx2 + (i >> 1);
     const T vp = xp[q], vc = xc[q];
-    rp -= Jb[12 * ncell] * vp + Jb[13 * ncell] * vc;
-    rc -= Jb[14 * ncell] * vp + Jb[15 * ncell] * vc;
+    rp -= Jb[12 * ncell] * vp;
+    rp -= Jb[13 * ncell] * vc;
+    rc -= Jb[14 * ncell] * vp;
+    rc -= Jb[15 * ncell] * vc;
   }
   if (j < G.ny - 1) {
     const int q = (j + 1) * hx2 + (i >> 1);
     const T vp = xp[q], vc = xc[q];
-    rp -= Jb[16 * ncell] * vp + Jb[17 * ncell] * vc;
-    rc -= Jb[18 * ncell] * vp + Jb[19 * ncell] * vc;
+    rp -= Jb[16 * ncell] * vp;
+    rp -= Jb[17 * ncell] * vc;
+    rc -= Jb[18 * ncell] * vp;
+    rc -= Jb[19 * ncell] * vc;
   }
   // planes 0..3 hold the inverse diagonal block
   x[own] = Jb[0] * rp + Jb[ncell] * rc;
@@ -614,26 +625,34 @@ __device__ __forceinline__ void apply_cell(const Geom& G, int i, int j, const T*
   if (i > 0) {
     const int q = cs_pos(i - 1, j, nx, half);
     vp = xp[q]; vc = xc[q];
-    ap += Jc[4 * ncell] * vp + Jc[5 * ncell] * vc;
-    ac += Jc[6 * ncell] * vp + Jc[7 * ncell] * vc;
+    ap += Jc[4 * ncell] * vp;
+    ap += Jc[5 * ncell] * vc;
+    ac += Jc[6 * ncell] * vp;
+    ac += Jc[7 * ncell] * vc;
   }
   if (i < nx - 1) {
     const int q = cs_pos(i + 1, j, nx, half);
     vp = xp[q]; vc = xc[q];
-    ap += Jc[8 * ncell] * vp + Jc[9 * ncell] * vc;
-    ac += Jc[10 * ncell] * vp + Jc[11 * ncell] * vc;
+    ap += Jc[8 * ncell] * vp;
+    ap += Jc[9 * ncell] * vc;
+    ac += Jc[10 * ncell] * vp;
+    ac += Jc[11 * ncell] * vc;
   }
   if (j > 0) {
     const int q = cs_pos(i, j - 1, nx, half);
     vp = xp[q]; vc = xc[q];
-    ap += Jc[12 * ncell] * vp + Jc[13 * ncell] * vc;
-    ac += Jc[14 * ncell] * vp + Jc[15 * ncell] * vc;
+    ap += Jc[12 * ncell] * vp;
+    ap += Jc[13 * ncell] * vc;
+    ac += Jc[14 * ncell] * vp;
+    ac += Jc[15 * ncell] * vc;
   }
   if (j < G.ny - 1) {
     const int q = cs_pos(i, j + 1, nx, half);
     vp = xp[q]; vc = xc[q];
-    ap += Jc[16 * ncell] * vp + Jc[17 * ncell] * vc;
-    ac += Jc[18 * ncell] * vp + Jc[19 * ncell] * vc;
+    ap += Jc[16 * ncell] * vp;
+    ap += Jc[17 * ncell] * vc;
+    ac += Jc[18 * ncell] * vp;
+    ac += Jc[19 * ncell] * vc;
   }
 }
 
@@ -971,6 +990,76 @@ __global__ void k_reduce_pressure(Phys P, Geom G, int B, const double* __restric
   const int cell = (int)(idx % G.ncell());
   const int j = cell / G.nx;
   pr[idx] = p[idx] - P.rho0 * P.g * (P.Ly - (j + 0.5) * G.hy);
+}
+
+// ---------------------------------------------------------------------------
+// V-cycles on levels 0..kc by one thread-block cluster per sample: the CL
+// blocks of a cluster split every phase's cells among them and are
+// separated by hardware cluster barriers (the blocks of a cluster are
+// co-scheduled, so the barrier cannot wait on a block that never runs).
+// Operators and vectors stay in global memory (L2 resident at these sizes);
+// the barrier's release/acquire semantics at cluster scope make each phase's
+// global writes visible to the whole cluster in the next phase.
+// Level kc takes b from and returns x to global memory like the batched
+// kernels; x_kc is read as the initial guess.
+// ---------------------------------------------------------------------------
+constexpr int kMaxCluster = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+k_vcycle_cluster(unsigned long long* ctr, SmallMG<T> M, int B, const int* __restrict__ active,
+                 const double* __restrict__ LU, const int* __restrict__ piv, int nu1, int nu2,
+                 int ncycles, int CL) {
+  HENRY_COUNT_LAUNCH(ctr);
+  namespace cg = cooperative_groups;
+  __shared__ double ysh[kMaxCoarseUnknowns];
+  const int b = blockIdx.x / CL;
+  const int rank = blockIdx.x - b * CL;
+  if (b >= B || !active[b]) return;           // uniform over the cluster
+  cg::cluster_group cl = cg::this_cluster();
+  auto sync = [&]() {
+    if (CL > 1) cl.sync(); else __syncthreads();
+  };
+  const int nthr = CL * blockDim.x;
+  const int gid = rank * blockDim.x + threadIdx.x;
+  const int kc = M.ks;
+  T* J[kMaxLevels];
+  T* bv[kMaxLevels];
+  T* xv[kMaxLevels];
+  for (int k = 0; k <= kc; ++k) {
+    const int64_t nc = M.g[k].ncell();
+    J[k] = M.J[k] + (int64_t)b * 20 * nc;
+    bv[k] = M.b[k] + (int64_t)b * 2 * nc;
+    xv[k] = M.x[k] + (int64_t)b * 2 * nc;
+  }
+  const double* A = LU + (int64_t)b * kMaxCoarseUnknowns * kMaxCoarseUnknowns;
+  const int* pv = piv + (int64_t)b * kMaxCoarseUnknowns;
+  for (int cyc = 0; cyc < ncycles; ++cyc) {
+    for (int k = kc; k >= 1; --k) {
+      const Geom& G = M.g[k];
+      for (int sw = 0; sw < nu1; ++sw)
+        for (int col = 0; col < 2; ++col) {
+          for (int pos = gid; pos < G.half(); pos += nthr) smooth_cell<T>(G, col, pos, J[k], bv[k], xv[k]);
+          sync();
+        }
+      for (int cell = gid; cell < M.g[k - 1].ncell(); cell += nthr)
+        restrict_cell<T>(G, M.g[k - 1], cell, J[k], bv[k], xv[k], bv[k - 1], xv[k - 1]);
+      sync();
+    }
+    if (rank == 0 && threadIdx.x < 32) coarse_solve_warp<T>(M.g[0], A, pv, bv[0], xv[0], ysh, threadIdx.x);
+    sync();
+    for (int k = 1; k <= kc; ++k) {
+      const Geom& G = M.g[k];
+      for (int cell = gid; cell < G.ncell(); cell += nthr)
+        prolong_cell<T>(M.g[k - 1], G, cell, xv[k - 1], xv[k]);
+      sync();
+      for (int sw = 0; sw < nu2; ++sw)
+        for (int col = 0; col < 2; ++col) {
+          for (int pos = gid; pos < G.half(); pos += nthr) smooth_cell<T>(G, col, pos, J[k], bv[k], xv[k]);
+          sync();
+        }
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -78,8 +78,14 @@ Solver::Solver(const henry_config& cfg, int nx, int ny, int nt) : cfg_(cfg), nt_
   tile_ = make_res_tile(geoms_.back().nx, geoms_.back().ny);
   nchunk_ = tile_.ntx * tile_.nty;
   ks_ = 0;
-  for (size_t k = 0; k < geoms_.size(); ++k)
+  kc_ = 0;
+  for (size_t k = 0; k < geoms_.size(); ++k) {
     if (geoms_[k].ncell() <= kSmallCells) ks_ = (int)k;
+    if (geoms_[k].ncell() <= cfg_.mg_cluster_cells) kc_ = (int)k;
+  }
+  const int per = geoms_[kc_].ncell() / 1024;
+  cl_ = per < 1 ? 1 : (per > kMaxCluster ? kMaxCluster : per);
+  if (!cfg_.mg_fusion) ks_ = kc_ = 0;
 }
 
 Solver::~Solver() { free_all(); }
@@ -227,9 +233,41 @@ void Solver::launch_small(int B, int ncycles, cudaStream_t s) {
 }
 
 template <typename T>
+void Solver::launch_cluster(int B, int ncycles, cudaStream_t s) {
+  SmallMG<T> M;
+  M.ks = kc_;
+  for (int k = 0; k <= kc_; ++k) {
+    M.g[k] = levels_[k].g;
+    M.J[k] = (T*)levels_[k].J;
+    M.b[k] = (T*)levels_[k].b;
+    M.x[k] = (T*)levels_[k].x;
+  }
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3((unsigned)(B * cl_));
+  lc.blockDim = dim3(kBlock);
+  lc.dynamicSmemBytes = 0;
+  lc.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cl_;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  cudaLaunchKernelEx(&lc, k_vcycle_cluster<T>, counter_, M, B, (const int*)active_,
+                     (const double*)lu_, (const int*)piv_, cfg_.nu1, cfg_.nu2, ncycles, cl_);
+}
+
+// Whole hierarchy fits the shared-memory kernel, or the cluster kernel, or
+// neither (then the top levels are launched one kernel at a time).
+template <typename T>
 void Solver::enqueue_vcycle(int k, int B, cudaStream_t s) {
   MGLevel& L = levels_[k];
   const Geom& G = L.g;
+  if (k == kc_ && kc_ > ks_ && k > 0) {
+    launch_cluster<T>(B, 1, s);
+    return;
+  }
   if (k == ks_ && k > 0) {
     launch_small<T>(B, 1, s);
     return;
@@ -290,6 +328,8 @@ void Solver::enqueue_vcycles(int B, cudaStream_t s) {
   const int nl = (int)levels_.size();
   if (ks_ == nl - 1 && nl > 1)
     launch_small<T>(B, cfg_.vcycles, s);
+  else if (kc_ == nl - 1 && nl > 1)
+    launch_cluster<T>(B, cfg_.vcycles, s);
   else
     for (int v = 0; v < cfg_.vcycles; ++v) enqueue_vcycle<T>(nl - 1, B, s);
 }

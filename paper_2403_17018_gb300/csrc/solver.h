@@ -82,6 +82,7 @@ class Solver {
   template <typename T> int step_graph(int B, cudaStream_t s);
   template <typename T> void launch_timed(int which, int B, cudaStream_t s);
   template <typename T> void launch_small(int B, int ncycles, cudaStream_t s);
+  template <typename T> void launch_cluster(int B, int ncycles, cudaStream_t s);
   int ensure(int B, cudaStream_t s);
   int ensure_adjoint(int B, int nckpt, int seglen);
   template <typename T> int adjoint_t(const double* xi, const double* logk, int B, int qoi, int kc,
@@ -120,6 +121,8 @@ class Solver {
   int nchunk_ = 0;            // residual blocks per sample
   ResTile tile_{};            // tiling of the residual kernel
   int ks_ = 0;                // top multigrid level handled by k_vcycle_small
+  int kc_ = 0;                // top multigrid level handled by k_vcycle_cluster
+  int cl_ = 1;                // blocks per cluster (one cluster per sample)
   size_t small_smem_ = 0;     // its dynamic shared memory per block
   // CUDA graph of one time step (HENRY_LOOP_GRAPH), rebuilt when B changes
   cudaGraphExec_t step_exec_ = nullptr;

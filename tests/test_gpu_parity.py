@@ -276,3 +276,23 @@ def test_full_size_level3_step_residual_under_the_oracle():
         r = H.solve(g, ph, xi[b].cpu().numpy())
         assert np.max(np.abs(out["c"][b].cpu().numpy() - r["c"])) <= C_TOL
         assert np.max(np.abs(out["p"][b].cpu().numpy() - r["p"])) <= P_TOL * np.max(np.abs(r["p"]))
+
+
+@pytest.mark.parametrize("precision", [hb.PREC_FP64, hb.PREC_FP32_MG])
+@pytest.mark.parametrize("level", [0, 2, 3, 4])
+def test_fused_multigrid_kernels_equal_plain_launches_bitwise(precision, level):
+    """The shared-memory V-cycle (level 0), the thread-block-cluster V-cycle
+    (levels 2, 3: 4 and 8 blocks per sample) and cluster + per-level launches
+    (level 4) perform the same per-cell operations in the same order as one
+    launch per operation, so the solutions agree bit for bit; a stale read
+    across the cluster's blocks would break this."""
+    res = []
+    for fusion in (0, 1):
+        cfg = tight_config(nlevels=level + 1, nt0=1, T=1800.0, precision=precision,
+                           mg_fusion=fusion, vcycles=2, mg_cluster_cells=32768)
+        ctx = hb.Context(cfg)
+        out = ctx.solve(level, xi_cuda(level, 0, 3), want_c=True, want_p=True, want_iters=True)
+        assert out["status"].cpu().numpy().tolist() == [0, 0, 0]
+        res.append(out)
+    for k in ("c", "p", "q", "iters"):
+        assert torch.equal(res[0][k], res[1][k]), k
