@@ -135,7 +135,8 @@ class Workload:
         for l in LEVELS:
             sc = schedules[l]
             cfg = hb.default_config(nlevels=4, precision=precision, vcycles=sc["vcycles"],
-                                    nu1=sc["nu1"], nu2=sc["nu2"])
+                                    nu1=sc["nu1"], nu2=sc["nu2"],
+                                    mg_small_cells=sc.get("mg_small_cells", 512))
             self.ctxs[l] = hb.Context(cfg)
         self.cfg = self.ctxs[0].cfg
         self.streams = {l: torch.cuda.Stream() for l in LEVELS}
@@ -181,10 +182,11 @@ class Workload:
 
 
 def tune_schedules(precision_name):
-    """Autotuned schedule per level: V-cycles per iteration x smoothing sweeps,
-    timed on a short solve (a few steps at the level's own time step)."""
+    """Autotuned schedule per level: V-cycles per iteration x smoothing sweeps
+    x shared-memory V-cycle threshold, timed on a short solve (a few steps at
+    the level's own time step)."""
     from paper_2403_17018_gb300 import autotune as A
-    A.CANDIDATES = {"vcycles": (2, 3), "nu": ((2, 2), (3, 3))}
+    A.CANDIDATES = {"vcycles": (2, 3), "nu": ((2, 2), (3, 3)), "small_cells": (0, 128, 512)}
     out = {}
     for l in LEVELS:
         best, _ = A.tune_level(l, BATCH[l], precision_name, steps=4, reps=1, splits=(1,))
@@ -412,7 +414,8 @@ def main():
         fp32 = {"value": round(pairs_per_step * world * K / (ms32 / 1e3), 2),
                 "ms_per_step": round(ms32 / K, 2), "per_level": per_level_rates(wl32, xis),
                 "gpu_launches": launches32,
-                "schedule": {f"L{l}": f"V({s['nu1']},{s['nu2']}) x{s['vcycles']}"
+                "schedule": {f"L{l}": f"V({s['nu1']},{s['nu2']}) x{s['vcycles']} "
+                                      f"smem<={s['mg_small_cells']}"
                              for l, s in sched32.items()},
                 "smoother_roofline": smoother_roofline(wl32, peaks)}
 
@@ -427,7 +430,8 @@ def main():
             "config": {"workload": WORKLOAD, "levels": list(LEVELS),
                        "batch": [BATCH[l] for l in LEVELS],
                        "multigrid": "FP64, autotuned per level: " + ", ".join(
-                           f"L{l} V({s['nu1']},{s['nu2']}) x{s['vcycles']}" for l, s in sched64.items()),
+                           f"L{l} V({s['nu1']},{s['nu2']}) x{s['vcycles']} smem<={s['mg_small_cells']}"
+                           for l, s in sched64.items()),
                        "newton_rtol": wl.cfg.newton_rtol, "newton_atol": wl.cfg.newton_atol,
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"{world} GPU(s), samples sharded, 4 level streams"},

@@ -97,7 +97,9 @@ typedef struct henry_config {
                           mg_cluster_cells); 0: one launch per operation */
   int mg_cluster_cells; /* largest multigrid level (cells per sample) run by
                            the cluster kernel; 0 (default) disables it */
-  int reserved[4];
+  int mg_small_cells;   /* largest multigrid level (cells per sample, at most
+                           512) run by the shared-memory kernel; default 512 */
+  int reserved[3];
 } henry_config;
 
 typedef struct henry_ctx henry_ctx; /* opaque: owns device workspaces */
@@ -264,7 +266,8 @@ int henry_level_info(const henry_ctx* ctx, int level, int* nx, int* ny, int* nt,
 /* Diagnostics: copy an internal array of the solver that serves `level`
  * (role 0: fine solves and level-l halves of pairs; role 1: the level-(l-1)
  * halves of pairs, addressed by their own level l-1) for multigrid level
- * mg_level (0 = coarsest). what: 0 J [B][20][ncell] (colour-split planes),
+ * mg_level (0 = coarsest). what: 0 J [B][24][ncell] (colour-split planes:
+ * inverse diagonal block, W, E, S, N blocks, diagonal block),
  * 1 b, 2 x ([B][2][ncell], colour-split), 3 p, 4 c, 5 phi, 6 K ([B][ncell],
  * natural), 7..10 face constants tx, dx, ty, dy, 11..12 face fluxes of the
  * linearisation point qx (east faces; the right side in the last column),

@@ -2,7 +2,8 @@
 
 For each MLMC level it times short batched solves (a few implicit Euler
 steps at the level's own time step) for every candidate schedule — V-cycles
-per defect-correction iteration and pre/post smoothing sweeps — and, for
+per defect-correction iteration, pre/post smoothing sweeps and the largest
+grid handed to the shared-memory V-cycle kernel — and, for
 the level's batch size, several batch splits, then keeps the schedule with
 the highest solves per second. Results are cached in a JSON file keyed by
 GPU name, level grid, precision and batch so that later runs reuse them.
@@ -23,7 +24,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuning", "schedules.json")
-CANDIDATES = {"vcycles": (1, 2, 3), "nu": ((1, 1), (2, 2), (3, 3))}
+CANDIDATES = {"vcycles": (1, 2, 3), "nu": ((1, 1), (2, 2), (3, 3)), "small_cells": (0, 128, 512)}
 
 
 def _key(gpu, level, precision, batch, nx0, ny0):
@@ -55,7 +56,8 @@ def best_schedule(level, precision, batch, gpu=None, nx0=32, ny0=16, path=CACHE)
 
 def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2), log=None):
     """Time every candidate schedule on `steps` steps of level `level`;
-    returns the best {vcycles, nu1, nu2, split, solves_per_s} and the table."""
+    returns the best {vcycles, nu1, nu2, mg_small_cells, split, solves_per_s}
+    and the table."""
     import torch
     from paper_2403_17018_gb300 import binding as hb
     from paper_2403_17018_gb300.inputs import xi_batch
@@ -64,11 +66,12 @@ def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2),
     k = max(1, steps // f)
     xi = torch.from_numpy(xi_batch(level, 0, batch)).cuda()
     table = []
-    for vc, (n1, n2), split in itertools.product(CANDIDATES["vcycles"], CANDIDATES["nu"], splits):
+    for vc, (n1, n2), sc, split in itertools.product(
+            CANDIDATES["vcycles"], CANDIDATES["nu"], CANDIDATES.get("small_cells", (512,)), splits):
         if batch % split:
             continue
         cfg = hb.default_config(nlevels=level + 1, precision=prec, vcycles=vc, nu1=n1, nu2=n2,
-                                nt0=k, T=1800.0 * k)
+                                mg_small_cells=sc, nt0=k, T=1800.0 * k)
         ctx = hb.Context(cfg)
         sub = batch // split
         parts = [xi[i * sub:(i + 1) * sub].contiguous() for i in range(split)]
@@ -82,7 +85,7 @@ def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2),
                 bad += int((ctx.solve(level, p)["status"] != 0).sum().item())
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / reps
-        row = {"vcycles": vc, "nu1": n1, "nu2": n2, "split": split,
+        row = {"vcycles": vc, "nu1": n1, "nu2": n2, "mg_small_cells": sc, "split": split,
                "solves_per_s": batch / dt, "failed": bad}
         table.append(row)
         if log:

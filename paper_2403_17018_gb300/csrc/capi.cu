@@ -86,7 +86,8 @@ int validate(const henry_config* c) {
   if (!(c->T > 0) || !(c->Lx > 0) || !(c->Ly > 0) || !(c->mu > 0) || !(c->K0 > 0) ||
       !(c->phi0 > 0) || !(c->D >= 0))
     return fail(HENRY_E_INVALID, "non-positive physical parameter");
-  if (c->newton_maxit < 0 || c->nu1 < 0 || c->nu2 < 0 || c->vcycles < 1 || c->mg_cluster_cells < 0)
+  if (c->newton_maxit < 0 || c->nu1 < 0 || c->nu2 < 0 || c->vcycles < 1 || c->mg_cluster_cells < 0 ||
+      c->mg_small_cells < 0 || c->mg_small_cells > 512)
     return fail(HENRY_E_INVALID, "bad solver parameter");
   for (int l = 0; l < c->nlevels; ++l) {
     std::vector<henry::Geom> g;
@@ -132,6 +133,7 @@ int henry_default_config(henry_config* c) {
   c->newton_stag_tol = 1e-9;
   c->mg_fusion = 1;
   c->mg_cluster_cells = 0;
+  c->mg_small_cells = 512;
   return HENRY_OK;
 }
 

@@ -19,11 +19,13 @@
 
 namespace henry {
 
-// Multigrid operators store the inverse of each cell's 2x2 diagonal block
-// in planes 0..3 (the off-diagonal blocks as they are): the smoother then
-// needs a 2x2 product per update instead of a determinant and a division,
-// which matters most for the FP64 multigrid on GB300's slow FP64 pipe.
-// Consumers that need the block itself invert it back (inv2).
+// Multigrid operators have kJP = 24 planes per cell: 0..3 the inverse of the
+// cell's 2x2 diagonal block, 4..19 the off-diagonal blocks (W, E, S, N),
+// 20..23 the diagonal block itself. The smoother then needs a 2x2 product
+// per update instead of a determinant and a division, and the residual of
+// the restriction and the coarse LU read the block without inverting it
+// back; both matter for the FP64 multigrid on GB300's slow FP64 pipe.
+constexpr int kJP = 24;
 template <typename T>
 __device__ __forceinline__ void inv2(T a, T b, T c, T d, T& ia, T& ib, T& ic, T& id) {
   const T r = (T)1 / (a * d - b * c);
@@ -321,8 +323,10 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double tau, int B, ResTile tl,
         bvec[ob + ncell + cs] = (T)(-Rc);
         xvec[ob + cs] = (T)0;
         xvec[ob + ncell + cs] = (T)0;
+        T* Jb = J + (int64_t)b * kJP * ncell + cs;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) Jb[(int64_t)(20 + m) * ncell] = Jc[m];
         inv2<T>(Jc[0], Jc[1], Jc[2], Jc[3], Jc[0], Jc[1], Jc[2], Jc[3]);
-        T* Jb = J + (int64_t)b * 20 * ncell + cs;
 #pragma unroll
         for (int m = 0; m < 20; ++m) Jb[(int64_t)m * ncell] = Jc[m];
         qx[o + id] = qE;
@@ -468,8 +472,10 @@ k_jac(unsigned long long* ctr, Phys P, Geom G, double tau, int B, const int* __r
   double Rp, Rc;
   T Jc[20];
   cell_residual<T, true, true>(P, G, tau, in, Rp, Rc, Jc);
+  T* Jb = J + (int64_t)b * kJP * ncell + cs_pos(i, j, G.nx, G.half());
+#pragma unroll
+  for (int m = 0; m < 4; ++m) Jb[(int64_t)(20 + m) * ncell] = Jc[m];
   inv2<T>(Jc[0], Jc[1], Jc[2], Jc[3], Jc[0], Jc[1], Jc[2], Jc[3]);
-  T* Jb = J + (int64_t)b * 20 * ncell + cs_pos(i, j, G.nx, G.half());
 #pragma unroll
   for (int m = 0; m < 20; ++m) Jb[(int64_t)m * ncell] = Jc[m];
 }
@@ -488,7 +494,7 @@ __global__ void k_coarse_lu(unsigned long long* ctr, Geom G, int B, const int* _
   if (b >= B || !active[b]) return;
   const int nc = G.ncell(), n = 2 * nc, half = G.half(), ld = n + 1;
   double* A = lu_sh + (size_t)w * n * ld;
-  const T* Jb = J + (int64_t)b * 20 * nc;
+  const T* Jb = J + (int64_t)b * kJP * nc;
   for (int e = l; e < n * ld; e += 32) A[e] = 0.0;
   __syncwarp();
   for (int cell = l; cell < nc; cell += 32) {
@@ -498,18 +504,11 @@ __global__ void k_coarse_lu(unsigned long long* ctr, Geom G, int B, const int* _
                        j > 0 ? cell - G.nx : -1, j < G.ny - 1 ? cell + G.nx : -1};
     for (int q = 0; q < 5; ++q) {
       if (nb[q] < 0) continue;
+      const int m0 = q == 0 ? 20 : 4 * q;   // the diagonal block itself is in planes 20..23
       for (int e = 0; e < 2; ++e)
         for (int v = 0; v < 2; ++v)
-          A[(2 * cell + e) * ld + 2 * nb[q] + v] = (double)Jb[(int64_t)(4 * q + 2 * e + v) * nc + cs];
+          A[(2 * cell + e) * ld + 2 * nb[q] + v] = (double)Jb[(int64_t)(m0 + 2 * e + v) * nc + cs];
     }
-    double d0, d1, d2, d3;   // planes 0..3 hold the inverse diagonal block
-    inv2<double>(A[(2 * cell) * ld + 2 * cell], A[(2 * cell) * ld + 2 * cell + 1],
-                 A[(2 * cell + 1) * ld + 2 * cell], A[(2 * cell + 1) * ld + 2 * cell + 1], d0, d1,
-                 d2, d3);
-    A[(2 * cell) * ld + 2 * cell] = d0;
-    A[(2 * cell) * ld + 2 * cell + 1] = d1;
-    A[(2 * cell + 1) * ld + 2 * cell] = d2;
-    A[(2 * cell + 1) * ld + 2 * cell + 1] = d3;
   }
   __syncwarp();
   int* pv = piv + (int64_t)b * kMaxCoarseUnknowns;
@@ -618,10 +617,10 @@ __device__ __forceinline__ void apply_cell(const Geom& G, int i, int j, const T*
   const T* xp = x;
   const T* xc = x + ncell;
   T vp = xp[cs], vc = xc[cs];
-  T d0, d1, d2, d3;
-  inv2<T>(Jc[0], Jc[ncell], Jc[2 * ncell], Jc[3 * ncell], d0, d1, d2, d3);
-  ap = d0 * vp + d1 * vc;
-  ac = d2 * vp + d3 * vc;
+  ap = Jc[20 * ncell] * vp;
+  ap += Jc[21 * ncell] * vc;
+  ac = Jc[22 * ncell] * vp;
+  ac += Jc[23 * ncell] * vc;
   if (i > 0) {
     const int q = cs_pos(i - 1, j, nx, half);
     vp = xp[q]; vc = xc[q];
@@ -776,7 +775,7 @@ k_smooth(unsigned long long* ctr, Geom G, int B, int colour, const int* __restri
   if (!active[b]) return;
   const int pos = (int)(idx - (int64_t)b * half);
   const int64_t ob = (int64_t)b * 2 * ncell;
-  smooth_cell<T>(G, colour, pos, J + (int64_t)b * 20 * ncell, bvec + ob, xvec + ob);
+  smooth_cell<T>(G, colour, pos, J + (int64_t)b * kJP * ncell, bvec + ob, xvec + ob);
 }
 
 template <typename T>
@@ -792,7 +791,7 @@ k_resid_restrict(unsigned long long* ctr, Geom Gf, Geom Gc, int B, const int* __
   const int b = (int)(idx / ncc);
   if (!active[b]) return;
   const int cell = (int)(idx - (int64_t)b * ncc);
-  restrict_cell<T>(Gf, Gc, cell, Jf + (int64_t)b * 20 * ncf, bf + (int64_t)b * 2 * ncf,
+  restrict_cell<T>(Gf, Gc, cell, Jf + (int64_t)b * kJP * ncf, bf + (int64_t)b * 2 * ncf,
                    xf + (int64_t)b * 2 * ncf, bc + (int64_t)b * 2 * ncc, xc + (int64_t)b * 2 * ncc);
 }
 
@@ -818,7 +817,7 @@ k_prolong(unsigned long long* ctr, Geom Gc, Geom Gf, int B, const int* __restric
 // phase of the cycle is separated by __syncthreads(). Level ks takes b from
 // and returns x to global memory (x_ks is read as the initial guess).
 // ---------------------------------------------------------------------------
-constexpr int kSmallCells = 512;
+constexpr int kSmallCells = 512;   // largest level the shared-memory kernel accepts
 constexpr int kMaxLevels = 12;
 
 template <typename T>
@@ -835,7 +834,7 @@ __host__ __device__ inline size_t small_smem_bytes(const SmallMG<T>& M) {
   size_t cells = 0;
   for (int k = 0; k <= M.ks; ++k) cells += (size_t)M.g[k].ncell();
   const int n = 2 * M.g[0].ncell();
-  return cells * 24 * sizeof(T) + (size_t)n * n * sizeof(double) + n * sizeof(double) +
+  return cells * (kJP + 4) * sizeof(T) + (size_t)n * n * sizeof(double) + n * sizeof(double) +
          n * sizeof(int) + 64;
 }
 
@@ -855,7 +854,7 @@ k_vcycle_small(unsigned long long* ctr, SmallMG<T> M, int B, const int* __restri
   T* p = (T*)smem;
   for (int k = 0; k <= ks; ++k) {
     const int nc = M.g[k].ncell();
-    J[k] = p; p += 20 * nc;
+    J[k] = p; p += kJP * nc;
     bv[k] = p; p += 2 * nc;
     xv[k] = p; p += 2 * nc;
   }
@@ -866,8 +865,8 @@ k_vcycle_small(unsigned long long* ctr, SmallMG<T> M, int B, const int* __restri
   // stage J of all small levels, b and x of the top one, the LU factors
   for (int k = 0; k <= ks; ++k) {
     const int nc = M.g[k].ncell();
-    const T* src = M.J[k] + (int64_t)bs * 20 * nc;
-    for (int e = threadIdx.x; e < 20 * nc; e += blockDim.x) J[k][e] = src[e];
+    const T* src = M.J[k] + (int64_t)bs * kJP * nc;
+    for (int e = threadIdx.x; e < kJP * nc; e += blockDim.x) J[k][e] = src[e];
   }
   {
     const int nc = M.g[ks].ncell();
@@ -1028,7 +1027,7 @@ k_vcycle_cluster(unsigned long long* ctr, SmallMG<T> M, int B, const int* __rest
   T* xv[kMaxLevels];
   for (int k = 0; k <= kc; ++k) {
     const int64_t nc = M.g[k].ncell();
-    J[k] = M.J[k] + (int64_t)b * 20 * nc;
+    J[k] = M.J[k] + (int64_t)b * kJP * nc;
     bv[k] = M.b[k] + (int64_t)b * 2 * nc;
     xv[k] = M.x[k] + (int64_t)b * 2 * nc;
   }
@@ -1105,8 +1104,8 @@ __global__ void k_transpose(unsigned long long* ctr, Geom G, int B, const int* _
   if (!active[b]) return;
   const int cell = (int)(idx - (int64_t)b * n);
   const int j = cell / nx, i = cell - j * nx;
-  const T* Jb = J + (int64_t)b * 20 * n;
-  T* Ob = JT + (int64_t)b * 20 * n;
+  const T* Jb = J + (int64_t)b * kJP * n;
+  T* Ob = JT + (int64_t)b * kJP * n;
   const int cs = cs_pos(i, j, nx, half);
   // (pp, pc, cp, cc) of the source block -> (pp, cp, pc, cc)
   auto put = [&](int dst_m0, int src_cs, int src_m0, bool has) {
@@ -1123,6 +1122,7 @@ __global__ void k_transpose(unsigned long long* ctr, Geom G, int B, const int* _
     Ob[(int64_t)(dst_m0 + 3) * n + cs] = d;
   };
   put(0, cs, 0, true);
+  put(20, cs, 20, true);
   put(4, i > 0 ? cs_pos(i - 1, j, nx, half) : 0, 8, i > 0);
   put(8, i < nx - 1 ? cs_pos(i + 1, j, nx, half) : 0, 4, i < nx - 1);
   put(12, j > 0 ? cs_pos(i, j - 1, nx, half) : 0, 16, j > 0);

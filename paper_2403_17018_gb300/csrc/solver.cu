@@ -80,7 +80,7 @@ Solver::Solver(const henry_config& cfg, int nx, int ny, int nt) : cfg_(cfg), nt_
   ks_ = 0;
   kc_ = 0;
   for (size_t k = 0; k < geoms_.size(); ++k) {
-    if (geoms_[k].ncell() <= kSmallCells) ks_ = (int)k;
+    if (geoms_[k].ncell() <= cfg_.mg_small_cells) ks_ = (int)k;
     if (geoms_[k].ncell() <= cfg_.mg_cluster_cells) kc_ = (int)k;
   }
   const int per = geoms_[kc_].ncell() / 1024;
@@ -119,7 +119,7 @@ int Solver::debug_copy(int mg_level, int what, void* dst, int64_t bytes) const {
   const MGLevel& L = levels_[mg_level];
   const size_t n = (size_t)L.g.ncell() * cap_;
   const void* src[13] = {L.J, L.b, L.x, L.p, L.c, L.phi, L.K, L.tx, L.dx, L.ty, L.dy, L.qx, L.qy};
-  const size_t size[13] = {20 * n * tsize_, 2 * n * tsize_, 2 * n * tsize_, n * 8, n * 8,
+  const size_t size[13] = {kJP * n * tsize_, 2 * n * tsize_, 2 * n * tsize_, n * 8, n * 8,
                            n * 8, n * 8, n * 8, n * 8, n * 8, n * 8, n * 8, n * 8};
   const size_t nb = (size_t)bytes < size[what] ? (size_t)bytes : size[what];
   CK(cudaDeviceSynchronize());
@@ -140,7 +140,7 @@ int Solver::ensure(int B, cudaStream_t s) {
   std::vector<Off> lo(levels_.size());
   for (size_t k = 0; k < levels_.size(); ++k) {
     const size_t n = (size_t)levels_[k].g.ncell() * Bz;
-    lo[k].J = take(20 * n * tsize_);
+    lo[k].J = take(kJP * n * tsize_);
     lo[k].b = take(2 * n * tsize_);
     lo[k].x = take(2 * n * tsize_);
     lo[k].p = take(n * 8);
@@ -549,7 +549,7 @@ int Solver::time_kernel(int which, int reps, cudaStream_t s, double* avg_ms, dou
     *flops = cells * 38.0;
   } else {
     const double cells = (double)B * G.ncell();
-    *bytes = cells * (8.0 * 8 + 24.0 * T + 16.0);
+    *bytes = cells * (8.0 * 8 + 28.0 * T + 16.0);
     *flops = cells * (46.0 + (tsize_ == sizeof(double) ? 84.0 : 0.0));
   }
   *avg_ms = ms / reps;
@@ -593,7 +593,7 @@ int Solver::ensure_adjoint(int B, int nckpt, int seglen) {
   const size_t o_p2 = take((size_t)adj_nchunk_ * B * 8);
   std::vector<size_t> o_jt(levels_.size());
   for (size_t k = 0; k < levels_.size(); ++k)
-    o_jt[k] = take(20 * (size_t)levels_[k].g.ncell() * B * tsize_);
+    o_jt[k] = take(kJP * (size_t)levels_[k].g.ncell() * B * tsize_);
   CK(cudaMalloc(&adj_arena_, off));
   char* a = (char*)adj_arena_;
   ckpt_ = (double*)(a + o_ck);

@@ -296,3 +296,24 @@ def test_fused_multigrid_kernels_equal_plain_launches_bitwise(precision, level):
         res.append(out)
     for k in ("c", "p", "q", "iters"):
         assert torch.equal(res[0][k], res[1][k]), k
+
+
+@pytest.mark.parametrize("precision", [hb.PREC_FP64, hb.PREC_FP32_MG])
+def test_shared_memory_vcycle_threshold_does_not_change_the_result(precision):
+    """Moving the boundary between per-level launches and the shared-memory
+    V-cycle kernel (no grid, the 32-cell grid, the 512-cell grid of level 2's
+    hierarchy) changes only which kernel runs each level's operations, so the
+    solutions agree bit for bit."""
+    res = []
+    for sc in (0, 32, 128, 512):
+        cfg = tight_config(nlevels=3, nt0=1, T=1800.0, precision=precision,
+                           mg_small_cells=sc, vcycles=2)
+        ctx = hb.Context(cfg)
+        out = ctx.solve(2, xi_cuda(2, 5, 3), want_c=True, want_p=True, want_iters=True)
+        assert out["status"].cpu().numpy().tolist() == [0, 0, 0]
+        res.append(out)
+    for r in res[1:]:
+        for k in ("c", "p", "q", "iters"):
+            assert torch.equal(res[0][k], r[k]), k
+    with pytest.raises(hb.HenryError):
+        hb.Context(hb.default_config(mg_small_cells=513))
