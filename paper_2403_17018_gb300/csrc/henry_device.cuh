@@ -68,14 +68,17 @@ struct FaceD {
 // q is the area-weighted face flux A q.n: computed from p unless Q_GIVEN, in
 // which case the caller supplies it (coarse multigrid levels linearise about
 // the restricted fine-level flux field) and the pressures are not used.
-template <typename JT, bool WANT_J, bool Q_GIVEN>
+// VERT: a vertical (south-north) face, the only kind with a gravity term;
+// horizontal faces skip it (and its derivative) instead of multiplying by a
+// zero gd.
+template <typename JT, bool WANT_J, bool Q_GIVEN, bool VERT>
 __device__ __forceinline__ void face_flux(const Phys& P, double pL, double cL, double pU, double cU,
                                           double t, double dco, double gd, double& q,
                                           double& Fm, double& Fs, FaceD<JT>& J) {
   const double rL = P.rho0 + P.drho * cL;
   const double rU = P.rho0 + P.drho * cU;
   const double rbar = 0.5 * (rL + rU);
-  if (!Q_GIVEN) q = -t * ((pU - pL) + (0.5 * P.drho) * (cL + cU) * gd);
+  if (!Q_GIVEN) q = VERT ? -t * ((pU - pL) + (0.5 * P.drho) * (cL + cU) * gd) : -t * (pU - pL);
   const bool up = q >= 0.0;
   const double rup = up ? rL : rU;
   const double rcup = up ? rL * cL : rU * cU;
@@ -88,19 +91,25 @@ __device__ __forceinline__ void face_flux(const Phys& P, double pL, double cL, d
     const JT t_ = (JT)t, q_ = (JT)q, dco_ = (JT)dco, cL_ = (JT)cL, cU_ = (JT)cU;
     const JT dr = (JT)P.drho, r0 = (JT)P.rho0;
     const JT rL_ = r0 + dr * cL_, rU_ = r0 + dr * cU_;
-    const JT s_ = -t_ * (JT)gd * (JT)0.5 * dr;       // dq/dc_L = dq/dc_U
     const JT rup_ = up ? rL_ : rU_;
     const JT rcup_ = up ? rL_ * cL_ : rU_ * cU_;
     const JT diffc = -dco_ * (JT)0.5 * dr * (cU_ - cL_);   // d(-dco rbar dc)/dc from rbar
     const JT drb = dco_ * (JT)0.5 * (rL_ + rU_);
     J.mLp = t_ * rup_;
     J.mUp = -t_ * rup_;
-    J.mLc = s_ * rup_ + (up ? q_ * dr : (JT)0);
-    J.mUc = s_ * rup_ + (up ? (JT)0 : q_ * dr);
+    J.mLc = up ? q_ * dr : (JT)0;
+    J.mUc = up ? (JT)0 : q_ * dr;
     J.sLp = t_ * rcup_;
     J.sUp = -t_ * rcup_;
-    J.sLc = s_ * rcup_ + (up ? q_ * (rL_ + dr * cL_) : (JT)0) + diffc + drb;
-    J.sUc = s_ * rcup_ + (up ? (JT)0 : q_ * (rU_ + dr * cU_)) + diffc - drb;
+    J.sLc = (up ? q_ * (rL_ + dr * cL_) : (JT)0) + diffc + drb;
+    J.sUc = (up ? (JT)0 : q_ * (rU_ + dr * cU_)) + diffc - drb;
+    if (VERT) {
+      const JT s_ = -t_ * (JT)gd * (JT)0.5 * dr;       // dq/dc_L = dq/dc_U
+      J.mLc += s_ * rup_;
+      J.mUc += s_ * rup_;
+      J.sLc += s_ * rcup_;
+      J.sUc += s_ * rcup_;
+    }
   }
 }
 
@@ -139,14 +148,14 @@ struct CellIn {
   double y;                          // cell-centre y (right boundary pressure)
 };
 
-// Residual (FP64) and, optionally, the 20 Jacobian entries of one cell:
+// Residual (FP64) and, optionally, the 20 Jacobian entries of one cell;
+// vtau = cell volume / time step:
 // J[0..3] = dR_P/du_P, J[4..7] W, J[8..11] E, J[12..15] S, J[16..19] N;
 // each block (pp, pc, cp, cc), row = equation, column = variable.
 template <typename JT, bool WANT_J, bool Q_GIVEN = false>
-__device__ __forceinline__ void cell_residual(const Phys& P, const Geom& G, double tau,
+__device__ __forceinline__ void cell_residual(const Phys& P, const Geom& G, double vtau,
                                               CellIn& in, double& Rp, double& Rc, JT* J) {
-  const double V = G.hx * G.hy;
-  const double vt = V * in.phi / tau;
+  const double vt = vtau * in.phi;
   const double rho = P.rho0 + P.drho * in.c;
   const double rho_o = P.rho0 + P.drho * in.c_old;
   Rp = vt * (rho - rho_o);
@@ -162,7 +171,7 @@ __device__ __forceinline__ void cell_residual(const Phys& P, const Geom& G, doub
   const double gdy = P.g * G.hy;
   // west face: L = W, U = P; contributes -F to P
   if (in.hasW) {
-    face_flux<JT, WANT_J, Q_GIVEN>(P, in.pW, in.cW, in.p, in.c, in.tW, in.dW, 0.0, in.qW, Fm, Fs, d);
+    face_flux<JT, WANT_J, Q_GIVEN, false>(P, in.pW, in.cW, in.p, in.c, in.tW, in.dW, 0.0, in.qW, Fm, Fs, d);
     Rp -= Fm;
     Rc -= Fs;
     if (WANT_J) {
@@ -180,7 +189,7 @@ __device__ __forceinline__ void cell_residual(const Phys& P, const Geom& G, doub
   }
   // east face: L = P, U = E; contributes +F to P
   if (in.hasE) {
-    face_flux<JT, WANT_J, Q_GIVEN>(P, in.p, in.c, in.pE, in.cE, in.tE, in.dE, 0.0, in.qE, Fm, Fs, d);
+    face_flux<JT, WANT_J, Q_GIVEN, false>(P, in.p, in.c, in.pE, in.cE, in.tE, in.dE, 0.0, in.qE, Fm, Fs, d);
     Rp += Fm;
     Rc += Fs;
     if (WANT_J) {
@@ -212,7 +221,7 @@ __device__ __forceinline__ void cell_residual(const Phys& P, const Geom& G, doub
   }
   // south face: L = S, U = P (e = +y); contributes -F
   if (in.hasS) {
-    face_flux<JT, WANT_J, Q_GIVEN>(P, in.pS, in.cS, in.p, in.c, in.tS, in.dS, gdy, in.qS, Fm, Fs, d);
+    face_flux<JT, WANT_J, Q_GIVEN, true>(P, in.pS, in.cS, in.p, in.c, in.tS, in.dS, gdy, in.qS, Fm, Fs, d);
     Rp -= Fm;
     Rc -= Fs;
     if (WANT_J) {
@@ -222,7 +231,7 @@ __device__ __forceinline__ void cell_residual(const Phys& P, const Geom& G, doub
   }
   // north face: L = P, U = N; contributes +F
   if (in.hasN) {
-    face_flux<JT, WANT_J, Q_GIVEN>(P, in.p, in.c, in.pN, in.cN, in.tN, in.dN, gdy, in.qN, Fm, Fs, d);
+    face_flux<JT, WANT_J, Q_GIVEN, true>(P, in.p, in.c, in.pN, in.cN, in.tN, in.dN, gdy, in.qN, Fm, Fs, d);
     Rp += Fm;
     Rc += Fs;
     if (WANT_J) {

@@ -177,8 +177,8 @@ __global__ void k_end_step(unsigned long long* ctr, int* __restrict__ step) {
 // R_p^2 + R_c^2 per block. NATURAL = true: writes R [B][2][ncell] and J
 // [B][20][ncell] in natural cell order (FP64), for tests.
 template <typename T, bool NATURAL>
-__global__ void __launch_bounds__(kBlock)
-k_resjac(unsigned long long* ctr, Phys P, Geom G, double tau, int B, ResTile tl,
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 8 ? 2 : 3)
+k_resjac(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, ResTile tl,
          const double* __restrict__ p, const double* __restrict__ c,
          const double* __restrict__ c_old, const double* __restrict__ phi,
          const double* __restrict__ K, const double* __restrict__ tx,
@@ -203,7 +203,6 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double tau, int B, ResTile tl,
   const int64_t o = (int64_t)b * ncell;
   const double* pb_ = p + o;
   const double* cb_ = c + o;
-  const double V = G.hx * G.hy;
   const double gdy = P.g * G.hy;
   const double A = G.hy;
   const double dcoL = 2.0 * A * P.D / G.hx;      // times phi_P
@@ -219,7 +218,7 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double tau, int B, ResTile tl,
     if (j0 > 0) {
       const int id = (j0 - 1) * nx + i;
       double q;
-      face_flux<T, true, false>(P, pb_[id], cb_[id], pP, cP, ty[o + id], dy[o + id], gdy, q, FmS,
+      face_flux<T, true, false, true>(P, pb_[id], cb_[id], pP, cP, ty[o + id], dy[o + id], gdy, q, FmS,
                                 FsS, dS);
     }
   }
@@ -234,7 +233,7 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double tau, int B, ResTile tl,
     if (cv) {
       phiP = phi[o + id];
       if (i < nx - 1) {
-        face_flux<T, true, false>(P, pP, cP, pb_[id + 1], cb_[id + 1], tx[o + id], dx[o + id], 0.0,
+        face_flux<T, true, false, false>(P, pP, cP, pb_[id + 1], cb_[id + 1], tx[o + id], dx[o + id], 0.0,
                                   qE, FmE, FsE, dE);
       } else {
         const double pbd = P.drho * P.g * (P.Ly - (j + 0.5) * G.hy);
@@ -258,7 +257,7 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double tau, int B, ResTile tl,
           dW.sLp = shD[4][t - 1]; dW.sLc = shD[5][t - 1]; dW.sUp = shD[6][t - 1]; dW.sUc = shD[7][t - 1];
         } else {
           double q;
-          face_flux<T, true, false>(P, pb_[id - 1], cb_[id - 1], pP, cP, tx[o + id - 1],
+          face_flux<T, true, false, false>(P, pb_[id - 1], cb_[id - 1], pP, cP, tx[o + id - 1],
                                     dx[o + id - 1], 0.0, q, FmW, FsW, dW);
         }
       }
@@ -268,10 +267,10 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double tau, int B, ResTile tl,
       if (j < ny - 1) {
         pN = pb_[id + nx];
         cN = cb_[id + nx];
-        face_flux<T, true, false>(P, pP, cP, pN, cN, ty[o + id], dy[o + id], gdy, qN, FmN, FsN, dN);
+        face_flux<T, true, false, true>(P, pP, cP, pN, cN, ty[o + id], dy[o + id], gdy, qN, FmN, FsN, dN);
       }
       // accumulation
-      const double vt = V * phiP / tau;
+      const double vt = vtau * phiP;
       const double rho = P.rho0 + P.drho * cP;
       const double cO = c_old[o + id];
       const double rho_o = P.rho0 + P.drho * cO;
@@ -445,7 +444,7 @@ __global__ void k_restrict_state(unsigned long long* ctr, Geom Gf, Geom Gc, int 
 // Jacobian of a coarse multigrid level from its own state and fields.
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
-k_jac(unsigned long long* ctr, Phys P, Geom G, double tau, int B, const int* __restrict__ active,
+k_jac(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, const int* __restrict__ active,
       const double* __restrict__ p, const double* __restrict__ c, const double* __restrict__ phi,
       const double* __restrict__ K, const double* __restrict__ tx, const double* __restrict__ dx,
       const double* __restrict__ ty, const double* __restrict__ dy, const double* __restrict__ qx,
@@ -471,7 +470,7 @@ k_jac(unsigned long long* ctr, Phys P, Geom G, double tau, int B, const int* __r
   in.qS = in.hasS ? qy[o + id - G.nx] : 0.0;
   double Rp, Rc;
   T Jc[20];
-  cell_residual<T, true, true>(P, G, tau, in, Rp, Rc, Jc);
+  cell_residual<T, true, true>(P, G, vtau, in, Rp, Rc, Jc);
   T* Jb = J + (int64_t)b * kJP * ncell + cs_pos(i, j, G.nx, G.half());
 #pragma unroll
   for (int m = 0; m < 4; ++m) Jb[(int64_t)(20 + m) * ncell] = Jc[m];

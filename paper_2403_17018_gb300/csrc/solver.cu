@@ -306,7 +306,7 @@ void Solver::enqueue_coarse_ops(int B, cudaStream_t s) {
     k_restrict_state<<<grid1((int64_t)B * C.g.ncell()), kBlock, 0, s>>>(
         counter_, F.g, C.g, B, active_, F.c, F.qx, F.qy, C.c, C.qx, C.qy);
     k_jac<T><<<grid1((int64_t)B * C.g.ncell()), kBlock, 0, s>>>(
-        counter_, phys_, C.g, tau_, B, active_, C.p, C.c, C.phi, C.K, C.tx, C.dx, C.ty, C.dy,
+        counter_, phys_, C.g, C.g.hx * C.g.hy / tau_, B, active_, C.p, C.c, C.phi, C.K, C.tx, C.dx, C.ty, C.dy,
         C.qx, C.qy, (T*)C.J);
   }
 }
@@ -350,7 +350,7 @@ void Solver::enqueue_resjac_check(int B, cudaStream_t s, bool set_cond) {
   MGLevel& F = levels_.back();
   const Geom& G = F.g;
   k_resjac<T, false><<<dim3(nchunk_, B), kBlock, 0, s>>>(
-      counter_, phys_, G, tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx, F.ty, F.dy, qin_,
+      counter_, phys_, G, G.hx * G.hy / tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx, F.ty, F.dy, qin_,
       active_, (T*)F.J, (T*)F.b, (T*)F.x, partial_, F.qx, F.qy);
   // residual scaled to units of c per step: RMS(R) * tau / (V phi0 rho0)
   const double scale = tau_ / (G.hx * G.hy * cfg_.phi0 * cfg_.rho0);
@@ -502,7 +502,7 @@ void Solver::launch_timed(int which, int B, cudaStream_t s) {
         counter_, F.g, B, 0, active_, (const T*)F.J, (const T*)F.b, (T*)F.x);
   } else {
     k_resjac<T, false><<<dim3(nchunk_, B), kBlock, 0, s>>>(
-        counter_, phys_, F.g, tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx, F.ty, F.dy,
+        counter_, phys_, F.g, F.g.hx * F.g.hy / tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx, F.ty, F.dy,
         qin_, active_, (T*)F.J, (T*)F.b, (T*)F.x, partial_, F.qx, F.qy);
   }
 }
@@ -679,10 +679,10 @@ int Solver::adjoint_t(const double* xi, const double* logk, int B, int qoi, int 
       k_activate<<<grid1(B), kBlock, 0, s>>>(counter_, B, status_w_, active_, it_step_);
       // operators of step st: J (multigrid type, every level) and exact FP64 J
       k_resjac<T, false><<<dim3(nchunk_, B), kBlock, 0, s>>>(
-          counter_, phys_, G, tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx, F.ty, F.dy,
+          counter_, phys_, G, G.hx * G.hy / tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx, F.ty, F.dy,
           qin_, active_, (T*)F.J, (T*)F.b, (T*)F.x, partial_, F.qx, F.qy);
       k_resjac<double, true><<<dim3(nchunk_, B), kBlock, 0, s>>>(
-          counter_, phys_, G, tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx, F.ty, F.dy,
+          counter_, phys_, G, G.hx * G.hy / tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx, F.ty, F.dy,
           qin_, active_, J64_, res_, nullptr, nullptr, nullptr, nullptr);
       enqueue_coarse_ops<T>(B, s);
       for (size_t k = 0; k < levels_.size(); ++k)
@@ -756,7 +756,7 @@ cudaError_t launch_residual_jacobian(const Phys& P, const Geom& G, double tau, i
   k_reduce_pressure<<<grid, kBlock, 0, s>>>(P, G, B, p, pr);
   const ResTile tl = make_res_tile(G.nx, G.ny);
   k_resjac<double, true><<<dim3(tl.ntx * tl.nty, B), kBlock, 0, s>>>(
-      nullptr, P, G, tau, B, tl, pr, c, c_old, phi, K, tx, dx, ty, dy, qin, nullptr, J, R, nullptr,
+      nullptr, P, G, G.hx * G.hy / tau, B, tl, pr, c, c_old, phi, K, tx, dx, ty, dy, qin, nullptr, J, R, nullptr,
       nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }

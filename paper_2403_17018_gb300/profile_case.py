@@ -26,6 +26,11 @@ def main(argv=None):
                     help="implicit Euler steps of the level (rounded to a multiple of 2^level)")
     ap.add_argument("--precision", choices=["fp64", "fp32mg"], default="fp64")
     ap.add_argument("--vcycles", type=int, default=2)
+    ap.add_argument("--nu", type=int, nargs=2, default=(2, 2), metavar=("NU1", "NU2"),
+                    help="pre- and post-smoothing sweeps")
+    ap.add_argument("--small-cells", type=int, default=512,
+                    help="largest multigrid level (cells per sample) run by the shared-memory "
+                         "V-cycle kernel; 0 disables it")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--loop", choices=["graph", "host"], default="graph",
                     help="host: plain launches with a host convergence check (visible to ncu "
@@ -43,6 +48,7 @@ def main(argv=None):
     # level l runs k 2^l steps with k = max(1, steps // 2^l)
     k = max(1, a.steps // f)
     cfg = hb.default_config(nlevels=a.level + 1, precision=prec, vcycles=a.vcycles,
+                            nu1=a.nu[0], nu2=a.nu[1], mg_small_cells=a.small_cells,
                             nt0=k, T=1800.0 * k,
                             loop_mode=hb.LOOP_HOST if a.loop == "host" else hb.LOOP_GRAPH)
     ctx = hb.Context(cfg)
