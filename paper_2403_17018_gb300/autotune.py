@@ -54,7 +54,7 @@ def best_schedule(level, precision, batch, gpu=None, nx0=32, ny0=16, path=CACHE)
     return load_cache(path).get(_key(gpu, level, precision, batch, nx0, ny0))
 
 
-def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2), log=None):
+def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2), log=None, n_xi=3):
     """Time every candidate schedule on `steps` steps of level `level`;
     returns the best {vcycles, nu1, nu2, mg_small_cells, split, solves_per_s}
     and the table."""
@@ -64,14 +64,14 @@ def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2),
     prec = hb.PREC_FP64 if precision == "fp64" else hb.PREC_FP32_MG
     f = 1 << level
     k = max(1, steps // f)
-    xi = torch.from_numpy(xi_batch(level, 0, batch)).cuda()
+    xi = torch.from_numpy(xi_batch(level, 0, batch, n_xi=n_xi)).cuda()
     table = []
     for vc, (n1, n2), sc, split in itertools.product(
             CANDIDATES["vcycles"], CANDIDATES["nu"], CANDIDATES.get("small_cells", (512,)), splits):
         if batch % split:
             continue
         cfg = hb.default_config(nlevels=level + 1, precision=prec, vcycles=vc, nu1=n1, nu2=n2,
-                                mg_small_cells=sc, nt0=k, T=1800.0 * k)
+                                mg_small_cells=sc, nt0=k, T=1800.0 * k, n_xi=n_xi)
         ctx = hb.Context(cfg)
         sub = batch // split
         parts = [xi[i * sub:(i + 1) * sub].contiguous() for i in range(split)]

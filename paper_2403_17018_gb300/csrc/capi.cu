@@ -124,7 +124,7 @@ int henry_default_config(henry_config* c) {
   c->precision = HENRY_PREC_FP64;
   c->loop_mode = HENRY_LOOP_GRAPH;
   c->newton_rtol = 1e-10;
-  c->newton_atol = 1e-12;
+  c->newton_atol = 1e-11;
   c->newton_maxit = 30;
   c->nu1 = 2;
   c->nu2 = 2;

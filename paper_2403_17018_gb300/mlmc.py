@@ -106,36 +106,80 @@ def fit_alpha(means):
 
 
 class GpuSampler:
-    """Level pairs on the GPU through the C ABI; statistics merged on device."""
+    """Level pairs on the GPU through the C ABI; statistics merged on device.
 
-    def __init__(self, cfg, rank=0, world=1):
+    `schedules` (level -> {vcycles, nu1, nu2, mg_small_cells}, e.g. from the
+    autotuner) gives every level its own context and multigrid schedule.
+    Each level has its own CUDA stream, so `batches` can run the pending
+    pairs of all levels at the same time."""
+
+    def __init__(self, cfg, rank=0, world=1, schedules=None):
         import torch
         from paper_2403_17018_gb300 import binding as hb
         self.torch = torch
         self.hb = hb
-        self.ctx = hb.Context(cfg)
         self.n_xi = cfg.n_xi
         self.rank, self.world = rank, world
+        self.ctxs = {}
+        shared = None
+        for l in range(cfg.nlevels):
+            sc = (schedules or {}).get(l)
+            if sc is None:
+                shared = shared or hb.Context(cfg)
+                self.ctxs[l] = shared
+            else:
+                kw = cfg.as_dict()
+                kw.update({k: sc[k] for k in ("vcycles", "nu1", "nu2", "mg_small_cells") if k in sc})
+                self.ctxs[l] = hb.Context(hb.default_config(**kw))
+        self.streams = {l: torch.cuda.Stream() for l in range(cfg.nlevels)}
+
+    def _slice(self, first, count):
+        lo = first + (count * self.rank) // self.world
+        hi = first + (count * (self.rank + 1)) // self.world
+        return lo, hi
+
+    def batches(self, requests):
+        """Run several (level, first, count) requests at once, one stream per
+        level (at most one request per level). Returns, per request, (n,
+        mean_f, m2_f, mean_d, m2_d, seconds, failed); seconds is the
+        request's device time on its stream (CUDA events)."""
+        from paper_2403_17018_gb300.inputs import xi_batch
+        torch = self.torch
+        assert len({r[0] for r in requests}) == len(requests), "one request per level"
+        launched = []
+        for level, first, count in requests:
+            lo, hi = self._slice(first, count)
+            if hi <= lo:
+                launched.append(None)
+                continue
+            s = self.streams[level]
+            xi = torch.from_numpy(xi_batch(level, lo, hi - lo, n_xi=self.n_xi)).pin_memory()
+            with torch.cuda.stream(s):
+                xi_d = xi.to("cuda", non_blocking=True)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                out = self.ctxs[level].sample_pairs(level, xi_d, stream=s)
+                e1.record(s)
+            launched.append((level, xi, xi_d, out, e0, e1))
+        res = []
+        for item in launched:
+            if item is None:
+                res.append((0, np.zeros(NQ), np.zeros(NQ), np.zeros(NQ), np.zeros(NQ), 0.0, 0))
+                continue
+            level, _, _, (qf, qc, _, _, st), e0, e1 = item
+            S = self.hb.LevelStats()
+            self.ctxs[level].level_stats(level, qf, qc, st, S, stream=self.streams[level])
+            e1.synchronize()
+            failed = int((st != 0).sum().item())
+            res.append((S.n, np.array(S.mean_f[:]), np.array(S.m2_f[:]), np.array(S.mean_d[:]),
+                        np.array(S.m2_d[:]), e0.elapsed_time(e1) / 1e3, failed))
+        return res
 
     def batch(self, level, first, count):
         """Run pairs first..first+count-1 of `level` (this rank's slice);
         returns (n, mean_f, m2_f, mean_d, m2_d, seconds, failed)."""
-        from paper_2403_17018_gb300.inputs import xi_batch
-        torch = self.torch
-        lo = first + (count * self.rank) // self.world
-        hi = first + (count * (self.rank + 1)) // self.world
-        if hi <= lo:
-            return 0, np.zeros(NQ), np.zeros(NQ), np.zeros(NQ), np.zeros(NQ), 0.0, 0
-        xi = torch.from_numpy(xi_batch(level, lo, hi - lo, n_xi=self.n_xi)).cuda()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        qf, qc, _, _, st = self.ctx.sample_pairs(level, xi)
-        S = self.hb.LevelStats()
-        self.ctx.level_stats(level, qf, qc, st, S)
-        dt = time.perf_counter() - t0
-        failed = int((st != 0).sum().item())
-        return (S.n, np.array(S.mean_f[:]), np.array(S.m2_f[:]), np.array(S.mean_d[:]),
-                np.array(S.m2_d[:]), dt, failed)
+        return self.batches([(level, first, count)])[0]
 
 
 def _merge_ranks(levels, dist):
@@ -158,8 +202,11 @@ def _merge_ranks(levels, dist):
 
 
 def run(sampler, L, eps, qois=(3, 4, 5), pilot=None, max_batch=None, var_budget_fraction=0.5,
-        max_rounds=20, log=None, dist=None, state=None):
+        max_rounds=20, log=None, dist=None, state=None, concurrent=True):
     """Adaptive MLMC on levels 0..L to RMSE eps for the QoIs `qois`.
+    With `concurrent` and a sampler that has `batches`, the pending pairs
+    of all levels run at the same time (cost per pair then measured under
+    sharing, which scales every level's cost alike to first order).
 
     Returns a dict with the estimate per QoI, Var Y, the bias estimate, the
     RMSE estimate, samples and cost per level and the wall time. `state`
@@ -173,18 +220,31 @@ def run(sampler, L, eps, qois=(3, 4, 5), pilot=None, max_batch=None, var_budget_
     rounds = 0
     qs = list(qois)
     levels = _merge_ranks(local, dist)
+    def record(l, cnt, out):
+        n, mf, m2f, md, m2d, dt, failed = out
+        chan_merge(local[l], n, mf, m2f, md, m2d)
+        local[l].drawn += cnt
+        local[l].seconds = dt
+        local[l].timed_pairs = cnt
+        local[l].failed += failed
+
     while True:
-        for l in range(L + 1):
-            need = target[l] - levels[l].n
-            while need > 0:
-                cnt = min(need, max_batch[l])
-                n, mf, m2f, md, m2d, dt, failed = sampler.batch(l, local[l].drawn, cnt)
-                chan_merge(local[l], n, mf, m2f, md, m2d)
-                local[l].drawn += cnt
-                local[l].seconds = dt
-                local[l].timed_pairs = cnt
-                local[l].failed += failed
-                need -= cnt
+        need = [target[l] - levels[l].n for l in range(L + 1)]
+        if concurrent and hasattr(sampler, "batches"):
+            # waves: the next batch of every level that still needs pairs,
+            # all levels at once (one stream per level)
+            while any(k > 0 for k in need):
+                wave = [(l, local[l].drawn, min(need[l], max_batch[l]))
+                        for l in range(L + 1) if need[l] > 0]
+                for (l, _, cnt), out in zip(wave, sampler.batches(wave)):
+                    record(l, cnt, out)
+                    need[l] -= cnt
+        else:
+            for l in range(L + 1):
+                while need[l] > 0:
+                    cnt = min(need[l], max_batch[l])
+                    record(l, cnt, sampler.batch(l, local[l].drawn, cnt))
+                    need[l] -= cnt
         levels = _merge_ranks(local, dist)
         V = np.array([[lv.var_d()[q] for q in qs] for lv in levels])          # [L+1, nq]
         bad = [l for l in range(L + 1) if not np.all(np.isfinite(V[l]))]
@@ -227,7 +287,12 @@ def main(argv=None):
     ap.add_argument("--eps", type=float, default=1e-3)
     ap.add_argument("--n-xi", type=int, default=6)
     ap.add_argument("--precision", choices=["fp64", "fp32mg"], default="fp32mg")
-    ap.add_argument("--vcycles", type=int, default=2)
+    ap.add_argument("--vcycles", type=int, default=3)
+    ap.add_argument("--tune", action="store_true",
+                    help="autotune the multigrid schedule of every level on its largest batch "
+                         "first (cached; the tuning time is reported apart from the MLMC wall time)")
+    ap.add_argument("--sequential", action="store_true",
+                    help="run the levels one after another instead of on concurrent streams")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     import torch
@@ -243,10 +308,32 @@ def main(argv=None):
         dist.init_process_group("nccl")
     cfg = hb.default_config(nlevels=a.levels, n_xi=a.n_xi, vcycles=a.vcycles,
                             precision=hb.PREC_FP64 if a.precision == "fp64" else hb.PREC_FP32_MG)
-    sampler = GpuSampler(cfg, rank, world)
+    schedules, tune_s = None, 0.0
+    if a.tune:
+        from paper_2403_17018_gb300 import autotune as A
+        # the schedules that won on some level of the batched benchmark
+        A.CANDIDATES = {"vcycles": (2, 3), "nu": ((2, 2), (3, 3)), "small_cells": (128, 512)}
+        t0 = time.perf_counter()
+        schedules = {}
+        gpu = torch.cuda.get_device_name(0)
+        cache = A.load_cache()
+        for l in range(a.levels):
+            B = max(1, max(32, 16384 >> (2 * l)) // world)
+            key = A._key(gpu, l, a.precision, B, cfg.nx0, cfg.ny0) + f"|xi{a.n_xi}"
+            if key not in cache:
+                cache[key], _ = A.tune_level(l, B, a.precision, steps=4, reps=1, splits=(1,),
+                                             n_xi=a.n_xi)
+            schedules[l] = cache[key]
+        A.save_cache(cache)
+        tune_s = time.perf_counter() - t0
+    sampler = GpuSampler(cfg, rank, world, schedules=schedules)
     log = (lambda d: print(json.dumps(d), flush=True)) if rank == 0 else None
-    res = run(sampler, a.levels - 1, a.eps, log=log, dist=dist)
-    res.update({"precision": a.precision, "n_gpus": world})
+    res = run(sampler, a.levels - 1, a.eps, log=log, dist=dist, concurrent=not a.sequential)
+    res.update({"precision": a.precision, "n_gpus": world, "tuning_s": tune_s,
+                "concurrent_levels": not a.sequential,
+                "schedules": {l: {k: v for k, v in sc.items() if k in ("vcycles", "nu1", "nu2",
+                                                                      "mg_small_cells")}
+                              for l, sc in (schedules or {}).items()}})
     if rank == 0:
         out = {k: v for k, v in res.items() if k != "state"}
         print(json.dumps(out))

@@ -134,3 +134,16 @@ def test_a_level_without_valid_samples_stops_the_run():
 
     with pytest.raises(RuntimeError, match="level"):
         M.run(Failing(), 2, 0.01, qois=(0,))
+
+
+def test_concurrent_waves_give_the_sequential_result():
+    """With a sampler that runs several levels at once, every level still
+    merges its batches in the same order, so the result is identical."""
+    class Multi(FakeSampler):
+        def batches(self, reqs):
+            return [self.batch(*r) for r in reqs]
+
+    seq = M.run(FakeSampler(), 3, 0.01, qois=(0, 1), max_batch=[64, 16, 8, 4], concurrent=False)
+    con = M.run(Multi(), 3, 0.01, qois=(0, 1), max_batch=[64, 16, 8, 4], concurrent=True)
+    for k in ("estimate", "var_Y", "n", "mean_l", "V_l"):
+        assert con[k] == seq[k], k

@@ -10,6 +10,8 @@ term, a wrong sign or index, or a swapped operand fails at least one of them:
   salt/fluid balance        -> interior face fluxes cancel (scatter signs)
   Jacobian vs central FD    -> colouring and assembly of the exact Jacobian
   time order                -> first order of implicit Euler (section 2.3)
+  grid convergence          -> h/tau scaling of every term of the coupled
+                               problem (successive levels approach each other)
   allocation table          -> Eq. M_ell against the paper's printed numbers
 """
 import json
@@ -278,3 +280,29 @@ def test_fit_rate_recovers_geometric_decay():
     vals = 3.0 * 2.0 ** (-1.7 * lev)
     rate, zeta = M.fit_rate(lev, vals, base=2.0)
     assert abs(rate - 1.7) < 1e-12 and abs(zeta - math.log2(3.0)) < 1e-12
+
+
+def test_grid_convergence_order_of_the_coupled_problem():
+    """Observed convergence of the full density-driven problem (section 2.3,
+    first order in h and tau together): on levels 0, 1, 2 with tau halved
+    with h (4, 8, 16 steps of 1800/2^l s) and one xi, the distance between
+    successive levels, || c_l - R c_{l+1} ||_2 with R the average over the
+    four children, shrinks by about 2 per level. A wrong scaling of a flux
+    or of the accumulation with h or tau stops the differences from
+    decaying like this."""
+    ph = H.Physics()
+    xi = np.array([0.3, -0.5, 0.7])
+    cs = []
+    for level in range(3):
+        g = _grid(32 << level, 16 << level, 4 << level, 4 * 1800.0)
+        cs.append(H.solve(g, ph, xi)["c"])
+
+    def R(c):
+        return 0.25 * (c[0::2, 0::2] + c[1::2, 0::2] + c[0::2, 1::2] + c[1::2, 1::2])
+
+    d = [math.sqrt(np.mean((cs[l] - R(cs[l + 1])) ** 2)) for l in range(2)]
+    assert 1.5 < d[0] / d[1] < 2.5, d
+    # and P0-prolongated coarse minus fine shrinks too (the MLMC field
+    # correction of the level pairs tends to zero)
+    P0 = [H.prolong_constant(cs[l]) - cs[l + 1] for l in range(2)]
+    assert math.sqrt(np.mean(P0[1] ** 2)) < math.sqrt(np.mean(P0[0] ** 2))
