@@ -655,17 +655,21 @@ __device__ __forceinline__ void apply_cell(const Geom& G, int i, int j, const T*
 }
 
 // Coarse cell `cell` of level k-1: b_c = sum over the four children of
-// (b - A x) on level k (finite-volume restriction), x_c = 0.
+// (b - A x) on level k (finite-volume restriction), x_c = 0. red_only: the
+// last operation on level k was a black half-sweep, which leaves the
+// residual of every black cell zero up to rounding, so only the two red
+// children (i + j even) are evaluated.
 template <typename T>
 __device__ __forceinline__ void restrict_cell(const Geom& Gf, const Geom& Gc, int cell,
                                               const T* __restrict__ Jf, const T* __restrict__ bf,
                                               const T* __restrict__ xf, T* __restrict__ bc,
-                                              T* __restrict__ xc) {
+                                              T* __restrict__ xc, bool red_only) {
   const int J = cell / Gc.nx, I = cell - J * Gc.nx;
   const int ncf = Gf.ncell(), hf = Gf.half(), ncc = Gc.ncell();
   T sp = 0, sc = 0;
 #pragma unroll
   for (int c4 = 0; c4 < 4; ++c4) {
+    if (red_only && (c4 == 1 || c4 == 2)) continue;
     const int i = 2 * I + (c4 & 1), j = 2 * J + (c4 >> 1);
     T ap, ac;
     apply_cell(Gf, i, j, Jf, xf, ap, ac);
@@ -680,9 +684,19 @@ __device__ __forceinline__ void restrict_cell(const Geom& Gf, const Geom& Gc, in
   xc[ncc + csc] = (T)0;
 }
 
+// Natural index of the black cell at colour-split position `pos`.
+__device__ __forceinline__ int black_cell(const Geom& G, int pos) {
+  const int hx2 = G.nx >> 1;
+  const int j = pos / hx2, k = pos - j * hx2;
+  return j * G.nx + 2 * k + ((j + 1) & 1);
+}
+
 // Fine cell `cell` of level k: x_f += P x_c, cell-centred bilinear
 // interpolation (9/16, 3/16, 3/16, 1/16), constant extrapolation at the
-// domain boundary.
+// domain boundary. When post-smoothing follows, only black cells are
+// corrected: the red half-sweep that comes next overwrites every red value
+// without reading it (a point update reads its neighbours only), so the
+// result is the same.
 template <typename T>
 __device__ __forceinline__ void prolong_cell(const Geom& Gc, const Geom& Gf, int cell,
                                              const T* __restrict__ xc, T* __restrict__ xf) {
@@ -781,7 +795,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock)
 k_resid_restrict(unsigned long long* ctr, Geom Gf, Geom Gc, int B, const int* __restrict__ active,
                  const T* __restrict__ Jf, const T* __restrict__ bf, const T* __restrict__ xf,
-                 T* __restrict__ bc, T* __restrict__ xc) {
+                 T* __restrict__ bc, T* __restrict__ xc, int red_only) {
   HENRY_COUNT_LAUNCH(ctr);
   const int ncc = Gc.ncell(), ncf = Gf.ncell();
   const int64_t n = (int64_t)B * ncc;
@@ -791,21 +805,24 @@ k_resid_restrict(unsigned long long* ctr, Geom Gf, Geom Gc, int B, const int* __
   if (!active[b]) return;
   const int cell = (int)(idx - (int64_t)b * ncc);
   restrict_cell<T>(Gf, Gc, cell, Jf + (int64_t)b * kJP * ncf, bf + (int64_t)b * 2 * ncf,
-                   xf + (int64_t)b * 2 * ncf, bc + (int64_t)b * 2 * ncc, xc + (int64_t)b * 2 * ncc);
+                   xf + (int64_t)b * 2 * ncf, bc + (int64_t)b * 2 * ncc, xc + (int64_t)b * 2 * ncc,
+                   red_only != 0);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 k_prolong(unsigned long long* ctr, Geom Gc, Geom Gf, int B, const int* __restrict__ active,
-          const T* __restrict__ xc, T* __restrict__ xf) {
+          const T* __restrict__ xc, T* __restrict__ xf, int black_only) {
   HENRY_COUNT_LAUNCH(ctr);
   const int ncf = Gf.ncell(), ncc = Gc.ncell();
-  const int64_t n = (int64_t)B * ncf;
+  const int per = black_only ? Gf.half() : ncf;   // cells corrected per sample
+  const int64_t n = (int64_t)B * per;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n) return;
-  const int b = (int)(idx / ncf);
+  const int b = (int)(idx / per);
   if (!active[b]) return;
-  const int cell = (int)(idx - (int64_t)b * ncf);
+  const int u = (int)(idx - (int64_t)b * per);
+  const int cell = black_only ? black_cell(Gf, u) : u;
   prolong_cell<T>(Gc, Gf, cell, xc + (int64_t)b * 2 * ncc, xf + (int64_t)b * 2 * ncf);
 }
 
@@ -887,15 +904,20 @@ k_vcycle_small(unsigned long long* ctr, SmallMG<T> M, int B, const int* __restri
           __syncthreads();
         }
       for (int cell = threadIdx.x; cell < M.g[k - 1].ncell(); cell += blockDim.x)
-        restrict_cell<T>(G, M.g[k - 1], cell, J[k], bv[k], xv[k], bv[k - 1], xv[k - 1]);
+        restrict_cell<T>(G, M.g[k - 1], cell, J[k], bv[k], xv[k], bv[k - 1], xv[k - 1],
+                         nu1 > 0);
       __syncthreads();
     }
     if (threadIdx.x < 32) coarse_solve_warp<T>(M.g[0], A, pv, bv[0], xv[0], y, threadIdx.x);
     __syncthreads();
     for (int k = 1; k <= ks; ++k) {
       const Geom& G = M.g[k];
-      for (int cell = threadIdx.x; cell < G.ncell(); cell += blockDim.x)
-        prolong_cell<T>(M.g[k - 1], G, cell, xv[k - 1], xv[k]);
+      if (nu2 > 0)
+        for (int pos = threadIdx.x; pos < G.half(); pos += blockDim.x)
+          prolong_cell<T>(M.g[k - 1], G, black_cell(G, pos), xv[k - 1], xv[k]);
+      else
+        for (int cell = threadIdx.x; cell < G.ncell(); cell += blockDim.x)
+          prolong_cell<T>(M.g[k - 1], G, cell, xv[k - 1], xv[k]);
       __syncthreads();
       for (int s = 0; s < nu2; ++s)
         for (int col = 0; col < 2; ++col) {
@@ -1041,15 +1063,20 @@ k_vcycle_cluster(unsigned long long* ctr, SmallMG<T> M, int B, const int* __rest
           sync();
         }
       for (int cell = gid; cell < M.g[k - 1].ncell(); cell += nthr)
-        restrict_cell<T>(G, M.g[k - 1], cell, J[k], bv[k], xv[k], bv[k - 1], xv[k - 1]);
+        restrict_cell<T>(G, M.g[k - 1], cell, J[k], bv[k], xv[k], bv[k - 1], xv[k - 1],
+                         nu1 > 0);
       sync();
     }
     if (rank == 0 && threadIdx.x < 32) coarse_solve_warp<T>(M.g[0], A, pv, bv[0], xv[0], ysh, threadIdx.x);
     sync();
     for (int k = 1; k <= kc; ++k) {
       const Geom& G = M.g[k];
-      for (int cell = gid; cell < G.ncell(); cell += nthr)
-        prolong_cell<T>(M.g[k - 1], G, cell, xv[k - 1], xv[k]);
+      if (nu2 > 0)
+        for (int pos = gid; pos < G.half(); pos += nthr)
+          prolong_cell<T>(M.g[k - 1], G, black_cell(G, pos), xv[k - 1], xv[k]);
+      else
+        for (int cell = gid; cell < G.ncell(); cell += nthr)
+          prolong_cell<T>(M.g[k - 1], G, cell, xv[k - 1], xv[k]);
       sync();
       for (int sw = 0; sw < nu2; ++sw)
         for (int col = 0; col < 2; ++col) {

@@ -285,10 +285,11 @@ void Solver::enqueue_vcycle(int k, int B, cudaStream_t s) {
   MGLevel& C = levels_[k - 1];
   k_resid_restrict<T><<<grid1((int64_t)B * C.g.ncell()), kBlock, 0, s>>>(
       counter_, G, C.g, B, active_, (const T*)L.J, (const T*)L.b, (const T*)L.x, (T*)C.b,
-      (T*)C.x);
+      (T*)C.x, cfg_.nu1 > 0);
   enqueue_vcycle<T>(k - 1, B, s);
-  k_prolong<T><<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(counter_, C.g, G, B, active_,
-                                                                (const T*)C.x, (T*)L.x);
+  const int black_only = cfg_.nu2 > 0;
+  k_prolong<T><<<grid1((int64_t)B * (black_only ? G.half() : G.ncell())), kBlock, 0, s>>>(
+      counter_, C.g, G, B, active_, (const T*)C.x, (T*)L.x, black_only);
   for (int sw = 0; sw < cfg_.nu2; ++sw)
     for (int col = 0; col < 2; ++col)
       k_smooth<T><<<gs, kBlock, 0, s>>>(counter_, G, B, col, active_, (const T*)L.J,
