@@ -136,7 +136,8 @@ class Workload:
             sc = schedules[l]
             cfg = hb.default_config(nlevels=4, precision=precision, vcycles=sc["vcycles"],
                                     nu1=sc["nu1"], nu2=sc["nu2"],
-                                    mg_small_cells=sc.get("mg_small_cells", 512))
+                                    mg_small_cells=sc.get("mg_small_cells", 512),
+                                    jac_lag=sc.get("jac_lag", 0))
             self.ctxs[l] = hb.Context(cfg)
         self.cfg = self.ctxs[0].cfg
         self.streams = {l: torch.cuda.Stream() for l in LEVELS}
@@ -183,13 +184,14 @@ class Workload:
 
 def tune_schedules(precision_name):
     """Autotuned schedule per level: V-cycles per iteration x smoothing sweeps
-    x shared-memory V-cycle threshold, timed on a short solve (a few steps at
-    the level's own time step)."""
+    x shared-memory V-cycle threshold, then the operator reuse factor, each
+    timed on one solve of the level over the whole horizon."""
     from paper_2403_17018_gb300 import autotune as A
-    A.CANDIDATES = {"vcycles": (2, 3), "nu": ((2, 2), (3, 3)), "small_cells": (0, 128, 512)}
+    A.CANDIDATES = {"vcycles": (2, 3), "nu": ((2, 2), (3, 3)), "small_cells": (0, 128, 512),
+                    "jac_lag": (0, 10, 30)}
     out = {}
     for l in LEVELS:
-        best, _ = A.tune_level(l, BATCH[l], precision_name, steps=4, reps=1, splits=(1,))
+        best, _ = A.tune_level(l, BATCH[l], precision_name, steps=None, reps=1, splits=(1,))
         out[l] = best
     return out
 
@@ -415,7 +417,7 @@ def main():
                 "ms_per_step": round(ms32 / K, 2), "per_level": per_level_rates(wl32, xis),
                 "gpu_launches": launches32,
                 "schedule": {f"L{l}": f"V({s['nu1']},{s['nu2']}) x{s['vcycles']} "
-                                      f"smem<={s['mg_small_cells']}"
+                                      f"smem<={s['mg_small_cells']} lag={s['jac_lag']}"
                              for l, s in sched32.items()},
                 "smoother_roofline": smoother_roofline(wl32, peaks)}
 
@@ -430,7 +432,8 @@ def main():
             "config": {"workload": WORKLOAD, "levels": list(LEVELS),
                        "batch": [BATCH[l] for l in LEVELS],
                        "multigrid": "FP64, autotuned per level: " + ", ".join(
-                           f"L{l} V({s['nu1']},{s['nu2']}) x{s['vcycles']} smem<={s['mg_small_cells']}"
+                           f"L{l} V({s['nu1']},{s['nu2']}) x{s['vcycles']} smem<={s['mg_small_cells']} "
+                           f"lag={s['jac_lag']}"
                            for l, s in sched64.items()),
                        "newton_rtol": wl.cfg.newton_rtol, "newton_atol": wl.cfg.newton_atol,
                        "l2": "flushed between timed steps (256 MB write)",

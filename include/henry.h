@@ -103,7 +103,14 @@ typedef struct henry_config {
                            the cluster kernel; 0 (default) disables it */
   int mg_small_cells;   /* largest multigrid level (cells per sample, at most
                            512) run by the shared-memory kernel; default 512 */
-  int reserved[3];
+  int jac_lag;          /* 0: Jacobian and multigrid operators rebuilt at
+                           every defect-correction iteration (Newton).
+                           k > 0: rebuilt at the first iteration of a step
+                           and after any iteration that reduced the residual
+                           by less than a factor k, reused otherwise (the
+                           residual is always the current FP64 one, so the
+                           converged solution satisfies the same tolerance) */
+  int reserved[2];
 } henry_config;
 
 typedef struct henry_ctx henry_ctx; /* opaque: owns device workspaces */

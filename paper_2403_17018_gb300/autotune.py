@@ -3,7 +3,8 @@
 For each MLMC level it times short batched solves (a few implicit Euler
 steps at the level's own time step) for every candidate schedule — V-cycles
 per defect-correction iteration, pre/post smoothing sweeps and the largest
-grid handed to the shared-memory V-cycle kernel — and, for
+grid handed to the shared-memory V-cycle kernel; then, for the winner, the
+operator reuse factor (jac_lag) — and, for
 the level's batch size, several batch splits, then keeps the schedule with
 the highest solves per second. Results are cached in a JSON file keyed by
 GPU name, level grid, precision and batch so that later runs reuse them.
@@ -24,7 +25,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuning", "schedules.json")
-CANDIDATES = {"vcycles": (1, 2, 3), "nu": ((1, 1), (2, 2), (3, 3)), "small_cells": (0, 128, 512)}
+CANDIDATES = {"vcycles": (1, 2, 3), "nu": ((1, 1), (2, 2), (3, 3)), "small_cells": (0, 128, 512),
+              "jac_lag": (0, 10, 30)}
 
 
 def _key(gpu, level, precision, batch, nx0, ny0):
@@ -55,23 +57,23 @@ def best_schedule(level, precision, batch, gpu=None, nx0=32, ny0=16, path=CACHE)
 
 
 def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2), log=None, n_xi=3):
-    """Time every candidate schedule on `steps` steps of level `level`;
-    returns the best {vcycles, nu1, nu2, mg_small_cells, split, solves_per_s}
-    and the table."""
+    """Time every candidate schedule on about `steps` steps of level `level`
+    at the level's own time step (steps=None: the whole 43200 s horizon,
+    whose early steps need more iterations than the later ones);
+    returns the best {vcycles, nu1, nu2, mg_small_cells, jac_lag, split,
+    solves_per_s} and the table."""
     import torch
     from paper_2403_17018_gb300 import binding as hb
     from paper_2403_17018_gb300.inputs import xi_batch
     prec = hb.PREC_FP64 if precision == "fp64" else hb.PREC_FP32_MG
     f = 1 << level
-    k = max(1, steps // f)
+    k = 24 if steps is None else min(24, max(1, steps // f))
     xi = torch.from_numpy(xi_batch(level, 0, batch, n_xi=n_xi)).cuda()
     table = []
-    for vc, (n1, n2), sc, split in itertools.product(
-            CANDIDATES["vcycles"], CANDIDATES["nu"], CANDIDATES.get("small_cells", (512,)), splits):
-        if batch % split:
-            continue
+
+    def timed(vc, n1, n2, sc, lag, split):
         cfg = hb.default_config(nlevels=level + 1, precision=prec, vcycles=vc, nu1=n1, nu2=n2,
-                                mg_small_cells=sc, nt0=k, T=1800.0 * k, n_xi=n_xi)
+                                mg_small_cells=sc, jac_lag=lag, nt0=k, T=1800.0 * k, n_xi=n_xi)
         ctx = hb.Context(cfg)
         sub = batch // split
         parts = [xi[i * sub:(i + 1) * sub].contiguous() for i in range(split)]
@@ -85,15 +87,29 @@ def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2),
                 bad += int((ctx.solve(level, p)["status"] != 0).sum().item())
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / reps
-        row = {"vcycles": vc, "nu1": n1, "nu2": n2, "mg_small_cells": sc, "split": split,
-               "solves_per_s": batch / dt, "failed": bad}
+        row = {"vcycles": vc, "nu1": n1, "nu2": n2, "mg_small_cells": sc, "jac_lag": lag,
+               "split": split, "solves_per_s": batch / dt, "failed": bad}
         table.append(row)
         if log:
             log(row)
         ctx.close()
-    ok = [r for r in table if r["failed"] == 0] or table
-    best = max(ok, key=lambda r: r["solves_per_s"])
-    return best, table
+        return row
+
+    def best_of(rows):
+        ok = [r for r in rows if r["failed"] == 0] or rows
+        return max(ok, key=lambda r: r["solves_per_s"])
+
+    for vc, (n1, n2), sc, split in itertools.product(
+            CANDIDATES["vcycles"], CANDIDATES["nu"], CANDIDATES.get("small_cells", (512,)), splits):
+        if batch % split:
+            continue
+        timed(vc, n1, n2, sc, 0, split)
+    best = best_of(table)
+    for lag in CANDIDATES.get("jac_lag", (0,)):
+        if lag:
+            timed(best["vcycles"], best["nu1"], best["nu2"], best["mg_small_cells"], lag,
+                  best["split"])
+    return best_of(table), table
 
 
 def main(argv=None):

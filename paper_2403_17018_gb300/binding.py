@@ -44,7 +44,7 @@ class HenryConfig(ctypes.Structure):
                 ("vcycles", ctypes.c_int), ("guess_extrapolation", ctypes.c_int),
                 ("newton_stag_tol", ctypes.c_double), ("mg_fusion", ctypes.c_int),
                 ("mg_cluster_cells", ctypes.c_int), ("mg_small_cells", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("jac_lag", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}

@@ -87,7 +87,7 @@ int validate(const henry_config* c) {
       !(c->phi0 > 0) || !(c->D >= 0))
     return fail(HENRY_E_INVALID, "non-positive physical parameter");
   if (c->newton_maxit < 0 || c->nu1 < 0 || c->nu2 < 0 || c->vcycles < 1 || c->mg_cluster_cells < 0 ||
-      c->mg_small_cells < 0 || c->mg_small_cells > 512)
+      c->mg_small_cells < 0 || c->mg_small_cells > 512 || c->jac_lag < 0)
     return fail(HENRY_E_INVALID, "bad solver parameter");
   for (int l = 0; l < c->nlevels; ++l) {
     std::vector<henry::Geom> g;
@@ -134,6 +134,7 @@ int henry_default_config(henry_config* c) {
   c->mg_fusion = 1;
   c->mg_cluster_cells = 0;
   c->mg_small_cells = 512;
+  c->jac_lag = 0;
   return HENRY_OK;
 }
 

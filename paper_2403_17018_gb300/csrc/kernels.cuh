@@ -175,8 +175,11 @@ __global__ void k_end_step(unsigned long long* ctr, int* __restrict__ step) {
 // MG layout (NATURAL = false): writes b = -R, x = 0, J (colour-split), the
 // face fluxes qx (east / right side) and qy (north), one partial sum of
 // R_p^2 + R_c^2 per block. NATURAL = true: writes R [B][2][ncell] and J
-// [B][20][ncell] in natural cell order (FP64), for tests.
-template <typename T, bool NATURAL>
+// [B][20][ncell] in natural cell order (FP64), for tests. WANT_J = false:
+// the residual outputs only (defect-correction iterations that reuse the
+// operators). refresh (optional, per sample): samples with refresh[b] == 0
+// are skipped.
+template <typename T, bool NATURAL, bool WANT_J = true>
 __global__ void __launch_bounds__(kBlock, sizeof(T) == 8 ? 2 : 3)
 k_resjac(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, ResTile tl,
          const double* __restrict__ p, const double* __restrict__ c,
@@ -186,13 +189,13 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, ResTile tl
          const double* __restrict__ dy, const double* __restrict__ qin,
          const int* __restrict__ active, T* __restrict__ J, T* __restrict__ bvec,
          T* __restrict__ xvec, double* __restrict__ partial, double* __restrict__ qx,
-         double* __restrict__ qy) {
+         double* __restrict__ qy, const int* __restrict__ refresh) {
   HENRY_COUNT_LAUNCH(ctr);
   __shared__ double shF[2][kBlock];
-  __shared__ T shD[8][kBlock];
+  __shared__ T shD[8][kBlock];   // face derivatives (unused, and removed, when !WANT_J)
   __shared__ double shr[kBlock / 32];
   const int b = blockIdx.y;
-  if (!NATURAL && !active[b]) return;
+  if (!NATURAL && (!active[b] || (refresh && !refresh[b]))) return;
   const int nx = G.nx, ny = G.ny, ncell = G.ncell(), half = G.half();
   const int t = threadIdx.x;
   const int col = t % tl.TX, rg = t / tl.TX;
@@ -218,8 +221,8 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, ResTile tl
     if (j0 > 0) {
       const int id = (j0 - 1) * nx + i;
       double q;
-      face_flux<T, true, false, true>(P, pb_[id], cb_[id], pP, cP, ty[o + id], dy[o + id], gdy, q, FmS,
-                                FsS, dS);
+      face_flux<T, WANT_J, false, true>(P, pb_[id], cb_[id], pP, cP, ty[o + id], dy[o + id], gdy, q,
+                                        FmS, FsS, dS);
     }
   }
   for (int r = 0; r < tl.R; ++r) {
@@ -233,16 +236,18 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, ResTile tl
     if (cv) {
       phiP = phi[o + id];
       if (i < nx - 1) {
-        face_flux<T, true, false, false>(P, pP, cP, pb_[id + 1], cb_[id + 1], tx[o + id], dx[o + id], 0.0,
-                                  qE, FmE, FsE, dE);
+        face_flux<T, WANT_J, false, false>(P, pP, cP, pb_[id + 1], cb_[id + 1], tx[o + id],
+                                           dx[o + id], 0.0, qE, FmE, FsE, dE);
       } else {
         const double pbd = P.drho * P.g * (P.Ly - (j + 0.5) * G.hy);
-        right_face<T, true, false>(P, pP, cP, tRf * K[o + id], dcoL * phiP, pbd, qE, FmE, FsE, dR);
+        right_face<T, WANT_J, false>(P, pP, cP, tRf * K[o + id], dcoL * phiP, pbd, qE, FmE, FsE, dR);
       }
       shF[0][t] = FmE;
       shF[1][t] = FsE;
-      shD[0][t] = dE.mLp; shD[1][t] = dE.mLc; shD[2][t] = dE.mUp; shD[3][t] = dE.mUc;
-      shD[4][t] = dE.sLp; shD[5][t] = dE.sLc; shD[6][t] = dE.sUp; shD[7][t] = dE.sUc;
+      if (WANT_J) {
+        shD[0][t] = dE.mLp; shD[1][t] = dE.mLc; shD[2][t] = dE.mUp; shD[3][t] = dE.mUc;
+        shD[4][t] = dE.sLp; shD[5][t] = dE.sLc; shD[6][t] = dE.sUp; shD[7][t] = dE.sUc;
+      }
     }
     __syncthreads();
     if (cv) {
@@ -253,12 +258,14 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, ResTile tl
         if (col > 0) {
           FmW = shF[0][t - 1];
           FsW = shF[1][t - 1];
-          dW.mLp = shD[0][t - 1]; dW.mLc = shD[1][t - 1]; dW.mUp = shD[2][t - 1]; dW.mUc = shD[3][t - 1];
-          dW.sLp = shD[4][t - 1]; dW.sLc = shD[5][t - 1]; dW.sUp = shD[6][t - 1]; dW.sUc = shD[7][t - 1];
+          if (WANT_J) {
+            dW.mLp = shD[0][t - 1]; dW.mLc = shD[1][t - 1]; dW.mUp = shD[2][t - 1]; dW.mUc = shD[3][t - 1];
+            dW.sLp = shD[4][t - 1]; dW.sLc = shD[5][t - 1]; dW.sUp = shD[6][t - 1]; dW.sUc = shD[7][t - 1];
+          }
         } else {
           double q;
-          face_flux<T, true, false, false>(P, pb_[id - 1], cb_[id - 1], pP, cP, tx[o + id - 1],
-                                    dx[o + id - 1], 0.0, q, FmW, FsW, dW);
+          face_flux<T, WANT_J, false, false>(P, pb_[id - 1], cb_[id - 1], pP, cP, tx[o + id - 1],
+                                             dx[o + id - 1], 0.0, q, FmW, FsW, dW);
         }
       }
       // north face (L = P, U = N)
@@ -267,7 +274,8 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, ResTile tl
       if (j < ny - 1) {
         pN = pb_[id + nx];
         cN = cb_[id + nx];
-        face_flux<T, true, false, true>(P, pP, cP, pN, cN, ty[o + id], dy[o + id], gdy, qN, FmN, FsN, dN);
+        face_flux<T, WANT_J, false, true>(P, pP, cP, pN, cN, ty[o + id], dy[o + id], gdy, qN, FmN,
+                                          FsN, dN);
       }
       // accumulation
       const double vt = vtau * phiP;
@@ -290,7 +298,7 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, ResTile tl
         const double rb = 0.5 * (rho + P.rho0);
         Rp += -A * P.rho0 * qin[(int64_t)b * ny + j];
         Rc += dco * rb * cP;
-        Jc[3] += (T)(dco * (0.5 * P.drho * cP + rb));
+        if (WANT_J) Jc[3] += (T)(dco * (0.5 * P.drho * cP + rb));
       }
       if (i < nx - 1) {
         Jc[0] += dE.mLp; Jc[1] += dE.mLc; Jc[2] += dE.sLp; Jc[3] += dE.sLc;
@@ -310,7 +318,7 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, ResTile tl
         double* Rn = (double*)bvec + (int64_t)b * 2 * ncell;
         Rn[id] = Rp;
         Rn[ncell + id] = Rc;
-        if (J) {
+        if (WANT_J && J) {
           T* Jn = J + (int64_t)b * 20 * ncell + id;
 #pragma unroll
           for (int m = 0; m < 20; ++m) Jn[(int64_t)m * ncell] = Jc[m];
@@ -322,12 +330,14 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, ResTile tl
         bvec[ob + ncell + cs] = (T)(-Rc);
         xvec[ob + cs] = (T)0;
         xvec[ob + ncell + cs] = (T)0;
-        T* Jb = J + (int64_t)b * kJP * ncell + cs;
+        if (WANT_J) {
+          T* Jb = J + (int64_t)b * kJP * ncell + cs;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) Jb[(int64_t)(20 + m) * ncell] = Jc[m];
-        inv2<T>(Jc[0], Jc[1], Jc[2], Jc[3], Jc[0], Jc[1], Jc[2], Jc[3]);
+          for (int m = 0; m < 4; ++m) Jb[(int64_t)(20 + m) * ncell] = Jc[m];
+          inv2<T>(Jc[0], Jc[1], Jc[2], Jc[3], Jc[0], Jc[1], Jc[2], Jc[3]);
 #pragma unroll
-        for (int m = 0; m < 20; ++m) Jb[(int64_t)m * ncell] = Jc[m];
+          for (int m = 0; m < 20; ++m) Jb[(int64_t)m * ncell] = Jc[m];
+        }
         qx[o + id] = qE;
         qy[o + id] = qN;
       }
@@ -356,7 +366,10 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, ResTile tl
 // count of still-active samples to acc[0]; the last block to finish
 // (acc[1] counts finished blocks) publishes the total to *n_active, resets
 // acc for the next launch and, when SET_COND, sets the while-loop condition
-// of the enclosing CUDA graph.
+// of the enclosing CUDA graph. With refresh (operator reuse factor lag > 0)
+// it also decides whether the next iteration rebuilds the Jacobian and the
+// multigrid operators: always after the step's initial residual, later only
+// when the last iteration reduced the residual by less than a factor lag.
 template <bool SET_COND>
 __global__ void k_check(unsigned long long* ctr, int B, int nchunk, int ncell,
                         const double* __restrict__ partial, double scale, double rtol,
@@ -365,7 +378,7 @@ __global__ void k_check(unsigned long long* ctr, int B, int nchunk, int ncell,
                         double* __restrict__ res_last, int* __restrict__ status,
                         int* __restrict__ iters, int* __restrict__ n_active,
                         unsigned int* __restrict__ acc, double stag_tol,
-                        cudaGraphConditionalHandle h) {
+                        cudaGraphConditionalHandle h, int* __restrict__ refresh, int lag) {
   HENRY_COUNT_LAUNCH(ctr);
   __shared__ int cnt;
   __shared__ bool last;
@@ -396,6 +409,7 @@ __global__ void k_check(unsigned long long* ctr, int B, int nchunk, int ncell,
         it_step[b] = it + 1;
         iters[b] += 1;
         atomicAdd(&cnt, 1);
+        if (refresh) refresh[b] = (it == 0 || r * lag > prev) ? 1 : 0;
       }
     }
   }
@@ -425,13 +439,13 @@ __global__ void k_restrict_state(unsigned long long* ctr, Geom Gf, Geom Gc, int 
                                  const int* __restrict__ active, const double* __restrict__ cf,
                                  const double* __restrict__ qxf, const double* __restrict__ qyf,
                                  double* __restrict__ cc, double* __restrict__ qxc,
-                                 double* __restrict__ qyc) {
+                                 double* __restrict__ qyc, const int* __restrict__ refresh) {
   HENRY_COUNT_LAUNCH(ctr);
   const int64_t n = (int64_t)B * Gc.ncell();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n) return;
   const int b = (int)(idx / Gc.ncell());
-  if (!active[b]) return;
+  if (!active[b] || (refresh && !refresh[b])) return;
   const int cell = (int)(idx - (int64_t)b * Gc.ncell());
   const int J = cell / Gc.nx, I = cell - J * Gc.nx;
   const int nx = Gf.nx;
@@ -448,14 +462,14 @@ k_jac(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, const int* __
       const double* __restrict__ p, const double* __restrict__ c, const double* __restrict__ phi,
       const double* __restrict__ K, const double* __restrict__ tx, const double* __restrict__ dx,
       const double* __restrict__ ty, const double* __restrict__ dy, const double* __restrict__ qx,
-      const double* __restrict__ qy, T* __restrict__ J) {
+      const double* __restrict__ qy, T* __restrict__ J, const int* __restrict__ refresh) {
   HENRY_COUNT_LAUNCH(ctr);
   const int ncell = G.ncell();
   const int64_t n = (int64_t)B * ncell;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n) return;
   const int b = (int)(idx / ncell);
-  if (!active[b]) return;
+  if (!active[b] || (refresh && !refresh[b])) return;
   const int cell = (int)(idx - (int64_t)b * ncell);
   const int j = cell / G.nx, i = cell - j * G.nx;
   const int64_t o = (int64_t)b * ncell;
@@ -485,12 +499,13 @@ k_jac(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, const int* __
 // memory: warps_per_block * n * (n + 1) doubles (dynamic).
 template <typename T>
 __global__ void k_coarse_lu(unsigned long long* ctr, Geom G, int B, const int* __restrict__ active,
-                            const T* __restrict__ J, double* __restrict__ LU, int* __restrict__ piv) {
+                            const T* __restrict__ J, double* __restrict__ LU, int* __restrict__ piv,
+                            const int* __restrict__ refresh) {
   HENRY_COUNT_LAUNCH(ctr);
   extern __shared__ double lu_sh[];
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int b = blockIdx.x * (blockDim.x >> 5) + w;
-  if (b >= B || !active[b]) return;
+  if (b >= B || !active[b] || (refresh && !refresh[b])) return;
   const int nc = G.ncell(), n = 2 * nc, half = G.half(), ld = n + 1;
   double* A = lu_sh + (size_t)w * n * ld;
   const T* Jb = J + (int64_t)b * kJP * nc;

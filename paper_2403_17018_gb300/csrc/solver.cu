@@ -165,6 +165,7 @@ int Solver::ensure(int B, cudaStream_t s) {
   const size_t o_lu = take(Bz * kMaxCoarseUnknowns * kMaxCoarseUnknowns * 8);
   const size_t o_piv = take(Bz * kMaxCoarseUnknowns * 4);
   const size_t o_act = take(Bz * 4);
+  const size_t o_ref = take(Bz * 4);
   const size_t o_its = take(Bz * 4);
   const size_t o_st = take(Bz * 4);
   const size_t o_it = take(Bz * 4);
@@ -200,6 +201,7 @@ int Solver::ensure(int B, cudaStream_t s) {
   lu_ = (double*)(a + o_lu);
   piv_ = (int*)(a + o_piv);
   active_ = (int*)(a + o_act);
+  refresh_ = (int*)(a + o_ref);
   it_step_ = (int*)(a + o_its);
   status_w_ = (int*)(a + o_st);
   iters_w_ = (int*)(a + o_it);
@@ -299,28 +301,28 @@ void Solver::enqueue_vcycle(int k, int B, cudaStream_t s) {
 // Coarse multigrid operators at the current iterate (linearised about the
 // restricted face fluxes).
 template <typename T>
-void Solver::enqueue_coarse_ops(int B, cudaStream_t s) {
+void Solver::enqueue_coarse_ops(int B, cudaStream_t s, const int* refresh) {
   const int nl = (int)levels_.size();
   for (int k = nl - 1; k >= 1; --k) {
     MGLevel& F = levels_[k];
     MGLevel& C = levels_[k - 1];
     k_restrict_state<<<grid1((int64_t)B * C.g.ncell()), kBlock, 0, s>>>(
-        counter_, F.g, C.g, B, active_, F.c, F.qx, F.qy, C.c, C.qx, C.qy);
+        counter_, F.g, C.g, B, active_, F.c, F.qx, F.qy, C.c, C.qx, C.qy, refresh);
     k_jac<T><<<grid1((int64_t)B * C.g.ncell()), kBlock, 0, s>>>(
         counter_, phys_, C.g, C.g.hx * C.g.hy / tau_, B, active_, C.p, C.c, C.phi, C.K, C.tx, C.dx, C.ty, C.dy,
-        C.qx, C.qy, (T*)C.J);
+        C.qx, C.qy, (T*)C.J, refresh);
   }
 }
 
 template <typename T>
-void Solver::enqueue_lu(int B, cudaStream_t s) {
+void Solver::enqueue_lu(int B, cudaStream_t s, const int* refresh) {
   {
     const int n = 2 * levels_[0].g.ncell();
     const size_t per_warp = (size_t)n * (n + 1) * sizeof(double);
     int wpb = (int)(40960 / per_warp);
     wpb = wpb < 1 ? 1 : (wpb > 8 ? 8 : wpb);
     k_coarse_lu<T><<<(B + wpb - 1) / wpb, 32 * wpb, per_warp * wpb, s>>>(
-        counter_, levels_[0].g, B, active_, (const T*)levels_[0].J, lu_, piv_);
+        counter_, levels_[0].g, B, active_, (const T*)levels_[0].J, lu_, piv_, refresh);
   }
 }
 
@@ -338,8 +340,16 @@ void Solver::enqueue_vcycles(int B, cudaStream_t s) {
 // Multigrid operators at the current iterate, V-cycles, state update.
 template <typename T>
 void Solver::enqueue_iteration(int B, cudaStream_t s) {
-  enqueue_coarse_ops<T>(B, s);
-  enqueue_lu<T>(B, s);
+  const int* refresh = cfg_.jac_lag ? refresh_ : nullptr;
+  if (refresh) {
+    // operators at the current iterate, for the samples that asked for them
+    MGLevel& F = levels_.back();
+    k_resjac<T, false><<<dim3(nchunk_, B), kBlock, 0, s>>>(
+        counter_, phys_, F.g, F.g.hx * F.g.hy / tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx,
+        F.dx, F.ty, F.dy, qin_, active_, (T*)F.J, (T*)F.b, (T*)F.x, partial_, F.qx, F.qy, refresh);
+  }
+  enqueue_coarse_ops<T>(B, s, refresh);
+  enqueue_lu<T>(B, s, refresh);
   enqueue_vcycles<T>(B, s);
   MGLevel& F = levels_.back();
   k_update<T><<<grid1((int64_t)B * F.g.ncell()), kBlock, 0, s>>>(counter_, F.g, B, active_,
@@ -350,9 +360,15 @@ template <typename T>
 void Solver::enqueue_resjac_check(int B, cudaStream_t s, bool set_cond) {
   MGLevel& F = levels_.back();
   const Geom& G = F.g;
-  k_resjac<T, false><<<dim3(nchunk_, B), kBlock, 0, s>>>(
-      counter_, phys_, G, G.hx * G.hy / tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx, F.ty, F.dy, qin_,
-      active_, (T*)F.J, (T*)F.b, (T*)F.x, partial_, F.qx, F.qy);
+  if (cfg_.jac_lag)   // residual only; the next iteration rebuilds operators where needed
+    k_resjac<T, false, false><<<dim3(nchunk_, B), kBlock, 0, s>>>(
+        counter_, phys_, G, G.hx * G.hy / tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx,
+        F.ty, F.dy, qin_, active_, (T*)F.J, (T*)F.b, (T*)F.x, partial_, F.qx, F.qy, nullptr);
+  else
+    k_resjac<T, false><<<dim3(nchunk_, B), kBlock, 0, s>>>(
+        counter_, phys_, G, G.hx * G.hy / tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx,
+        F.ty, F.dy, qin_, active_, (T*)F.J, (T*)F.b, (T*)F.x, partial_, F.qx, F.qy, nullptr);
+  int* refresh = cfg_.jac_lag ? refresh_ : nullptr;
   // residual scaled to units of c per step: RMS(R) * tau / (V phi0 rho0)
   const double scale = tau_ / (G.hx * G.hy * cfg_.phi0 * cfg_.rho0);
   const int gb = (B + 7) / 8;
@@ -362,12 +378,14 @@ void Solver::enqueue_resjac_check(int B, cudaStream_t s, bool set_cond) {
                                         cfg_.newton_rtol, cfg_.newton_atol, cfg_.newton_maxit,
                                         active_, it_step_, res0_, res_last_, status_w_, iters_w_,
                                         n_active_, check_acc_, stag_tol,
-                                        (cudaGraphConditionalHandle)cond_handle_);
+                                        (cudaGraphConditionalHandle)cond_handle_, refresh,
+                                        cfg_.jac_lag);
   else
     k_check<false><<<gb, kBlock, 0, s>>>(counter_, B, nchunk_, G.ncell(), partial_, scale,
                                          cfg_.newton_rtol, cfg_.newton_atol, cfg_.newton_maxit,
                                          active_, it_step_, res0_, res_last_, status_w_, iters_w_,
-                                         n_active_, check_acc_, stag_tol, 0);
+                                         n_active_, check_acc_, stag_tol, 0, refresh,
+                                         cfg_.jac_lag);
 }
 
 // One implicit Euler step as a CUDA graph: begin, residual + check, then a
@@ -504,7 +522,7 @@ void Solver::launch_timed(int which, int B, cudaStream_t s) {
   } else {
     k_resjac<T, false><<<dim3(nchunk_, B), kBlock, 0, s>>>(
         counter_, phys_, F.g, F.g.hx * F.g.hy / tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx, F.ty, F.dy,
-        qin_, active_, (T*)F.J, (T*)F.b, (T*)F.x, partial_, F.qx, F.qy);
+        qin_, active_, (T*)F.J, (T*)F.b, (T*)F.x, partial_, F.qx, F.qy, nullptr);
   }
 }
 
@@ -681,24 +699,25 @@ int Solver::adjoint_t(const double* xi, const double* logk, int B, int qoi, int 
       // operators of step st: J (multigrid type, every level) and exact FP64 J
       k_resjac<T, false><<<dim3(nchunk_, B), kBlock, 0, s>>>(
           counter_, phys_, G, G.hx * G.hy / tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx, F.ty, F.dy,
-          qin_, active_, (T*)F.J, (T*)F.b, (T*)F.x, partial_, F.qx, F.qy);
+          qin_, active_, (T*)F.J, (T*)F.b, (T*)F.x, partial_, F.qx, F.qy, nullptr);
       k_resjac<double, true><<<dim3(nchunk_, B), kBlock, 0, s>>>(
           counter_, phys_, G, G.hx * G.hy / tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx, F.ty, F.dy,
-          qin_, active_, J64_, res_, nullptr, nullptr, nullptr, nullptr);
-      enqueue_coarse_ops<T>(B, s);
+          qin_, active_, J64_, res_, nullptr, nullptr, nullptr, nullptr, nullptr);
+      enqueue_coarse_ops<T>(B, s, nullptr);
       for (size_t k = 0; k < levels_.size(); ++k)
         k_transpose<T><<<grid1((int64_t)B * levels_[k].g.ncell()), kBlock, 0, s>>>(
             counter_, levels_[k].g, B, active_, (const T*)levels_[k].J, (T*)JT_[k]);
       // the multigrid cycles below read the transposed operators
       for (size_t k = 0; k < levels_.size(); ++k) std::swap(levels_[k].J, JT_[k]);
-      enqueue_lu<T>(B, s);
+      enqueue_lu<T>(B, s, nullptr);
       CK(cudaMemsetAsync(lam_, 0, 2 * n * 8, s));
       for (;;) {
         k_adj_residual<T><<<dim3(adj_nchunk_, B), kBlock, 0, s>>>(
             counter_, G, B, active_, J64_, rhs_, lam_, res_, (T*)F.b, (T*)F.x, partial2_);
         k_check<false><<<(B + 7) / 8, kBlock, 0, s>>>(
             counter_, B, adj_nchunk_, G.ncell(), partial2_, 1.0, adj_rtol, 0.0, cfg_.newton_maxit,
-            active_, it_step_, res0_, res_last_, status_w_, iters_w_, n_active_, check_acc_, 0.0, 0);
+            active_, it_step_, res0_, res_last_, status_w_, iters_w_, n_active_, check_acc_, 0.0, 0,
+            nullptr, 0);
         CK(cudaMemcpyAsync(n_active_host_, n_active_, sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (*n_active_host_ == 0) break;
@@ -758,7 +777,7 @@ cudaError_t launch_residual_jacobian(const Phys& P, const Geom& G, double tau, i
   const ResTile tl = make_res_tile(G.nx, G.ny);
   k_resjac<double, true><<<dim3(tl.ntx * tl.nty, B), kBlock, 0, s>>>(
       nullptr, P, G, G.hx * G.hy / tau, B, tl, pr, c, c_old, phi, K, tx, dx, ty, dy, qin, nullptr, J, R, nullptr,
-      nullptr, nullptr, nullptr);
+      nullptr, nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
 

@@ -73,8 +73,8 @@ class Solver {
                                   int status_or, cudaStream_t s);
   template <typename T> int setup_t(const double* xi, const double* logk, int B, cudaStream_t s);
   template <typename T> int step_t(int B, cudaStream_t s);
-  template <typename T> void enqueue_coarse_ops(int B, cudaStream_t s);
-  template <typename T> void enqueue_lu(int B, cudaStream_t s);
+  template <typename T> void enqueue_coarse_ops(int B, cudaStream_t s, const int* refresh);
+  template <typename T> void enqueue_lu(int B, cudaStream_t s, const int* refresh);
   template <typename T> void enqueue_vcycles(int B, cudaStream_t s);
   template <typename T> void enqueue_iteration(int B, cudaStream_t s);
   template <typename T> void enqueue_vcycle(int k, int B, cudaStream_t s);
@@ -111,6 +111,7 @@ class Solver {
   double* lu_ = nullptr;
   int* piv_ = nullptr;
   int* active_ = nullptr;
+  int* refresh_ = nullptr;      // per sample: rebuild operators next iteration (jac_lag)
   int* it_step_ = nullptr;
   int* status_w_ = nullptr;
   int* iters_w_ = nullptr;

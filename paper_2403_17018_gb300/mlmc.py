@@ -108,7 +108,7 @@ def fit_alpha(means):
 class GpuSampler:
     """Level pairs on the GPU through the C ABI; statistics merged on device.
 
-    `schedules` (level -> {vcycles, nu1, nu2, mg_small_cells}, e.g. from the
+    `schedules` (level -> {vcycles, nu1, nu2, mg_small_cells, jac_lag}, e.g. from the
     autotuner) gives every level its own context and multigrid schedule.
     Each level has its own CUDA stream, so `batches` can run the pending
     pairs of all levels at the same time."""
@@ -129,7 +129,8 @@ class GpuSampler:
                 self.ctxs[l] = shared
             else:
                 kw = cfg.as_dict()
-                kw.update({k: sc[k] for k in ("vcycles", "nu1", "nu2", "mg_small_cells") if k in sc})
+                kw.update({k: sc[k] for k in ("vcycles", "nu1", "nu2", "mg_small_cells", "jac_lag")
+                           if k in sc})
                 self.ctxs[l] = hb.Context(hb.default_config(**kw))
         self.streams = {l: torch.cuda.Stream() for l in range(cfg.nlevels)}
 
@@ -312,16 +313,17 @@ def main(argv=None):
     if a.tune:
         from paper_2403_17018_gb300 import autotune as A
         # the schedules that won on some level of the batched benchmark
-        A.CANDIDATES = {"vcycles": (2, 3), "nu": ((2, 2), (3, 3)), "small_cells": (128, 512)}
+        A.CANDIDATES = {"vcycles": (2, 3), "nu": ((2, 2), (3, 3)), "small_cells": (128, 512),
+                        "jac_lag": (0, 10, 30)}
         t0 = time.perf_counter()
         schedules = {}
         gpu = torch.cuda.get_device_name(0)
         cache = A.load_cache()
         for l in range(a.levels):
             B = max(1, max(32, 16384 >> (2 * l)) // world)
-            key = A._key(gpu, l, a.precision, B, cfg.nx0, cfg.ny0) + f"|xi{a.n_xi}"
+            key = A._key(gpu, l, a.precision, B, cfg.nx0, cfg.ny0) + f"|xi{a.n_xi}|lag"
             if key not in cache:
-                cache[key], _ = A.tune_level(l, B, a.precision, steps=4, reps=1, splits=(1,),
+                cache[key], _ = A.tune_level(l, B, a.precision, steps=64, reps=1, splits=(1,),
                                              n_xi=a.n_xi)
             schedules[l] = cache[key]
         A.save_cache(cache)
@@ -332,7 +334,7 @@ def main(argv=None):
     res.update({"precision": a.precision, "n_gpus": world, "tuning_s": tune_s,
                 "concurrent_levels": not a.sequential,
                 "schedules": {l: {k: v for k, v in sc.items() if k in ("vcycles", "nu1", "nu2",
-                                                                      "mg_small_cells")}
+                                                                      "mg_small_cells", "jac_lag")}
                               for l, sc in (schedules or {}).items()}})
     if rank == 0:
         out = {k: v for k, v in res.items() if k != "state"}

@@ -343,3 +343,30 @@ def test_shared_memory_vcycle_threshold_does_not_change_the_result(precision):
             assert torch.equal(res[0][k], r[k]), k
     with pytest.raises(hb.HenryError):
         hb.Context(hb.default_config(mg_small_cells=513))
+
+
+@pytest.mark.parametrize("precision", [hb.PREC_FP64, hb.PREC_FP32_MG])
+def test_operator_reuse_keeps_parity_and_determinism(precision):
+    """Reusing the Jacobian and the multigrid operators across defect-
+    correction iterations (jac_lag) changes the iteration path, not the
+    equations: level-1 pairs still match the oracle, the graph loop equals
+    the host loop bit for bit, and a sample's result does not depend on its
+    batch (the reuse decision is per sample)."""
+    cfg = tight_config(nlevels=2, precision=precision, jac_lag=10)
+    ctx = hb.Context(cfg)
+    xi = xi_cuda(1, 0, 4)
+    qf, qc, cf, cc, st = ctx.sample_pairs(1, xi, want_c=True)
+    assert st.cpu().numpy().tolist() == [0] * 4
+    for b in range(2):
+        _, c1, q1 = oracle_solve(cfg, 1, xi[b].cpu().numpy())
+        _, c0, _ = oracle_solve(cfg, 0, xi[b].cpu().numpy())
+        assert np.max(np.abs(cf[b].cpu().numpy() - c1)) <= C_TOL
+        assert np.max(np.abs(cc[b].cpu().numpy() - c0)) <= C_TOL
+        assert np.allclose(qf[b].cpu().numpy(), q1, rtol=1e-9, atol=1e-9)
+    part = ctx.solve(1, xi[1:3].contiguous(), want_c=True, want_iters=True)
+    full = ctx.solve(1, xi, want_c=True, want_iters=True)
+    assert torch.equal(full["c"][1:3], part["c"]) and torch.equal(full["iters"][1:3], part["iters"])
+    host = hb.Context(tight_config(nlevels=2, precision=precision, jac_lag=10,
+                                   loop_mode=hb.LOOP_HOST)).solve(1, xi, want_c=True,
+                                                                  want_iters=True)
+    assert torch.equal(full["c"], host["c"]) and torch.equal(full["iters"], host["iters"])
