@@ -243,10 +243,16 @@ def per_level_rates(wl, xis, reps=1):
 
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x FP64 FMA/clk x 2 FLOP x max clock
 
+# DRAM bytes (read + write) of one launch of the roofline kernels, from the
+# ncu captures summarised in profiles/k_smooth_fp64_level3_256x128_b16.md and
+# profiles/k_smooth_fp32_level5_1024x512_b16.md; valid while the kernels are
+# unchanged since those captures.
+NCU_TRAFFIC_BYTES = {"k_smooth<double> L3": 50209536 + 171264}
+
 
 def roofline(wl, peaks):
     """Dominant kernel of the FP64 form (ncu launch list, level 3: the
-    smoother is ~40% of device time): the FP64 red-black block Gauss-Seidel
+    smoother is ~56% of device time): the FP64 red-black block Gauss-Seidel
     half-sweep on the finest grid of level 3, bound by the FP64 pipe on
     GB300 (FP64 is 1/64 of FP32), so reported against the FP64 peak derived
     from unit counts and clock. The FP64 residual/Jacobian kernel, next in
@@ -255,7 +261,8 @@ def roofline(wl, peaks):
     ach = fl / (ms / 1e3) / 1e12
     ms2, by2, fl2 = wl.ctxs[3].time_kernel(3, 0, 1, reps=20)
     return {"bound": "alu", "achieved": round(ach, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
-            "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4), "traffic": None,
+            "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
+            "traffic": NCU_TRAFFIC_BYTES["k_smooth<double> L3"],
             "kernel": "k_smooth<double> red half-sweep (level 3: 256x128 cells x 16 samples)",
             "flops_per_launch": fl, "bytes_per_launch": by, "ms_per_launch": round(ms, 5),
             "achieved_gbs": round(by / (ms / 1e3) / 1e9, 1),
