@@ -19,12 +19,17 @@
 
 namespace henry {
 
-// Multigrid operators have kJP = 24 planes per cell: 0..3 the inverse of the
-// cell's 2x2 diagonal block, 4..19 the off-diagonal blocks (W, E, S, N),
-// 20..23 the diagonal block itself. The smoother then needs a 2x2 product
-// per update instead of a determinant and a division, and the residual of
-// the restriction and the coarse LU read the block without inverting it
-// back; both matter for the FP64 multigrid on GB300's slow FP64 pipe.
+// Multigrid operators are stored row-scaled by the inverse of each cell's
+// 2x2 diagonal block D: the equations of cell P read
+//   x_P + sum_Q Dinv_P A_PQ x_Q = Dinv_P b_P,
+// and every level keeps the scaled right-hand side bt = Dinv b. kJP = 24
+// planes per cell: 0..3 Dinv_P, 4..19 the scaled off-diagonal blocks
+// At_PQ = Dinv_P A_PQ (Q = W, E, S, N), 20..23 D_P itself. A point
+// Gauss-Seidel update is then x_P = bt_P - sum_Q At_PQ x_Q: 16 operator
+// values and 16 multiply-adds, no 2x2 product (the smoother is HBM-bound in
+// FP32 on large grids and FP64-pipe-bound in FP64, so both count). The
+// restriction forms the unscaled residual D_P (bt_P - x_P - sum At x_Q) and
+// scales the coarse right-hand side by the coarse Dinv.
 constexpr int kJP = 24;
 template <typename T>
 __device__ __forceinline__ void inv2(T a, T b, T c, T d, T& ia, T& ib, T& ic, T& id) {
@@ -33,6 +38,26 @@ __device__ __forceinline__ void inv2(T a, T b, T c, T d, T& ia, T& ib, T& ic, T&
   ib = -b * r;
   ic = -c * r;
   id = a * r;
+}
+
+// Store one cell's operator: Jc holds the unscaled blocks (0..3 diagonal,
+// 4..19 W, E, S, N; each block (pp, pc, cp, cc), row = equation). Returns
+// Dinv in d[0..3] for scaling the right-hand side.
+template <typename T>
+__device__ __forceinline__ void store_operator(T* __restrict__ Jb, int ncell, const T* Jc, T* d) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) Jb[(int64_t)(20 + m) * ncell] = Jc[m];
+  inv2<T>(Jc[0], Jc[1], Jc[2], Jc[3], d[0], d[1], d[2], d[3]);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) Jb[(int64_t)m * ncell] = d[m];
+#pragma unroll
+  for (int q = 1; q <= 4; ++q) {
+    const T a = Jc[4 * q], b = Jc[4 * q + 1], c = Jc[4 * q + 2], e = Jc[4 * q + 3];
+    Jb[(int64_t)(4 * q + 0) * ncell] = d[0] * a + d[1] * c;
+    Jb[(int64_t)(4 * q + 1) * ncell] = d[0] * b + d[1] * e;
+    Jb[(int64_t)(4 * q + 2) * ncell] = d[2] * a + d[3] * c;
+    Jb[(int64_t)(4 * q + 3) * ncell] = d[2] * b + d[3] * e;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -326,18 +351,19 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, ResTile tl
       } else {
         const int cs = cs_pos(i, j, nx, half);
         const int64_t ob = (int64_t)b * 2 * ncell;
-        bvec[ob + cs] = (T)(-Rp);
-        bvec[ob + ncell + cs] = (T)(-Rc);
+        T* Jb = J + (int64_t)b * kJP * ncell + cs;
+        T d[4];   // Dinv of the operator the multigrid will use
+        if (WANT_J) {
+          store_operator<T>(Jb, ncell, Jc, d);
+        } else {
+#pragma unroll
+          for (int m = 0; m < 4; ++m) d[m] = Jb[(int64_t)m * ncell];
+        }
+        const T mp = (T)(-Rp), mc = (T)(-Rc);
+        bvec[ob + cs] = d[0] * mp + d[1] * mc;
+        bvec[ob + ncell + cs] = d[2] * mp + d[3] * mc;
         xvec[ob + cs] = (T)0;
         xvec[ob + ncell + cs] = (T)0;
-        if (WANT_J) {
-          T* Jb = J + (int64_t)b * kJP * ncell + cs;
-#pragma unroll
-          for (int m = 0; m < 4; ++m) Jb[(int64_t)(20 + m) * ncell] = Jc[m];
-          inv2<T>(Jc[0], Jc[1], Jc[2], Jc[3], Jc[0], Jc[1], Jc[2], Jc[3]);
-#pragma unroll
-          for (int m = 0; m < 20; ++m) Jb[(int64_t)m * ncell] = Jc[m];
-        }
         qx[o + id] = qE;
         qy[o + id] = qN;
       }
@@ -486,11 +512,8 @@ k_jac(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, const int* __
   T Jc[20];
   cell_residual<T, true, true>(P, G, vtau, in, Rp, Rc, Jc);
   T* Jb = J + (int64_t)b * kJP * ncell + cs_pos(i, j, G.nx, G.half());
-#pragma unroll
-  for (int m = 0; m < 4; ++m) Jb[(int64_t)(20 + m) * ncell] = Jc[m];
-  inv2<T>(Jc[0], Jc[1], Jc[2], Jc[3], Jc[0], Jc[1], Jc[2], Jc[3]);
-#pragma unroll
-  for (int m = 0; m < 20; ++m) Jb[(int64_t)m * ncell] = Jc[m];
+  T d[4];
+  store_operator<T>(Jb, ncell, Jc, d);
 }
 
 // Dense LU with partial pivoting of the coarsest system (Gaussian
@@ -516,12 +539,14 @@ __global__ void k_coarse_lu(unsigned long long* ctr, Geom G, int B, const int* _
     const int cs = cs_pos(i, j, G.nx, half);
     const int nb[5] = {cell, i > 0 ? cell - 1 : -1, i < G.nx - 1 ? cell + 1 : -1,
                        j > 0 ? cell - G.nx : -1, j < G.ny - 1 ? cell + G.nx : -1};
-    for (int q = 0; q < 5; ++q) {
+    // the scaled system: identity diagonal blocks, At off the diagonal
+    A[(2 * cell) * ld + 2 * cell] = 1.0;
+    A[(2 * cell + 1) * ld + 2 * cell + 1] = 1.0;
+    for (int q = 1; q < 5; ++q) {
       if (nb[q] < 0) continue;
-      const int m0 = q == 0 ? 20 : 4 * q;   // the diagonal block itself is in planes 20..23
       for (int e = 0; e < 2; ++e)
         for (int v = 0; v < 2; ++v)
-          A[(2 * cell + e) * ld + 2 * nb[q] + v] = (double)Jb[(int64_t)(m0 + 2 * e + v) * nc + cs];
+          A[(2 * cell + e) * ld + 2 * nb[q] + v] = (double)Jb[(int64_t)(4 * q + 2 * e + v) * nc + cs];
     }
   }
   __syncwarp();
@@ -562,15 +587,16 @@ __global__ void k_coarse_lu(unsigned long long* ctr, Geom G, int B, const int* _
 }
 
 // ---------------------------------------------------------------------------
-// multigrid building blocks on one sample's arrays (J: [20][ncell], b, x:
+// multigrid building blocks on one sample's arrays (J: [kJP][ncell], b, x:
 // [2][ncell], colour-split planes). Used by the batched kernels below, with
 // global-memory bases, and by k_vcycle_small, with shared-memory copies.
 // ---------------------------------------------------------------------------
 
 // Point-block Gauss-Seidel update of the cell at colour-split position
-// `pos` of colour `colour`: x_P = D_P^{-1} (b_P - sum_Q A_PQ x_Q). Each
-// product is subtracted on its own so that it compiles to one FMA (the
-// FP64 form of this kernel is bound by GB300's FP64 pipe).
+// `pos` of colour `colour`, on the row-scaled system: x_P = bt_P - sum_Q
+// At_PQ x_Q (= D_P^{-1} (b_P - sum_Q A_PQ x_Q)). Each product is subtracted
+// on its own so that it compiles to one FMA (the FP64 form of this kernel
+// is bound by GB300's FP64 pipe).
 template <typename T>
 __device__ __forceinline__ void smooth_cell(const Geom& G, int colour, int pos,
                                             const T* __restrict__ J, const T* __restrict__ b,
@@ -616,85 +642,89 @@ __device__ __forceinline__ void smooth_cell(const Geom& G, int colour, int pos,
     rc -= Jb[18 * ncell] * vp;
     rc -= Jb[19 * ncell] * vc;
   }
-  // planes 0..3 hold the inverse diagonal block
-  x[own] = Jb[0] * rp + Jb[ncell] * rc;
-  x[ncell + own] = Jb[2 * ncell] * rp + Jb[3 * ncell] * rc;
+  x[own] = rp;
+  x[ncell + own] = rc;
 }
 
-// A x at cell (i, j).
+// Unscaled residual b - A x at cell (i, j) from the row-scaled system:
+// D_P (bt_P - x_P - sum_Q At_PQ x_Q).
 template <typename T>
-__device__ __forceinline__ void apply_cell(const Geom& G, int i, int j, const T* __restrict__ Jb,
-                                           const T* __restrict__ x, T& ap, T& ac) {
+__device__ __forceinline__ void residual_cell(const Geom& G, int i, int j, const T* __restrict__ Jb,
+                                              const T* __restrict__ b, const T* __restrict__ x,
+                                              T& rp, T& rc) {
   const int ncell = G.ncell(), half = G.half(), nx = G.nx;
   const int cs = cs_pos(i, j, nx, half);
   const T* Jc = Jb + cs;
   const T* xp = x;
   const T* xc = x + ncell;
-  T vp = xp[cs], vc = xc[cs];
-  ap = Jc[20 * ncell] * vp;
-  ap += Jc[21 * ncell] * vc;
-  ac = Jc[22 * ncell] * vp;
-  ac += Jc[23 * ncell] * vc;
+  rp = b[cs] - xp[cs];
+  rc = b[ncell + cs] - xc[cs];
+  T vp, vc;
   if (i > 0) {
     const int q = cs_pos(i - 1, j, nx, half);
     vp = xp[q]; vc = xc[q];
-    ap += Jc[4 * ncell] * vp;
-    ap += Jc[5 * ncell] * vc;
-    ac += Jc[6 * ncell] * vp;
-    ac += Jc[7 * ncell] * vc;
+    rp -= Jc[4 * ncell] * vp;
+    rp -= Jc[5 * ncell] * vc;
+    rc -= Jc[6 * ncell] * vp;
+    rc -= Jc[7 * ncell] * vc;
   }
   if (i < nx - 1) {
     const int q = cs_pos(i + 1, j, nx, half);
     vp = xp[q]; vc = xc[q];
-    ap += Jc[8 * ncell] * vp;
-    ap += Jc[9 * ncell] * vc;
-    ac += Jc[10 * ncell] * vp;
-    ac += Jc[11 * ncell] * vc;
+    rp -= Jc[8 * ncell] * vp;
+    rp -= Jc[9 * ncell] * vc;
+    rc -= Jc[10 * ncell] * vp;
+    rc -= Jc[11 * ncell] * vc;
   }
   if (j > 0) {
     const int q = cs_pos(i, j - 1, nx, half);
     vp = xp[q]; vc = xc[q];
-    ap += Jc[12 * ncell] * vp;
-    ap += Jc[13 * ncell] * vc;
-    ac += Jc[14 * ncell] * vp;
-    ac += Jc[15 * ncell] * vc;
+    rp -= Jc[12 * ncell] * vp;
+    rp -= Jc[13 * ncell] * vc;
+    rc -= Jc[14 * ncell] * vp;
+    rc -= Jc[15 * ncell] * vc;
   }
   if (j < G.ny - 1) {
     const int q = cs_pos(i, j + 1, nx, half);
     vp = xp[q]; vc = xc[q];
-    ap += Jc[16 * ncell] * vp;
-    ap += Jc[17 * ncell] * vc;
-    ac += Jc[18 * ncell] * vp;
-    ac += Jc[19 * ncell] * vc;
+    rp -= Jc[16 * ncell] * vp;
+    rp -= Jc[17 * ncell] * vc;
+    rc -= Jc[18 * ncell] * vp;
+    rc -= Jc[19 * ncell] * vc;
   }
+  const T sp = rp, sc = rc;
+  rp = Jc[20 * ncell] * sp + Jc[21 * ncell] * sc;
+  rc = Jc[22 * ncell] * sp + Jc[23 * ncell] * sc;
 }
 
 // Coarse cell `cell` of level k-1: b_c = sum over the four children of
-// (b - A x) on level k (finite-volume restriction), x_c = 0. red_only: the
-// last operation on level k was a black half-sweep, which leaves the
-// residual of every black cell zero up to rounding, so only the two red
-// children (i + j even) are evaluated.
+// (b - A x) on level k (finite-volume restriction), stored scaled by the
+// coarse Dinv (planes 0..3 of Jc), x_c = 0. red_only: the last operation on
+// level k was a black half-sweep, which leaves the residual of every black
+// cell zero up to rounding, so only the two red children (i + j even) are
+// evaluated.
 template <typename T>
 __device__ __forceinline__ void restrict_cell(const Geom& Gf, const Geom& Gc, int cell,
                                               const T* __restrict__ Jf, const T* __restrict__ bf,
-                                              const T* __restrict__ xf, T* __restrict__ bc,
-                                              T* __restrict__ xc, bool red_only) {
+                                              const T* __restrict__ xf, const T* __restrict__ Jc,
+                                              T* __restrict__ bc, T* __restrict__ xc,
+                                              bool red_only) {
   const int J = cell / Gc.nx, I = cell - J * Gc.nx;
-  const int ncf = Gf.ncell(), hf = Gf.half(), ncc = Gc.ncell();
+  const int ncc = Gc.ncell();
   T sp = 0, sc = 0;
 #pragma unroll
   for (int c4 = 0; c4 < 4; ++c4) {
     if (red_only && (c4 == 1 || c4 == 2)) continue;
     const int i = 2 * I + (c4 & 1), j = 2 * J + (c4 >> 1);
-    T ap, ac;
-    apply_cell(Gf, i, j, Jf, xf, ap, ac);
-    const int cs = cs_pos(i, j, Gf.nx, hf);
-    sp += bf[cs] - ap;
-    sc += bf[ncf + cs] - ac;
+    T rp, rc;
+    residual_cell(Gf, i, j, Jf, bf, xf, rp, rc);
+    sp += rp;
+    sc += rc;
   }
   const int csc = cs_pos(I, J, Gc.nx, Gc.half());
-  bc[csc] = sp;
-  bc[ncc + csc] = sc;
+  const T* d = Jc + csc;
+  bc[csc] = d[0] * sp + d[ncc] * sc;
+  bc[ncc + csc] = d[2 * ncc] * sp + d[3 * ncc] * sc;
   xc[csc] = (T)0;
   xc[ncc + csc] = (T)0;
 }
@@ -810,7 +840,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock)
 k_resid_restrict(unsigned long long* ctr, Geom Gf, Geom Gc, int B, const int* __restrict__ active,
                  const T* __restrict__ Jf, const T* __restrict__ bf, const T* __restrict__ xf,
-                 T* __restrict__ bc, T* __restrict__ xc, int red_only) {
+                 const T* __restrict__ Jc, T* __restrict__ bc, T* __restrict__ xc, int red_only) {
   HENRY_COUNT_LAUNCH(ctr);
   const int ncc = Gc.ncell(), ncf = Gf.ncell();
   const int64_t n = (int64_t)B * ncc;
@@ -820,8 +850,8 @@ k_resid_restrict(unsigned long long* ctr, Geom Gf, Geom Gc, int B, const int* __
   if (!active[b]) return;
   const int cell = (int)(idx - (int64_t)b * ncc);
   restrict_cell<T>(Gf, Gc, cell, Jf + (int64_t)b * kJP * ncf, bf + (int64_t)b * 2 * ncf,
-                   xf + (int64_t)b * 2 * ncf, bc + (int64_t)b * 2 * ncc, xc + (int64_t)b * 2 * ncc,
-                   red_only != 0);
+                   xf + (int64_t)b * 2 * ncf, Jc + (int64_t)b * kJP * ncc, bc + (int64_t)b * 2 * ncc,
+                   xc + (int64_t)b * 2 * ncc, red_only != 0);
 }
 
 template <typename T>
@@ -919,8 +949,8 @@ k_vcycle_small(unsigned long long* ctr, SmallMG<T> M, int B, const int* __restri
           __syncthreads();
         }
       for (int cell = threadIdx.x; cell < M.g[k - 1].ncell(); cell += blockDim.x)
-        restrict_cell<T>(G, M.g[k - 1], cell, J[k], bv[k], xv[k], bv[k - 1], xv[k - 1],
-                         nu1 > 0);
+        restrict_cell<T>(G, M.g[k - 1], cell, J[k], bv[k], xv[k], J[k - 1], bv[k - 1],
+                         xv[k - 1], nu1 > 0);
       __syncthreads();
     }
     if (threadIdx.x < 32) coarse_solve_warp<T>(M.g[0], A, pv, bv[0], xv[0], y, threadIdx.x);
@@ -1078,8 +1108,8 @@ k_vcycle_cluster(unsigned long long* ctr, SmallMG<T> M, int B, const int* __rest
           sync();
         }
       for (int cell = gid; cell < M.g[k - 1].ncell(); cell += nthr)
-        restrict_cell<T>(G, M.g[k - 1], cell, J[k], bv[k], xv[k], bv[k - 1], xv[k - 1],
-                         nu1 > 0);
+        restrict_cell<T>(G, M.g[k - 1], cell, J[k], bv[k], xv[k], J[k - 1], bv[k - 1],
+                         xv[k - 1], nu1 > 0);
       sync();
     }
     if (rank == 0 && threadIdx.x < 32) coarse_solve_warp<T>(M.g[0], A, pv, bv[0], xv[0], ysh, threadIdx.x);
@@ -1131,9 +1161,12 @@ __global__ void k_adj_seed(unsigned long long* ctr, Phys P, Geom G, int B, int q
   lam[o + n + cell] = 0.0;
 }
 
-// Transposed operator of one multigrid level: (J^T)_{P,Q} = (J_{Q,P})^T, so
-// P's west block is the transposed east block of its west neighbour, etc.
-// Both in the colour-split layout of type T.
+// Transposed operator of one multigrid level, row-scaled like the forward
+// one. With M = A^T: M_PP = D_P^T and M_PQ = (A_QP)^T = (D_Q At_QP)^T, so the
+// stored blocks are Dinv'_P = (Dinv_P)^T, D'_P = D_P^T and
+//   Mt_PQ = (D_P^T)^{-1} (D_Q At_QP)^T = (D_Q At_QP Dinv_P)^T,
+// At_QP being the block of neighbour Q in the direction of P (P's west
+// block comes from the east block of its west neighbour, etc.).
 template <typename T>
 __global__ void k_transpose(unsigned long long* ctr, Geom G, int B, const int* __restrict__ active,
                             const T* __restrict__ J, T* __restrict__ JT) {
@@ -1148,37 +1181,55 @@ __global__ void k_transpose(unsigned long long* ctr, Geom G, int B, const int* _
   const T* Jb = J + (int64_t)b * kJP * n;
   T* Ob = JT + (int64_t)b * kJP * n;
   const int cs = cs_pos(i, j, nx, half);
-  // (pp, pc, cp, cc) of the source block -> (pp, cp, pc, cc)
-  auto put = [&](int dst_m0, int src_cs, int src_m0, bool has) {
-    T a = 0, bb = 0, cc = 0, d = 0;
-    if (has) {
-      a = Jb[(int64_t)(src_m0 + 0) * n + src_cs];
-      bb = Jb[(int64_t)(src_m0 + 1) * n + src_cs];
-      cc = Jb[(int64_t)(src_m0 + 2) * n + src_cs];
-      d = Jb[(int64_t)(src_m0 + 3) * n + src_cs];
-    }
-    Ob[(int64_t)(dst_m0 + 0) * n + cs] = a;
-    Ob[(int64_t)(dst_m0 + 1) * n + cs] = cc;
-    Ob[(int64_t)(dst_m0 + 2) * n + cs] = bb;
-    Ob[(int64_t)(dst_m0 + 3) * n + cs] = d;
+  auto blk = [&](int m0, int at, T* v) {
+    for (int e = 0; e < 4; ++e) v[e] = Jb[(int64_t)(m0 + e) * n + at];
   };
-  put(0, cs, 0, true);
-  put(20, cs, 20, true);
-  put(4, i > 0 ? cs_pos(i - 1, j, nx, half) : 0, 8, i > 0);
-  put(8, i < nx - 1 ? cs_pos(i + 1, j, nx, half) : 0, 4, i < nx - 1);
-  put(12, j > 0 ? cs_pos(i, j - 1, nx, half) : 0, 16, j > 0);
-  put(16, j < G.ny - 1 ? cs_pos(i, j + 1, nx, half) : 0, 12, j < G.ny - 1);
+  auto put = [&](int m0, const T* v) {   // store v transposed: (pp, pc, cp, cc) -> (pp, cp, pc, cc)
+    Ob[(int64_t)(m0 + 0) * n + cs] = v[0];
+    Ob[(int64_t)(m0 + 1) * n + cs] = v[2];
+    Ob[(int64_t)(m0 + 2) * n + cs] = v[1];
+    Ob[(int64_t)(m0 + 3) * n + cs] = v[3];
+  };
+  auto mul = [](const T* x, const T* y, T* z) {   // z = x y, 2x2 row-major
+    z[0] = x[0] * y[0] + x[1] * y[2];
+    z[1] = x[0] * y[1] + x[1] * y[3];
+    z[2] = x[2] * y[0] + x[3] * y[2];
+    z[3] = x[2] * y[1] + x[3] * y[3];
+  };
+  T dinv[4], d[4];
+  blk(0, cs, dinv);
+  blk(20, cs, d);
+  put(0, dinv);
+  put(20, d);
+  // (dst plane of P, neighbour, plane of the neighbour pointing back to P)
+  const int nbr[4] = {i > 0 ? cs_pos(i - 1, j, nx, half) : -1,
+                      i < nx - 1 ? cs_pos(i + 1, j, nx, half) : -1,
+                      j > 0 ? cs_pos(i, j - 1, nx, half) : -1,
+                      j < G.ny - 1 ? cs_pos(i, j + 1, nx, half) : -1};
+  const int back[4] = {8, 4, 16, 12};
+  for (int q = 0; q < 4; ++q) {
+    T g[4] = {0, 0, 0, 0};
+    if (nbr[q] >= 0) {
+      T dq[4], aq[4], t[4];
+      blk(20, nbr[q], dq);
+      blk(back[q], nbr[q], aq);
+      mul(dq, aq, t);
+      mul(t, dinv, g);
+    }
+    put(4 + 4 * q, g);
+  }
 }
 
 // res = rhs - J^T lam with the FP64 Jacobian J64 in natural layout
-// ([B][20][ncell]); b = res in the multigrid type (colour-split), x = 0;
+// ([B][20][ncell]); b = Dinv' res in the multigrid type (colour-split; Dinv'
+// from the transposed multigrid operator Jmg), x = 0;
 // one partial sum of res^2 per block. grid = (chunks of 256 cells, B).
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 k_adj_residual(unsigned long long* ctr, Geom G, int B, const int* __restrict__ active,
                const double* __restrict__ J64, const double* __restrict__ rhs,
-               const double* __restrict__ lam, double* __restrict__ res, T* __restrict__ bvec,
-               T* __restrict__ xvec, double* __restrict__ partial) {
+               const double* __restrict__ lam, double* __restrict__ res, const T* __restrict__ Jmg,
+               T* __restrict__ bvec, T* __restrict__ xvec, double* __restrict__ partial) {
   HENRY_COUNT_LAUNCH(ctr);
   __shared__ double sh[kBlock / 32];
   const int b = blockIdx.y;
@@ -1209,8 +1260,11 @@ k_adj_residual(unsigned long long* ctr, Geom G, int B, const int* __restrict__ a
     res[o + cell] = rp;
     res[o + n + cell] = rc;
     const int cs = cs_pos(i, j, nx, G.half());
-    bvec[o + cs] = (T)rp;
-    bvec[o + n + cs] = (T)rc;
+    // right-hand side of the row-scaled transposed multigrid system
+    const T* d = Jmg + (int64_t)b * kJP * n + cs;
+    const T mp = (T)rp, mc = (T)rc;
+    bvec[o + cs] = d[0] * mp + d[n] * mc;
+    bvec[o + n + cs] = d[2 * n] * mp + d[3 * n] * mc;
     xvec[o + cs] = (T)0;
     xvec[o + n + cs] = (T)0;
     v = rp * rp + rc * rc;

@@ -286,8 +286,8 @@ void Solver::enqueue_vcycle(int k, int B, cudaStream_t s) {
                                        (const T*)L.b, (T*)L.x);
   MGLevel& C = levels_[k - 1];
   k_resid_restrict<T><<<grid1((int64_t)B * C.g.ncell()), kBlock, 0, s>>>(
-      counter_, G, C.g, B, active_, (const T*)L.J, (const T*)L.b, (const T*)L.x, (T*)C.b,
-      (T*)C.x, cfg_.nu1 > 0);
+      counter_, G, C.g, B, active_, (const T*)L.J, (const T*)L.b, (const T*)L.x,
+      (const T*)C.J, (T*)C.b, (T*)C.x, cfg_.nu1 > 0);
   enqueue_vcycle<T>(k - 1, B, s);
   const int black_only = cfg_.nu2 > 0;
   k_prolong<T><<<grid1((int64_t)B * (black_only ? G.half() : G.ncell())), kBlock, 0, s>>>(
@@ -564,12 +564,14 @@ int Solver::time_kernel(int which, int reps, cudaStream_t s, double* avg_ms, dou
   const double T = (double)tsize_;
   if (which == 0) {
     const double cells = (double)B * G.half();
-    *bytes = cells * 26.0 * T;
-    *flops = cells * 38.0;
+    // 16 scaled operator values + 2 rhs read, 2 unknowns written, 2 neighbour
+    // unknowns read per update (the other two come from cache); 16 FMA
+    *bytes = cells * 22.0 * T;
+    *flops = cells * 32.0;
   } else {
     const double cells = (double)B * G.ncell();
     *bytes = cells * (8.0 * 8 + 28.0 * T + 16.0);
-    *flops = cells * (46.0 + (tsize_ == sizeof(double) ? 84.0 : 0.0));
+    *flops = cells * (46.0 + (tsize_ == sizeof(double) ? 116.0 : 0.0));
   }
   *avg_ms = ms / reps;
   return HENRY_OK;
@@ -713,7 +715,8 @@ int Solver::adjoint_t(const double* xi, const double* logk, int B, int qoi, int 
       CK(cudaMemsetAsync(lam_, 0, 2 * n * 8, s));
       for (;;) {
         k_adj_residual<T><<<dim3(adj_nchunk_, B), kBlock, 0, s>>>(
-            counter_, G, B, active_, J64_, rhs_, lam_, res_, (T*)F.b, (T*)F.x, partial2_);
+            counter_, G, B, active_, J64_, rhs_, lam_, res_, (const T*)F.J, (T*)F.b, (T*)F.x,
+            partial2_);
         k_check<false><<<(B + 7) / 8, kBlock, 0, s>>>(
             counter_, B, adj_nchunk_, G.ncell(), partial2_, 1.0, adj_rtol, 0.0, cfg_.newton_maxit,
             active_, it_step_, res0_, res_last_, status_w_, iters_w_, n_active_, check_acc_, 0.0, 0,

@@ -320,10 +320,11 @@ def main(argv=None):
         gpu = torch.cuda.get_device_name(0)
         cache = A.load_cache()
         for l in range(a.levels):
-            B = max(1, max(32, 16384 >> (2 * l)) // world)
+            # tuned on at most 1024 pairs and about 24 steps of the level
+            B = min(1024, max(1, max(32, 16384 >> (2 * l)) // world))
             key = A._key(gpu, l, a.precision, B, cfg.nx0, cfg.ny0) + f"|xi{a.n_xi}|lag"
             if key not in cache:
-                cache[key], _ = A.tune_level(l, B, a.precision, steps=64, reps=1, splits=(1,),
+                cache[key], _ = A.tune_level(l, B, a.precision, steps=24, reps=1, splits=(1,),
                                              n_xi=a.n_xi)
             schedules[l] = cache[key]
         A.save_cache(cache)
