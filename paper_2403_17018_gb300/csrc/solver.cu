@@ -3,6 +3,7 @@
 
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <utility>
 
@@ -127,7 +128,34 @@ int Solver::debug_copy(int mg_level, int what, void* dst, int64_t bytes) const {
   return HENRY_OK;
 }
 
+// The dynamic shared-memory limit of k_vcycle_small<T> is an attribute of
+// the function in the device's context, shared by every solver of the
+// process: it is only ever raised, to the largest size any solver needs,
+// and outside stream capture (from ensure()), so that no solver's graph
+// capture can meet a limit lowered by another solver.
+template <typename T>
+static cudaError_t raise_small_smem_limit(size_t smem) {
+  static std::mutex mu;
+  static size_t cur = 0;
+  std::lock_guard<std::mutex> lock(mu);
+  if (smem <= cur) return cudaSuccess;
+  const cudaError_t e =
+      cudaFuncSetAttribute(k_vcycle_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) cur = smem;
+  return e;
+}
+
 int Solver::ensure(int B, cudaStream_t s) {
+  if (ks_ > 0) {
+    SmallMG<float> Mf;
+    SmallMG<double> Md;
+    Mf.ks = Md.ks = ks_;
+    for (int k = 0; k <= ks_; ++k) Mf.g[k] = Md.g[k] = geoms_[k];
+    if (tsize_ == sizeof(float))
+      CK(raise_small_smem_limit<float>(small_smem_bytes(Mf)));
+    else
+      CK(raise_small_smem_limit<double>(small_smem_bytes(Md)));
+  }
   if (B <= cap_) return HENRY_OK;
   unsigned long long count = 0;
   if (counter_) CK(cudaMemcpy(&count, counter_, sizeof(count), cudaMemcpyDeviceToHost));
@@ -226,10 +254,6 @@ void Solver::launch_small(int B, int ncycles, cudaStream_t s) {
     M.x[k] = (T*)levels_[k].x;
   }
   const size_t smem = small_smem_bytes(M);
-  if (smem != small_smem_) {
-    cudaFuncSetAttribute(k_vcycle_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    small_smem_ = smem;
-  }
   k_vcycle_small<T><<<B, kBlock, smem, s>>>(counter_, M, B, active_, lu_, piv_, cfg_.nu1, cfg_.nu2,
                                             ncycles);
 }

@@ -124,7 +124,6 @@ class Solver {
   int ks_ = 0;                // top multigrid level handled by k_vcycle_small
   int kc_ = 0;                // top multigrid level handled by k_vcycle_cluster
   int cl_ = 1;                // blocks per cluster (one cluster per sample)
-  size_t small_smem_ = 0;     // its dynamic shared memory per block
   // CUDA graph of one time step (HENRY_LOOP_GRAPH), rebuilt when B changes
   cudaGraphExec_t step_exec_ = nullptr;
   cudaGraph_t step_graph_ = nullptr;

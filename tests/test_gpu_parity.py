@@ -370,3 +370,20 @@ def test_operator_reuse_keeps_parity_and_determinism(precision):
                                    loop_mode=hb.LOOP_HOST)).solve(1, xi, want_c=True,
                                                                   want_iters=True)
     assert torch.equal(full["c"], host["c"]) and torch.equal(full["iters"], host["iters"])
+
+
+def test_contexts_with_different_shared_memory_kernels_interleave():
+    """The shared-memory V-cycle's dynamic shared-memory limit belongs to the
+    kernel, not to a context: a context that captures a new step graph (a
+    larger batch) after another context with a smaller shared-memory
+    hierarchy has run must still launch it."""
+    big = hb.Context(hb.default_config(nlevels=2, precision=hb.PREC_FP32_MG, mg_small_cells=512,
+                                       nt0=1, T=1800.0))
+    small = hb.Context(hb.default_config(nlevels=2, precision=hb.PREC_FP32_MG,
+                                         mg_small_cells=128, nt0=1, T=1800.0))
+    a = big.solve(1, xi_cuda(1, 0, 2))
+    small.solve(1, xi_cuda(1, 0, 2))
+    b = big.solve(1, xi_cuda(1, 0, 3))        # new batch size: graph captured again
+    small.solve(1, xi_cuda(1, 0, 5))
+    assert b["status"].cpu().numpy().tolist() == [0, 0, 0]
+    assert torch.equal(a["q"], b["q"][:2])
