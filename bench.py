@@ -247,7 +247,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x FP64 FMA/clk x 2 FLOP x
 # ncu captures summarised in profiles/k_smooth_fp64_level3_256x128_b16.md and
 # profiles/k_smooth_fp32_level5_1024x512_b16.md; valid while the kernels are
 # unchanged since those captures.
-NCU_TRAFFIC_BYTES = {"k_smooth<double> L3": None}
+NCU_TRAFFIC_BYTES = {"k_smooth<double> L3": 41820160 + 64512}
 
 
 def roofline(wl, peaks):
