@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-multigrid variant")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the discrete-adjoint timing")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return ap.parse_args()
 
@@ -194,6 +195,35 @@ def tune_schedules(precision_name):
         best, _ = A.tune_level(l, BATCH[l], precision_name, steps=None, reps=1, splits=(1,))
         out[l] = best
     return out
+
+
+def adjoint_timing(rank, world, B=256, ckpt=8):
+    """Discrete adjoint of the configuration with 128x64 cells, 96 steps and
+    256 samples (checkpoint every 8 steps): dQ_S/dxi and dQ_S/dlogK for
+    every sample, FP32 multigrid inside the FP64 defect corrections, timed
+    with CUDA events against the forward solve of the same batch."""
+    import torch
+    from paper_2403_17018_gb300 import binding as hb
+    from paper_2403_17018_gb300.inputs import logk_perturbation, xi_batch
+    ctx = hb.Context(hb.default_config(nlevels=3, precision=hb.PREC_FP32_MG, vcycles=3))
+    xi = torch.from_numpy(xi_batch(2, rank * B, B)).cuda()
+    lk = torch.from_numpy(logk_perturbation(64, 128, B, seed=2403017018 + rank)).cuda()
+    ctx.adjoint(2, xi, logk=lk, ckpt_every=ckpt)          # warm-up: workspaces, graphs
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    ctx.solve(2, xi, logk=lk)
+    ev[1].record()
+    q, g, gl, st = ctx.adjoint(2, xi, logk=lk, ckpt_every=ckpt)
+    ev[2].record()
+    torch.cuda.synchronize()
+    fwd, adj = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    ctx.close()
+    return {"config": f"128x64 cells, 96 steps, {B} samples per GPU, checkpoint every {ckpt} "
+                      "steps, QoI Q_S, gradients w.r.t. xi and per-cell log K (8192)",
+            "gradients_per_s": round(B * world / (adj / 1e3), 2), "adjoint_ms": round(adj, 1),
+            "forward_ms": round(fwd, 1), "adjoint_over_forward": round(adj / fwd, 2),
+            "failed": int((st != 0).sum().item())}
 
 
 def flush_l2(buf):
@@ -428,6 +458,10 @@ def main():
                              for l, s in sched32.items()},
                 "smoother_roofline": smoother_roofline(wl32, peaks)}
 
+    adj = None
+    if not args.no_adjoint:
+        adj = adjoint_timing(rank, world)
+
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         cpu = cpu_baseline()
@@ -449,7 +483,7 @@ def main():
             "roofline": roof, "clocks": clk, "gpu_launches": launches,
             "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "fp32_mg": fp32, "cpu_baseline": cpu,
+            "fp32_mg": fp32, "adjoint": adj, "cpu_baseline": cpu,
             "step_ms": [round(x, 2) for x in per_step]}
     if rank == 0:
         print(json.dumps(line))
