@@ -1,6 +1,7 @@
 """MLMC estimator pieces of the paper's section 3 (test infrastructure only).
 
-Plain two-pass statistics and the closed-form sample allocation.
+Plain two-pass statistics, the closed-form sample allocation and the number
+of levels from the weak-error model.
 """
 from __future__ import annotations
 
@@ -81,3 +82,25 @@ def fit_rate(levels, values, base=2.0):
     A = np.vstack([-l, np.ones_like(l)]).T
     (rate, zeta), *_ = np.linalg.lstsq(A, y, rcond=None)
     return float(rate), float(zeta)
+
+
+def weak_error_constants(levels, means_d):
+    """Weak-error model of Eq. weak_error_model, |E(g_l - g)| <= c1 4^(-alpha l),
+    from the level corrections E Y_l = E(g_l - g_(l-1)), l >= 1: least-squares
+    fit log_4 |E Y_l| = -alpha l + zeta (the paper's log_4 convention, one
+    level = h halved = cells x 4), c_Y = 4^zeta, and the bias of level L read
+    as the tail of the finer corrections, sum_(k > L) c_Y 4^(-alpha k) =
+    c_Y 4^(-alpha L) / (4^alpha - 1), so c1 = c_Y / (4^alpha - 1).
+    Returns (alpha, c1)."""
+    alpha, zeta = fit_rate(levels, means_d, base=4.0)
+    c_y = 4.0 ** zeta
+    return alpha, c_y / (4.0 ** alpha - 1.0)
+
+
+def num_levels(eps, E0, c1, alpha):
+    """Eq. num_levels: the finest level L with c1 4^(-alpha L) = eps E0 / sqrt(2),
+    L = -(1/alpha) log_4(eps E0 / (sqrt(2) c1)), taken as the smallest integer
+    level that meets the bias bound (never below 0). E0 = 1 for an absolute
+    eps, E0 = |E g_0| for the paper's relative error."""
+    L = -math.log(eps * E0 / (math.sqrt(2.0) * c1), 4.0) / alpha
+    return max(0, int(math.ceil(L - 1e-12)))

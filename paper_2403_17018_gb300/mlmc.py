@@ -105,6 +105,25 @@ def fit_alpha(means):
     return float(max(alpha, 0.5))
 
 
+def levels_needed(means_d, eps):
+    """Finest level from the weak-error model (Eq. weak_error_model, Eq.
+    num_levels): fit log_4 |E Y_l| = -alpha l + zeta over l >= 1, read the
+    bias of level L as the tail of the finer corrections, c1 4^(-alpha L)
+    with c1 = 4^zeta / (4^alpha - 1), and return the smallest L with
+    c1 4^(-alpha L) <= eps / sqrt(2) (eps absolute), with (alpha, c1)."""
+    l = np.arange(1, len(means_d))
+    y = np.abs(np.asarray(means_d[1:], dtype=np.float64))
+    ok = y > 0
+    if ok.sum() < 2:
+        return None, None, None
+    A = np.vstack([-l[ok], np.ones(ok.sum())]).T
+    (alpha, zeta), *_ = np.linalg.lstsq(A, np.log(y[ok]) / math.log(4.0), rcond=None)
+    alpha = max(float(alpha), 0.25)          # no slower than h^(1/2)
+    c1 = 4.0 ** float(zeta) / (4.0 ** alpha - 1.0)
+    L = -math.log(eps / (math.sqrt(2.0) * c1), 4.0) / alpha
+    return max(0, int(math.ceil(L - 1e-12))), alpha, c1
+
+
 class GpuSampler:
     """Level pairs on the GPU through the C ABI; statistics merged on device.
 
@@ -203,17 +222,28 @@ def _merge_ranks(levels, dist):
 
 
 def run(sampler, L, eps, qois=(3, 4, 5), pilot=None, max_batch=None, var_budget_fraction=0.5,
-        max_rounds=20, log=None, dist=None, state=None, concurrent=True):
+        max_rounds=20, log=None, dist=None, state=None, concurrent=True, adaptive_levels=False,
+        L_start=2, relative=False):
     """Adaptive MLMC on levels 0..L to RMSE eps for the QoIs `qois`.
     With `concurrent` and a sampler that has `batches`, the pending pairs
     of all levels run at the same time (cost per pair then measured under
     sharing, which scales every level's cost alike to first order).
 
+    adaptive_levels: start on levels 0..L_start and add a level whenever the
+    weak-error model fitted to the level means (Eq. num_levels) asks for a
+    finer one, up to L. relative: eps is relative to E0 = |E g_0| of each
+    QoI (the paper's scaling, Eq. scaled_m_l_S), estimated from level 0.
+
     Returns a dict with the estimate per QoI, Var Y, the bias estimate, the
     RMSE estimate, samples and cost per level and the wall time. `state`
     (from a previous result's "state") resumes a run."""
-    pilot = pilot or [max(16, 512 >> (2 * l)) for l in range(L + 1)]
-    max_batch = max_batch or [max(32, 16384 >> (2 * l)) for l in range(L + 1)]
+    L_max = L
+    if state is not None:
+        L = len(state) - 1
+    elif adaptive_levels:
+        L = min(L_start, L_max)
+    pilot = pilot or [max(16, 512 >> (2 * l)) for l in range(L_max + 1)]
+    max_batch = max_batch or [max(32, 16384 >> (2 * l)) for l in range(L_max + 1)]
     local = [LevelState() for _ in range(L + 1)] if state is None else \
         [LevelState.from_json(d) for d in state]
     target = [max(pilot[l], local[l].n) for l in range(L + 1)]
@@ -221,6 +251,8 @@ def run(sampler, L, eps, qois=(3, 4, 5), pilot=None, max_batch=None, var_budget_
     rounds = 0
     qs = list(qois)
     levels = _merge_ranks(local, dist)
+    level_choice = []
+
     def record(l, cnt, out):
         n, mf, m2f, md, m2d, dt, failed = out
         chan_merge(local[l], n, mf, m2f, md, m2d)
@@ -255,12 +287,30 @@ def run(sampler, L, eps, qois=(3, 4, 5), pilot=None, max_batch=None, var_budget_
                 f"(valid samples {[levels[l].n for l in bad]}, failed "
                 f"{[levels[l].failed for l in bad]}); the solves of these levels did not converge")
         s = np.array([max(lv.seconds, 1e-9) / max(lv.timed_pairs, 1) for lv in levels])
-        m = np.max(np.stack([allocate(V[:, k], s, eps, var_budget_fraction)
+        eps_q = [eps * abs(levels[0].mean_f[q]) if relative else eps for q in qs]
+        m = np.max(np.stack([allocate(V[:, k], s, eps_q[k], var_budget_fraction)
                              for k in range(len(qs))]), axis=0)
         rounds += 1
         if log:
             log({"round": rounds, "n": [lv.n for lv in levels], "m": m.tolist(),
                  "V": V.max(axis=1).tolist(), "s": s.tolist()})
+        if adaptive_levels and L < L_max and L >= 2:
+            fits = [levels_needed([lv.mean_d[q] for lv in levels], eps_q[k])
+                    for k, q in enumerate(qs)]
+            chosen = [f[0] for f in fits if f[0] is not None]
+            L_need = max(chosen) if chosen else L
+            level_choice.append({"levels_fitted": L + 1, "L_needed": L_need,
+                                 "alpha4": [f[1] for f in fits], "c1": [f[2] for f in fits]})
+            if log:
+                log({"round": rounds, "L": L, "L_needed": L_need})
+            if L_need > L:
+                # one finer level at a time, with its pilot; the next round
+                # re-allocates every level with the new level's V and cost
+                L += 1
+                local.append(LevelState())
+                levels = _merge_ranks(local, dist)
+                target = [int(max(levels[l].n, m[l])) for l in range(L)] + [pilot[L]]
+                continue
         if all(m[l] <= levels[l].n for l in range(L + 1)) or rounds >= max_rounds:
             break
         target = [int(max(levels[l].n, m[l])) for l in range(L + 1)]
@@ -272,7 +322,8 @@ def run(sampler, L, eps, qois=(3, 4, 5), pilot=None, max_batch=None, var_budget_
     bias = np.array([abs(levels[L].mean_d[q]) / (2.0 ** alphas[q] - 1.0) if L >= 1 else 0.0
                      for q in range(NQ)])
     rmse = np.sqrt(varY + bias ** 2)
-    return {"levels": L + 1, "eps": eps, "qois": qs, "estimate": Y.tolist(),
+    return {"levels": L + 1, "eps": eps, "relative": relative, "qois": qs,
+            "level_choice": level_choice, "estimate": Y.tolist(),
             "var_Y": varY.tolist(), "bias": bias.tolist(), "alpha": alphas,
             "rmse": rmse.tolist(), "rmse_sampling": np.sqrt(varY).tolist(),
             "n": n.astype(int).tolist(), "V_l": [lv.var_d().tolist() for lv in levels],
@@ -292,6 +343,11 @@ def main(argv=None):
     ap.add_argument("--tune", action="store_true",
                     help="autotune the multigrid schedule of every level on its largest batch "
                          "first (cached; the tuning time is reported apart from the MLMC wall time)")
+    ap.add_argument("--adaptive-levels", action="store_true",
+                    help="start on levels 0..2 and add levels while the fitted weak-error model "
+                         "(Eq. num_levels) asks for them, up to --levels")
+    ap.add_argument("--relative", action="store_true",
+                    help="eps relative to |E g_0| of each QoI (the paper's scaling)")
     ap.add_argument("--sequential", action="store_true",
                     help="run the levels one after another instead of on concurrent streams")
     ap.add_argument("--out", default=None)
@@ -331,7 +387,8 @@ def main(argv=None):
         tune_s = time.perf_counter() - t0
     sampler = GpuSampler(cfg, rank, world, schedules=schedules)
     log = (lambda d: print(json.dumps(d), flush=True)) if rank == 0 else None
-    res = run(sampler, a.levels - 1, a.eps, log=log, dist=dist, concurrent=not a.sequential)
+    res = run(sampler, a.levels - 1, a.eps, log=log, dist=dist, concurrent=not a.sequential,
+              adaptive_levels=a.adaptive_levels, relative=a.relative)
     res.update({"precision": a.precision, "n_gpus": world, "tuning_s": tune_s,
                 "concurrent_levels": not a.sequential,
                 "schedules": {l: {k: v for k, v in sc.items() if k in ("vcycles", "nu1", "nu2",

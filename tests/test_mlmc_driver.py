@@ -147,3 +147,34 @@ def test_concurrent_waves_give_the_sequential_result():
     con = M.run(Multi(), 3, 0.01, qois=(0, 1), max_batch=[64, 16, 8, 4], concurrent=True)
     for k in ("estimate", "var_Y", "n", "mean_l", "V_l"):
         assert con[k] == seq[k], k
+
+
+@pytest.mark.parametrize("eps", [2e-2, 5e-3, 1e-3])
+def test_adaptive_level_count_matches_the_bias_model(eps):
+    """With corrections E Y_l = a 2^-l and (almost) no noise, the driver adds
+    levels until Eq. num_levels is met: the finest level is the smallest L
+    whose tail bias a 2^-L is at most eps / sqrt(2), as the oracle's
+    weak-error fit and level formula give for the same level means."""
+    s = FakeSampler(v=1e-20)
+    res = M.run(s, 12, eps, qois=(0,), adaptive_levels=True, L_start=2)
+    L = res["levels"] - 1
+    brute = next(k for k in range(40) if s.a * 2.0 ** -k <= eps / math.sqrt(2.0))
+    assert L == max(brute, 2)
+    alpha, c1 = OM.weak_error_constants(list(range(1, L + 1)), [m[0] for m in res["mean_l"][1:]])
+    assert OM.num_levels(eps, 1.0, c1, alpha) == brute
+    # levels were added one at a time, each decision from the levels so far
+    assert [c["levels_fitted"] for c in res["level_choice"]][:L - 2] == list(range(3, L + 1))
+
+
+def test_relative_tolerance_scales_by_level_zero_mean():
+    """relative=True: eps is relative to E0 = |E g_0| (Eq. scaled_m_l_S): the
+    run ends with Var Y within (eps E0)^2 / 2, E0 the level-0 mean of g, and
+    allocates Eq. M_ell with eps E0."""
+    s = FakeSampler()
+    eps = 0.01
+    res = M.run(s, 3, eps, qois=(0,), relative=True, pilot=[32, 16, 8, 8])
+    E0 = abs(res["state"][0]["mean_f"][0])
+    assert res["var_Y"][0] <= (eps * E0) ** 2 / 2 * (1 + 1e-12)
+    V = np.array(res["V_l"])[:, 0]
+    m = OM.allocation(V, np.array(res["seconds_per_pair"]), eps * E0)
+    assert all(n >= k for n, k in zip(res["n"], m))

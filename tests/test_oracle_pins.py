@@ -306,3 +306,22 @@ def test_grid_convergence_order_of_the_coupled_problem():
     # correction of the level pairs tends to zero)
     P0 = [H.prolong_constant(cs[l]) - cs[l + 1] for l in range(2)]
     assert math.sqrt(np.mean(P0[1] ** 2)) < math.sqrt(np.mean(P0[0] ** 2))
+
+
+@pytest.mark.parametrize("a,eps,E0", [(0.3, 1e-3, 1.0), (0.05, 2e-3, 0.52), (2.0, 1e-2, 336.0)])
+def test_num_levels_is_the_smallest_level_meeting_the_bias_bound(a, eps, E0):
+    """Eq. num_levels with the weak-error model of Eq. weak_error_model: for
+    corrections E Y_l = a 2^-l (first order in h, the paper's alpha = 1/2 in
+    its log_4 convention) the bias of level L is the tail sum over the finer
+    corrections, a 2^-L. The fitted (alpha, c1) and the chosen L must agree
+    with that tail, summed term by term, and with the smallest L meeting
+    |bias| <= eps E0 / sqrt(2), found by brute force."""
+    levels = [1, 2, 3, 4]
+    alpha, c1 = M.weak_error_constants(levels, [a * 2.0 ** -l for l in levels])
+    assert abs(alpha - 0.5) < 1e-12
+    for L in (0, 3, 7):
+        tail = sum(a * 2.0 ** -k for k in range(L + 1, L + 200))
+        assert abs(c1 * 4.0 ** (-alpha * L) - tail) <= 1e-12 * tail
+    brute = next(L for L in range(200)
+                 if sum(a * 2.0 ** -k for k in range(L + 1, L + 200)) <= eps * E0 / math.sqrt(2.0))
+    assert M.num_levels(eps, E0, c1, alpha) == brute
