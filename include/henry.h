@@ -220,6 +220,19 @@ int mlmc_field_stats(henry_ctx* ctx, int level, const double* c_fine, const doub
                      int B, const int* status, int64_t* n, double* mean_f, double* m2_f,
                      double* mean_d, double* m2_d, void* stream);
 
+/* Per-cell exceedance counts of the c field of one level (section 4: the
+ * probability that the salt mass fraction at a location exceeds a threshold,
+ * P(c(T, x) > threshold), estimated as count / n by the caller):
+ * count[cell] += number of samples b with status[b] == 0 and
+ * c[b][cell] > threshold. Integer counts, so the result does not depend on
+ * how the samples are batched. Asynchronous on `stream`.
+ *   c         device [B][ny_l][nx_l]
+ *   status    device int [B] or NULL (all samples valid)
+ *   count     device int64 [ny_l*nx_l], accumulated in place (caller zeroes it)
+ * Errors: HENRY_E_INVALID (bad level, B < 0, NaN threshold, NULL), HENRY_E_CUDA. */
+int mlmc_field_exceedance(henry_ctx* ctx, int level, const double* c, int B, const int* status,
+                          double threshold, int64_t* count, void* stream);
+
 /* Evaluate the FP64 finite-volume residual of one implicit Euler step and,
  * optionally, its exact Jacobian, for B states on an nx x ny grid (Eqs.
  * 1-5 integrated over each cell). Context-free; for tests and tools.

@@ -11,6 +11,8 @@ Modules
   mlmc     -- two-pass level statistics, the telescoping estimator and the
               optimal sample allocation (paper section 3).
   adjoint  -- discrete adjoint of a QoI through the implicit time stepping.
+  qmc      -- sample quantiles, exceedance fractions and randomised-QMC
+              replicate estimates (paper section 4, tests A1-A3).
 
 Parity status: every function here is pinned by `tests/test_oracle_pins.py`
 against closed forms, invariants or the paper's printed numbers, except the

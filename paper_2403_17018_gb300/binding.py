@@ -84,6 +84,7 @@ def load():
         "henry_sample_pairs": (I, [P, I, V, I, V, V, V, V, V, V]),
         "mlmc_level_stats": (I, [P, I, V, V, I, V, ctypes.POINTER(LevelStats), V]),
         "mlmc_field_stats": (I, [P, I, V, V, I, V, V, V, V, V, V, V]),
+        "mlmc_field_exceedance": (I, [P, I, V, I, V, D, V, V]),
         "henry_residual_jacobian": (I, [cfgp, I, I, D, I, V, V, V, V, V, V, V, V, V]),
         "henry_residual_jacobian_noalloc": (I, [cfgp, I, I, D, I, V, V, V, V, V, V, V, V, V]),
         "henry_fields": (I, [P, I, V, V, I, V, V, V, V]),
@@ -258,6 +259,17 @@ class Context:
             _ptr(acc["mean_d"], torch.float64), _ptr(acc["m2_d"], torch.float64),
             _stream(stream)))
         return acc
+
+    def field_exceedance(self, level, c, status, threshold, count, stream=None):
+        """mlmc_field_exceedance: count (device int64 [ny*nx]) += samples with
+        c > threshold, per cell."""
+        import torch
+        B = c.shape[0]
+        _check(self.lib.mlmc_field_exceedance(
+            self._h, level, _ptr(c, torch.float64, None, "c"), B,
+            _ptr(status, torch.int32, (B,), "status"), float(threshold),
+            _ptr(count, torch.int64), _stream(stream)))
+        return count
 
     def adjoint(self, level, xi, logk=None, qoi="Q_S", ckpt_every=8, want_logk=True, stream=None):
         """henry_adjoint: (q [B], dq_dxi [B,n_xi], dq_dlogk [B,ny,nx] or None, status [B])."""

@@ -13,6 +13,9 @@
 namespace henry {
 cudaError_t launch_level_stats(unsigned long long* ctr, int B, const double* qf, const double* qc,
                                const int* status, double* out, cudaStream_t s);
+cudaError_t launch_field_exceed(unsigned long long* ctr, int ncell, int B, const double* c,
+                                const int* status, double threshold, int64_t* count,
+                                cudaStream_t s);
 cudaError_t launch_field_stats(unsigned long long* ctr, int nx, int ny, int B, const double* cf,
                                const double* cc, const int* status, int64_t* n, double* mean_f,
                                double* m2_f, double* mean_d, double* m2_d, cudaStream_t s);
@@ -315,6 +318,21 @@ int mlmc_field_stats(henry_ctx* ctx, int level, const double* c_fine, const doub
   const int nx = ctx->cfg.nx0 << level, ny = ctx->cfg.ny0 << level;
   CKR(henry::launch_field_stats(ctx->ctr, nx, ny, B, c_fine, c_coarse, status, n, mean_f, m2_f,
                                 mean_d, m2_d, (cudaStream_t)stream));
+  return HENRY_OK;
+}
+
+int mlmc_field_exceedance(henry_ctx* ctx, int level, const double* c, int B, const int* status,
+                          double threshold, int64_t* count, void* stream) {
+  if (!ctx) return fail(HENRY_E_INVALID, "ctx is NULL");
+  if (level < 0 || level >= ctx->cfg.nlevels) return fail(HENRY_E_INVALID, "bad level");
+  if (B < 0) return fail(HENRY_E_INVALID, "B < 0");
+  if (!(threshold == threshold)) return fail(HENRY_E_INVALID, "threshold is NaN");
+  if (B == 0) return HENRY_OK;
+  if (!c || !count) return fail(HENRY_E_INVALID, "NULL argument");
+  CKR(cudaSetDevice(ctx->device));
+  const int ncell = (ctx->cfg.nx0 << level) * (ctx->cfg.ny0 << level);
+  CKR(henry::launch_field_exceed(ctx->ctr, ncell, B, c, status, threshold, count,
+                                 (cudaStream_t)stream));
   return HENRY_OK;
 }
 

@@ -111,6 +111,31 @@ __global__ void k_field_stats(unsigned long long* ctr, int nx, int ny, int B,
   m2_d[cell] = sd;
 }
 
+// Per-cell exceedance counts (section 4: probability that the salt mass
+// fraction at a location exceeds a threshold): count[cell] += number of
+// valid samples b with c_b[cell] > threshold. One thread per cell, samples in
+// order, integer counts (exact, independent of batching).
+__global__ void k_field_exceed(unsigned long long* ctr, int ncell, int B,
+                               const double* __restrict__ c, const int* __restrict__ status,
+                               double threshold, int64_t* __restrict__ count) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= ncell) return;
+  int64_t k = 0;
+  for (int b = 0; b < B; ++b) {
+    if (status && status[b] != 0) continue;
+    k += c[(int64_t)b * ncell + cell] > threshold ? 1 : 0;
+  }
+  count[cell] += k;
+}
+
+cudaError_t launch_field_exceed(unsigned long long* ctr, int ncell, int B, const double* c,
+                                const int* status, double threshold, int64_t* count,
+                                cudaStream_t s) {
+  k_field_exceed<<<(ncell + 255) / 256, 256, 0, s>>>(ctr, ncell, B, c, status, threshold, count);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_level_stats(unsigned long long* ctr, int B, const double* qf, const double* qc,
                                const int* status, double* out, cudaStream_t s) {
   k_level_stats<<<1, kStatThreads, 0, s>>>(ctr, B, qf, qc, status, out);

@@ -1,0 +1,134 @@
+"""Halton points, sample quantiles and exceedance statistics of the QMC runs
+(section 4, tests A1-A3), and (GPU) a small QMC run against the oracle."""
+import numpy as np
+import pytest
+
+from oracle import qmc as OQ
+from paper_2403_17018_gb300.inputs import halton, radical_inverse, xi_halton
+from paper_2403_17018_gb300.qmc import sample_quantiles
+
+
+def test_radical_inverse_textbook_values():
+    """van der Corput: base 2 gives 0, 1/2, 1/4, 3/4, 1/8, 5/8, ...; base 3
+    gives 0, 1/3, 2/3, 1/9, 4/9, 7/9, 2/9, ..."""
+    assert radical_inverse(np.arange(8), 2).tolist() == [0, .5, .25, .75, .125, .625, .375, .875]
+    b3 = [0, 1 / 3, 2 / 3, 1 / 9, 4 / 9, 7 / 9, 2 / 9, 5 / 9, 8 / 9]
+    assert np.allclose(radical_inverse(np.arange(9), 3), b3, rtol=0, atol=1e-15)
+    # 1234 = 1*5^4 + 4*5^3 + 4*5^2 + 1*5 + 4: digits 4, 1, 4, 4, 1 mirrored
+    assert radical_inverse(np.array([1234]), 5)[0] == pytest.approx(
+        sum(d * 5.0 ** -(k + 1) for k, d in enumerate([4, 1, 4, 4, 1])), abs=1e-15)
+
+
+@pytest.mark.parametrize("base,k", [(2, 10), (3, 6), (5, 4), (13, 2)])
+def test_first_b_to_the_k_points_are_equidistributed(base, k):
+    """The first b^k radical inverses in base b are exactly {j / b^k}."""
+    n = base ** k
+    u = np.sort(radical_inverse(np.arange(n), base))
+    assert np.allclose(u, np.arange(n) / n, rtol=0, atol=1e-14)
+
+
+def test_halton_dimensions_and_shift():
+    u = halton(1, 100, 6)
+    assert u.shape == (100, 6) and np.all((u >= 0) & (u < 1))
+    assert np.array_equal(u[:, 1], radical_inverse(np.arange(1, 101), 3))
+    a, b = halton(1, 50, 3, shift_seed=5), halton(1, 50, 3, shift_seed=5)
+    assert np.array_equal(a, b)
+    d = np.mod(a - halton(1, 50, 3), 1.0)     # one shift per coordinate
+    assert np.allclose(d, d[0], atol=1e-12)
+    xi = xi_halton(1, 10, 3)
+    assert np.all((xi >= -1) & (xi < 1)) and np.allclose(xi, 2 * halton(1, 10, 3) - 1)
+
+
+def test_oracle_quantile_closed_forms():
+    """Definition 7 on a permutation of 0..n-1 gives (n-1) p; on {a, b},
+    a + p (b - a); the median of an odd sample is its middle order statistic."""
+    for n in (2, 5, 600):
+        for p in (0.0, 0.025, 0.25, 0.5, 0.975, 1.0):
+            assert OQ.quantile(np.random.default_rng(n).permutation(n), p) == \
+                pytest.approx((n - 1) * p, abs=1e-12)
+    assert OQ.quantile([3.0, 1.0], 0.25) == pytest.approx(1.5)
+    assert OQ.quantile([5.0, -2.0, 9.0, 0.5, 7.0], 0.5) == 5.0
+
+
+def test_driver_quantiles_match_the_oracle():
+    rng = np.random.default_rng(1)
+    probs = (0.025, 0.25, 0.5, 0.75, 0.975)
+    for n in (1, 7, 600):
+        x = rng.standard_normal((n, 3))
+        got = sample_quantiles(x, probs)
+        for i, p in enumerate(probs):
+            for k in range(3):
+                assert got[i, k] == pytest.approx(OQ.quantile(x[:, k], p), abs=1e-14)
+
+
+def test_replicate_estimate_closed_form():
+    m, se = OQ.replicate_estimate([[1.0], [3.0]])
+    assert m[0] == 2.0 and se[0] == pytest.approx(1.0)
+
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.mark.gpu
+def test_exceedance_counts_are_exact():
+    """mlmc_field_exceedance counts c > threshold per cell over valid
+    samples, accumulated over batches: equal to numpy brute force."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2403_17018_gb300 import binding as hb
+    ctx = hb.Context(hb.default_config(nlevels=2))
+    rng = np.random.default_rng(3)
+    c = rng.random((37, 64 * 32))
+    c[5, :10] = 0.5                               # ties at the threshold do not count
+    st = np.zeros(37, dtype=np.int32)
+    st[[2, 30]] = 1
+    count = torch.zeros(64 * 32, dtype=torch.int64, device="cuda")
+    cd = torch.from_numpy(c).cuda()
+    sd = torch.from_numpy(st).cuda()
+    ctx.field_exceedance(1, cd[:20].contiguous(), sd[:20].contiguous(), 0.5, count)
+    ctx.field_exceedance(1, cd[20:].contiguous(), sd[20:].contiguous(), 0.5, count)
+    want = np.sum(c[st == 0] > 0.5, axis=0)
+    assert np.array_equal(count.cpu().numpy(), want)
+    with pytest.raises(hb.HenryError):
+        ctx.field_exceedance(1, cd, sd, float("nan"), count)
+
+
+@pytest.mark.gpu
+def test_qmc_run_matches_the_oracle():
+    """12 Halton points per replicate on level 0 in batches of 5 (ragged),
+    two shifted replicates: the replicate means, the quantiles and the
+    exceedance field agree with the oracle's solves of the same xi."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from gpu_helpers import oracle_solve, tight_config
+    from paper_2403_17018_gb300 import binding as hb
+    from paper_2403_17018_gb300 import qmc as Q
+    cfg = tight_config(nlevels=1)
+    ctx = hb.Context(cfg)
+    res = Q.run(ctx, 0, 12, batch=5, replicates=2, thresholds=(0.3,))
+    assert res["failed"] == 0
+    qs, cs = [], []
+    for r in range(2):
+        xi = xi_halton(1, 12, 3, 2403017018 + 7919 * (r + 1))
+        sol = [oracle_solve(cfg, 0, x) for x in xi]
+        q = np.array([s[2] for s in sol])
+        assert np.allclose(res["replicate_means"][r], q.mean(axis=0), rtol=1e-9, atol=1e-10)
+        qs.append(q)
+        cs.append(np.array([s[1] for s in sol]))
+    q = np.concatenate(qs)
+    for i, p in enumerate(res["quantile_probs"]):
+        for k in range(q.shape[1]):
+            assert res["quantiles"][i, k] == pytest.approx(OQ.quantile(q[:, k], p), rel=1e-9,
+                                                           abs=1e-10)
+    mean, se = OQ.replicate_estimate(res["replicate_means"])
+    assert np.allclose(res["mean"], mean, rtol=1e-14) and np.allclose(res["std_error"], se,
+                                                                       rtol=1e-12)
+    c = np.concatenate(cs)
+    assert res["n_field"] == c.shape[0]
+    near = np.any(np.abs(c - 0.3) < 1e-8, axis=0)   # decisions the 1e-9 parity may flip
+    want = np.sum(c > 0.3, axis=0)
+    got = res["counts"][0]
+    bad = np.argwhere((got != want) & ~near)
+    assert len(bad) == 0, [(int(j), int(i), int(got[j, i]), int(want[j, i])) for j, i in bad[:8]]
+    ex = OQ.exceedance(c, 0.3)
+    assert np.array_equal(res["exceedance"][0][~near], ex[~near])
