@@ -55,13 +55,19 @@ extern "C" {
 #define HENRY_S_BADINPUT 4       /* xi was not finite                        */
 
 /* ---- quantities of interest (q[] outputs, HENRY_NQ per sample) --------- */
-#define HENRY_NQ 6
+#define HENRY_NQ 22
 /* 0  Q_S   = int c rho dx                    (section 4, Eq. integral_s)
  * 1  M     = int phi rho c dx                (stored salt mass, Eq. 2)
  * 2  toe   = int c (Lx - x) dx               (salt-wedge penetration)
  * 3..5     c at (1.40,0.05), (1.65,0.25), (1.90,0.50): the paper's points
  *          3, 9 and 15 of Eq. 12points shifted into y in [0,1]; bilinear
- *          interpolation of cell values clamped to the outer cell centres. */
+ *          interpolation of cell values clamped to the outer cell centres.
+ * 6  Q_FW  = area where c <= 0.012178        (fresh water, Eq. integral_fw)
+ * 7..21    Q_1..Q_15 = int c rho dx over [x_i - 0.1, x_i + 0.1] x
+ *          [y_i - 0.1, y_i + 0.1] clipped to the domain (Eq. integral_box),
+ *          points of Eq. 12points in the order printed there (rows y_p =
+ *          -0.95, -0.75, -0.50, i.e. y = 0.05, 0.25, 0.50; x = 0.90, 1.15,
+ *          1.40, 1.65, 1.90); c constant per cell. */
 
 #define HENRY_PREC_FP64 0        /* multigrid in FP64                        */
 #define HENRY_PREC_FP32_MG 1     /* FP32 V-cycles inside FP64 defect correction */
@@ -110,7 +116,16 @@ typedef struct henry_config {
                            by less than a factor k, reused otherwise (the
                            residual is always the current FP64 one, so the
                            converged solution satisfies the same tolerance) */
-  int reserved[2];
+  int field_model;      /* 0 (default): the smooth fields of k_fields' 3 or 6
+                           variables; 1: the paper's two-layer multiscale
+                           porosity (Eq. poro_2levels), Kozeny-Carman
+                           permeability K = kappa phi^3 / (1 - phi^2) with
+                           kappa = K0 (1 - phi0^2) / phi0^3 (Eq.
+                           e_perm_Kozeny_Carman; Table 1's kappa_KC), and the
+                           recharge q0 (1 + 0.5 xi3)(1 + sin(pi t / 40)) taken
+                           at the end of each step (Eq. e_recharge_of_param);
+                           needs n_xi = 3; no adjoint */
+  int reserved[1];
 } henry_config;
 
 typedef struct henry_ctx henry_ctx; /* opaque: owns device workspaces */
@@ -192,7 +207,8 @@ int henry_sample_pairs(henry_ctx* ctx, int level, const double* xi, int B,
  *   dq_dlogk   device [B][ny][nx] out, or NULL
  *   status     device int [B] out (HENRY_S_* bits of forward and adjoint)
  * Synchronises the stream once per defect-correction iteration of the
- * backward pass. Errors as henry_solve. */
+ * backward pass. Errors as henry_solve; HENRY_E_INVALID for a context with
+ * field_model != 0 (the adjoint contracts the smooth model's fields). */
 int henry_adjoint(henry_ctx* ctx, int level, const double* xi, const double* logk, int B,
                   int qoi_id, int ckpt_every, double* q, double* dq_dxi, double* dq_dlogk,
                   int* status, void* stream);

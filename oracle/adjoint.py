@@ -43,6 +43,8 @@ def qoi_value(name, grid, phys, c):
 
 def adjoint(grid, phys, xi, qoi="Q_S", logk=None):
     """Returns dict(q, dq_dxi [n_xi], dq_dlogk [ny, nx], lam (per step))."""
+    if phys.field_model != 0:
+        raise NotImplementedError("the adjoint covers the smooth field model (field_model 0)")
     xi = np.asarray(xi, dtype=float)
     ny, nx = grid.ny, grid.nx
     lk = np.zeros((ny, nx)) if logk is None else np.asarray(logk, dtype=float)

@@ -57,6 +57,15 @@ class Physics:
     q0: float = 6.6e-5            # freshwater inflow [m/s] (6.6e-2 kg/s / rho0)
     Lx: float = 2.0
     Ly: float = 1.0
+    field_model: int = 0          # 0: smooth 3/6-variable fields; 1: the paper's
+                                  # Eq. poro_2levels + Kozeny-Carman + recharge
+
+    @property
+    def kappa_kc(self) -> float:
+        """Kozeny-Carman scaling (Eq. e_perm_Kozeny_Carman) chosen so that the
+        mean porosity gives the reference permeability: K0 (1 - phi0^2) / phi0^3
+        (Table 1 lists kappa_KC = 2.088415e-8 m^2 beside K0 and phi0)."""
+        return self.K0 * (1.0 - self.phi0 ** 2) / self.phi0 ** 3
 
 
 @dataclass(frozen=True)
@@ -85,7 +94,14 @@ def level_grid(level: int, nx0: int = 32, ny0: int = 16, nt0: int = 24,
 # (1.40,-0.95), (1.65,-0.75), (1.90,-0.50), shifted into y in [0, 1].
 OBS_POINTS = ((1.40, 0.05), (1.65, 0.25), (1.90, 0.50))
 
-QOI_NAMES = ("Q_S", "salt_mass", "toe", "c_x3", "c_x9", "c_x15")
+# The paper's 15 points (Eq. 12points) in the frame y in [0, 1], and the
+# freshwater threshold of Eq. integral_fw.
+POINTS15 = tuple((x, y) for y in (0.05, 0.25, 0.50) for x in (0.90, 1.15, 1.40, 1.65, 1.90))
+BOX_HALF = 0.1
+FRESH_C = 0.012178
+
+QOI_NAMES = ("Q_S", "salt_mass", "toe", "c_x3", "c_x9", "c_x15", "Q_FW") + tuple(
+    f"Q_{i + 1}" for i in range(15))
 NQ = len(QOI_NAMES)
 
 
@@ -108,9 +124,17 @@ class Fields:
 
 
 def fields(grid: Grid, phys: Physics, xi, logk=None) -> Fields:
-    """phi = phi0 (1 + 0.1 xi1 cos(pi x/2) sin(pi y) [+ 0.05 xi4 cos(pi x) sin(2 pi y)])
+    """field_model 0 (the configs' smooth fields):
+    phi = phi0 (1 + 0.1 xi1 cos(pi x/2) sin(pi y) [+ 0.05 xi4 cos(pi x) sin(2 pi y)])
     K   = K0 exp(0.5 xi2 sin(pi x/2) cos(pi y) [+ 0.05 xi5 sin(pi x) cos(2 pi y)] + theta)
     q_in = q0 (1 + 0.1 xi3 [+ 0.05 xi6 cos(pi y)])
+    field_model 1 (the paper's, Eq. poro_2levels with y_p = y - Ly in its frame):
+    phi = phi0 C0 C1 C2, C0 = 1.2 (1 + 0.2 xi1) for y_p < -0.8 else 1,
+      C1 = 1 + 0.15 (xi2 cos(pi x/2) - xi2 sin(2 pi y_p) + xi1 cos(2 pi x)),
+      C2 = 1 + 0.2 (xi1 sin(64 pi x) + xi2 sin(32 pi y_p));
+    K = kappa_KC phi^3 / (1 - phi^2) exp(theta) (Eq. e_perm_Kozeny_Carman);
+    q_in = q0 (1 + 0.5 xi3), the base of Eq. e_recharge_of_param (its time
+    factor is applied per step by `solve`).
     Evaluated at cell centres of this grid (the paper evaluates its fields at
     integration points rather than from a precomputed raster, section
     "Uncertain porosity and recharge"). `xi` may be complex (complex step).
@@ -118,6 +142,17 @@ def fields(grid: Grid, phys: Physics, xi, logk=None) -> Fields:
     xi = np.asarray(xi)
     x, y = cell_centres(grid, phys)
     X, Y = np.meshgrid(x, y)
+    if phys.field_model == 1:
+        Yp = Y - phys.Ly
+        C0 = np.where(Yp < -0.8, 1.2 * (1.0 + 0.2 * xi[0]), 1.0 + 0.0 * xi[0])
+        C1 = 1.0 + 0.15 * (xi[1] * np.cos(np.pi * X / 2) - xi[1] * np.sin(2 * np.pi * Yp)
+                           + xi[0] * np.cos(2 * np.pi * X))
+        C2 = 1.0 + 0.2 * (xi[0] * np.sin(64 * np.pi * X) + xi[1] * np.sin(32 * np.pi * Yp))
+        phi = phys.phi0 * C0 * C1 * C2
+        K = phys.kappa_kc * phi ** 3 / (1.0 - phi ** 2)
+        if logk is not None:
+            K = K * np.exp(logk)
+        return Fields(phi=phi, K=K, qin=phys.q0 * (1.0 + 0.5 * xi[2]) + 0.0 * y)
     a = 0.1 * xi[0] * np.cos(np.pi * X / 2) * np.sin(np.pi * Y)
     b = 0.5 * xi[1] * np.sin(np.pi * X / 2) * np.cos(np.pi * Y)
     qf = 1.0 + 0.1 * xi[2] + 0.0 * y
@@ -302,8 +337,14 @@ def solve(grid: Grid, phys: Physics, xi, logk=None, c0=None, p0=None,
     p = hydrostatic_guess(grid, phys) if p0 is None else np.array(p0, dtype=float)
     its = []
     states = [(p.copy(), c.copy())] if keep_states else None
-    for _ in range(grid.nt):
-        p, c, it = newton_step(grid, phys, f, p, c, c.copy())
+    for n in range(grid.nt):
+        fn = f
+        if phys.field_model == 1:
+            # Eq. e_recharge_of_param: inflow times (1 + sin(pi t / 40)), t in
+            # seconds, taken at the new time level t^(n+1) of the implicit step
+            t = (n + 1) * grid.tau
+            fn = Fields(phi=f.phi, K=f.K, qin=f.qin * (1.0 + math.sin(math.pi * t / 40.0)))
+        p, c, it = newton_step(grid, phys, fn, p, c, c.copy())
         its.append(it)
         if keep_states:
             states.append((p.copy(), c.copy()))
@@ -326,11 +367,25 @@ def point_value(grid: Grid, phys: Physics, c, x, y):
             + (1 - tx) * ty * c[j0 + 1, i0] + tx * ty * c[j0 + 1, i0 + 1])
 
 
+def box_integral(grid: Grid, phys: Physics, g, x0, y0, half=BOX_HALF):
+    """Integral of the cell-wise constant field g over the box
+    [x0 - half, x0 + half] x [y0 - half, y0 + half] clipped to the domain:
+    sum over cells of g times the area of the cell inside the box."""
+    hx, hy = grid.lengths(phys)
+    xl = np.arange(grid.nx) * hx
+    yl = np.arange(grid.ny) * hy
+    ox = np.clip(np.minimum(xl + hx, x0 + half) - np.maximum(xl, x0 - half), 0.0, None)
+    oy = np.clip(np.minimum(yl + hy, y0 + half) - np.maximum(yl, y0 - half), 0.0, None)
+    return float(np.sum(g * oy[:, None] * ox[None, :]))
+
+
 def qoi(grid: Grid, phys: Physics, f: Fields, c):
-    """[Q_S, salt mass, toe, c(x3), c(x9), c(x15)]:
+    """[Q_S, salt mass, toe, c(x3), c(x9), c(x15), Q_FW, Q_1..Q_15]:
     Q_S = int c rho dx (Eq. integral_s), salt mass = int phi rho c dx (the
-    conserved quantity of Eq. 2), toe = int c (Lx - x) dx, and c at the three
-    observation points."""
+    conserved quantity of Eq. 2), toe = int c (Lx - x) dx, c at the three
+    observation points, Q_FW = area where c <= 0.012178 (Eq. integral_fw),
+    Q_i = int over the box of half-width 0.1 around point i of c rho dx
+    (Eq. integral_box, points of Eq. 12points), with c constant per cell."""
     hx, hy = grid.lengths(phys)
     V = hx * hy
     rho = phys.rho0 + (phys.rho1 - phys.rho0) * c
@@ -338,6 +393,8 @@ def qoi(grid: Grid, phys: Physics, f: Fields, c):
     out = [np.sum(c * rho) * V, np.sum(f.phi * rho * c) * V,
            np.sum(c * (phys.Lx - x)[None, :]) * V]
     out += [point_value(grid, phys, c, px, py) for px, py in OBS_POINTS]
+    out.append(float(np.sum(c <= FRESH_C)) * V)
+    out += [box_integral(grid, phys, c * rho, px, py) for px, py in POINTS15]
     return np.array(out)
 
 

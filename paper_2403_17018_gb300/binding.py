@@ -17,7 +17,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "libhenry.so")
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "henry.h")
 
-NQ = 6
+NQ = 22
 QOI_NAMES = ("Q_S", "salt_mass", "toe", "c_x3", "c_x9", "c_x15")
 PREC_FP64 = 0
 PREC_FP32_MG = 1
@@ -44,7 +44,8 @@ class HenryConfig(ctypes.Structure):
                 ("vcycles", ctypes.c_int), ("guess_extrapolation", ctypes.c_int),
                 ("newton_stag_tol", ctypes.c_double), ("mg_fusion", ctypes.c_int),
                 ("mg_cluster_cells", ctypes.c_int), ("mg_small_cells", ctypes.c_int),
-                ("jac_lag", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("jac_lag", ctypes.c_int), ("field_model", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}

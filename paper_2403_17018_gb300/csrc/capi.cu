@@ -90,7 +90,8 @@ int validate(const henry_config* c) {
       !(c->phi0 > 0) || !(c->D >= 0))
     return fail(HENRY_E_INVALID, "non-positive physical parameter");
   if (c->newton_maxit < 0 || c->nu1 < 0 || c->nu2 < 0 || c->vcycles < 1 || c->mg_cluster_cells < 0 ||
-      c->mg_small_cells < 0 || c->mg_small_cells > 512 || c->jac_lag < 0)
+      c->mg_small_cells < 0 || c->mg_small_cells > 512 || c->jac_lag < 0 ||
+      c->field_model < 0 || c->field_model > 1 || (c->field_model == 1 && c->n_xi != 3))
     return fail(HENRY_E_INVALID, "bad solver parameter");
   for (int l = 0; l < c->nlevels; ++l) {
     std::vector<henry::Geom> g;
@@ -138,6 +139,7 @@ int henry_default_config(henry_config* c) {
   c->mg_cluster_cells = 0;
   c->mg_small_cells = 512;
   c->jac_lag = 0;
+  c->field_model = 0;
   return HENRY_OK;
 }
 
@@ -255,6 +257,8 @@ int henry_adjoint(henry_ctx* ctx, int level, const double* xi, const double* log
   if (level < 0 || level >= ctx->cfg.nlevels) return fail(HENRY_E_INVALID, "bad level");
   if (B < 0) return fail(HENRY_E_INVALID, "B < 0");
   if (qoi_id != 0 && qoi_id != 2) return fail(HENRY_E_INVALID, "qoi_id must be 0 (Q_S) or 2 (toe)");
+  if (ctx->cfg.field_model != 0)
+    return fail(HENRY_E_INVALID, "the adjoint covers field_model 0 only");
   if (B == 0) return HENRY_OK;
   if (!xi || !q || !dq_dxi || !status) return fail(HENRY_E_INVALID, "xi, q, dq_dxi, status required");
   CKR(cudaSetDevice(ctx->device));

@@ -6,7 +6,7 @@
 
 namespace henry {
 
-constexpr int kNQ = 6;
+constexpr int kNQ = 22;
 constexpr int kStatusMaxit = 1;
 constexpr int kStatusNonfinite = 2;
 constexpr int kStatusBadInput = 4;

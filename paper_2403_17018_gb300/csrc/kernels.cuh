@@ -66,7 +66,7 @@ __device__ __forceinline__ void store_operator(T* __restrict__ Jb, int ncell, co
 
 // Random fields at cell centres (workload stand-in for the paper's Eq.
 // poro_2levels; see henry.h for the formulas) and the inflow per row.
-__global__ void k_fields(unsigned long long* ctr, Phys P, Geom G, int B, int n_xi,
+__global__ void k_fields(unsigned long long* ctr, Phys P, Geom G, int B, int n_xi, int model,
                          const double* __restrict__ xi, const double* __restrict__ logk,
                          double* __restrict__ phi, double* __restrict__ K, double* __restrict__ qin,
                          int* __restrict__ status) {
@@ -80,6 +80,31 @@ __global__ void k_fields(unsigned long long* ctr, Phys P, Geom G, int B, int n_x
   const double x = (i + 0.5) * G.hx, y = (j + 0.5) * G.hy;
   const double* z = xi + (int64_t)b * n_xi;
   const double pi = 3.14159265358979323846;
+  if (model == 1) {
+    // Eq. poro_2levels in the paper's frame y_p = y - Ly: two layers split
+    // at y_p = -0.8, a smooth and a high-frequency (64 pi x, 32 pi y) factor;
+    // K from Eq. e_perm_Kozeny_Carman with kappa_KC = K0 (1 - phi0^2) / phi0^3
+    // (the mean porosity gives K0); q_in base of Eq. e_recharge_of_param
+    // (its time factor is applied per step by k_begin_step)
+    const double yp = y - P.Ly;
+    const double c0 = yp < -0.8 ? 1.2 * (1.0 + 0.2 * z[0]) : 1.0;
+    const double c1 = 1.0 + 0.15 * (z[1] * cos(pi * x / 2) - z[1] * sin(2 * pi * yp) +
+                                    z[0] * cos(2 * pi * x));
+    const double c2 = 1.0 + 0.2 * (z[0] * sin(64 * pi * x) + z[1] * sin(32 * pi * yp));
+    const double ph = P.phi0 * c0 * c1 * c2;
+    const double kappa = P.K0 * (1.0 - P.phi0 * P.phi0) / (P.phi0 * P.phi0 * P.phi0);
+    double k = kappa * (ph * ph * ph) / (1.0 - ph * ph);
+    if (logk) k *= exp(logk[idx]);
+    phi[idx] = ph;
+    K[idx] = k;
+    if (i == 0) qin[(int64_t)b * G.ny + j] = P.q0 * (1.0 + 0.5 * z[2]);
+    if (cell == 0) {
+      bool ok = true;
+      for (int m = 0; m < n_xi; ++m) ok = ok && isfinite(z[m]);
+      status[b] = ok ? 0 : kStatusBadInput;
+    }
+    return;
+  }
   double a = 0.1 * z[0] * cos(0.5 * pi * x) * sin(pi * y);
   double e = 0.5 * z[1] * sin(0.5 * pi * x) * cos(pi * y);
   double qf = 1.0 + 0.1 * z[2];
@@ -163,11 +188,20 @@ __global__ void k_begin_step(unsigned long long* ctr, Geom G, int B, double* __r
                              double* __restrict__ c, double* __restrict__ p_prev,
                              double* __restrict__ c_old, const int* __restrict__ status,
                              int* __restrict__ active, int* __restrict__ it_step,
-                             const int* __restrict__ step, int extrapolate) {
+                             const int* __restrict__ step, int extrapolate,
+                             const double* __restrict__ qin0, double* __restrict__ qin,
+                             double tau) {
   HENRY_COUNT_LAUNCH(ctr);
   const int64_t n = (int64_t)B * G.ncell();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n) return;
+  if (qin0 && idx < (int64_t)B * G.ny) {
+    // Eq. e_recharge_of_param: inflow times (1 + sin(pi t / 40)), t in
+    // seconds at the new time level t^(n+1) of this implicit step
+    const double pi = 3.14159265358979323846;
+    const double t = (*step + 1) * tau;
+    qin[idx] = qin0[idx] * (1.0 + sin(pi * t / 40.0));
+  }
   const double cn = c[idx], pn = p[idx];
   if (extrapolate && *step > 1) {
     const double c2 = c_old[idx], p2 = p_prev[idx];
@@ -999,6 +1033,9 @@ __global__ void k_update(unsigned long long* ctr, Geom G, int B, const int* __re
 // ---------------------------------------------------------------------------
 // quantities of interest (section 4): one block per sample
 // ---------------------------------------------------------------------------
+constexpr double kFreshC = 0.012178;   // fresh-water threshold of Eq. integral_fw
+constexpr double kBoxHalf = 0.1;        // half-width of the boxes of Eq. integral_box
+
 __device__ __forceinline__ double bilinear(const Geom& G, const double* c, double x, double y) {
   const double fx = x / G.hx - 0.5, fy = y / G.hy - 0.5;
   int i0 = (int)floor(fx), j0 = (int)floor(fy);
@@ -1019,7 +1056,14 @@ k_qoi(unsigned long long* ctr, Phys P, Geom G, int B, const double* __restrict__
   const int b = blockIdx.x;
   const int ncell = G.ncell();
   const int64_t o = (int64_t)b * ncell;
-  double s0 = 0, s1 = 0, s2 = 0;
+  double s0 = 0, s1 = 0, s2 = 0, fw = 0;
+  double box[15];
+#pragma unroll
+  for (int m = 0; m < 15; ++m) box[m] = 0.0;
+  // box columns and rows of Eq. integral_box around the points of Eq.
+  // 12points (frame y in [0, 1]), half-width 0.1, clipped to the domain
+  const double bx[5] = {0.90, 1.15, 1.40, 1.65, 1.90};
+  const double by[3] = {0.05, 0.25, 0.50};
   for (int cell = threadIdx.x; cell < ncell; cell += blockDim.x) {
     const double cv = c[o + cell];
     const double rho = P.rho0 + P.drho * cv;
@@ -1028,6 +1072,18 @@ k_qoi(unsigned long long* ctr, Phys P, Geom G, int B, const double* __restrict__
     s0 += cv * rho;
     s1 += phi[o + cell] * rho * cv;
     s2 += cv * (P.Lx - x);
+    fw += cv <= kFreshC ? 1.0 : 0.0;
+    const double xl = i * G.hx, yl = j * G.hy;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const double oy = fmax(fmin(yl + G.hy, by[r] + kBoxHalf) - fmax(yl, by[r] - kBoxHalf), 0.0);
+      if (oy == 0.0) continue;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        const double ox = fmax(fmin(xl + G.hx, bx[k] + kBoxHalf) - fmax(xl, bx[k] - kBoxHalf), 0.0);
+        box[5 * r + k] += cv * rho * oy * ox;
+      }
+    }
     if (c_out) c_out[o + cell] = cv;
     if (p_out) p_out[o + cell] = p[o + cell] + P.rho0 * P.g * (P.Ly - (j + 0.5) * G.hy);
   }
@@ -1035,6 +1091,9 @@ k_qoi(unsigned long long* ctr, Phys P, Geom G, int B, const double* __restrict__
   s0 = block_sum(s0, sh);
   s1 = block_sum(s1, sh);
   s2 = block_sum(s2, sh);
+  fw = block_sum(fw, sh);
+#pragma unroll
+  for (int m = 0; m < 15; ++m) box[m] = block_sum(box[m], sh);
   if (threadIdx.x == 0) {
     double* qb = q + (int64_t)b * kNQ;
     qb[0] = s0 * V;
@@ -1043,6 +1102,9 @@ k_qoi(unsigned long long* ctr, Phys P, Geom G, int B, const double* __restrict__
     qb[3] = bilinear(G, c + o, 1.40, 0.05);
     qb[4] = bilinear(G, c + o, 1.65, 0.25);
     qb[5] = bilinear(G, c + o, 1.90, 0.50);
+    qb[6] = fw * V;
+#pragma unroll
+    for (int m = 0; m < 15; ++m) qb[7 + m] = box[m];
   }
 }
 

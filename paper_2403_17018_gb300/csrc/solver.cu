@@ -187,6 +187,7 @@ int Solver::ensure(int B, cudaStream_t s) {
   const size_t o_pprev = take((size_t)F.ncell() * Bz * 8);
   const size_t o_step = take(8);
   const size_t o_qin = take((size_t)F.ny * Bz * 8);
+  const size_t o_qin0 = take((size_t)F.ny * Bz * 8);
   const size_t o_part = take((size_t)nchunk_ * Bz * 8);
   const size_t o_res0 = take(Bz * 8);
   const size_t o_resl = take(Bz * 8);
@@ -223,6 +224,7 @@ int Solver::ensure(int B, cudaStream_t s) {
   p_prev_ = (double*)(a + o_pprev);
   step_ = (int*)(a + o_step);
   qin_ = (double*)(a + o_qin);
+  qin0_ = (double*)(a + o_qin0);
   partial_ = (double*)(a + o_part);
   res0_ = (double*)(a + o_res0);
   res_last_ = (double*)(a + o_resl);
@@ -433,7 +435,7 @@ int Solver::step_graph(int B, cudaStream_t s) {
     MGLevel& F = levels_.back();
     k_begin_step<<<grid1((int64_t)B * F.g.ncell()), kBlock, 0, cs>>>(
         counter_, F.g, B, F.p, F.c, p_prev_, c_old_, status_w_, active_, it_step_, step_,
-        cfg_.guess_extrapolation);
+        cfg_.guess_extrapolation, cfg_.field_model == 1 ? qin0_ : nullptr, qin_, tau_);
     enqueue_resjac_check<T>(B, cs, true);
     cudaStreamCaptureStatus st;
     cudaGraph_t cg;
@@ -471,8 +473,8 @@ int Solver::fields(const double* xi, const double* logk, int B, double* phi, dou
   int rc = ensure(B, s);
   if (rc) return rc;
   const Geom& G = levels_.back().g;
-  k_fields<<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(counter_, phys_, G, B, cfg_.n_xi, xi,
-                                                            logk, phi, K, qin, status_w_);
+  k_fields<<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(
+      counter_, phys_, G, B, cfg_.n_xi, cfg_.field_model, xi, logk, phi, K, qin, status_w_);
   CK(cudaGetLastError());
   return HENRY_OK;
 }
@@ -482,8 +484,11 @@ int Solver::setup_t(const double* xi, const double* logk, int B, cudaStream_t s)
   const int nl = (int)levels_.size();
   MGLevel& F = levels_.back();
   const Geom& G = F.g;
-  k_fields<<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(counter_, phys_, G, B, cfg_.n_xi, xi,
-                                                            logk, F.phi, F.K, qin_, status_w_);
+  // the paper's field model has a time-dependent inflow: its base goes to
+  // qin0_ and k_begin_step forms each step's inflow in qin_
+  k_fields<<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(
+      counter_, phys_, G, B, cfg_.n_xi, cfg_.field_model, xi, logk, F.phi, F.K,
+      cfg_.field_model == 1 ? qin0_ : qin_, status_w_);
   for (int k = nl - 1; k >= 1; --k)
     k_coarsen_fields<<<grid1((int64_t)B * levels_[k - 1].g.ncell()), kBlock, 0, s>>>(
         counter_, levels_[k].g, levels_[k - 1].g, B, levels_[k].phi, levels_[k].K,
@@ -507,7 +512,7 @@ int Solver::step_t(int B, cudaStream_t s) {
   const Geom& G = F.g;
   k_begin_step<<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(
       counter_, G, B, F.p, F.c, p_prev_, c_old_, status_w_, active_, it_step_, step_,
-      cfg_.guess_extrapolation);
+      cfg_.guess_extrapolation, cfg_.field_model == 1 ? qin0_ : nullptr, qin_, tau_);
   for (;;) {
     enqueue_resjac_check<T>(B, s, false);
     CK(cudaMemcpyAsync(n_active_host_, n_active_, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -105,6 +105,7 @@ class Solver {
   double* p_prev_ = nullptr;    // p of the previous step (initial-guess extrapolation)
   int* step_ = nullptr;         // completed steps of the current solve (device)
   double* qin_ = nullptr;
+  double* qin0_ = nullptr;     // inflow base of the paper field model (time factor per step)
   double* partial_ = nullptr;
   double* res0_ = nullptr;
   double* res_last_ = nullptr;

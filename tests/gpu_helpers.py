@@ -11,7 +11,8 @@ from paper_2403_17018_gb300.inputs import xi_batch
 
 def oracle_physics(cfg) -> H.Physics:
     return H.Physics(rho0=cfg.rho0, rho1=cfg.rho1, mu=cfg.mu, g=cfg.g, D=cfg.D, K0=cfg.K0,
-                     phi0=cfg.phi0, q0=cfg.q0, Lx=cfg.Lx, Ly=cfg.Ly)
+                     phi0=cfg.phi0, q0=cfg.q0, Lx=cfg.Lx, Ly=cfg.Ly,
+                     field_model=cfg.field_model)
 
 
 def oracle_grid(cfg, level) -> H.Grid:
@@ -30,7 +31,8 @@ def _oracle_solve_cached(key):
 def oracle_solve(cfg, level, xi):
     """(p, c, q) of the oracle for one sample (cached by value)."""
     ph = oracle_physics(cfg)
-    phys_t = (ph.rho0, ph.rho1, ph.mu, ph.g, ph.D, ph.K0, ph.phi0, ph.q0, ph.Lx, ph.Ly)
+    phys_t = (ph.rho0, ph.rho1, ph.mu, ph.g, ph.D, ph.K0, ph.phi0, ph.q0, ph.Lx, ph.Ly,
+              ph.field_model)
     key = (cfg.nx0, cfg.ny0, cfg.nt0, cfg.T, level, tuple(float(v) for v in xi), phys_t)
     return _oracle_solve_cached(key)
 

@@ -1,0 +1,74 @@
+"""The paper's own workload on the CUDA path (field_model 1): two-layer
+multiscale porosity (Eq. poro_2levels), Kozeny-Carman permeability (Eq.
+e_perm_Kozeny_Carman), periodic recharge (Eq. e_recharge_of_param), T = 6016 s,
+and the QoIs Q_FW (Eq. integral_fw) and Q_1..Q_15 (Eq. integral_box),
+against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import henry as H
+from paper_2403_17018_gb300 import binding as hb
+from paper_2403_17018_gb300.inputs import logk_perturbation
+
+from gpu_helpers import oracle_grid, oracle_physics, oracle_solve, tight_config, xi_cuda
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    hb.load()
+
+
+def test_paper_fields_match_oracle():
+    """phi, K (with and without a log-K perturbation) and the inflow base at
+    the cell centres of level 2, where sin(64 pi x) is resolved."""
+    cfg = hb.default_config(nlevels=3, field_model=1)
+    ctx = hb.Context(cfg)
+    xi = xi_cuda(2, 0, 4)
+    lk = torch.from_numpy(logk_perturbation(64, 128, 4)).cuda()
+    g, ph = oracle_grid(cfg, 2), oracle_physics(cfg)
+    for logk in (None, lk):
+        phi, K, qin = ctx.fields(2, xi, logk)
+        for b in range(4):
+            f = H.fields(g, ph, xi[b].cpu().numpy(), None if logk is None else lk[b].cpu().numpy())
+            assert np.allclose(phi[b].cpu().numpy(), f.phi, rtol=1e-14, atol=0)
+            assert np.allclose(K[b].cpu().numpy(), f.K, rtol=1e-13, atol=0)
+            assert np.allclose(qin[b].cpu().numpy(), f.qin, rtol=1e-15, atol=0)
+    assert float(phi.min()) < 0.25 and float(phi.max()) > 0.5      # multiscale, two layers
+
+
+@pytest.mark.parametrize("precision", [hb.PREC_FP64, hb.PREC_FP32_MG])
+def test_paper_workload_solve_matches_oracle(precision):
+    """Level 0 over the paper's horizon T = 6016 s in 94 steps of 64 s (the
+    recharge period is 80 s): c, p and all 22 QoIs against the oracle."""
+    cfg = tight_config(nlevels=1, field_model=1, T=6016.0, nt0=94, precision=precision)
+    ctx = hb.Context(cfg)
+    xi = xi_cuda(0, 3, 2)
+    out = ctx.solve(0, xi, want_c=True, want_p=True)
+    assert out["status"].cpu().numpy().tolist() == [0, 0]
+    V = (cfg.Lx / cfg.nx0) * (cfg.Ly / cfg.ny0)
+    for b in range(2):
+        p_o, c_o, q_o = oracle_solve(cfg, 0, xi[b].cpu().numpy())
+        c_g = out["c"][b].cpu().numpy()
+        assert np.max(np.abs(c_g - c_o)) <= 1e-9
+        assert np.max(np.abs(out["p"][b].cpu().numpy() - p_o)) <= 1e-9 * np.max(np.abs(p_o))
+        q_g = out["q"][b].cpu().numpy()
+        keep = np.arange(hb.NQ) != 6
+        assert np.allclose(q_g[keep], q_o[keep], rtol=1e-9, atol=1e-9)
+        # Q_FW counts cells with c <= 0.012178: only cells within the
+        # parity bound of the threshold may be decided differently
+        near = int(np.sum(np.abs(c_o - H.FRESH_C) <= 1e-9))
+        assert abs(q_g[6] - q_o[6]) <= near * V + 1e-12
+        assert q_o[6] > 0 and q_o[7:22].max() > 0
+
+
+def test_adjoint_rejects_the_paper_model():
+    ctx = hb.Context(hb.default_config(nlevels=1, field_model=1))
+    with pytest.raises(hb.HenryError):
+        ctx.adjoint(0, xi_cuda(0, 0, 2))
+    with pytest.raises(hb.HenryError):
+        hb.Context(hb.default_config(nlevels=1, field_model=1, n_xi=6))

@@ -255,7 +255,7 @@ def test_fp32_multigrid_matches_fp64_multigrid_on_identical_xi():
         assert out[prec]["status"].cpu().numpy().tolist() == [0] * 4
     dc = (out[hb.PREC_FP64]["c"] - out[hb.PREC_FP32_MG]["c"]).abs().max().item()
     assert dc <= 1e-9
-    dq = (out[hb.PREC_FP64]["q"][:, 3:] - out[hb.PREC_FP32_MG]["q"][:, 3:]).abs().max().item()
+    dq = (out[hb.PREC_FP64]["q"][:, 3:6] - out[hb.PREC_FP32_MG]["q"][:, 3:6]).abs().max().item()
     assert dq <= 1e-9
 
 

@@ -325,3 +325,72 @@ def test_num_levels_is_the_smallest_level_meeting_the_bias_bound(a, eps, E0):
     brute = next(L for L in range(200)
                  if sum(a * 2.0 ** -k for k in range(L + 1, L + 200)) <= eps * E0 / math.sqrt(2.0))
     assert M.num_levels(eps, E0, c1, alpha) == brute
+
+
+# ---------------------------------------------------------------------------
+# the paper's own workload: Eq. poro_2levels, Eq. e_perm_Kozeny_Carman,
+# Eq. e_recharge_of_param, Eqs. integral_fw and integral_box
+# ---------------------------------------------------------------------------
+def test_kozeny_carman_scaling_is_table_1s():
+    """Table 1 lists kappa_KC = 2.088415e-8 m^2 beside K0 = 1.020408e-9 and
+    phi0 = 0.35: the Kozeny-Carman law through the mean porosity gives K0."""
+    ph = H.Physics(field_model=1)
+    assert ph.kappa_kc == pytest.approx(2.088415e-8, rel=5e-7)
+
+
+def test_paper_porosity_layers_at_xi_zero():
+    """xi = 0: C1 = C2 = 1, so phi = 0.35 above y_p = -0.8 and 0.35 * 1.2 in
+    the lower layer (y < 0.2 in this frame), and K = K0 where phi = phi0."""
+    ph = H.Physics(field_model=1)
+    g = _grid(40, 20, 1, 1.0)
+    f = H.fields(g, ph, np.zeros(3))
+    _, y = H.cell_centres(g, ph)
+    low = y < 0.2
+    assert np.allclose(f.phi[low], 0.42, rtol=1e-15) and np.allclose(f.phi[~low], 0.35, rtol=1e-15)
+    assert np.allclose(f.K[~low], ph.K0, rtol=1e-14)
+    assert np.allclose(f.qin, ph.q0, rtol=1e-15)
+    f3 = H.fields(g, ph, np.array([0.0, 0.0, 1.0]))
+    assert np.allclose(f3.qin, 1.5 * ph.q0, rtol=1e-15)
+
+
+def test_box_integrals_and_fresh_water_area_of_known_fields():
+    """c = 1: Q_i = rho1 |Delta_i in D| (0.2 x 0.15 for the five boxes cut
+    by y = 0, 0.04 otherwise), Q_FW = 0. c = 1 above y = 0.5 only: the boxes
+    around y_p = -0.5 are half full, the others empty, Q_FW = 1. c = 1 left
+    of x = 1 only: the boxes at x = 0.9 are full, at x = 1.15 empty."""
+    ph = H.Physics(field_model=1)
+    g = _grid(64, 32, 1, 1.0)
+    f = H.fields(g, ph, np.zeros(3))
+    x, y = H.cell_centres(g, ph)
+    X, Y = np.meshgrid(x, y)
+    q = H.qoi(g, ph, f, np.ones((32, 64)))
+    area = np.array([0.03] * 5 + [0.04] * 10)
+    assert np.allclose(q[7:22], ph.rho1 * area, rtol=1e-13) and q[6] == 0.0
+    q = H.qoi(g, ph, f, (Y > 0.5).astype(float))
+    assert np.allclose(q[7:17], 0.0) and np.allclose(q[17:22], ph.rho1 * 0.02, rtol=1e-13)
+    assert q[6] == pytest.approx(1.0, rel=1e-14)
+    q = H.qoi(g, ph, f, (X < 1.0).astype(float))
+    assert np.allclose(q[[7, 12, 17]], ph.rho1 * area[[0, 5, 10]], rtol=1e-13)
+    assert np.allclose(q[[8, 13, 18]], 0.0)
+    # threshold of Eq. integral_fw: c <= 0.012178 counts as fresh water
+    assert H.qoi(g, ph, f, np.full((32, 64), 0.012178))[6] == pytest.approx(2.0, rel=1e-14)
+    assert H.qoi(g, ph, f, np.full((32, 64), 0.0122))[6] == 0.0
+
+
+def test_recharge_enters_at_the_new_time_level():
+    """With rho1 = rho0 the fluid is incompressible and decoupled from c, so
+    after every implicit step the outflow through the seaward side equals
+    the inflow of that step: rho0 Ly q0 (1 + 0.5 xi3)(1 + sin(pi t^(n+1) / 40))
+    (Eq. e_recharge_of_param at the end of the step, as implicit Euler
+    takes boundary data)."""
+    ph = H.Physics(field_model=1, rho1=1000.0)
+    g = _grid(16, 8, 5, 5 * 13.0)
+    xi = np.array([0.3, -0.4, 0.6])
+    r = H.solve(g, ph, xi, keep_states=True)
+    f = r["fields"]
+    for n in range(1, 6):
+        p, c = r["states"][n]
+        F = H.face_fluxes(g, ph, f, p, c)
+        out = np.sum(F["mass_right"])
+        want = ph.rho0 * ph.Ly * ph.q0 * (1 + 0.5 * xi[2]) * (1 + math.sin(math.pi * n * 13.0 / 40))
+        assert out == pytest.approx(want, rel=1e-10)
