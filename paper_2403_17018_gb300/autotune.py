@@ -56,7 +56,8 @@ def best_schedule(level, precision, batch, gpu=None, nx0=32, ny0=16, path=CACHE)
     return load_cache(path).get(_key(gpu, level, precision, batch, nx0, ny0))
 
 
-def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2), log=None, n_xi=3):
+def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2), log=None, n_xi=3,
+               cfg_extra=None):
     """Time every candidate schedule on about `steps` steps of level `level`
     at the level's own time step (steps=None: the whole 43200 s horizon,
     whose early steps need more iterations than the later ones);
@@ -67,13 +68,18 @@ def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2),
     from paper_2403_17018_gb300.inputs import xi_batch
     prec = hb.PREC_FP64 if precision == "fp64" else hb.PREC_FP32_MG
     f = 1 << level
-    k = 24 if steps is None else min(24, max(1, steps // f))
+    extra = dict(cfg_extra or {})
+    nt_full = extra.pop("nt0", 24)
+    T_full = extra.pop("T", 43200.0)
+    tau0 = T_full / nt_full                  # level-0 step of the workload
+    k = nt_full if steps is None else min(nt_full, max(1, steps // f))
     xi = torch.from_numpy(xi_batch(level, 0, batch, n_xi=n_xi)).cuda()
     table = []
 
     def timed(vc, n1, n2, sc, lag, split):
         cfg = hb.default_config(nlevels=level + 1, precision=prec, vcycles=vc, nu1=n1, nu2=n2,
-                                mg_small_cells=sc, jac_lag=lag, nt0=k, T=1800.0 * k, n_xi=n_xi)
+                                mg_small_cells=sc, jac_lag=lag, nt0=k, T=tau0 * k, n_xi=n_xi,
+                                **extra)
         ctx = hb.Context(cfg)
         sub = batch // split
         parts = [xi[i * sub:(i + 1) * sub].contiguous() for i in range(split)]

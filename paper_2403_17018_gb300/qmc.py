@@ -121,17 +121,24 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=600)
     ap.add_argument("--precision", choices=["fp64", "fp32mg"], default="fp32mg")
     ap.add_argument("--threshold", type=float, nargs="*", default=[0.5])
+    ap.add_argument("--paper-workload", action="store_true",
+                    help="field_model 1, T = 6016 s in 94 steps on level 0 (the paper's setting)")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     import __graft_entry__
     __graft_entry__.build()
     from paper_2403_17018_gb300 import binding as hb
+    extra = {"field_model": 1, "T": 6016.0, "nt0": 94} if a.paper_workload else {}
+    if a.paper_workload:
+        a.n_xi = 3
     cfg = hb.default_config(nlevels=a.level + 1, n_xi=a.n_xi,
-                            precision=hb.PREC_FP64 if a.precision == "fp64" else hb.PREC_FP32_MG)
+                            precision=hb.PREC_FP64 if a.precision == "fp64" else hb.PREC_FP32_MG,
+                            **extra)
     ctx = hb.Context(cfg)
     res = run(ctx, a.level, a.samples, n_xi=a.n_xi, batch=a.batch, replicates=a.replicates,
               thresholds=a.threshold, log=lambda d: print(json.dumps(d), flush=True))
     summary = {"level": a.level, "samples": a.samples, "replicates": a.replicates,
+               "paper_workload": a.paper_workload,
                "precision": a.precision, "mean": res["mean"].tolist(),
                "std_error": res["std_error"].tolist(), "quantile_probs": res["quantile_probs"],
                "quantiles": res["quantiles"].tolist(),
