@@ -125,7 +125,14 @@ typedef struct henry_config {
                            recharge q0 (1 + 0.5 xi3)(1 + sin(pi t / 40)) taken
                            at the end of each step (Eq. e_recharge_of_param);
                            needs n_xi = 3; no adjoint */
-  int reserved[1];
+  int krylov_iters;     /* 0 (default): each defect-correction iteration
+                           applies `vcycles` V-cycles. k > 0: it runs k
+                           iterations of BiCGStab on the finest-level
+                           system instead, right-preconditioned by one
+                           V-cycle per application (two per iteration).
+                           Use k >= 2: with k = 1 some samples of the
+                           smooth field model broke down (non-finite
+                           residual, reported in status) */
 } henry_config;
 
 typedef struct henry_ctx henry_ctx; /* opaque: owns device workspaces */
@@ -307,12 +314,15 @@ int henry_level_info(const henry_ctx* ctx, int level, int* nx, int* ny, int* nt,
  * (role 0: fine solves and level-l halves of pairs; role 1: the level-(l-1)
  * halves of pairs, addressed by their own level l-1) for multigrid level
  * mg_level (0 = coarsest). what: 0 J [B][24][ncell] (colour-split planes:
- * inverse diagonal block, W, E, S, N blocks, diagonal block),
+ * inverse diagonal block, W, E, S, N blocks row-scaled by it, diagonal
+ * block),
  * 1 b, 2 x ([B][2][ncell], colour-split), 3 p, 4 c, 5 phi, 6 K ([B][ncell],
  * natural), 7..10 face constants tx, dx, ty, dy, 11..12 face fluxes of the
  * linearisation point qx (east faces; the right side in the last column),
- * qy (north faces). Element size is 4 bytes
- * for J, b, x with FP32 multigrid, else 8. Copies min(bytes, size) bytes
+ * qy (north faces), 13 the BiCGStab scalars of the last defect correction
+ * ([B][8] FP64: rho, alpha, omega, beta, then unused; only with
+ * krylov_iters > 0). Element size is 4 bytes for J, b, x with FP32
+ * multigrid, else 8. Copies min(bytes, size) bytes
  * to the device or host pointer dst and synchronises the device.
  * Errors: HENRY_E_INVALID if the solver does not exist yet or an index is
  * out of range. */

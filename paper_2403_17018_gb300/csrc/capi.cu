@@ -91,7 +91,8 @@ int validate(const henry_config* c) {
     return fail(HENRY_E_INVALID, "non-positive physical parameter");
   if (c->newton_maxit < 0 || c->nu1 < 0 || c->nu2 < 0 || c->vcycles < 1 || c->mg_cluster_cells < 0 ||
       c->mg_small_cells < 0 || c->mg_small_cells > 512 || c->jac_lag < 0 ||
-      c->field_model < 0 || c->field_model > 1 || (c->field_model == 1 && c->n_xi != 3))
+      c->field_model < 0 || c->field_model > 1 || (c->field_model == 1 && c->n_xi != 3) ||
+      c->krylov_iters < 0 || c->krylov_iters > 64)
     return fail(HENRY_E_INVALID, "bad solver parameter");
   for (int l = 0; l < c->nlevels; ++l) {
     std::vector<henry::Geom> g;
@@ -140,6 +141,7 @@ int henry_default_config(henry_config* c) {
   c->mg_small_cells = 512;
   c->jac_lag = 0;
   c->field_model = 0;
+  c->krylov_iters = 0;
   return HENRY_OK;
 }
 

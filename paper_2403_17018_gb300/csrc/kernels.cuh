@@ -1195,6 +1195,188 @@ k_vcycle_cluster(unsigned long long* ctr, SmallMG<T> M, int B, const int* __rest
 }
 
 // ---------------------------------------------------------------------------
+// BiCGStab on the row-scaled finest-level system At x = bt, right-
+// preconditioned by one multigrid V-cycle (van der Vorst's algorithm; the
+// paper's linear solver is a Krylov method preconditioned by geometric
+// multigrid, section 2.3). Vectors are [B][2][ncell] in the multigrid type
+// and colour-split layout; per-sample scalars in S[B][kKryS] (FP64):
+//   0 rho, 1 alpha, 2 omega, 3 beta, 4..6 dot products.
+// Samples that are inactive are skipped by every kernel.
+// ---------------------------------------------------------------------------
+constexpr int kKryS = 8;
+
+// (At y)_P = y_P + sum_Q At_PQ y_Q at cell (i, j).
+template <typename T>
+__device__ __forceinline__ void scaled_apply_cell(const Geom& G, int i, int j,
+                                                  const T* __restrict__ Jb,
+                                                  const T* __restrict__ y, T& ap, T& ac) {
+  const int ncell = G.ncell(), half = G.half(), nx = G.nx;
+  const int cs = cs_pos(i, j, nx, half);
+  const T* Jc = Jb + cs;
+  const T* yp = y;
+  const T* yc = y + ncell;
+  ap = yp[cs];
+  ac = yc[cs];
+  T vp, vc;
+  if (i > 0) {
+    const int q = cs_pos(i - 1, j, nx, half);
+    vp = yp[q]; vc = yc[q];
+    ap += Jc[4 * ncell] * vp; ap += Jc[5 * ncell] * vc;
+    ac += Jc[6 * ncell] * vp; ac += Jc[7 * ncell] * vc;
+  }
+  if (i < nx - 1) {
+    const int q = cs_pos(i + 1, j, nx, half);
+    vp = yp[q]; vc = yc[q];
+    ap += Jc[8 * ncell] * vp; ap += Jc[9 * ncell] * vc;
+    ac += Jc[10 * ncell] * vp; ac += Jc[11 * ncell] * vc;
+  }
+  if (j > 0) {
+    const int q = cs_pos(i, j - 1, nx, half);
+    vp = yp[q]; vc = yc[q];
+    ap += Jc[12 * ncell] * vp; ap += Jc[13 * ncell] * vc;
+    ac += Jc[14 * ncell] * vp; ac += Jc[15 * ncell] * vc;
+  }
+  if (j < G.ny - 1) {
+    const int q = cs_pos(i, j + 1, nx, half);
+    vp = yp[q]; vc = yc[q];
+    ap += Jc[16 * ncell] * vp; ap += Jc[17 * ncell] * vc;
+    ac += Jc[18 * ncell] * vp; ac += Jc[19 * ncell] * vc;
+  }
+}
+
+// out = At y, one thread per cell of every active sample.
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+k_kry_matvec(unsigned long long* ctr, Geom G, int B, const int* __restrict__ active,
+             const T* __restrict__ J, const T* __restrict__ y, T* __restrict__ out) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int ncell = G.ncell();
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)B * ncell) return;
+  const int b = (int)(idx / ncell);
+  if (!active[b]) return;
+  const int cell = (int)(idx - (int64_t)b * ncell);
+  const int j = cell / G.nx, i = cell - j * G.nx;
+  const int64_t o = (int64_t)b * 2 * ncell;
+  T ap, ac;
+  scaled_apply_cell<T>(G, i, j, J + (int64_t)b * kJP * ncell, y + o, ap, ac);
+  const int cs = cs_pos(i, j, G.nx, G.half());
+  out[o + cs] = ap;
+  out[o + ncell + cs] = ac;
+}
+
+// Partial sums of up to two dot products (a1, b1) and (a2, b2) over one
+// sample's 2 ncell entries, in FP64: grid (chunks, B), each block sums
+// kBlock * 4 consecutive entries; partial[k][b][chunk].
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+k_kry_dot(unsigned long long* ctr, int n2, int B, const int* __restrict__ active,
+          const T* __restrict__ a1, const T* __restrict__ b1, const T* __restrict__ a2,
+          const T* __restrict__ b2, double* __restrict__ partial) {
+  HENRY_COUNT_LAUNCH(ctr);
+  __shared__ double sh[kBlock / 32];
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  const int64_t o = (int64_t)b * n2;
+  const int base = blockIdx.x * kBlock * 4;
+  double s1 = 0.0, s2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int e = base + k * kBlock + threadIdx.x;
+    if (e < n2) {
+      s1 += (double)a1[o + e] * (double)b1[o + e];
+      if (a2) s2 += (double)a2[o + e] * (double)b2[o + e];
+    }
+  }
+  s1 = block_sum(s1, sh);
+  if (a2) s2 = block_sum(s2, sh);
+  if (threadIdx.x == 0) {
+    partial[(int64_t)b * gridDim.x + blockIdx.x] = s1;
+    if (a2) partial[((int64_t)B + b) * gridDim.x + blockIdx.x] = s2;
+  }
+}
+
+// Per-sample BiCGStab scalars, one thread per sample (fixed-order sums of
+// the dot partials). stage 0: rho_new = (rh, r), beta = (rho_new / rho)
+// (alpha / omega), rho = rho_new; stage 1: alpha = rho / (rh, v); stage 2:
+// omega = (t, s) / (t, t). A zero denominator gives a zero coefficient (the
+// outer defect correction, whose residual is the FP64 one, carries on).
+__global__ void k_kry_scalars(unsigned long long* ctr, int B, int nchunk, int stage,
+                              const int* __restrict__ active, const double* __restrict__ partial,
+                              double* __restrict__ S) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B || !active[b]) return;
+  double d1 = 0.0, d2 = 0.0;
+  for (int k = 0; k < nchunk; ++k) {
+    d1 += partial[(int64_t)b * nchunk + k];
+    if (stage == 2) d2 += partial[((int64_t)B + b) * nchunk + k];
+  }
+  double* s = S + (int64_t)b * kKryS;
+  if (stage == 0) {
+    const double den = s[0] * s[2];
+    s[3] = den != 0.0 ? (d1 / s[0]) * (s[1] / s[2]) : 0.0;
+    s[0] = d1;
+  } else if (stage == 1) {
+    s[1] = d1 != 0.0 ? s[0] / d1 : 0.0;
+  } else {
+    s[2] = d2 != 0.0 ? d1 / d2 : 0.0;
+  }
+}
+
+// Vector updates of one BiCGStab iteration, one thread per entry of every
+// active sample. op 0 (start): r = rh = bt, p = v = xk = 0, scalars 1.
+// op 1: p = r + beta (p - omega v); b = p, x = 0 (preconditioner input).
+// op 2: xk += alpha y (y = x); r -= alpha v; b = r, x = 0.
+// op 3: xk += omega z (z = x); r -= omega t.
+// op 4: x = xk (the correction handed to the state update).
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+k_kry_update(unsigned long long* ctr, int n2, int B, int op, const int* __restrict__ active,
+             double* __restrict__ S, T* __restrict__ r, T* __restrict__ rh, T* __restrict__ p,
+             T* __restrict__ v, T* __restrict__ t, T* __restrict__ xk, T* __restrict__ bvec,
+             T* __restrict__ xvec) {
+  HENRY_COUNT_LAUNCH(ctr);
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)B * n2) return;
+  const int b = (int)(idx / n2);
+  if (!active[b]) return;
+  const double* s = S + (int64_t)b * kKryS;
+  switch (op) {
+    case 0: {
+      const T bt = bvec[idx];
+      r[idx] = bt; rh[idx] = bt; p[idx] = (T)0; v[idx] = (T)0; xk[idx] = (T)0;
+      if (idx - (int64_t)b * n2 == 0) {
+        double* w = S + (int64_t)b * kKryS;
+        w[0] = w[1] = w[2] = 1.0;
+      }
+      break;
+    }
+    case 1: {
+      const T beta = (T)s[3], omega = (T)s[2];
+      const T pn = r[idx] + beta * (p[idx] - omega * v[idx]);
+      p[idx] = pn; bvec[idx] = pn; xvec[idx] = (T)0;
+      break;
+    }
+    case 2: {
+      const T alpha = (T)s[1];
+      xk[idx] += alpha * xvec[idx];
+      const T sn = r[idx] - alpha * v[idx];
+      r[idx] = sn; bvec[idx] = sn; xvec[idx] = (T)0;
+      break;
+    }
+    case 3: {
+      const T omega = (T)s[2];
+      xk[idx] += omega * xvec[idx];
+      r[idx] -= omega * t[idx];
+      break;
+    }
+    default:
+      xvec[idx] = xk[idx];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // discrete adjoint through the implicit Euler steps (section 2.3 time
 // discretisation): with R^n(u^n, u^{n-1}) = 0 and Q = Q(u^r),
 //   J_r^T lam_r = dQ/du^r,   J_n^T lam_n = -(dR^{n+1}/du^n)^T lam_{n+1},

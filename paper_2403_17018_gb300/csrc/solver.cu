@@ -114,9 +114,16 @@ unsigned long long Solver::launches() const {
 }
 
 int Solver::debug_copy(int mg_level, int what, void* dst, int64_t bytes) const {
-  if (mg_level < 0 || mg_level >= (int)levels_.size() || what < 0 || what > 12 || !dst || bytes < 0)
+  if (mg_level < 0 || mg_level >= (int)levels_.size() || what < 0 || what > 13 || !dst || bytes < 0)
     return HENRY_E_INVALID;
   if (cap_ == 0) return HENRY_E_INVALID;
+  if (what == 13) {   // per-sample BiCGStab scalars [cap][8] (krylov_iters > 0)
+    if (!cfg_.krylov_iters) return HENRY_E_INVALID;
+    const size_t nb = (size_t)bytes < (size_t)cap_ * kKryS * 8 ? (size_t)bytes : (size_t)cap_ * kKryS * 8;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(dst, kry_S_, nb, cudaMemcpyDefault));
+    return HENRY_OK;
+  }
   const MGLevel& L = levels_[mg_level];
   const size_t n = (size_t)L.g.ncell() * cap_;
   const void* src[13] = {L.J, L.b, L.x, L.p, L.c, L.phi, L.K, L.tx, L.dx, L.ty, L.dy, L.qx, L.qy};
@@ -200,6 +207,15 @@ int Solver::ensure(int B, cudaStream_t s) {
   const size_t o_it = take(Bz * 4);
   const size_t o_na = take(4);
   const size_t o_acc = take(8);
+  // BiCGStab vectors r, rh, p, v, t, xk ([B][2][ncell] of the finest level),
+  // per-sample scalars and dot partials (only with krylov_iters > 0)
+  const size_t n2 = (size_t)2 * F.ncell();
+  const size_t kvec = cfg_.krylov_iters ? n2 * Bz * tsize_ : 0;
+  size_t o_kv[6];
+  for (int k = 0; k < 6; ++k) o_kv[k] = take(kvec);
+  kry_nchunk_ = (int)((n2 + kBlock * 4 - 1) / (kBlock * 4));
+  const size_t o_ks = take(cfg_.krylov_iters ? Bz * kKryS * 8 : 0);
+  const size_t o_kp = take(cfg_.krylov_iters ? 2 * Bz * kry_nchunk_ * 8 : 0);
   const size_t o_ctr = take(8);
   CK(cudaMalloc(&arena_, off));
   CK(cudaHostAlloc((void**)&n_active_host_, sizeof(int), cudaHostAllocDefault));
@@ -237,6 +253,9 @@ int Solver::ensure(int B, cudaStream_t s) {
   iters_w_ = (int*)(a + o_it);
   n_active_ = (int*)(a + o_na);
   check_acc_ = (unsigned int*)(a + o_acc);
+  for (int k = 0; k < 6; ++k) kry_v_[k] = a + o_kv[k];
+  kry_S_ = (double*)(a + o_ks);
+  kry_part_ = (double*)(a + o_kp);
   counter_ = (unsigned long long*)(a + o_ctr);
   CK(cudaMemset(arena_, 0, off));
   CK(cudaMemcpy(counter_, &count, sizeof(count), cudaMemcpyHostToDevice));
@@ -363,6 +382,63 @@ void Solver::enqueue_vcycles(int B, cudaStream_t s) {
     for (int v = 0; v < cfg_.vcycles; ++v) enqueue_vcycle<T>(nl - 1, B, s);
 }
 
+// One V-cycle on the finest level's b and x (the BiCGStab preconditioner).
+template <typename T>
+void Solver::enqueue_precond(int B, cudaStream_t s) {
+  const int nl = (int)levels_.size();
+  if (ks_ == nl - 1 && nl > 1)
+    launch_small<T>(B, 1, s);
+  else if (kc_ == nl - 1 && nl > 1)
+    launch_cluster<T>(B, 1, s);
+  else
+    enqueue_vcycle<T>(nl - 1, B, s);
+}
+
+// krylov_iters iterations of BiCGStab on At x = bt (finest level), each
+// with two preconditioner applications; leaves the correction in x.
+template <typename T>
+void Solver::enqueue_bicgstab(int B, cudaStream_t s) {
+  MGLevel& F = levels_.back();
+  const Geom& G = F.g;
+  const int n2 = 2 * G.ncell();
+  const int gv = grid1((int64_t)B * n2);
+  T* r = (T*)kry_v_[0];
+  T* rh = (T*)kry_v_[1];
+  T* p = (T*)kry_v_[2];
+  T* v = (T*)kry_v_[3];
+  T* t = (T*)kry_v_[4];
+  T* xk = (T*)kry_v_[5];
+  T* b = (T*)F.b;
+  T* x = (T*)F.x;
+  const dim3 gd(kry_nchunk_, B);
+  const int gs = (B + kBlock - 1) / kBlock;
+  auto upd = [&](int op) {
+    k_kry_update<T><<<gv, kBlock, 0, s>>>(counter_, n2, B, op, active_, kry_S_, r, rh, p, v, t,
+                                          xk, b, x);
+  };
+  upd(0);
+  for (int it = 0; it < cfg_.krylov_iters; ++it) {
+    k_kry_dot<T><<<gd, kBlock, 0, s>>>(counter_, n2, B, active_, rh, r, (const T*)nullptr,
+                                       (const T*)nullptr, kry_part_);
+    k_kry_scalars<<<gs, kBlock, 0, s>>>(counter_, B, kry_nchunk_, 0, active_, kry_part_, kry_S_);
+    upd(1);                                            // p; b = p, x = 0
+    enqueue_precond<T>(B, s);                          // y = M p in x
+    k_kry_matvec<T><<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(
+        counter_, G, B, active_, (const T*)F.J, (const T*)x, v);
+    k_kry_dot<T><<<gd, kBlock, 0, s>>>(counter_, n2, B, active_, rh, v, (const T*)nullptr,
+                                       (const T*)nullptr, kry_part_);
+    k_kry_scalars<<<gs, kBlock, 0, s>>>(counter_, B, kry_nchunk_, 1, active_, kry_part_, kry_S_);
+    upd(2);                                            // xk += alpha y; s = r - alpha v
+    enqueue_precond<T>(B, s);                          // z = M s in x
+    k_kry_matvec<T><<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(
+        counter_, G, B, active_, (const T*)F.J, (const T*)x, t);
+    k_kry_dot<T><<<gd, kBlock, 0, s>>>(counter_, n2, B, active_, t, r, t, t, kry_part_);
+    k_kry_scalars<<<gs, kBlock, 0, s>>>(counter_, B, kry_nchunk_, 2, active_, kry_part_, kry_S_);
+    upd(3);                                            // xk += omega z; r -= omega t
+  }
+  upd(4);                                              // x = xk
+}
+
 // Multigrid operators at the current iterate, V-cycles, state update.
 template <typename T>
 void Solver::enqueue_iteration(int B, cudaStream_t s) {
@@ -376,7 +452,10 @@ void Solver::enqueue_iteration(int B, cudaStream_t s) {
   }
   enqueue_coarse_ops<T>(B, s, refresh);
   enqueue_lu<T>(B, s, refresh);
-  enqueue_vcycles<T>(B, s);
+  if (cfg_.krylov_iters)
+    enqueue_bicgstab<T>(B, s);
+  else
+    enqueue_vcycles<T>(B, s);
   MGLevel& F = levels_.back();
   k_update<T><<<grid1((int64_t)B * F.g.ncell()), kBlock, 0, s>>>(counter_, F.g, B, active_,
                                                                  (const T*)F.x, F.p, F.c);

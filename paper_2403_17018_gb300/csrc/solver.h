@@ -76,6 +76,8 @@ class Solver {
   template <typename T> void enqueue_coarse_ops(int B, cudaStream_t s, const int* refresh);
   template <typename T> void enqueue_lu(int B, cudaStream_t s, const int* refresh);
   template <typename T> void enqueue_vcycles(int B, cudaStream_t s);
+  template <typename T> void enqueue_precond(int B, cudaStream_t s);
+  template <typename T> void enqueue_bicgstab(int B, cudaStream_t s);
   template <typename T> void enqueue_iteration(int B, cudaStream_t s);
   template <typename T> void enqueue_vcycle(int k, int B, cudaStream_t s);
   template <typename T> void enqueue_resjac_check(int B, cudaStream_t s, bool set_cond);
@@ -117,6 +119,10 @@ class Solver {
   int* status_w_ = nullptr;
   int* iters_w_ = nullptr;
   int* n_active_ = nullptr;     // device
+  void* kry_v_[6] = {};           // BiCGStab vectors r, rh, p, v, t, xk (krylov_iters > 0)
+  double* kry_S_ = nullptr;       // per-sample BiCGStab scalars [B][kKryS]
+  double* kry_part_ = nullptr;    // dot-product partials [2][B][kry_nchunk_]
+  int kry_nchunk_ = 1;
   unsigned int* check_acc_ = nullptr;  // k_check's block count / active count (2 words)
   int* n_active_host_ = nullptr;  // pinned
   unsigned long long* counter_ = nullptr;  // device launch counter

@@ -387,3 +387,31 @@ def test_contexts_with_different_shared_memory_kernels_interleave():
     small.solve(1, xi_cuda(1, 0, 5))
     assert b["status"].cpu().numpy().tolist() == [0, 0, 0]
     assert torch.equal(a["q"], b["q"][:2])
+
+
+@pytest.mark.parametrize("precision", [hb.PREC_FP64, hb.PREC_FP32_MG])
+@pytest.mark.parametrize("kry", [1, 2])
+def test_bicgstab_preconditioned_by_multigrid_keeps_parity(precision, kry):
+    """krylov_iters > 0: each defect correction solves the finest-level
+    system with BiCGStab right-preconditioned by V-cycles instead of plain
+    V-cycles. The FP64 residual still decides convergence, so level-1 pairs
+    match the oracle; graph and host loops agree bit for bit, and a sample's
+    result does not depend on its batch (every scalar is per sample)."""
+    cfg = tight_config(nlevels=2, precision=precision, krylov_iters=kry)
+    ctx = hb.Context(cfg)
+    xi = xi_cuda(1, 2, 3)
+    qf, qc, cf, cc, st = ctx.sample_pairs(1, xi, want_c=True)
+    assert st.cpu().numpy().tolist() == [0, 0, 0]
+    for b in range(2):
+        _, c1, q1 = oracle_solve(cfg, 1, xi[b].cpu().numpy())
+        _, c0, _ = oracle_solve(cfg, 0, xi[b].cpu().numpy())
+        assert np.max(np.abs(cf[b].cpu().numpy() - c1)) <= C_TOL
+        assert np.max(np.abs(cc[b].cpu().numpy() - c0)) <= C_TOL
+        assert np.allclose(qf[b].cpu().numpy(), q1, rtol=1e-9, atol=1e-9)
+    full = ctx.solve(1, xi, want_c=True, want_iters=True)
+    part = ctx.solve(1, xi[1:].contiguous(), want_c=True, want_iters=True)
+    assert torch.equal(full["c"][1:], part["c"]) and torch.equal(full["iters"][1:], part["iters"])
+    host = hb.Context(tight_config(nlevels=2, precision=precision, krylov_iters=kry,
+                                   loop_mode=hb.LOOP_HOST)).solve(1, xi, want_c=True,
+                                                                  want_iters=True)
+    assert torch.equal(full["c"], host["c"]) and torch.equal(full["iters"], host["iters"])
