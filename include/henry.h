@@ -180,6 +180,15 @@ int henry_solve(henry_ctx* ctx, int level, const double* xi, const double* logk,
                 double* q, double* c_out, double* p_out, int* status, int* iters,
                 void* stream);
 
+/* henry_solve with the QoI time series (section 4, test A3: realisations
+ * and quantiles of Q_FW(t) and Q_S(t)): after steps every, 2 every, ..., of
+ * the r_l steps of the level, the HENRY_NQ QoIs of every sample.
+ *   q_series  device [B][r_l / every][HENRY_NQ] out (step k*every in slot k-1)
+ *   q         device [B][HENRY_NQ] out (at T);  status as henry_solve
+ * Errors: HENRY_E_INVALID (every < 1, NULL), HENRY_E_CUDA, HENRY_E_NOMEM. */
+int henry_solve_series(henry_ctx* ctx, int level, const double* xi, const double* logk, int B,
+                       int every, double* q_series, double* q, int* status, void* stream);
+
 /* MLMC level pair (Eq. A): the same xi drives a level-l solve and a
  * level-(l-1) solve. At level 0 only the fine solve runs and q_coarse,
  * c_coarse must be NULL.

@@ -83,6 +83,7 @@ def load():
         "henry_destroy": (None, [P]),
         "henry_solve": (I, [P, I, V, V, I, V, V, V, V, V, V]),
         "henry_sample_pairs": (I, [P, I, V, I, V, V, V, V, V, V]),
+        "henry_solve_series": (I, [P, I, V, V, I, I, V, V, V, V]),
         "mlmc_level_stats": (I, [P, I, V, V, I, V, ctypes.POINTER(LevelStats), V]),
         "mlmc_field_stats": (I, [P, I, V, V, I, V, V, V, V, V, V, V]),
         "mlmc_field_exceedance": (I, [P, I, V, I, V, D, V, V]),
@@ -218,6 +219,21 @@ class Context:
             _ptr(logk, torch.float64, (B, li.ny, li.nx), "logk"), B, _ptr(q), _ptr(c), _ptr(p),
             _ptr(st), _ptr(it), _stream(stream)))
         return {"q": q, "status": st, "c": c, "p": p, "iters": it}
+
+    def solve_series(self, level, xi, every, logk=None, stream=None):
+        """henry_solve_series: dict(series [B, nt/every, NQ], q [B, NQ], status [B])."""
+        import torch
+        B = xi.shape[0]
+        li = self.level_info(level)
+        dev = xi.device
+        series = torch.empty((B, li.nt // every, NQ), dtype=torch.float64, device=dev)
+        q = torch.empty((B, NQ), dtype=torch.float64, device=dev)
+        st = torch.empty((B,), dtype=torch.int32, device=dev)
+        _check(self.lib.henry_solve_series(
+            self._h, level, _ptr(xi, torch.float64, (B, self.cfg.n_xi), "xi"),
+            _ptr(logk, torch.float64, (B, li.ny, li.nx), "logk"), B, int(every), _ptr(series),
+            _ptr(q), _ptr(st), _stream(stream)))
+        return {"series": series, "q": q, "status": st}
 
     def sample_pairs(self, level, xi, want_c=False, stream=None):
         """henry_sample_pairs: (q_fine, q_coarse or None, c_fine, c_coarse, status)."""

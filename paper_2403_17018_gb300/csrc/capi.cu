@@ -211,6 +211,20 @@ int henry_solve(henry_ctx* ctx, int level, const double* xi, const double* logk,
                                         (cudaStream_t)stream);
 }
 
+int henry_solve_series(henry_ctx* ctx, int level, const double* xi, const double* logk, int B,
+                       int every, double* q_series, double* q, int* status, void* stream) {
+  if (!ctx) return fail(HENRY_E_INVALID, "ctx is NULL");
+  if (level < 0 || level >= ctx->cfg.nlevels) return fail(HENRY_E_INVALID, "bad level");
+  if (B < 0) return fail(HENRY_E_INVALID, "B < 0");
+  if (every < 1) return fail(HENRY_E_INVALID, "every must be >= 1");
+  if (B == 0) return HENRY_OK;
+  if (!xi || !q_series || !q || !status)
+    return fail(HENRY_E_INVALID, "xi, q_series, q and status are required");
+  CKR(cudaSetDevice(ctx->device));
+  return get_solver(ctx, level, 0)->run_series(xi, logk, B, every, q_series, q, status,
+                                               (cudaStream_t)stream);
+}
+
 int henry_sample_pairs(henry_ctx* ctx, int level, const double* xi, int B, double* q_fine,
                        double* q_coarse, double* c_fine, double* c_coarse, int* status,
                        void* stream) {

@@ -1050,7 +1050,7 @@ __device__ __forceinline__ double bilinear(const Geom& G, const double* c, doubl
 __global__ void __launch_bounds__(kBlock)
 k_qoi(unsigned long long* ctr, Phys P, Geom G, int B, const double* __restrict__ p,
       const double* __restrict__ c, const double* __restrict__ phi, double* __restrict__ q,
-      double* __restrict__ c_out, double* __restrict__ p_out) {
+      double* __restrict__ c_out, double* __restrict__ p_out, int qstride) {
   HENRY_COUNT_LAUNCH(ctr);
   __shared__ double sh[kBlock / 32];
   const int b = blockIdx.x;
@@ -1095,7 +1095,7 @@ k_qoi(unsigned long long* ctr, Phys P, Geom G, int B, const double* __restrict__
 #pragma unroll
   for (int m = 0; m < 15; ++m) box[m] = block_sum(box[m], sh);
   if (threadIdx.x == 0) {
-    double* qb = q + (int64_t)b * kNQ;
+    double* qb = q + (int64_t)b * qstride;   // [B][...][kNQ]: sample stride qstride
     qb[0] = s0 * V;
     qb[1] = s1 * V;
     qb[2] = s2 * V;

@@ -608,13 +608,20 @@ int Solver::run_t(const double* xi, const double* logk, int B, double* q, double
                   double* p_out, int* status, int* iters, int status_or, cudaStream_t s) {
   int rc = setup_t<T>(xi, logk, B, s);
   if (rc) return rc;
+  const int nout = series_every_ > 0 ? nt_ / series_every_ : 0;
   for (int n = 0; n < nt_; ++n) {
     rc = step_t<T>(B, s);
     if (rc) return rc;
+    if (series_ && (n + 1) % series_every_ == 0) {
+      MGLevel& F = levels_.back();
+      const int k = (n + 1) / series_every_ - 1;
+      k_qoi<<<B, kBlock, 0, s>>>(counter_, phys_, F.g, B, F.p, F.c, F.phi, series_ + k * kNQ,
+                                 nullptr, nullptr, nout * kNQ);
+    }
   }
   MGLevel& F = levels_.back();
   const Geom& G = F.g;
-  k_qoi<<<B, kBlock, 0, s>>>(counter_, phys_, G, B, F.p, F.c, F.phi, q, c_out, p_out);
+  k_qoi<<<B, kBlock, 0, s>>>(counter_, phys_, G, B, F.p, F.c, F.phi, q, c_out, p_out, kNQ);
   k_copy_int<<<grid1(B), kBlock, 0, s>>>(counter_, B, status_w_, status, status_or);
   if (iters) k_copy_int<<<grid1(B), kBlock, 0, s>>>(counter_, B, iters_w_, iters, 0);
   CK(cudaGetLastError());
@@ -683,6 +690,16 @@ int Solver::time_kernel(int which, int reps, cudaStream_t s, double* avg_ms, dou
   }
   *avg_ms = ms / reps;
   return HENRY_OK;
+}
+
+int Solver::run_series(const double* xi, const double* logk, int B, int every, double* series,
+                       double* q, int* status, cudaStream_t s) {
+  series_ = series;
+  series_every_ = every;
+  const int rc = run(xi, logk, B, q, nullptr, nullptr, status, nullptr, 0, s);
+  series_ = nullptr;
+  series_every_ = 0;
+  return rc;
 }
 
 int Solver::run(const double* xi, const double* logk, int B, double* q, double* c_out,
@@ -777,7 +794,7 @@ int Solver::adjoint_t(const double* xi, const double* logk, int B, int qoi, int 
     if (st % kc == 0) { if ((rc = save(ck(st / kc), true))) return rc; }
     else if (st == nt_) { if ((rc = save(ck(nck - 1), true))) return rc; }
   }
-  k_qoi<<<B, kBlock, 0, s>>>(counter_, phys_, G, B, F.p, F.c, F.phi, qtmp_, nullptr, nullptr);
+  k_qoi<<<B, kBlock, 0, s>>>(counter_, phys_, G, B, F.p, F.c, F.phi, qtmp_, nullptr, nullptr, kNQ);
   CK(cudaMemcpy2DAsync(q, sizeof(double), qtmp_ + qoi, kNQ * sizeof(double), sizeof(double), B,
                        cudaMemcpyDeviceToDevice, s));
   // seed and zero the sensitivities

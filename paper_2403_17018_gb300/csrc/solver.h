@@ -49,6 +49,10 @@ class Solver {
   // per-sample status into `status` instead of overwriting it.
   int run(const double* xi, const double* logk, int B, double* q, double* c_out, double* p_out,
           int* status, int* iters, int status_or, cudaStream_t s);
+  // run() that also stores the QoIs after steps every, 2 every, ...:
+  // series [B][nt / every][kNQ]
+  int run_series(const double* xi, const double* logk, int B, int every, double* series,
+                 double* q, int* status, cudaStream_t s);
   // Discrete adjoint of QoI `qoi` (0 Q_S, 2 toe); see henry_adjoint.
   int adjoint(const double* xi, const double* logk, int B, int qoi, int ckpt_every, double* q,
               double* dq_dxi, double* dq_dlogk, int* status, cudaStream_t s);
@@ -123,6 +127,8 @@ class Solver {
   double* kry_S_ = nullptr;       // per-sample BiCGStab scalars [B][kKryS]
   double* kry_part_ = nullptr;    // dot-product partials [2][B][kry_nchunk_]
   int kry_nchunk_ = 1;
+  double* series_ = nullptr;      // QoI time series output of run_series (else NULL)
+  int series_every_ = 0;
   unsigned int* check_acc_ = nullptr;  // k_check's block count / active count (2 words)
   int* n_active_host_ = nullptr;  // pinned
   unsigned long long* counter_ = nullptr;  // device launch counter

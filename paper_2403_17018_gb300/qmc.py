@@ -50,19 +50,22 @@ def sample_quantiles(values, probs):
 
 
 def run(ctx, level, n_samples, n_xi=3, batch=256, replicates=1, thresholds=(0.5,),
-        probs=QUANTILES, first=1, log=None):
+        probs=QUANTILES, first=1, log=None, series_every=0):
     """QMC on `level` with n_samples Halton points per replicate. Returns a
     dict: per-QoI mean (over replicates) and standard error (R > 1), the
     per-replicate means and variances, quantiles of every QoI over all
     valid samples, and per-cell mean, variance and exceedance probability
-    fields of c (numpy), plus timing and failed samples."""
+    fields of c (numpy), plus timing and failed samples. series_every = k > 0
+    also solves through henry_solve_series (without the c field statistics)
+    and returns the quantiles of every QoI after each k-th step (test A3:
+    "series_quantiles" [steps/k, probs, NQ], "series_steps")."""
     import torch
     from paper_2403_17018_gb300 import binding as hb
     from paper_2403_17018_gb300.inputs import xi_halton
     li = ctx.level_info(level)
     ncell = li.ny * li.nx
     dev = torch.device("cuda")
-    rep_means, rep_vars, all_q = [], [], []
+    rep_means, rep_vars, all_q, all_series = [], [], [], []
     fstats = {k: torch.zeros(ncell, dtype=torch.float64, device=dev)
               for k in ("mean_f", "m2_f", "mean_d", "m2_d")}
     fstats["n"] = torch.zeros(ncell, dtype=torch.int64, device=dev)
@@ -75,16 +78,22 @@ def run(ctx, level, n_samples, n_xi=3, batch=256, replicates=1, thresholds=(0.5,
         for k in range(0, n_samples, batch):
             cnt = min(batch, n_samples - k)
             xi = torch.from_numpy(xi_halton(first + k, cnt, n_xi, shift)).to(dev)
-            out = ctx.solve(level, xi, want_c=True)
+            if series_every:
+                out = ctx.solve_series(level, xi, series_every)
+            else:
+                out = ctx.solve(level, xi, want_c=True)
             st = out["status"]
             ctx.level_stats(level, out["q"], None, st, S)
-            c = out["c"].reshape(cnt, ncell)
-            ctx.field_stats(level, c, None, st, fstats)
-            for th, cn in zip(thresholds, counts):
-                ctx.field_exceedance(level, c, st, th, cn)
+            if not series_every:
+                c = out["c"].reshape(cnt, ncell)
+                ctx.field_stats(level, c, None, st, fstats)
+                for th, cn in zip(thresholds, counts):
+                    ctx.field_exceedance(level, c, st, th, cn)
             ok = (st == 0).cpu().numpy()
             failed += int((~ok).sum())
             all_q.append(out["q"].cpu().numpy()[ok])
+            if series_every:
+                all_series.append(out["series"].cpu().numpy()[ok])
         n = S.n
         rep_means.append(np.array(S.mean_f[:]))
         rep_vars.append(np.array(S.m2_f[:]) / (n - 1) if n > 1 else np.full(hb.NQ, np.nan))
@@ -109,7 +118,13 @@ def run(ctx, level, n_samples, n_xi=3, batch=256, replicates=1, thresholds=(0.5,
             # exact counts divided on the host (a device division by a scalar
             # may go through its reciprocal and differ in the last bit)
             "exceedance": [k / max(nf, 1) for k in cnts],
-            "failed": failed, "wall_s": wall}
+            "failed": failed, "wall_s": wall,
+            "series_steps": (list(range(series_every, li.nt + 1, series_every))
+                             if series_every else []),
+            "series_quantiles": (np.stack([sample_quantiles(v, probs)
+                                           for v in np.concatenate(all_series, axis=0)
+                                           .transpose(1, 0, 2)])
+                                 if series_every else None)}
 
 
 def main(argv=None):
@@ -121,6 +136,9 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=600)
     ap.add_argument("--precision", choices=["fp64", "fp32mg"], default="fp32mg")
     ap.add_argument("--threshold", type=float, nargs="*", default=[0.5])
+    ap.add_argument("--series-every", type=int, default=0,
+                    help="also record the QoIs after every k-th step and report their "
+                         "quantiles over time (test A3)")
     ap.add_argument("--paper-workload", action="store_true",
                     help="field_model 1, T = 6016 s in 94 steps on level 0 (the paper's setting)")
     ap.add_argument("--out", default=None)
@@ -136,7 +154,8 @@ def main(argv=None):
                             **extra)
     ctx = hb.Context(cfg)
     res = run(ctx, a.level, a.samples, n_xi=a.n_xi, batch=a.batch, replicates=a.replicates,
-              thresholds=a.threshold, log=lambda d: print(json.dumps(d), flush=True))
+              thresholds=a.threshold, log=lambda d: print(json.dumps(d), flush=True),
+              series_every=a.series_every)
     summary = {"level": a.level, "samples": a.samples, "replicates": a.replicates,
                "paper_workload": a.paper_workload,
                "precision": a.precision, "mean": res["mean"].tolist(),
@@ -144,6 +163,9 @@ def main(argv=None):
                "quantiles": res["quantiles"].tolist(),
                "exceedance_area_fraction": [float(e.mean()) for e in res["exceedance"]],
                "max_var_c": float(res["var_field"].max()), "failed": res["failed"],
+               "series_steps": res["series_steps"],
+               "series_quantiles_Q_FW_Q_S": (res["series_quantiles"][:, :, [6, 0]].tolist()
+                                             if a.series_every else None),
                "wall_s": res["wall_s"]}
     print(json.dumps(summary))
     if a.out:

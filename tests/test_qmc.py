@@ -132,3 +132,37 @@ def test_qmc_run_matches_the_oracle():
     assert len(bad) == 0, [(int(j), int(i), int(got[j, i]), int(want[j, i])) for j, i in bad[:8]]
     ex = OQ.exceedance(c, 0.3)
     assert np.array_equal(res["exceedance"][0][~near], ex[~near])
+
+
+@pytest.mark.gpu
+def test_qoi_series_matches_the_oracle_states():
+    """henry_solve_series: the 22 QoIs after every 4th of the 24 level-0
+    steps equal the oracle's QoIs of its states at those steps, and the last
+    entry is the QoI vector at T; QMC quantiles over time come from them."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from gpu_helpers import oracle_grid, oracle_physics, tight_config
+    from oracle import henry as H
+    from paper_2403_17018_gb300 import binding as hb
+    from paper_2403_17018_gb300 import qmc as Q
+    cfg = tight_config(nlevels=1)
+    ctx = hb.Context(cfg)
+    xi = torch.from_numpy(xi_halton(1, 3, 3)).cuda()
+    out = ctx.solve_series(0, xi, 4)
+    assert out["series"].shape == (3, 6, hb.NQ)
+    assert torch.equal(out["series"][:, -1], out["q"])
+    g, ph = oracle_grid(cfg, 0), oracle_physics(cfg)
+    V = (cfg.Lx / cfg.nx0) * (cfg.Ly / cfg.ny0)
+    for b in range(3):
+        r = H.solve(g, ph, xi[b].cpu().numpy(), keep_states=True)
+        for k in range(6):
+            c = r["states"][4 * (k + 1)][1]
+            want = H.qoi(g, ph, r["fields"], c)
+            got = out["series"][b, k].cpu().numpy()
+            keep = np.arange(hb.NQ) != 6
+            assert np.allclose(got[keep], want[keep], rtol=1e-9, atol=1e-9)
+            assert abs(got[6] - want[6]) <= V * np.sum(np.abs(c - H.FRESH_C) <= 1e-9) + 1e-12
+    res = Q.run(ctx, 0, 5, batch=3, series_every=6)
+    assert res["series_steps"] == [6, 12, 18, 24]
+    assert res["series_quantiles"].shape == (4, 5, hb.NQ)
+    assert np.allclose(res["series_quantiles"][-1], res["quantiles"], rtol=0, atol=0)
