@@ -41,10 +41,17 @@ def qoi_value(name, grid, phys, c):
     return float(np.sum(qoi_integrand(name, grid, phys, c)))
 
 
+def _step_fields(grid, phys, f, n):
+    """Fields of step n (1-based): with the paper's model the inflow carries
+    the recharge factor (1 + sin(pi t / 40)) at t = n tau (as oracle.henry.solve)."""
+    if phys.field_model != 1:
+        return f
+    fac = 1.0 + np.sin(np.pi * n * grid.tau / 40.0)
+    return H.Fields(phi=f.phi, K=f.K, qin=f.qin * fac)
+
+
 def adjoint(grid, phys, xi, qoi="Q_S", logk=None):
     """Returns dict(q, dq_dxi [n_xi], dq_dlogk [ny, nx], lam (per step))."""
-    if phys.field_model != 0:
-        raise NotImplementedError("the adjoint covers the smooth field model (field_model 0)")
     xi = np.asarray(xi, dtype=float)
     ny, nx = grid.ny, grid.nx
     lk = np.zeros((ny, nx)) if logk is None else np.asarray(logk, dtype=float)
@@ -68,11 +75,12 @@ def adjoint(grid, phys, xi, qoi="Q_S", logk=None):
             # -(dR^{n+1}/du^n)^T lam_{n+1}: R^{n+1} sees u^n through c_old only,
             # cell by cell (diagonal), so one complex step gives it
             p1, c1 = states[n + 1]
-            Rp, Rc = H.residual(grid, phys, f, p1, c1, c_n + 1j * _H)
+            Rp, Rc = H.residual(grid, phys, _step_fields(grid, phys, f, n + 1), p1, c1,
+                                c_n + 1j * _H)
             dp, dc = Rp.imag / _H, Rc.imag / _H
             lp, lc = lam_next[0::2].reshape(ny, nx), lam_next[1::2].reshape(ny, nx)
             rhs = H.interleave(np.zeros((ny, nx)), -(dp * lp + dc * lc))
-        Jn = H.jacobian(grid, phys, f, p_n, c_n, c_prev)
+        Jn = H.jacobian(grid, phys, _step_fields(grid, phys, f, n), p_n, c_n, c_prev)
         lam = spla.spsolve(Jn.T.tocsc(), rhs)
         lams[n] = lam
         lp, lc = lam[0::2].reshape(ny, nx), lam[1::2].reshape(ny, nx)
@@ -80,14 +88,14 @@ def adjoint(grid, phys, xi, qoi="Q_S", logk=None):
         for j in range(xi.shape[0]):
             xz = xi.astype(complex)
             xz[j] += 1j * _H
-            fz = H.fields(grid, phys, xz, lk)
+            fz = _step_fields(grid, phys, H.fields(grid, phys, xz, lk), n)
             Rp, Rc = H.residual(grid, phys, fz, p_n, c_n, c_prev)
             dq_dxi[j] -= np.sum(lp * Rp.imag / _H + lc * Rc.imag / _H)
         # per-cell log K: coloured complex steps (theta_P reaches the
         # residual of P and its four neighbours only)
         for col in range(5):
             mask = colour == col
-            fz = H.fields(grid, phys, xi, lk + 1j * _H * mask)
+            fz = _step_fields(grid, phys, H.fields(grid, phys, xi, lk + 1j * _H * mask), n)
             Rp, Rc = H.residual(grid, phys, fz, p_n, c_n, c_prev)
             w = lp * Rp.imag / _H + lc * Rc.imag / _H          # lam_Q dR_Q / dtheta_P
             Pj, Pi = np.nonzero(mask)

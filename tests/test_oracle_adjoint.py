@@ -57,3 +57,27 @@ def test_transposed_solve_dot_product_identity():
     assert abs(np.dot(J @ v, w) - np.dot(v, J.T @ w)) <= 1e-12 * np.linalg.norm(J @ v) * np.linalg.norm(w)
     lam = spla.spsolve(J.T.tocsc(), w)
     assert np.linalg.norm(J.T @ lam - w) <= 1e-10 * np.linalg.norm(w)
+
+
+def test_adjoint_of_the_paper_model_matches_central_differences():
+    """The paper's field model (two-layer multiscale porosity, Kozeny-Carman
+    permeability, recharge with its time factor at each step's end): the
+    adjoint gradient in xi_1..xi_3 and in log K against central differences
+    of the forward solve (steps of 13 s so that the recharge factor varies)."""
+    ph = H.Physics(field_model=1)
+    g = H.Grid(nx=16, ny=8, nt=6, T=6 * 13.0)
+    xi = xi_batch(0, 6, 1)[0]
+    lk = logk_perturbation(g.ny, g.nx, 1)[0]
+    adj = A.adjoint(g, ph, xi, "Q_S", lk)
+    h = 1e-4
+    for j in range(3):
+        e = np.zeros(3)
+        e[j] = h
+        fd = (A.forward_qoi(g, ph, xi + e, "Q_S", lk) - A.forward_qoi(g, ph, xi - e, "Q_S", lk)) / (2 * h)
+        assert abs(adj["dq_dxi"][j] - fd) <= 1e-5 * max(abs(fd), 1e-3 * abs(adj["q"])), (j, fd)
+    scale = np.max(np.abs(adj["dq_dlogk"]))
+    for (j, i) in ((0, 0), (3, 7), (7, 15)):
+        e = np.zeros_like(lk)
+        e[j, i] = h
+        fd = (A.forward_qoi(g, ph, xi, "Q_S", lk + e) - A.forward_qoi(g, ph, xi, "Q_S", lk - e)) / (2 * h)
+        assert abs(adj["dq_dlogk"][j, i] - fd) <= 1e-5 * scale, ((j, i), fd)
