@@ -124,7 +124,7 @@ typedef struct henry_config {
                            e_perm_Kozeny_Carman; Table 1's kappa_KC), and the
                            recharge q0 (1 + 0.5 xi3)(1 + sin(pi t / 40)) taken
                            at the end of each step (Eq. e_recharge_of_param);
-                           needs n_xi = 3; no adjoint */
+                           needs n_xi = 3 */
   int krylov_iters;     /* 0 (default): each defect-correction iteration
                            applies `vcycles` V-cycles. k > 0: it runs k
                            iterations of BiCGStab on the finest-level
@@ -223,8 +223,9 @@ int henry_sample_pairs(henry_ctx* ctx, int level, const double* xi, int B,
  *   dq_dlogk   device [B][ny][nx] out, or NULL
  *   status     device int [B] out (HENRY_S_* bits of forward and adjoint)
  * Synchronises the stream once per defect-correction iteration of the
- * backward pass. Errors as henry_solve; HENRY_E_INVALID for a context with
- * field_model != 0 (the adjoint contracts the smooth model's fields). */
+ * backward pass. Both field models: with field_model 1 the inflow
+ * sensitivity of each step carries that step's recharge factor. Errors as
+ * henry_solve. */
 int henry_adjoint(henry_ctx* ctx, int level, const double* xi, const double* logk, int B,
                   int qoi_id, int ckpt_every, double* q, double* dq_dxi, double* dq_dlogk,
                   int* status, void* stream);

@@ -273,8 +273,6 @@ int henry_adjoint(henry_ctx* ctx, int level, const double* xi, const double* log
   if (level < 0 || level >= ctx->cfg.nlevels) return fail(HENRY_E_INVALID, "bad level");
   if (B < 0) return fail(HENRY_E_INVALID, "B < 0");
   if (qoi_id != 0 && qoi_id != 2) return fail(HENRY_E_INVALID, "qoi_id must be 0 (Q_S) or 2 (toe)");
-  if (ctx->cfg.field_model != 0)
-    return fail(HENRY_E_INVALID, "the adjoint covers field_model 0 only");
   if (B == 0) return HENRY_OK;
   if (!xi || !q || !dq_dxi || !status) return fail(HENRY_E_INVALID, "xi, q, dq_dxi, status required");
   CKR(cudaSetDevice(ctx->device));

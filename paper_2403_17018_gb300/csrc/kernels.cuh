@@ -1543,7 +1543,7 @@ __global__ void k_adj_update(unsigned long long* ctr, Geom G, int B, const int* 
 // right side's flux is proportional to K_P, its and the left side's
 // diffusion to phi_P. Each cell evaluates its four faces itself (no
 // atomics); p is the reduced pressure.
-__global__ void k_adj_sens(unsigned long long* ctr, Phys P, Geom G, double tau, int B,
+__global__ void k_adj_sens(unsigned long long* ctr, Phys P, Geom G, double tau, double qfac, int B,
                            const double* __restrict__ p, const double* __restrict__ c,
                            const double* __restrict__ c_old, const double* __restrict__ phi,
                            const double* __restrict__ K, const double* __restrict__ tx,
@@ -1595,7 +1595,7 @@ __global__ void k_adj_sens(unsigned long long* ctr, Phys P, Geom G, double tau, 
   if (i == 0) {
     const double rb = 0.5 * (rho + P.rho0);
     sphi += lc[cell] * dcoF * rb * cP;
-    gq[(int64_t)b * ny + j] -= lp[cell] * (-A * P.rho0);
+    gq[(int64_t)b * ny + j] -= lp[cell] * (-A * P.rho0) * qfac;   // inflow factor of this step
   }
   if (i == nx - 1) {
     const double rho1 = P.rho0 + P.drho;
@@ -1633,15 +1633,45 @@ __global__ void k_adj_prev_rhs(unsigned long long* ctr, Phys P, Geom G, double t
 // dQ/dxi from the per-cell and per-row sensitivities (fields of k_fields);
 // one block per sample.
 __global__ void __launch_bounds__(kBlock)
-k_adj_contract(unsigned long long* ctr, Phys P, Geom G, int B, int n_xi,
-               const double* __restrict__ gK, const double* __restrict__ gphi,
-               const double* __restrict__ gq, double* __restrict__ dq_dxi) {
+k_adj_contract(unsigned long long* ctr, Phys P, Geom G, int B, int n_xi, int model,
+               const double* __restrict__ xi, const double* __restrict__ gK,
+               const double* __restrict__ gphi, const double* __restrict__ gq,
+               double* __restrict__ dq_dxi) {
   HENRY_COUNT_LAUNCH(ctr);
   __shared__ double sh[kBlock / 32];
   const int b = blockIdx.x;
   const int n = G.ncell();
   const double pi = 3.14159265358979323846;
   double s[6] = {0, 0, 0, 0, 0, 0};
+  if (model == 1) {
+    // Eq. poro_2levels: phi = phi0 C0 C1 C2 with C0 = 1.2 (1 + 0.2 xi1) in the
+    // lower layer, C1 = 1 + 0.15 (xi2 a + xi1 cw), C2 = 1 + 0.2 (xi1 d + xi2 e);
+    // log K = log kappa + 3 log phi - log(1 - phi^2) + theta, so
+    // dlogK/dxi = (3/phi + 2 phi/(1 - phi^2)) dphi/dxi; q_in base q0 (1 + 0.5 xi3)
+    const double z0 = xi[(int64_t)b * n_xi], z1 = xi[(int64_t)b * n_xi + 1];
+    for (int cell = threadIdx.x; cell < n; cell += blockDim.x) {
+      const int j = cell / G.nx, i = cell - j * G.nx;
+      const double x = (i + 0.5) * G.hx, yp = (j + 0.5) * G.hy - P.Ly;
+      const bool low = yp < -0.8;
+      const double c0 = low ? 1.2 * (1.0 + 0.2 * z0) : 1.0, dc0 = low ? 1.2 * 0.2 : 0.0;
+      const double a = cos(pi * x / 2) - sin(2 * pi * yp), cw = cos(2 * pi * x);
+      const double d = sin(64 * pi * x), e = sin(32 * pi * yp);
+      const double c1 = 1.0 + 0.15 * (z1 * a + z0 * cw), c2 = 1.0 + 0.2 * (z0 * d + z1 * e);
+      const double ph = P.phi0 * c0 * c1 * c2;
+      const double dph0 = P.phi0 * (dc0 * c1 * c2 + c0 * 0.15 * cw * c2 + c0 * c1 * 0.2 * d);
+      const double dph1 = P.phi0 * (c0 * 0.15 * a * c2 + c0 * c1 * 0.2 * e);
+      const double dlk = 3.0 / ph + 2.0 * ph / (1.0 - ph * ph);
+      const double gp = gphi[(int64_t)b * n + cell], gk = gK[(int64_t)b * n + cell];
+      s[0] += (gp + gk * dlk) * dph0;
+      s[1] += (gp + gk * dlk) * dph1;
+    }
+    for (int j = threadIdx.x; j < G.ny; j += blockDim.x) s[2] += gq[(int64_t)b * G.ny + j] * P.q0 * 0.5;
+    for (int k = 0; k < n_xi; ++k) {
+      const double t = block_sum(s[k], sh);
+      if (threadIdx.x == 0) dq_dxi[(int64_t)b * n_xi + k] = t;
+    }
+    return;
+  }
   for (int cell = threadIdx.x; cell < n; cell += blockDim.x) {
     const int j = cell / G.nx, i = cell - j * G.nx;
     const double x = (i + 0.5) * G.hx, y = (j + 0.5) * G.hy;

@@ -854,7 +854,11 @@ int Solver::adjoint_t(const double* xi, const double* logk, int B, int qoi, int 
                                                              (const T*)F.x, lam_);
       }
       for (size_t k = 0; k < levels_.size(); ++k) std::swap(levels_[k].J, JT_[k]);
-      k_adj_sens<<<grid1((int64_t)n), kBlock, 0, s>>>(counter_, phys_, G, tau_, B, F.p, F.c, c_old_,
+      // Eq. e_recharge_of_param: the inflow of step st carries (1 + sin(pi t / 40)), t = st tau
+      const double qfac =
+          cfg_.field_model == 1 ? 1.0 + sin(3.14159265358979323846 * st * tau_ / 40.0) : 1.0;
+      k_adj_sens<<<grid1((int64_t)n), kBlock, 0, s>>>(counter_, phys_, G, tau_, qfac, B, F.p, F.c,
+                                                      c_old_,
                                                       F.phi, F.K, F.tx, F.dx, F.ty, F.dy, lam_, gK_,
                                                       gphi_, gq_);
       if (st > 1)
@@ -862,7 +866,8 @@ int Solver::adjoint_t(const double* xi, const double* logk, int B, int qoi, int 
                                                             c_old_, lam_, rhs_);
     }
   }
-  k_adj_contract<<<B, kBlock, 0, s>>>(counter_, phys_, G, B, cfg_.n_xi, gK_, gphi_, gq_, dq_dxi);
+  k_adj_contract<<<B, kBlock, 0, s>>>(counter_, phys_, G, B, cfg_.n_xi, cfg_.field_model, xi, gK_,
+                                      gphi_, gq_, dq_dxi);
   if (dq_dlogk) CK(cudaMemcpyAsync(dq_dlogk, gK_, n * 8, cudaMemcpyDeviceToDevice, s));
   k_copy_int<<<grid1(B), kBlock, 0, s>>>(counter_, B, status_w_, status, 0);
   CK(cudaGetLastError());

@@ -66,9 +66,6 @@ def test_paper_workload_solve_matches_oracle(precision):
         assert q_o[6] > 0 and q_o[7:22].max() > 0
 
 
-def test_adjoint_rejects_the_paper_model():
-    ctx = hb.Context(hb.default_config(nlevels=1, field_model=1))
-    with pytest.raises(hb.HenryError):
-        ctx.adjoint(0, xi_cuda(0, 0, 2))
+def test_paper_model_needs_three_variables():
     with pytest.raises(hb.HenryError):
         hb.Context(hb.default_config(nlevels=1, field_model=1, n_xi=6))
