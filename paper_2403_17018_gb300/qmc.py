@@ -49,8 +49,27 @@ def sample_quantiles(values, probs):
     return np.stack(out)                      # [len(probs), k]
 
 
+def _chan(n_a, mean_a, m2_a, n_b, mean_b, m2_b):
+    """Chan, Golub and LeVeque's merge of two (count, mean, M2) states."""
+    n = n_a + n_b
+    if n == 0:
+        return 0, mean_a, m2_a
+    d = mean_b - mean_a
+    return n, mean_a + d * (n_b / n), m2_a + m2_b + d * d * (n_a * n_b / n)
+
+
+def _chan_cells(n_a, mean_a, m2_a, n_b, mean_b, m2_b):
+    """_chan per cell (arrays; cells with no samples stay at zero)."""
+    n = n_a + n_b
+    safe = np.maximum(n, 1.0)
+    d = mean_b - mean_a
+    return (n, mean_a + np.where(n > 0, d * (n_b / safe), 0.0),
+            m2_a + m2_b + np.where(n > 0, d * d * (n_a * n_b / safe), 0.0))
+
+
 def run(ctx, level, n_samples, n_xi=3, batch=256, replicates=1, thresholds=(0.5,),
-        probs=QUANTILES, first=1, log=None, series_every=0):
+        probs=QUANTILES, first=1, log=None, series_every=0, rank=0, world=1, dist=None,
+        device="cuda"):
     """QMC on `level` with n_samples Halton points per replicate. Returns a
     dict: per-QoI mean (over replicates) and standard error (R > 1), the
     per-replicate means and variances, quantiles of every QoI over all
@@ -58,13 +77,19 @@ def run(ctx, level, n_samples, n_xi=3, batch=256, replicates=1, thresholds=(0.5,
     fields of c (numpy), plus timing and failed samples. series_every = k > 0
     also solves through henry_solve_series (without the c field statistics)
     and returns the quantiles of every QoI after each k-th step (test A3:
-    "series_quantiles" [steps/k, probs, NQ], "series_steps")."""
+    "series_quantiles" [steps/k, probs, NQ], "series_steps").
+
+    Under torch.distributed (world > 1, `dist` the module) every rank solves
+    a disjoint slice of each batch; the replicate statistics and the
+    per-cell fields are merged with Chan's formula, the exceedance counts
+    summed and the QoI values gathered for the quantiles, so every rank
+    returns the result of the whole run."""
     import torch
     from paper_2403_17018_gb300 import binding as hb
     from paper_2403_17018_gb300.inputs import xi_halton
     li = ctx.level_info(level)
     ncell = li.ny * li.nx
-    dev = torch.device("cuda")
+    dev = torch.device(device)
     rep_means, rep_vars, all_q, all_series = [], [], [], []
     fstats = {k: torch.zeros(ncell, dtype=torch.float64, device=dev)
               for k in ("mean_f", "m2_f", "mean_d", "m2_d")}
@@ -76,8 +101,12 @@ def run(ctx, level, n_samples, n_xi=3, batch=256, replicates=1, thresholds=(0.5,
         shift = None if replicates == 1 else 2403017018 + 7919 * (r + 1)
         S = hb.LevelStats()
         for k in range(0, n_samples, batch):
-            cnt = min(batch, n_samples - k)
-            xi = torch.from_numpy(xi_halton(first + k, cnt, n_xi, shift)).to(dev)
+            cnt_all = min(batch, n_samples - k)
+            lo = (cnt_all * rank) // world
+            cnt = (cnt_all * (rank + 1)) // world - lo
+            if cnt == 0:
+                continue
+            xi = torch.from_numpy(xi_halton(first + k + lo, cnt, n_xi, shift)).to(dev)
             if series_every:
                 out = ctx.solve_series(level, xi, series_every)
             else:
@@ -94,26 +123,48 @@ def run(ctx, level, n_samples, n_xi=3, batch=256, replicates=1, thresholds=(0.5,
             all_q.append(out["q"].cpu().numpy()[ok])
             if series_every:
                 all_series.append(out["series"].cpu().numpy()[ok])
-        n = S.n
-        rep_means.append(np.array(S.mean_f[:]))
-        rep_vars.append(np.array(S.m2_f[:]) / (n - 1) if n > 1 else np.full(hb.NQ, np.nan))
+        n, mf, m2 = int(S.n), np.array(S.mean_f[:]), np.array(S.m2_f[:])
+        if dist is not None and world > 1:
+            parts = [None] * world
+            dist.all_gather_object(parts, (n, mf, m2))
+            n, mf, m2 = 0, np.zeros(hb.NQ), np.zeros(hb.NQ)
+            for nb, mb, m2b in parts:
+                n, mf, m2 = _chan(n, mf, m2, nb, mb, m2b)
+        rep_means.append(mf)
+        rep_vars.append(m2 / (n - 1) if n > 1 else np.full(hb.NQ, np.nan))
         if log:
             log({"replicate": r, "n": n, "mean": rep_means[-1].tolist()})
-    torch.cuda.synchronize()
+    if dev.type == "cuda":
+        torch.cuda.synchronize()
+    fs = {k: v.cpu().numpy() for k, v in fstats.items()}
+    cnts = [cn.cpu().numpy().reshape(li.ny, li.nx) for cn in counts]
+    if dist is not None and world > 1:
+        parts = [None] * world
+        dist.all_gather_object(parts, (fs, cnts, all_q, all_series, failed))
+        fs = {k: np.zeros_like(v) for k, v in fs.items()}
+        n_c = np.zeros(ncell)
+        for f, _, _, _, _ in parts:
+            n_c, fs["mean_f"], fs["m2_f"] = _chan_cells(n_c, fs["mean_f"], fs["m2_f"],
+                                                       f["n"].astype(np.float64), f["mean_f"],
+                                                       f["m2_f"])
+        fs["n"] = n_c.astype(np.int64)
+        cnts = [sum(p[1][i] for p in parts) for i in range(len(thresholds))]
+        all_q = [a for p in parts for a in p[2]]
+        all_series = [a for p in parts for a in p[3]]
+        failed = sum(p[4] for p in parts)
     wall = time.perf_counter() - t0
     rm = np.array(rep_means)
     mean = rm.sum(axis=0) / replicates
     se = (np.sqrt(((rm - mean) ** 2).sum(axis=0) / (replicates - 1) / replicates)
           if replicates > 1 else np.full(mean.shape, np.nan))
     q = np.concatenate(all_q, axis=0)
-    nf = int(fstats["n"][0].item())
-    cnts = [cn.cpu().numpy().reshape(li.ny, li.nx) for cn in counts]
+    nf = int(fs["n"][0])
     return {"level": level, "samples": n_samples, "replicates": replicates,
             "mean": mean, "std_error": se, "replicate_means": rm,
             "replicate_vars": np.array(rep_vars),
             "quantile_probs": list(probs), "quantiles": sample_quantiles(q, probs), "q": q,
-            "mean_field": fstats["mean_f"].cpu().numpy().reshape(li.ny, li.nx),
-            "var_field": (fstats["m2_f"] / max(nf - 1, 1)).cpu().numpy().reshape(li.ny, li.nx),
+            "mean_field": fs["mean_f"].reshape(li.ny, li.nx),
+            "var_field": (fs["m2_f"] / max(nf - 1, 1)).reshape(li.ny, li.nx),
             "thresholds": list(thresholds), "counts": cnts, "n_field": nf,
             # exact counts divided on the host (a device division by a scalar
             # may go through its reciprocal and differ in the last bit)
@@ -146,6 +197,14 @@ def main(argv=None):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2403_17018_gb300 import binding as hb
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
     extra = {"field_model": 1, "T": 6016.0, "nt0": 94} if a.paper_workload else {}
     if a.paper_workload:
         a.n_xi = 3
@@ -154,8 +213,9 @@ def main(argv=None):
                             **extra)
     ctx = hb.Context(cfg)
     res = run(ctx, a.level, a.samples, n_xi=a.n_xi, batch=a.batch, replicates=a.replicates,
-              thresholds=a.threshold, log=lambda d: print(json.dumps(d), flush=True),
-              series_every=a.series_every)
+              thresholds=a.threshold,
+              log=(lambda d: print(json.dumps(d), flush=True)) if rank == 0 else None,
+              series_every=a.series_every, rank=rank, world=world, dist=dist)
     summary = {"level": a.level, "samples": a.samples, "replicates": a.replicates,
                "paper_workload": a.paper_workload,
                "precision": a.precision, "mean": res["mean"].tolist(),
@@ -167,9 +227,13 @@ def main(argv=None):
                "series_quantiles_Q_FW_Q_S": (res["series_quantiles"][:, :, [6, 0]].tolist()
                                              if a.series_every else None),
                "wall_s": res["wall_s"]}
-    print(json.dumps(summary))
-    if a.out:
-        np.savez(a.out, **{k: v for k, v in res.items() if isinstance(v, np.ndarray)})
+    summary["n_gpus"] = world
+    if rank == 0:
+        print(json.dumps(summary))
+        if a.out:
+            np.savez(a.out, **{k: v for k, v in res.items() if isinstance(v, np.ndarray)})
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 if __name__ == "__main__":

@@ -166,3 +166,94 @@ def test_qoi_series_matches_the_oracle_states():
     assert res["series_steps"] == [6, 12, 18, 24]
     assert res["series_quantiles"].shape == (4, 5, hb.NQ)
     assert np.allclose(res["series_quantiles"][-1], res["quantiles"], rtol=0, atol=0)
+
+
+class _FakeCtx:
+    """Stand-in for a context on the CPU: q and c are fixed smooth functions
+    of xi, and the statistics entry points are plain numpy Welford/Chan
+    updates, so that the driver's host logic (sharding, merging) can run on
+    gloo ranks without a GPU."""
+
+    class _Info:
+        ny, nx, nt = 4, 6, 12
+
+    def level_info(self, level):
+        return self._Info()
+
+    def solve(self, level, xi, want_c=False):
+        import torch
+        x = xi.numpy()
+        from paper_2403_17018_gb300 import binding as hb
+        q = np.stack([np.sin(x[:, 0] * (k + 1)) + x[:, 1] * k + x[:, 2] ** 2 for k in range(hb.NQ)], 1)
+        cells = np.arange(24)
+        c = 0.5 + 0.4 * np.sin(x[:, :1] * 3 + cells[None, :] * 0.7 + x[:, 1:2])
+        st = np.zeros(len(x), dtype=np.int32)
+        st[np.abs(x[:, 2]) > 0.97] = 1                       # a few "failed" samples
+        return {"q": torch.from_numpy(q), "c": torch.from_numpy(c.reshape(-1, 4, 6)),
+                "status": torch.from_numpy(st)}
+
+    def level_stats(self, level, q, qc, st, S):
+        ok = st.numpy() == 0
+        v = q.numpy()[ok]
+        nb = len(v)
+        if nb == 0:
+            return
+        mb = v.mean(0)
+        m2b = ((v - mb) ** 2).sum(0)
+        n = S.n + nb
+        d = mb - np.array(S.mean_f[:])
+        mean = np.array(S.mean_f[:]) + d * nb / n
+        m2 = np.array(S.m2_f[:]) + m2b + d * d * S.n * nb / n
+        S.n = n
+        S.mean_f[:] = mean.tolist()
+        S.m2_f[:] = m2.tolist()
+
+    def field_stats(self, level, c, cc, st, acc):
+        ok = st.numpy() == 0
+        for row in c.numpy()[ok]:
+            n = acc["n"] + 1
+            d = row - acc["mean_f"].numpy()
+            acc["mean_f"] += torch.from_numpy(d / n.numpy())
+            acc["m2_f"] += torch.from_numpy(d * (row - acc["mean_f"].numpy()))
+            acc["n"] += 1
+
+    def field_exceedance(self, level, c, st, th, count):
+        ok = st.numpy() == 0
+        count += torch.from_numpy(np.sum(c.numpy()[ok] > th, axis=0))
+
+
+def _qmc_rank(rank, world, port, out):
+    import os
+    import torch.distributed as dist
+    from paper_2403_17018_gb300 import qmc as Q
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    res = Q.run(_FakeCtx(), 0, 23, batch=7, replicates=2, thresholds=(0.5,), rank=rank,
+                world=world, dist=dist, device="cpu")
+    if rank == 0:
+        np.savez(out, mean=res["mean"], se=res["std_error"], quant=res["quantiles"],
+                 var=res["var_field"], mf=res["mean_field"], ex=res["exceedance"][0],
+                 failed=res["failed"])
+    dist.destroy_process_group()
+
+
+def test_qmc_on_two_gloo_ranks_equals_one_rank(tmp_path):
+    """Each rank solves a disjoint slice of every batch; the merged replicate
+    statistics, fields, exceedance and quantiles equal the one-rank run."""
+    import socket
+    import torch.multiprocessing as mp
+    from paper_2403_17018_gb300 import qmc as Q
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    out = str(tmp_path / "r.npz")
+    mp.start_processes(_qmc_rank, args=(2, port, out), nprocs=2, start_method="spawn")
+    got = np.load(out)
+    ref = Q.run(_FakeCtx(), 0, 23, batch=7, replicates=2, thresholds=(0.5,), device="cpu")
+    assert got["failed"] == ref["failed"] > 0
+    assert np.allclose(got["mean"], ref["mean"], rtol=1e-13, atol=1e-15)
+    assert np.allclose(got["se"], ref["std_error"], rtol=1e-10, atol=1e-15)
+    assert np.array_equal(got["quant"], ref["quantiles"])
+    assert np.allclose(got["mf"], ref["mean_field"], rtol=1e-13)
+    assert np.allclose(got["var"], ref["var_field"], rtol=1e-12)
+    assert np.array_equal(got["ex"], ref["exceedance"][0])
