@@ -5,7 +5,7 @@ Workload (one step): MLMC levels 0..3 of the Henry problem on [0,2]x[0,1]
 (32x16, 64x32, 128x64, 256x128 cells; 24, 48, 96, 192 implicit Euler steps
 to T = 43200 s) with 1024 / 256 / 64 / 16 level pairs, each pair a fine solve
 at level l and a coarse solve at level l-1 sharing one xi ~ U[-1,1]^3, then
-the per-level MLMC statistics of the six QoIs. The four levels run
+the per-level MLMC statistics of the 22 QoIs. The four levels run
 concurrently on four CUDA streams. The headline runs the multigrid in FP64
 (the plain FP64 GPU form); the same workload with FP32 multigrid inside FP64
 defect correction is reported beside it.
