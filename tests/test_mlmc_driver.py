@@ -178,3 +178,19 @@ def test_relative_tolerance_scales_by_level_zero_mean():
     V = np.array(res["V_l"])[:, 0]
     m = OM.allocation(V, np.array(res["seconds_per_pair"]), eps * E0)
     assert all(n >= k for n, k in zip(res["n"], m))
+
+
+def test_adaptive_run_resumes_from_its_state():
+    """Resuming an adaptive-level run at a tighter eps keeps every drawn
+    sample, draws only new indices, and may add finer levels; the result
+    equals a fresh adaptive run whose pilots are the first run's counts."""
+    s1 = FakeSampler(v=1e-20)
+    r1 = M.run(s1, 10, 2e-2, qois=(0,), adaptive_levels=True)
+    s2 = FakeSampler(v=1e-20)
+    r2 = M.run(s2, 10, 2e-3, qois=(0,), adaptive_levels=True, state=r1["state"])
+    drawn = {l: r1["state"][l]["drawn"] for l in range(len(r1["state"]))}
+    for (l, first, count) in s2.calls:
+        assert first >= drawn.get(l, 0)
+    assert r2["levels"] >= r1["levels"]
+    brute = next(k for k in range(40) if s2.a * 2.0 ** -k <= 2e-3 / math.sqrt(2.0))
+    assert r2["levels"] - 1 == brute
