@@ -36,3 +36,24 @@ def test_error_strings_and_invalid_config(lib):
     assert b"n_xi" in lib.henry_last_error()
     cfg = hb.default_config(nx0=30, ny0=15)
     assert lib.henry_create_levels(ctypes.byref(cfg), ctypes.byref(h)) == -5
+
+
+@pytest.mark.parametrize("kw", [
+    {"field_model": 2}, {"field_model": 1, "n_xi": 6}, {"krylov_iters": -1},
+    {"krylov_iters": 65}, {"jac_lag": -1}, {"mg_small_cells": 513}, {"mg_small_cells": -1},
+    {"vcycles": 0}, {"nu1": -1}, {"precision": 2}, {"nlevels": 0},
+])
+def test_config_validation_rejects_out_of_range_options(lib, kw):
+    """henry_create_levels validates the whole config before touching the
+    device, so these checks run without a GPU: every option outside its
+    documented range is rejected as an invalid argument."""
+    cfg = hb.default_config(**kw)
+    h = ctypes.c_void_p()
+    assert lib.henry_create_levels(ctypes.byref(cfg), ctypes.byref(h)) == -1, kw
+    assert not h.value
+
+
+def test_new_options_default_off(lib):
+    cfg = hb.default_config()
+    assert (cfg.field_model, cfg.krylov_iters, cfg.jac_lag) == (0, 0, 0)
+    assert cfg.mg_small_cells == 512 and cfg.newton_atol == 1e-11
