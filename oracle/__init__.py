@@ -17,5 +17,8 @@ Modules
 Parity status: every function here is pinned by `tests/test_oracle_pins.py`
 against closed forms, invariants or the paper's printed numbers, except the
 physical QoI values of the random-field model, which the paper does not print
-("parity unpinned" for absolute QoI values; their ingredients are pinned).
+("parity unpinned" for absolute QoI values; their ingredients are pinned), and
+the form of the oscillating factors of the paper's porosity model beyond
+xi = 0 ("parity unpinned": pinned through Table 1's Kozeny-Carman scale, the
+layers and the recharge timing only).
 """
