@@ -17,8 +17,9 @@ Modules
 Parity status: every function here is pinned by `tests/test_oracle_pins.py`
 against closed forms, invariants or the paper's printed numbers, except the
 physical QoI values of the random-field model, which the paper does not print
-("parity unpinned" for absolute QoI values; their ingredients are pinned), and
-the form of the oscillating factors of the paper's porosity model beyond
-xi = 0 ("parity unpinned": pinned through Table 1's Kozeny-Carman scale, the
-layers and the recharge timing only).
+("parity unpinned" for absolute QoI values; their ingredients are pinned).
+The paper's porosity model (Eq. poro_2levels) is pinned factor by factor:
+the layer factor C0 through row means over a period, C1 and C2 through the
+exact spectra of phi along x and along y (frequencies, amplitudes, sine or
+cosine, signs), the Kozeny-Carman scale through Table 1.
 """

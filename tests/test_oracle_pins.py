@@ -353,6 +353,93 @@ def test_paper_porosity_layers_at_xi_zero():
     assert np.allclose(f3.qin, 1.5 * ph.q0, rtol=1e-15)
 
 
+def _unit_dft(v, axis):
+    """DFT over the last (or given) axis scaled so that a sampled
+    cos(2 pi k s) at s_i = (i + 1/2) / N has coefficient exp(i pi k / N) at
+    bin k (and sin(2 pi k s) the coefficient -i exp(i pi k / N)): the
+    half-cell phase is removed, so a cosine term reads as a real number and
+    a sine term as an imaginary one."""
+    N = v.shape[axis]
+    X = np.fft.fft(v, axis=axis) / (N / 2)
+    k = np.arange(N)
+    shape = [1] * v.ndim
+    shape[axis] = N
+    return X * np.exp(-1j * np.pi * k / N).reshape(shape)
+
+
+def test_paper_porosity_layer_factor_c0():
+    """Eq. poro_2levels_C: with xi2 = 0 the oscillating factors C1, C2
+    depend on x only and average to one over a period (cos 2 pi x, sin 64 pi x
+    and their product are orthogonal to the constant on [0, 1), also on the
+    midpoint grid), so the x-average of each row over [0, 1) is
+    0.35 C0(xi1): 0.35 * 1.2 (1 + 0.2 xi1) below y_p = -0.8 (y < 0.2 in this
+    frame) and 0.35 above. A flipped sign, a swapped layer test or the
+    commented draft's threshold (-0.75) fails."""
+    ph = H.Physics(field_model=1)
+    g = _grid(256, 40, 1, 1.0)              # 128 cells per metre, rows every 0.025 m
+    _, y = H.cell_centres(g, ph)
+    for a in (0.7, -0.45):
+        f = H.fields(g, ph, np.array([a, 0.0, 0.3]))
+        mean = f.phi[:, :128].mean(axis=1)
+        want = np.where(y < 0.2, 0.35 * 1.2 * (1.0 + 0.2 * a), 0.35)
+        assert np.allclose(mean, want, rtol=1e-14, atol=0)
+
+
+def test_paper_porosity_x_spectrum_of_the_xi1_terms():
+    """Eq. poro_2levels with xi = (a, 0, 0): phi / (0.35 C0) = (1 + 0.15 a
+    cos 2 pi x)(1 + 0.2 a sin 64 pi x), independent of y inside a layer and
+    of period 1 in x. Its spectrum over one period has exactly five lines:
+    1 (bin 0); 0.15 a, a cosine at 1 cycle/m; 0.2 a, a sine at 32 cycles/m;
+    and the product 0.03 a^2 cos 2 pi x sin 64 pi x = 0.015 a^2 (sin 62 pi x
+    + sin 66 pi x), sines at 31 and 33 cycles/m. A swapped coordinate, a
+    wrong frequency, a sine for a cosine or a flipped sign fails."""
+    ph = H.Physics(field_model=1)
+    g = _grid(256, 40, 1, 1.0)
+    _, y = H.cell_centres(g, ph)
+    a = 0.8
+    f = H.fields(g, ph, np.array([a, 0.0, 0.0]))
+    C0 = np.where(y < 0.2, 1.2 * (1.0 + 0.2 * a), 1.0)
+    r = f.phi / (0.35 * C0[:, None])
+    assert np.allclose(r, r[:1], rtol=1e-15, atol=0)                     # no y dependence
+    assert np.allclose(r[:, :128], r[:, 128:], rtol=1e-14, atol=0)       # period 1 in x
+    X = _unit_dft(r[0, :128], axis=0)
+    want = np.zeros(128, dtype=complex)
+    want[0] = 2.0                      # the constant 1 (bin 0 counts it twice)
+    want[1] = 0.15 * a
+    want[32] = -1j * 0.2 * a
+    want[31] = want[33] = -1j * 0.015 * a * a
+    assert np.allclose(X[:64], want[:64], rtol=0, atol=1e-13)
+
+
+def test_paper_porosity_y_spectrum_of_the_xi2_terms():
+    """Eq. poro_2levels with xi = (0, b, 0): C0 does not depend on xi, so
+    phi(xi) / phi(0) = C1 C2 = (1 + 0.15 b (cos(pi x/2) - sin 2 pi y_p))
+    (1 + 0.2 b sin 32 pi y_p), y_p = y - 1. Over y in [0, 1) at a column x
+    the spectrum has exactly: bin 0, 1 + 0.15 b cos(pi x/2); a sine at 1
+    cycle/m with coefficient -0.15 b; a sine at 16 cycles/m with coefficient
+    0.2 b (1 + 0.15 b cos(pi x/2)); and the product -0.03 b^2 sin 2 pi y sin
+    32 pi y = -0.015 b^2 (cos 30 pi y - cos 34 pi y), cosines at 15 and 17
+    cycles/m. The columns x and 2 - x differ only in the sign of cos(pi x/2)."""
+    ph = H.Physics(field_model=1)
+    g = _grid(20, 128, 1, 1.0)
+    x, _ = H.cell_centres(g, ph)
+    b = -0.6
+    r = H.fields(g, ph, np.array([0.0, b, 0.0])).phi / H.fields(g, ph, np.zeros(3)).phi
+    X = _unit_dft(r, axis=0)                       # [bin, column]
+    for i in range(g.nx):
+        cx = np.cos(np.pi * x[i] / 2)
+        want = np.zeros(64, dtype=complex)
+        want[0] = 2.0 * (1.0 + 0.15 * b * cx)
+        want[1] = -1j * (-0.15 * b)
+        want[16] = -1j * 0.2 * b * (1.0 + 0.15 * b * cx)
+        want[15] = -0.015 * b * b
+        want[17] = 0.015 * b * b
+        assert np.allclose(X[:64, i], want, rtol=0, atol=1e-13), i
+    # mirror columns: the sum removes the cos(pi x/2) term
+    s = r + r[:, ::-1]
+    assert np.allclose(s, s[:, :1], rtol=1e-14, atol=0)
+
+
 def test_box_integrals_and_fresh_water_area_of_known_fields():
     """c = 1: Q_i = rho1 |Delta_i in D| (0.2 x 0.15 for the five boxes cut
     by y = 0, 0.04 otherwise), Q_FW = 0. c = 1 above y = 0.5 only: the boxes
