@@ -48,6 +48,13 @@ extern "C" {
 #define HENRY_E_TIMEOUT (-4)     /* a bounded device wait gave up             */
 #define HENRY_E_UNSUPPORTED (-5) /* grid cannot be coarsened to <= 32 cells  */
 
+/* Largest batch B of one call of the entry points that launch one grid row
+ * per sample (henry_solve, henry_solve_series, henry_sample_pairs,
+ * henry_adjoint, henry_fields, henry_residual_jacobian[_noalloc]): larger
+ * batches are rejected with HENRY_E_INVALID before any work is enqueued;
+ * split them into several calls. */
+#define HENRY_MAX_BATCH 65535
+
 /* ---- per-sample status bits (status[] outputs) ------------------------- */
 #define HENRY_S_OK 0
 #define HENRY_S_MAXIT 1          /* some time step hit newton_maxit          */
@@ -130,9 +137,15 @@ typedef struct henry_config {
                            iterations of BiCGStab on the finest-level
                            system instead, right-preconditioned by one
                            V-cycle per application (two per iteration).
-                           Use k >= 2: with k = 1 some samples of the
-                           smooth field model broke down (non-finite
-                           residual, reported in status) */
+                           k = 1 is rejected: with a single BiCGStab step
+                           per correction some samples of the smooth field
+                           model broke down (non-finite residual) */
+  double adjoint_rtol;  /* henry_adjoint: each transposed step system
+                           J_n^T lam = rhs is solved until its FP64 residual
+                           norm is below adjoint_rtol times its initial one,
+                           or, once below 1e3 adjoint_rtol times it, an
+                           iteration reduces it by less than half (the FP64
+                           rounding floor). Default 1e-14 */
 } henry_config;
 
 typedef struct henry_ctx henry_ctx; /* opaque: owns device workspaces */
@@ -286,19 +299,22 @@ int henry_residual_jacobian(const henry_config* cfg, int nx, int ny, double tau,
 
 /* henry_residual_jacobian without any device allocation. The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
- * device memory during the call -- code running inside a CUDA stream
- * capture or a graph that must not contain allocation nodes, processes whose
- * device memory is entirely owned by another allocator (a framework's
- * caching pool or a fixed memory budget), and latency-critical loops where
- * an allocation could synchronise or fail. Arguments, layouts, outputs and
- * errors are those of henry_residual_jacobian; the caller still provides
- * every input and output buffer.
+ * device memory during the call -- processes whose device memory is
+ * entirely owned by another allocator (a framework's caching pool or a
+ * fixed memory budget, where a cudaMalloc of our own could fail or fragment
+ * it), and latency-critical loops where an allocation could synchronise the
+ * device or fail part-way. Arguments, layouts, outputs and errors are those
+ * of henry_residual_jacobian; the caller still provides every input and
+ * output buffer.
  * Scratch: 5 doubles per cell and sample in a file-scope device array of
  * 2^20 doubles (8 MiB), held by every GPU that loads the library until the
  * process exits; B * nx * ny above 209715 cells is rejected with
- * HENRY_E_INVALID. The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture. Every call shares the array and it keeps
+ * HENRY_E_INVALID (as is B > HENRY_MAX_BATCH). The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current and caches it for the process; make that first call
+ * before any stream capture. The cached address does not survive
+ * cudaDeviceReset() (the module is reloaded at a new address): do not call
+ * this entry point on a device after resetting it. Every call shares the array and it keeps
  * the last call's contents; each call writes every scratch element it reads
  * before reading it, so nothing needs to start at zero. Calls that overlap
  * on the GPU (on different streams, or from different host threads) race on

@@ -45,7 +45,7 @@ class HenryConfig(ctypes.Structure):
                 ("newton_stag_tol", ctypes.c_double), ("mg_fusion", ctypes.c_int),
                 ("mg_cluster_cells", ctypes.c_int), ("mg_small_cells", ctypes.c_int),
                 ("jac_lag", ctypes.c_int), ("field_model", ctypes.c_int),
-                ("krylov_iters", ctypes.c_int)]
+                ("krylov_iters", ctypes.c_int), ("adjoint_rtol", ctypes.c_double)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}

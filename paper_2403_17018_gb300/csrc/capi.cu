@@ -94,6 +94,10 @@ int validate(const henry_config* c) {
       c->field_model < 0 || c->field_model > 1 || (c->field_model == 1 && c->n_xi != 3) ||
       c->krylov_iters < 0 || c->krylov_iters > 64)
     return fail(HENRY_E_INVALID, "bad solver parameter");
+  if (c->krylov_iters == 1)
+    return fail(HENRY_E_INVALID, "krylov_iters = 1 is rejected (BiCGStab breakdown); use 0 or >= 2");
+  if (!(c->adjoint_rtol > 0.0) || !(c->adjoint_rtol < 1e-3))
+    return fail(HENRY_E_INVALID, "adjoint_rtol must be in (0, 1e-3)");
   for (int l = 0; l < c->nlevels; ++l) {
     std::vector<henry::Geom> g;
     if (!henry::build_hierarchy(c->nx0 << l, c->ny0 << l, c->Lx, c->Ly, g))
@@ -142,6 +146,7 @@ int henry_default_config(henry_config* c) {
   c->jac_lag = 0;
   c->field_model = 0;
   c->krylov_iters = 0;
+  c->adjoint_rtol = 1e-14;
   return HENRY_OK;
 }
 
@@ -203,7 +208,7 @@ int henry_solve(henry_ctx* ctx, int level, const double* xi, const double* logk,
                 double* c_out, double* p_out, int* status, int* iters, void* stream) {
   if (!ctx) return fail(HENRY_E_INVALID, "ctx is NULL");
   if (level < 0 || level >= ctx->cfg.nlevels) return fail(HENRY_E_INVALID, "bad level");
-  if (B < 0) return fail(HENRY_E_INVALID, "B < 0");
+  if (B < 0 || B > HENRY_MAX_BATCH) return fail(HENRY_E_INVALID, "B must be in 0..65535");
   if (B == 0) return HENRY_OK;
   if (!xi || !q || !status) return fail(HENRY_E_INVALID, "xi, q and status are required");
   CKR(cudaSetDevice(ctx->device));
@@ -215,7 +220,7 @@ int henry_solve_series(henry_ctx* ctx, int level, const double* xi, const double
                        int every, double* q_series, double* q, int* status, void* stream) {
   if (!ctx) return fail(HENRY_E_INVALID, "ctx is NULL");
   if (level < 0 || level >= ctx->cfg.nlevels) return fail(HENRY_E_INVALID, "bad level");
-  if (B < 0) return fail(HENRY_E_INVALID, "B < 0");
+  if (B < 0 || B > HENRY_MAX_BATCH) return fail(HENRY_E_INVALID, "B must be in 0..65535");
   if (every < 1) return fail(HENRY_E_INVALID, "every must be >= 1");
   if (B == 0) return HENRY_OK;
   if (!xi || !q_series || !q || !status)
@@ -230,7 +235,7 @@ int henry_sample_pairs(henry_ctx* ctx, int level, const double* xi, int B, doubl
                        void* stream) {
   if (!ctx) return fail(HENRY_E_INVALID, "ctx is NULL");
   if (level < 0 || level >= ctx->cfg.nlevels) return fail(HENRY_E_INVALID, "bad level");
-  if (B < 0) return fail(HENRY_E_INVALID, "B < 0");
+  if (B < 0 || B > HENRY_MAX_BATCH) return fail(HENRY_E_INVALID, "B must be in 0..65535");
   if (level == 0 && (q_coarse || c_coarse))
     return fail(HENRY_E_INVALID, "level 0 has no coarse solve: q_coarse and c_coarse must be NULL");
   if (level > 0 && !q_coarse) return fail(HENRY_E_INVALID, "q_coarse is required for level > 0");
@@ -271,7 +276,7 @@ int henry_adjoint(henry_ctx* ctx, int level, const double* xi, const double* log
                   int* status, void* stream) {
   if (!ctx) return fail(HENRY_E_INVALID, "ctx is NULL");
   if (level < 0 || level >= ctx->cfg.nlevels) return fail(HENRY_E_INVALID, "bad level");
-  if (B < 0) return fail(HENRY_E_INVALID, "B < 0");
+  if (B < 0 || B > HENRY_MAX_BATCH) return fail(HENRY_E_INVALID, "B must be in 0..65535");
   if (qoi_id != 0 && qoi_id != 2) return fail(HENRY_E_INVALID, "qoi_id must be 0 (Q_S) or 2 (toe)");
   if (B == 0) return HENRY_OK;
   if (!xi || !q || !dq_dxi || !status) return fail(HENRY_E_INVALID, "xi, q, dq_dxi, status required");
@@ -284,7 +289,7 @@ int henry_fields(henry_ctx* ctx, int level, const double* xi, const double* logk
                  double* phi, double* K, double* qin, void* stream) {
   if (!ctx) return fail(HENRY_E_INVALID, "ctx is NULL");
   if (level < 0 || level >= ctx->cfg.nlevels) return fail(HENRY_E_INVALID, "bad level");
-  if (B < 0) return fail(HENRY_E_INVALID, "B < 0");
+  if (B < 0 || B > HENRY_MAX_BATCH) return fail(HENRY_E_INVALID, "B must be in 0..65535");
   if (B == 0) return HENRY_OK;
   if (!xi || !phi || !K || !qin) return fail(HENRY_E_INVALID, "NULL argument");
   CKR(cudaSetDevice(ctx->device));
@@ -359,7 +364,8 @@ int henry_residual_jacobian(const henry_config* cfg, int nx, int ny, double tau,
                             const double* c, const double* c_old, double* R, double* J,
                             void* stream) {
   if (!cfg) return fail(HENRY_E_INVALID, "config is NULL");
-  if (nx < 2 || ny < 1 || B < 0 || !(tau > 0)) return fail(HENRY_E_INVALID, "bad sizes");
+  if (nx < 2 || ny < 1 || B < 0 || B > HENRY_MAX_BATCH || !(tau > 0))
+    return fail(HENRY_E_INVALID, "bad sizes (nx >= 2, ny >= 1, 0 <= B <= 65535, tau > 0)");
   if (B == 0) return HENRY_OK;
   if (!phi || !K || !qin || !p || !c || !c_old || !R) return fail(HENRY_E_INVALID, "NULL argument");
   henry::Phys P{cfg->rho0, cfg->rho1 - cfg->rho0, cfg->mu, cfg->g, cfg->D, cfg->K0, cfg->phi0,

@@ -420,9 +420,10 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, ResTile tl
 // Per-sample convergence decision after k_resjac, one warp per sample:
 // sums the sample's partials in a fixed order, scales the RMS residual to
 // units of c per step, updates active / status / counters. A sample is
-// converged when r <= max(rtol r0, atol), or when r <= stag_tol and the
-// last iteration reduced r by less than half (the residual has reached the
-// FP64 rounding floor of the grid, which grows with resolution). Blocks add their
+// converged when r <= max(rtol r0, atol), or when r <= max(stag_tol,
+// stag_rel r0) and the last iteration reduced r by less than half (the
+// residual has reached the FP64 rounding floor of the grid, which grows with
+// resolution). Blocks add their
 // count of still-active samples to acc[0]; the last block to finish
 // (acc[1] counts finished blocks) publishes the total to *n_active, resets
 // acc for the next launch and, when SET_COND, sets the while-loop condition
@@ -438,7 +439,8 @@ __global__ void k_check(unsigned long long* ctr, int B, int nchunk, int ncell,
                         double* __restrict__ res_last, int* __restrict__ status,
                         int* __restrict__ iters, int* __restrict__ n_active,
                         unsigned int* __restrict__ acc, double stag_tol,
-                        cudaGraphConditionalHandle h, int* __restrict__ refresh, int lag) {
+                        cudaGraphConditionalHandle h, int* __restrict__ refresh, int lag,
+                        double stag_rel = 0.0) {
   HENRY_COUNT_LAUNCH(ctr);
   __shared__ int cnt;
   __shared__ bool last;
@@ -460,7 +462,8 @@ __global__ void k_check(unsigned long long* ctr, int B, int nchunk, int ncell,
       if (!isfinite(r)) {
         status[b] |= kStatusNonfinite;
         active[b] = 0;
-      } else if (r <= fmax(rtol * res0[b], atol) || (it > 0 && r <= stag_tol && r > 0.5 * prev)) {
+      } else if (r <= fmax(rtol * res0[b], atol) ||
+                 (it > 0 && r <= fmax(stag_tol, stag_rel * res0[b]) && r > 0.5 * prev)) {
         active[b] = 0;
       } else if (it >= maxit) {
         status[b] |= kStatusMaxit;

@@ -59,7 +59,8 @@ extern "C" int henry_residual_jacobian_noalloc(const henry_config* cfg, int nx, 
                                                const double* c, const double* c_old, double* R,
                                                double* J, void* stream) {
   if (!cfg) return fail(HENRY_E_INVALID, "config is NULL");
-  if (nx < 2 || ny < 1 || B < 0 || !(tau > 0)) return fail(HENRY_E_INVALID, "bad sizes");
+  if (nx < 2 || ny < 1 || B < 0 || B > HENRY_MAX_BATCH || !(tau > 0))
+    return fail(HENRY_E_INVALID, "bad sizes (nx >= 2, ny >= 1, 0 <= B <= 65535, tau > 0)");
   if (B == 0) return HENRY_OK;
   if (!phi || !K || !qin || !p || !c || !c_old || !R) return fail(HENRY_E_INVALID, "NULL argument");
   const size_t need = (size_t)5 * (size_t)B * (size_t)nx * (size_t)ny;

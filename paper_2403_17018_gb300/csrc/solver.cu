@@ -802,7 +802,10 @@ int Solver::adjoint_t(const double* xi, const double* logk, int B, int qoi, int 
   CK(cudaMemsetAsync(gK_, 0, n * 8, s));
   CK(cudaMemsetAsync(gphi_, 0, n * 8, s));
   CK(cudaMemsetAsync(gq_, 0, (size_t)G.ny * B * 8, s));
-  const double adj_rtol = 1e-11;
+  // transposed solves: relative tolerance, and the rounding-floor stop once
+  // the residual is within 1e3 of it (see adjoint_rtol in henry.h)
+  const double adj_rtol = cfg_.adjoint_rtol;
+  const double adj_stag = 1e3 * cfg_.adjoint_rtol;
   for (int m = nck - 2; m >= 0; --m) {
     const int n0 = slot_step(m), n1 = slot_step(m + 1);
     // recompute the segment's states from its checkpoint (bitwise the forward's)
@@ -845,7 +848,7 @@ int Solver::adjoint_t(const double* xi, const double* logk, int B, int qoi, int 
         k_check<false><<<(B + 7) / 8, kBlock, 0, s>>>(
             counter_, B, adj_nchunk_, G.ncell(), partial2_, 1.0, adj_rtol, 0.0, cfg_.newton_maxit,
             active_, it_step_, res0_, res_last_, status_w_, iters_w_, n_active_, check_acc_, 0.0, 0,
-            nullptr, 0);
+            nullptr, 0, adj_stag);
         CK(cudaMemcpyAsync(n_active_host_, n_active_, sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (*n_active_host_ == 0) break;

@@ -41,7 +41,8 @@ def test_error_strings_and_invalid_config(lib):
 @pytest.mark.parametrize("kw", [
     {"field_model": 2}, {"field_model": 1, "n_xi": 6}, {"krylov_iters": -1},
     {"krylov_iters": 65}, {"jac_lag": -1}, {"mg_small_cells": 513}, {"mg_small_cells": -1},
-    {"vcycles": 0}, {"nu1": -1}, {"precision": 2}, {"nlevels": 0},
+    {"vcycles": 0}, {"nu1": -1}, {"precision": 2}, {"nlevels": 0}, {"krylov_iters": 1},
+    {"adjoint_rtol": 0.0}, {"adjoint_rtol": 1e-2}, {"adjoint_rtol": float("nan")},
 ])
 def test_config_validation_rejects_out_of_range_options(lib, kw):
     """henry_create_levels validates the whole config before touching the
@@ -57,3 +58,17 @@ def test_new_options_default_off(lib):
     cfg = hb.default_config()
     assert (cfg.field_model, cfg.krylov_iters, cfg.jac_lag) == (0, 0, 0)
     assert cfg.mg_small_cells == 512 and cfg.newton_atol == 1e-11
+    assert cfg.adjoint_rtol == 1e-14
+
+
+@pytest.mark.parametrize("name", ["henry_residual_jacobian", "henry_residual_jacobian_noalloc"])
+def test_batches_beyond_the_grid_limit_are_rejected_before_any_work(lib, name):
+    """B > HENRY_MAX_BATCH (65535, one grid row per sample) is an invalid
+    argument, returned before any pointer is touched or kernel enqueued, so
+    this runs without a GPU (the pointers below are never dereferenced)."""
+    cfg = hb.default_config()
+    fake = ctypes.c_void_p(0x1000)
+    fn = getattr(lib, name)
+    rc = fn(ctypes.byref(cfg), 2, 1, 1.0, 65536, fake, fake, fake, fake, fake, fake, fake, None, None)
+    assert rc == -1
+    assert b"65535" in lib.henry_last_error()

@@ -1,9 +1,10 @@
 """henry_residual_jacobian_noalloc: the residual/Jacobian entry point for
-callers that cannot allocate device memory during a call (code inside a
-stream capture, processes whose device memory belongs to another allocator,
-latency-critical loops). It must give the same R and J as the allocating
-henry_residual_jacobian, call after call, although every call shares one
-file-scope scratch array; it must refuse batches larger than that array.
+callers that cannot allocate device memory during a call (processes whose
+device memory belongs to another allocator or a fixed budget,
+latency-critical loops where an allocation could synchronise or fail). It
+must give the same R and J as the allocating henry_residual_jacobian, call
+after call, although every call shares one file-scope scratch array; it
+must refuse batches larger than that array.
 
 Kept in a file of its own, collected last, so that a run stopping at the
 first failure has already run every other test.
@@ -68,6 +69,18 @@ def test_noalloc_matches_allocating_entry_point_on_two_calls():
         for m in range(20):
             jscale = max(np.max(np.abs(J0[:, m])), 1e-300)
             assert np.max(np.abs(J1[:, m] - J0[:, m])) <= 1e-11 * jscale
+
+
+def test_noalloc_residual_only_call_matches():
+    """J = NULL: only R is written, equal to the allocating entry point's."""
+    cfg, tau, t = _case(24, 12, 4, 5)
+    args = (cfg, tau, t["phi"], t["K"], t["qin"], t["p"], t["c"], t["c_old"])
+    R0, _ = hb.residual_jacobian(*args, want_J=False)
+    R1, J1 = hb.residual_jacobian(*args, want_J=False, noalloc=True)
+    torch.cuda.synchronize()
+    assert J1 is None
+    R0, R1 = R0.cpu().numpy(), R1.cpu().numpy()
+    assert np.max(np.abs(R1 - R0)) <= 1e-12 * np.max(np.abs(R0))
 
 
 def test_noalloc_rejects_batches_beyond_its_scratch():
