@@ -15,6 +15,17 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
+# GPU adjoint against the oracle's adjoint, relative to the largest
+# component. The transposed step systems are solved to the default
+# adjoint_rtol = 1e-14 (relative residual): the error of the adjoint
+# variables is about cond(J_n^T) times that tolerance, and with the paper's
+# oscillating porosity field J_n is badly enough conditioned that the former
+# 1e-11 left 1e-8 in dQ/dxi (measured: 1e-11 -> 1.1e-8 / 2.1e-8 for Q_S /
+# toe, 1e-12 -> 4.7e-9, 1e-13 and 1e-14 -> 2.3e-11; the smooth fields give
+# 2e-13 at any of them).
+ADJ_TOL = 1e-9
+
+
 @pytest.fixture(scope="module", autouse=True)
 def _cuda():
     if not torch.cuda.is_available():
@@ -43,9 +54,9 @@ def test_adjoint_matches_oracle_adjoint(precision, qoi):
         o = A.adjoint(grid, ph, xi[b].cpu().numpy(), qoi, lk[b].cpu().numpy())
         assert abs(q[b].item() - o["q"]) <= 1e-9 * abs(o["q"])
         gs = np.max(np.abs(o["dq_dxi"]))
-        assert np.max(np.abs(g[b].cpu().numpy() - o["dq_dxi"])) <= 1e-8 * gs
+        assert np.max(np.abs(g[b].cpu().numpy() - o["dq_dxi"])) <= ADJ_TOL * gs
         ls = np.max(np.abs(o["dq_dlogk"]))
-        assert np.max(np.abs(gl[b].cpu().numpy() - o["dq_dlogk"])) <= 1e-8 * ls
+        assert np.max(np.abs(gl[b].cpu().numpy() - o["dq_dlogk"])) <= ADJ_TOL * ls
 
 
 def test_checkpoint_interval_does_not_change_the_gradient():
@@ -89,26 +100,25 @@ def test_autograd_function_returns_the_adjoint_gradient():
 
 
 @pytest.mark.parametrize("precision", [hb.PREC_FP64, hb.PREC_FP32_MG])
-def test_adjoint_of_the_paper_model_matches_oracle(precision):
+@pytest.mark.parametrize("qoi", ["Q_S", "toe"])
+def test_adjoint_of_the_paper_model_matches_oracle(precision, qoi):
     """field_model 1 (multiscale two-layer porosity, Kozeny-Carman K, the
     recharge factor at the end of every step; 6 steps of 13 s so that the
-    factor varies): q, dq/dxi and dq/dlogK against the oracle's adjoint.
-    Measured agreement 1.1e-8 of the largest component, the same with both
-    multigrid precisions and with a forward solve converged 100x tighter,
-    so the bound here is 5e-8 (1e-8 for the smooth model above)."""
-    tol = 5e-8
+    factor varies): q, dq/dxi and dq/dlogK against the oracle's adjoint,
+    within 1e-9 of the largest component (measured 2.3e-11)."""
+    tol = ADJ_TOL
     cfg = tight_config(nx0=16, ny0=8, nt0=6, T=6 * 13.0, nlevels=1, field_model=1,
                        precision=precision)
     ctx = hb.Context(cfg)
     B = 2
     xi = torch.from_numpy(xi_batch(0, 40, B)).cuda()
     lk = torch.from_numpy(logk_perturbation(8, 16, B)).cuda()
-    q, g, gl, st = ctx.adjoint(0, xi, lk, qoi="Q_S", ckpt_every=4)
+    q, g, gl, st = ctx.adjoint(0, xi, lk, qoi=qoi, ckpt_every=4)
     assert st.cpu().numpy().tolist() == [0] * B
     ph = oracle_physics(cfg)
     grid = H.Grid(nx=16, ny=8, nt=6, T=6 * 13.0)
     for b in range(B):
-        o = A.adjoint(grid, ph, xi[b].cpu().numpy(), "Q_S", lk[b].cpu().numpy())
+        o = A.adjoint(grid, ph, xi[b].cpu().numpy(), qoi, lk[b].cpu().numpy())
         assert abs(q[b].item() - o["q"]) <= 1e-9 * abs(o["q"])
         assert np.max(np.abs(g[b].cpu().numpy() - o["dq_dxi"])) <= tol * np.max(np.abs(o["dq_dxi"]))
         ls = np.max(np.abs(o["dq_dlogk"]))
