@@ -357,16 +357,33 @@ int henry_debug_copy(henry_ctx* ctx, int level, int role, int mg_level, int what
 
 /* Kernel timing for roofline reports: replays one kernel of the solver that
  * served `level` (role as in henry_debug_copy) on its current workspace,
- * `reps` times between two CUDA events on `stream`, after one untimed
- * launch; the solver must have run a solve of `batch` samples before.
+ * `reps` times on `stream`, after one untimed launch; the solver must have
+ * run a solve before (the replay uses that solve's batch).
  * which: 0 red half-sweep of the block Gauss-Seidel smoother on the finest
  * multigrid level; 1 the FP64 residual + Jacobian kernel of the finest level.
+ * flush, flush_bytes: optional device buffer (NULL, 0 for none). When
+ * given, every timed launch is preceded by a write of flush_bytes bytes to
+ * it (larger than the L2 cache: each launch starts cold) and is timed by its
+ * own pair of CUDA events, the flush excluded; without it the reps launches
+ * run back to back between two events.
  * Outputs the average duration of one launch [ms], its algorithmic DRAM
- * bytes (every array read or written once) and its FP64 + FP32 floating
- * point operations (FMA = 2). Synchronises the stream. The replay changes
- * the workspace (not the caller's outputs). */
-int henry_time_kernel(henry_ctx* ctx, int level, int role, int which, int reps, void* stream,
-                      double* avg_ms, double* bytes, double* flops);
+ * bytes (the method's per-cell figures: smoother 26 values of the multigrid
+ * type per updated cell -- operator 20, b 2, x read 2 and written 2;
+ * residual + Jacobian 56 B + 20 values per cell) and its FP64 + FP32
+ * floating point operations (FMA = 2). Synchronises the stream. The replay
+ * changes the workspace (not the caller's outputs). */
+int henry_time_kernel(henry_ctx* ctx, int level, int role, int which, int reps, void* flush,
+                      int64_t flush_bytes, void* stream, double* avg_ms, double* bytes,
+                      double* flops);
+
+/* Measured FP64 FMA throughput of this GPU [TFLOP/s], the denominator of
+ * the FP64-pipe fraction in roofline reports (GB300 has no published
+ * dense-FP64 figure to use instead): one launch of 152 x 8 blocks of 256
+ * threads, each running 8 independent FMA chains of 512 * reps steps,
+ * timed with CUDA events on `stream` after one warm-up launch; reps 1..1000.
+ * Allocates and frees a small result buffer (stream-ordered). Synchronises
+ * the stream. */
+int henry_probe_fp64(int reps, void* stream, double* tflops);
 
 /* Device kernel launches issued by this context since creation (counts
  * every launch, including those replayed inside CUDA graphs). */

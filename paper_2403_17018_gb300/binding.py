@@ -95,8 +95,9 @@ def load():
                                  ctypes.POINTER(I)]),
         "henry_launch_count": (ctypes.c_int64, [P]),
         "henry_debug_copy": (I, [P, I, I, I, I, V, ctypes.c_int64]),
-        "henry_time_kernel": (I, [P, I, I, I, I, V, ctypes.POINTER(D), ctypes.POINTER(D),
-                                  ctypes.POINTER(D)]),
+        "henry_time_kernel": (I, [P, I, I, I, I, V, ctypes.c_int64, V, ctypes.POINTER(D),
+                                  ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "henry_probe_fp64": (I, [I, V, ctypes.POINTER(D)]),
         "henry_strerror": (ctypes.c_char_p, [I]),
         "henry_last_error": (ctypes.c_char_p, []),
     }
@@ -192,11 +193,15 @@ class Context:
                                          buf.ctypes.data_as(ctypes.c_void_p), nbytes))
         return buf
 
-    def time_kernel(self, level, role, which, reps=20, stream=None):
-        """henry_time_kernel: (avg ms per launch, algorithmic bytes, flops)."""
+    def time_kernel(self, level, role, which, reps=20, flush=None, stream=None):
+        """henry_time_kernel: (avg ms per launch, algorithmic bytes, flops).
+        flush: a CUDA tensor larger than L2, overwritten before every timed
+        launch (each launch then starts cold and is timed on its own)."""
         ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
-        _check(self.lib.henry_time_kernel(self._h, level, role, which, reps, _stream(stream),
-                                          ctypes.byref(ms), ctypes.byref(by), ctypes.byref(fl)))
+        fb = 0 if flush is None else flush.numel() * flush.element_size()
+        _check(self.lib.henry_time_kernel(self._h, level, role, which, reps, _ptr(flush), fb,
+                                          _stream(stream), ctypes.byref(ms), ctypes.byref(by),
+                                          ctypes.byref(fl)))
         return ms.value, by.value, fl.value
 
     def launch_count(self) -> int:
@@ -317,6 +322,13 @@ class Context:
                                      _ptr(logk, torch.float64, (B, li.ny, li.nx), "logk"), B,
                                      _ptr(phi), _ptr(K), _ptr(qin), _stream(stream)))
         return phi, K, qin
+
+
+def probe_fp64(reps=40, stream=None):
+    """henry_probe_fp64: measured FP64 FMA throughput of the GPU [TFLOP/s]."""
+    v = ctypes.c_double()
+    _check(load().henry_probe_fp64(int(reps), _stream(stream), ctypes.byref(v)))
+    return v.value
 
 
 def new_field_accumulator(ny, nx, device="cuda"):

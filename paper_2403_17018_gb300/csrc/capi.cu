@@ -24,6 +24,8 @@ cudaError_t launch_residual_jacobian(const Phys& P, const Geom& G, double tau, i
                                      const double* p, const double* c, const double* c_old,
                                      double* R, double* J, double* scratch, cudaStream_t s);
 int or_status(const int* src, int* dst, int B, unsigned long long* ctr, cudaStream_t s);
+constexpr int kProbeThreads = 152 * 8 * 256;
+cudaError_t probe_fp64(int reps, double* out, cudaStream_t s, double* tflops);
 }  // namespace henry
 
 using henry::Solver;
@@ -394,16 +396,30 @@ int henry_debug_copy(henry_ctx* ctx, int level, int role, int mg_level, int what
   return HENRY_OK;
 }
 
-int henry_time_kernel(henry_ctx* ctx, int level, int role, int which, int reps, void* stream,
-                      double* avg_ms, double* bytes, double* flops) {
+int henry_time_kernel(henry_ctx* ctx, int level, int role, int which, int reps, void* flush,
+                      int64_t flush_bytes, void* stream, double* avg_ms, double* bytes,
+                      double* flops) {
   if (!ctx || level < 0 || level >= ctx->cfg.nlevels || role < 0 || role > 1 || !avg_ms ||
       !bytes || !flops)
     return fail(HENRY_E_INVALID, "bad argument");
   const auto& s = ctx->role[role][level];
   if (!s) return fail(HENRY_E_INVALID, "no solver has run for this level and role");
   CKR(cudaSetDevice(ctx->device));
-  int rc = s->time_kernel(which, reps, (cudaStream_t)stream, avg_ms, bytes, flops);
-  if (rc) return fail(rc, "time_kernel failed (which, reps or no previous solve)");
+  int rc = s->time_kernel(which, reps, (cudaStream_t)stream, flush, flush_bytes, avg_ms, bytes,
+                          flops);
+  if (rc) return fail(rc, "time_kernel failed (which, reps, flush buffer or no previous solve)");
+  return HENRY_OK;
+}
+
+int henry_probe_fp64(int reps, void* stream, double* tflops) {
+  if (reps < 1 || reps > 1000 || !tflops) return fail(HENRY_E_INVALID, "bad argument");
+  double* out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  CKR(cudaMallocAsync((void**)&out, sizeof(double) * henry::kProbeThreads, s));
+  const cudaError_t e = henry::probe_fp64(reps, out, s, tflops);
+  const cudaError_t e2 = cudaFreeAsync(out, s);
+  CKR(e);
+  CKR(e2);
   return HENRY_OK;
 }
 

@@ -641,20 +641,30 @@ void Solver::launch_timed(int which, int B, cudaStream_t s) {
   }
 }
 
-// Algorithmic counts per launch (each array read or written once):
-//  smoother half-sweep, per updated cell: J 20, b 2, x write 2, neighbour x
-//    read 2 values of the type T; FP ops: 16 neighbour products (FMA, 32
-//    FLOP) + the product with the stored inverse diagonal block (2 mul + 2
-//    FMA, 6 FLOP) = 38 FLOP.
-//  residual + Jacobian, per cell: p, c, c_old, phi, tx, dx, ty, dy read (8
-//    doubles), b 2, x 2, J 20 of type T and qx, qy (2 doubles) written;
-//    FP ops counted from the face-based code: 2 faces x 15 (flux) + 16
+// Algorithmic counts per launch, the per-cell figures of the method's byte
+// model (every array read or written once per launch, neighbour values
+// reused on chip):
+//  smoother half-sweep, per updated cell: operator A (20 values), b (2),
+//    x read (2, the other colour) and written (2) = 26 values of type T
+//    (104 B FP32, 208 B FP64). The row-scaled storage reads 16 operator
+//    values instead of 20, so the kernel moves 22 values: the figure above
+//    credits it with the unscaled operator's bytes. FP ops: 16 FMA per
+//    update (32 FLOP).
+//  residual + Jacobian, per cell: p, c, c_old, phi, K read (40 B), R written
+//    (16 B), J written (20 values of type T): 136 B (FP32 J) or 216 B. FP
+//    ops counted from the face-based code: 2 faces x 15 (flux) + 16
 //    (accumulation, sums, norm) = 46 FP64 operations, plus the Jacobian,
-//    2 faces x 30 + 24 = 84 operations in the multigrid type (FP64 or
-//    FP32). The figure reported is the FP64 count: 46 + (84 if T = double).
-int Solver::time_kernel(int which, int reps, cudaStream_t s, double* avg_ms, double* bytes,
-                        double* flops) {
-  if (which < 0 || which > 1 || reps < 1 || last_B_ < 1) return HENRY_E_INVALID;
+//    2 faces x 30 + 24 = 84 operations in the multigrid type; the figure
+//    reported is the FP64 count: 46 + (116 if T = double).
+// flush (optional): before every timed launch `flush_bytes` bytes of
+// `flush` are overwritten (cudaMemsetAsync), so that each launch starts
+// with cold caches when flush_bytes exceeds the L2; every launch is then
+// timed by its own event pair and the flush is not counted.
+int Solver::time_kernel(int which, int reps, cudaStream_t s, void* flush, int64_t flush_bytes,
+                        double* avg_ms, double* bytes, double* flops) {
+  if (which < 0 || which > 1 || reps < 1 || reps > 100000 || last_B_ < 1 || flush_bytes < 0 ||
+      (flush_bytes > 0 && !flush))
+    return HENRY_E_INVALID;
   const int B = last_B_;
   // all samples active for the replay
   std::vector<int> ones(B, 1);
@@ -664,28 +674,51 @@ int Solver::time_kernel(int which, int reps, cudaStream_t s, double* avg_ms, dou
     else launch_timed<double>(which, B, s);
   };
   launch();
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
-  CK(cudaEventRecord(e0, s));
-  for (int r = 0; r < reps; ++r) launch();
-  CK(cudaEventRecord(e1, s));
-  CK(cudaEventSynchronize(e1));
+  const int nev = flush_bytes > 0 ? reps : 1;
+  std::vector<cudaEvent_t> e0(nev, nullptr), e1(nev, nullptr);
+  int rc = HENRY_OK;
+  for (int r = 0; r < nev && rc == HENRY_OK; ++r) {
+    if (cudaEventCreate(&e0[r]) != cudaSuccess || cudaEventCreate(&e1[r]) != cudaSuccess)
+      rc = HENRY_E_CUDA;
+  }
   float ms = 0.f;
-  CK(cudaEventElapsedTime(&ms, e0, e1));
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  if (rc == HENRY_OK) {
+    if (flush_bytes > 0) {
+      for (int r = 0; r < reps; ++r) {
+        cudaMemsetAsync(flush, r & 0xff, (size_t)flush_bytes, s);
+        cudaEventRecord(e0[r], s);
+        launch();
+        cudaEventRecord(e1[r], s);
+      }
+    } else {
+      cudaEventRecord(e0[0], s);
+      for (int r = 0; r < reps; ++r) launch();
+      cudaEventRecord(e1[0], s);
+    }
+    if (cudaEventSynchronize(e1[nev - 1]) != cudaSuccess) rc = HENRY_E_CUDA;
+    for (int r = 0; r < nev && rc == HENRY_OK; ++r) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, e0[r], e1[r]) != cudaSuccess) rc = HENRY_E_CUDA;
+      ms += t;
+    }
+  }
+  for (int r = 0; r < nev; ++r) {
+    if (e0[r]) cudaEventDestroy(e0[r]);
+    if (e1[r]) cudaEventDestroy(e1[r]);
+  }
+  if (rc != HENRY_OK) {
+    set_last_error(std::string("time_kernel: ") + cudaGetErrorString(cudaGetLastError()));
+    return rc;
+  }
   const Geom& G = levels_.back().g;
   const double T = (double)tsize_;
   if (which == 0) {
     const double cells = (double)B * G.half();
-    // 16 scaled operator values + 2 rhs read, 2 unknowns written, 2 neighbour
-    // unknowns read per update (the other two come from cache); 16 FMA
-    *bytes = cells * 22.0 * T;
+    *bytes = cells * 26.0 * T;
     *flops = cells * 32.0;
   } else {
     const double cells = (double)B * G.ncell();
-    *bytes = cells * (8.0 * 8 + 28.0 * T + 16.0);
+    *bytes = cells * (40.0 + 16.0 + 20.0 * T);
     *flops = cells * (46.0 + (tsize_ == sizeof(double) ? 116.0 : 0.0));
   }
   *avg_ms = ms / reps;

@@ -65,8 +65,8 @@ class Solver {
   int n_mg() const { return (int)levels_.size(); }
   unsigned long long launches() const;
   // Time one kernel of the finest level (see henry_time_kernel).
-  int time_kernel(int which, int reps, cudaStream_t s, double* avg_ms, double* bytes,
-                  double* flops);
+  int time_kernel(int which, int reps, cudaStream_t s, void* flush, int64_t flush_bytes,
+                  double* avg_ms, double* bytes, double* flops);
   int batch() const { return last_B_; }
   // Copy an internal array (see henry_debug_copy); returns HENRY_* code.
   int debug_copy(int mg_level, int what, void* dst, int64_t bytes) const;

@@ -25,6 +25,7 @@ of every batch and the per-level statistics are merged with Chan's formula.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -333,6 +334,70 @@ def run(sampler, L, eps, qois=(3, 4, 5), pilot=None, max_batch=None, var_budget_
             "state": [lv.to_json() for lv in local]}
 
 
+TUNE_CANDIDATES = {"vcycles": (2, 3), "nu": ((2, 2), (3, 3)), "small_cells": (128, 512),
+                   "jac_lag": (0, 10, 30)}
+
+
+def tuned_schedules(levels, precision, n_xi, nx0=32, ny0=16, world=1, extra=None,
+                    paper_workload=False, candidates=None):
+    """Autotuned multigrid schedule of every level (autotune.tune_level on at
+    most 1024 pairs and about 24 steps of the level), cached by GPU, level,
+    precision, batch and workload. Returns (schedules, seconds spent)."""
+    import torch
+    from paper_2403_17018_gb300 import autotune as A
+    A.CANDIDATES = dict(candidates or TUNE_CANDIDATES)
+    tag = "" if candidates is None else "|c" + hashlib.sha1(
+        json.dumps(candidates, sort_keys=True).encode()).hexdigest()[:8]
+    t0 = time.perf_counter()
+    schedules = {}
+    gpu = torch.cuda.get_device_name(0)
+    cache = A.load_cache()
+    for l in range(levels):
+        B = min(1024, max(1, max(32, 16384 >> (2 * l)) // world))
+        key = A._key(gpu, l, precision, B, nx0, ny0) + f"|xi{n_xi}|lag" + (
+            "|paper" if paper_workload else "") + tag
+        if key not in cache:
+            cache[key], _ = A.tune_level(l, B, precision, steps=24, reps=1, splits=(1,),
+                                         n_xi=n_xi, cfg_extra=extra or {})
+        schedules[l] = cache[key]
+    A.save_cache(cache)
+    return schedules, time.perf_counter() - t0
+
+
+def tuned_run(levels=6, eps=1e-3, n_xi=6, precision="fp32mg", vcycles=3, tune=True, qois=(3, 4, 5),
+              adaptive_levels=False, relative=False, paper_workload=False, concurrent=True,
+              candidates=None, log=None, rank=0, world=1, dist=None):
+    """Adaptive MLMC to RMSE eps on levels 0..levels-1 (config 5 by default:
+    6 levels 32x16 .. 1024x512, 6 random variables, RMSE 1e-3 on c at the
+    three points), with the schedules autotuned first (the tuning time is
+    reported apart from the MLMC wall time). Returns run()'s dict plus the
+    precision, tuning time and schedules."""
+    from paper_2403_17018_gb300 import binding as hb
+    extra = {}
+    if paper_workload:
+        extra = {"field_model": 1, "T": 6016.0, "nt0": 94}
+        n_xi = 3
+    cfg = hb.default_config(nlevels=levels, n_xi=n_xi, vcycles=vcycles,
+                            precision=hb.PREC_FP64 if precision == "fp64" else hb.PREC_FP32_MG,
+                            **extra)
+    schedules, tune_s = None, 0.0
+    if tune:
+        schedules, tune_s = tuned_schedules(levels, precision, n_xi, cfg.nx0, cfg.ny0, world, extra,
+                                            paper_workload, candidates)
+    sampler = GpuSampler(cfg, rank, world, schedules=schedules)
+    res = run(sampler, levels - 1, eps, qois=tuple(qois), log=log, dist=dist,
+              concurrent=concurrent, adaptive_levels=adaptive_levels, relative=relative)
+    for ctx in {id(c): c for c in sampler.ctxs.values()}.values():
+        ctx.close()
+    res["paper_workload"] = paper_workload
+    res.update({"precision": precision, "n_gpus": world, "tuning_s": tune_s,
+                "concurrent_levels": concurrent,
+                "schedules": {l: {k: v for k, v in sc.items() if k in ("vcycles", "nu1", "nu2",
+                                                                      "mg_small_cells", "jac_lag")}
+                              for l, sc in (schedules or {}).items()}})
+    return res
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--levels", type=int, default=6)
@@ -359,14 +424,9 @@ def main(argv=None):
                          "three points (3 4 5)")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
-    extra = {}
-    if a.paper_workload:
-        extra = {"field_model": 1, "T": 6016.0, "nt0": 94}
-        a.n_xi = 3
     import torch
     import __graft_entry__
     __graft_entry__.build()
-    from paper_2403_17018_gb300 import binding as hb
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None
@@ -374,41 +434,10 @@ def main(argv=None):
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
-    cfg = hb.default_config(nlevels=a.levels, n_xi=a.n_xi, vcycles=a.vcycles,
-                            precision=hb.PREC_FP64 if a.precision == "fp64" else hb.PREC_FP32_MG,
-                            **extra)
-    schedules, tune_s = None, 0.0
-    if a.tune:
-        from paper_2403_17018_gb300 import autotune as A
-        # the schedules that won on some level of the batched benchmark
-        A.CANDIDATES = {"vcycles": (2, 3), "nu": ((2, 2), (3, 3)), "small_cells": (128, 512),
-                        "jac_lag": (0, 10, 30)}
-        t0 = time.perf_counter()
-        schedules = {}
-        gpu = torch.cuda.get_device_name(0)
-        cache = A.load_cache()
-        for l in range(a.levels):
-            # tuned on at most 1024 pairs and about 24 steps of the level
-            B = min(1024, max(1, max(32, 16384 >> (2 * l)) // world))
-            key = A._key(gpu, l, a.precision, B, cfg.nx0, cfg.ny0) + f"|xi{a.n_xi}|lag" + (
-                "|paper" if a.paper_workload else "")
-            if key not in cache:
-                cache[key], _ = A.tune_level(l, B, a.precision, steps=24, reps=1, splits=(1,),
-                                             n_xi=a.n_xi, cfg_extra=extra)
-            schedules[l] = cache[key]
-        A.save_cache(cache)
-        tune_s = time.perf_counter() - t0
-    sampler = GpuSampler(cfg, rank, world, schedules=schedules)
     log = (lambda d: print(json.dumps(d), flush=True)) if rank == 0 else None
-    res = run(sampler, a.levels - 1, a.eps, qois=tuple(a.qois or (3, 4, 5)), log=log, dist=dist,
-              concurrent=not a.sequential, adaptive_levels=a.adaptive_levels,
-              relative=a.relative)
-    res["paper_workload"] = a.paper_workload
-    res.update({"precision": a.precision, "n_gpus": world, "tuning_s": tune_s,
-                "concurrent_levels": not a.sequential,
-                "schedules": {l: {k: v for k, v in sc.items() if k in ("vcycles", "nu1", "nu2",
-                                                                      "mg_small_cells", "jac_lag")}
-                              for l, sc in (schedules or {}).items()}})
+    res = tuned_run(a.levels, a.eps, a.n_xi, a.precision, a.vcycles, a.tune,
+                    tuple(a.qois or (3, 4, 5)), a.adaptive_levels, a.relative, a.paper_workload,
+                    not a.sequential, log=log, rank=rank, world=world, dist=dist)
     if rank == 0:
         out = {k: v for k, v in res.items() if k != "state"}
         print(json.dumps(out))
