@@ -66,6 +66,10 @@ def parse():
                     help="host: the same solves with the host-side Newton loop (plain kernel "
                          "launches, bitwise the same results); for ncu launch lists, which do "
                          "not enter the conditional graph bodies of the default loop")
+    ap.add_argument("--pairs", default="graph", choices=["graph", "streams"],
+                    help="graph: all level pairs of a step through henry_sample_levels (one "
+                         "graph launch per coarse time step); streams: henry_sample_pairs per "
+                         "level on four streams")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-multigrid variant")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the discrete-adjoint timing")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -183,54 +187,62 @@ def make_inputs(rank, n_xi=3):
 
 
 class Workload:
-    """One context per level (its schedule autotuned), one stream per level."""
+    """One context for the four levels, each level with its autotuned
+    schedule (henry_set_schedule). pairs="graph": a step is one
+    henry_sample_levels call (one CUDA graph launch per coarse time step for
+    all level pairs); pairs="streams": henry_sample_pairs per level on four
+    streams."""
 
-    def __init__(self, precision, schedules, loop_mode):
+    def __init__(self, precision, schedules, loop_mode, pairs="graph"):
         import torch
         from paper_2403_17018_gb300 import binding as hb
         self.hb = hb
-        self.ctxs = {}
+        self.ctx = hb.Context(hb.default_config(nlevels=4, precision=precision,
+                                                loop_mode=loop_mode))
+        self.schedules = schedules
         for l in LEVELS:
-            sc = schedules[l]
-            cfg = hb.default_config(nlevels=4, precision=precision, vcycles=sc["vcycles"],
-                                    nu1=sc["nu1"], nu2=sc["nu2"],
-                                    mg_small_cells=sc.get("mg_small_cells", 512),
-                                    jac_lag=sc.get("jac_lag", 0), loop_mode=loop_mode)
-            self.ctxs[l] = hb.Context(cfg)
-        self.cfg = self.ctxs[0].cfg
+            self.ctx.set_schedule(l, **schedules[l])
+        self.cfg = self.ctx.cfg
         self.T = 8 if precision == hb.PREC_FP64 else 4
+        self.pairs = pairs
         self.streams = {l: torch.cuda.Stream() for l in LEVELS}
         self.out = {}
 
     def launch_count(self):
-        return sum(c.launch_count() for c in self.ctxs.values())
+        return self.ctx.launch_count()
 
     def close(self):
-        for c in self.ctxs.values():
-            c.close()
+        self.ctx.close()
 
     def step(self, xis, host=None):
-        """Enqueue all level pairs; then merge level statistics (synchronous
-        per level). With `host` = dict of pinned buffers, copy xi in from
-        host memory and the QoIs back to host memory inside the step."""
+        """All level pairs, then the per-level statistics (synchronous per
+        level). With `host` = dict of pinned buffers, copy xi in from host
+        memory and the QoIs back to host memory inside the step."""
         import torch
         main = torch.cuda.current_stream()
-        ev = torch.cuda.Event()
-        ev.record(main)
-        for l in LEVELS:
-            s = self.streams[l]
-            s.wait_event(ev)
-            with torch.cuda.stream(s):
-                xi = xis[l]
-                if host is not None:
-                    xi.copy_(host["xi"][l], non_blocking=True)
-                self.out[l] = self.ctxs[l].sample_pairs(l, xi, stream=s)
+        if self.pairs == "graph":
+            if host is not None:
+                for l in LEVELS:
+                    xis[l].copy_(host["xi"][l], non_blocking=True)
+            self.out = self.ctx.sample_levels({l: xis[l] for l in LEVELS})
+            streams = {l: main for l in LEVELS}
+        else:
+            ev = torch.cuda.Event()
+            ev.record(main)
+            for l in LEVELS:
+                s = self.streams[l]
+                s.wait_event(ev)
+                with torch.cuda.stream(s):
+                    if host is not None:
+                        xis[l].copy_(host["xi"][l], non_blocking=True)
+                    self.out[l] = self.ctx.sample_pairs(l, xis[l], stream=s)
+            streams = self.streams
         stats = {}
         for l in LEVELS:
-            s = self.streams[l]
+            s = streams[l]
             qf, qc, _, _, st = self.out[l]
             S = self.hb.LevelStats()
-            self.ctxs[l].level_stats(l, qf, qc, st, S, stream=s)
+            self.ctx.level_stats(l, qf, qc, st, S, stream=s)
             stats[l] = S
             if host is not None:
                 with torch.cuda.stream(s):
@@ -238,10 +250,11 @@ class Workload:
                     if qc is not None:
                         host["qc"][l].copy_(qc, non_blocking=True)
                     host["st"][l].copy_(st, non_blocking=True)
-        for l in LEVELS:
-            e = torch.cuda.Event()
-            e.record(self.streams[l])
-            main.wait_event(e)
+        if self.pairs != "graph":
+            for l in LEVELS:
+                e = torch.cuda.Event()
+                e.record(self.streams[l])
+                main.wait_event(e)
         return stats
 
 
@@ -251,7 +264,7 @@ def tune_schedules(precision_name):
     timed on one solve of the level over the whole horizon."""
     from paper_2403_17018_gb300 import autotune as A
     A.CANDIDATES = {"vcycles": (2, 3), "nu": ((2, 2), (3, 3)), "small_cells": (0, 128, 512),
-                    "jac_lag": (0, 10, 30)}
+                    "jac_lag": (0, 10, 30), "res_rows": (0, 2, 16)}
     out = {}
     for l in LEVELS:
         best, _ = A.tune_level(l, BATCH[l], precision_name, steps=None, reps=1, splits=(1,))
@@ -260,7 +273,8 @@ def tune_schedules(precision_name):
 
 
 def sched_str(s):
-    return f"V({s['nu1']},{s['nu2']}) x{s['vcycles']} smem<={s['mg_small_cells']} lag={s['jac_lag']}"
+    return (f"V({s['nu1']},{s['nu2']}) x{s['vcycles']} smem<={s['mg_small_cells']} "
+            f"lag={s['jac_lag']} rows={s.get('res_rows', 0)}")
 
 
 def time_steps(wl, xis, K, W, barrier, flush, host=None):
@@ -297,7 +311,7 @@ def per_level_rates(wl, xis):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record()
-        wl.ctxs[l].sample_pairs(l, xis[l])
+        wl.ctx.sample_pairs(l, xis[l])
         e1.record()
         torch.cuda.synchronize()
         rates[f"L{l}"] = round(BATCH[l] / (e0.elapsed_time(e1) / 1e3), 2)
@@ -310,9 +324,9 @@ def whole_level(wl, xis, hbm):
     the solve took, reported by the solver) over its device time."""
     import torch
     out = {}
+    ctx = wl.ctx
     for l in LEVELS:
-        ctx = wl.ctxs[l]
-        cfg = ctx.cfg
+        sc = wl.schedules[l]
         li = ctx.level_info(l)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -322,7 +336,8 @@ def whole_level(wl, xis, hbm):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         its = int(res["iters"].sum().item())
-        by = solve_bytes(li.nx * li.ny, BATCH[l], li.nt, its, wl.T, cfg.vcycles, cfg.nu1, cfg.nu2)
+        by = solve_bytes(li.nx * li.ny, BATCH[l], li.nt, its, wl.T, sc["vcycles"], sc["nu1"],
+                         sc["nu2"])
         gbs = by / (ms / 1e3) / 1e9
         out[f"L{l}"] = {"solve_ms": round(ms, 2), "iters_per_step": round(its / BATCH[l] / li.nt, 3),
                         "bytes": by, "achieved_gbs": round(gbs, 1), "frac": round(gbs / hbm, 4)}
@@ -632,7 +647,7 @@ def main():
 
     # ---- headline: FP64 multigrid ------------------------------------------
     sched64 = tune_schedules("fp64")
-    wl = Workload(hb.PREC_FP64, sched64, loop)
+    wl = Workload(hb.PREC_FP64, sched64, loop, args.pairs)
     clocks = ClockSampler(local)
     clocks.start()
     ms, per_step, launches, stats = time_steps(wl, xis, K, W, barrier, flush)
@@ -659,21 +674,21 @@ def main():
     rates64 = per_level_rates(wl, xis) if extra else None
     levels64 = whole_level(wl, xis, hbm) if extra else None
     fp64_tflops = hb.probe_fp64(reps=40)
-    roof = roofline(wl.ctxs[3], flush_buf, peaks, fp64_tflops)
+    roof = roofline(wl.ctx, flush_buf, peaks, fp64_tflops)
     wl.close()
 
     # ---- FP32 multigrid inside FP64 defect correction, same workload -------
     fp32 = None
     if not args.no_fp32:
         sched32 = tune_schedules("fp32mg")
-        wl32 = Workload(hb.PREC_FP32_MG, sched32, loop)
+        wl32 = Workload(hb.PREC_FP32_MG, sched32, loop, args.pairs)
         ms32, _, launches32, _ = time_steps(wl32, xis, K, W, barrier, flush)
         fp32 = {"value": round(pairs_per_step * world * K / (ms32 / 1e3), 2),
                 "ms_per_step": round(ms32 / K, 2), "per_level": per_level_rates(wl32, xis),
                 "gpu_launches": launches32,
                 "schedule": {f"L{l}": sched_str(s) for l, s in sched32.items()},
                 "whole_level": whole_level(wl32, xis, hbm),
-                "smoother_cold": kernel_line(wl32.ctxs[3], 3, 0, 50, flush_buf, hbm, fp64_tflops,
+                "smoother_cold": kernel_line(wl32.ctx, 3, 0, 50, flush_buf, hbm, fp64_tflops,
                                              4, "k_smooth<float> red half-sweep, level 3 "
                                                 "(256x128 x 16), cold")}
         wl32.close()
@@ -694,7 +709,7 @@ def main():
             "data": "synthetic (seeded SplitMix64 xi ~ U[-1,1]^3)",
             "config": dict(CONFIG, parallelism=f"{world} GPU(s), samples sharded, 4 level streams"),
             "schedule": {f"L{l}": sched_str(s) for l, s in sched64.items()},
-            "loop": args.loop,
+            "loop": args.loop, "pairs": args.pairs,
             "per_level": rates64, "whole_level": levels64, "failed_samples": bad,
             "roofline": roof, "streaming": stream, "clocks": clk, "gpu_launches": launches,
             "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -146,6 +146,11 @@ typedef struct henry_config {
                            or, once below 1e3 adjoint_rtol times it, an
                            iteration reduces it by less than half (the FP64
                            rounding floor). Default 1e-14 */
+  int res_rows;         /* rows of cells one thread of the residual/Jacobian
+                           kernel walks (its tile height per row group),
+                           1..64; 0 (default): 8. A schedule knob for the
+                           autotuner: it trades blocks per sample against
+                           recomputed faces at tile edges */
 } henry_config;
 
 typedef struct henry_ctx henry_ctx; /* opaque: owns device workspaces */
@@ -216,6 +221,46 @@ int henry_solve_series(henry_ctx* ctx, int level, const double* xi, const double
 int henry_sample_pairs(henry_ctx* ctx, int level, const double* xi, int B,
                        double* q_fine, double* q_coarse, double* c_fine, double* c_coarse,
                        int* status, void* stream);
+
+/* Multigrid schedule of one MLMC level (the autotuner's knobs; meanings as
+ * the henry_config fields of the same names). */
+typedef struct henry_schedule {
+  int vcycles, nu1, nu2, mg_small_cells, jac_lag, res_rows;
+} henry_schedule;
+
+/* Give MLMC level `level` its own schedule: the fine solves of level l
+ * (henry_solve, the fine half of the pairs of level l) and the coarse half
+ * (level l-1) of the pairs of level l use it; the context's config is kept
+ * for every other field. Synchronises the device and drops that level's
+ * workspaces (rebuilt on the next call). Errors: HENRY_E_INVALID (bad
+ * level or out-of-range knob), HENRY_E_CUDA. */
+int henry_set_schedule(henry_ctx* ctx, int level, const henry_schedule* sched);
+
+/* One level's pairs for henry_sample_levels; arguments as henry_sample_pairs. */
+typedef struct henry_level_batch {
+  int level, B;
+  const double* xi;   /* device [B][n_xi]                                    */
+  double* q_fine;     /* device [B][HENRY_NQ] out                            */
+  double* q_coarse;   /* device [B][HENRY_NQ] out; NULL at level 0           */
+  double* c_fine;     /* device [B][ny_l][nx_l] out, or NULL                 */
+  double* c_coarse;   /* device [B][ny_{l-1}][nx_{l-1}] out, or NULL         */
+  int* status;        /* device int [B] out, OR of both solves' bits         */
+} henry_level_batch;
+
+/* The level pairs of one MLMC round, several levels at once (Eq. A, one
+ * batch per level, at most one batch per level): results bitwise equal to
+ * henry_sample_pairs called for each batch. With the graph loop (the
+ * default) every solver involved advances together: the implicit steps of
+ * one coarse (level-0) time step -- 2^l steps of each level-l solve and
+ * 2^(l-1) of its coarse half, each step with its device-side Newton loop --
+ * form ONE CUDA graph whose branches run concurrently, launched nt0 times
+ * on `stream` (one launch per coarse step for all levels); the field
+ * set-up before and the QoIs after are plain launches on `stream`. The
+ * graph is kept and relaunched while the levels, batches and workspaces are
+ * unchanged. With the host loop the batches run one level after another.
+ * Errors: HENRY_E_INVALID (n outside 1..nlevels, a level twice, B outside
+ * 0..HENRY_MAX_BATCH, NULL arrays), HENRY_E_CUDA, HENRY_E_NOMEM. */
+int henry_sample_levels(henry_ctx* ctx, const henry_level_batch* batches, int n, void* stream);
 
 /* Discrete adjoint of one QoI through the implicit Euler time stepping
  * (section 2.3), for B samples of level `level`: with R^n(u^n, u^{n-1}) = 0
@@ -379,7 +424,7 @@ int henry_time_kernel(henry_ctx* ctx, int level, int role, int which, int reps, 
 /* Measured FP64 FMA throughput of this GPU [TFLOP/s], the denominator of
  * the FP64-pipe fraction in roofline reports (GB300 has no published
  * dense-FP64 figure to use instead): one launch of 152 x 8 blocks of 256
- * threads, each running 8 independent FMA chains of 512 * reps steps,
+ * threads, each running 16 independent FMA chains of 512 * reps steps,
  * timed with CUDA events on `stream` after one warm-up launch; reps 1..1000.
  * Allocates and frees a small result buffer (stream-ordered). Synchronises
  * the stream. */

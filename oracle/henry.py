@@ -123,6 +123,41 @@ class Fields:
     qin: np.ndarray      # [ny] left-side inflow velocity per row [m/s]
 
 
+def field_at(phys: Physics, xi, X, Y, logk=None):
+    """Porosity and permeability of the random field at points (X, Y) (any
+    array shape, frame y in [0, Ly]); see `fields` for the formulas."""
+    if phys.field_model == 1:
+        Yp = Y - phys.Ly
+        C0 = np.where(Yp < -0.8, 1.2 * (1.0 + 0.2 * xi[0]), 1.0 + 0.0 * xi[0])
+        C1 = 1.0 + 0.15 * (xi[1] * np.cos(np.pi * X / 2) - xi[1] * np.sin(2 * np.pi * Yp)
+                           + xi[0] * np.cos(2 * np.pi * X))
+        C2 = 1.0 + 0.2 * (xi[0] * np.sin(64 * np.pi * X) + xi[1] * np.sin(32 * np.pi * Yp))
+        phi = phys.phi0 * C0 * C1 * C2
+        K = phys.kappa_kc * phi ** 3 / (1.0 - phi ** 2)
+        if logk is not None:
+            K = K * np.exp(logk)
+        return phi, K
+    a = 0.1 * xi[0] * np.cos(np.pi * X / 2) * np.sin(np.pi * Y)
+    b = 0.5 * xi[1] * np.sin(np.pi * X / 2) * np.cos(np.pi * Y)
+    if xi.shape[0] >= 6:
+        a = a + 0.05 * xi[3] * np.cos(np.pi * X) * np.sin(2 * np.pi * Y)
+        b = b + 0.05 * xi[4] * np.sin(np.pi * X) * np.cos(2 * np.pi * Y)
+    if logk is not None:
+        b = b + logk
+    return phys.phi0 * (1.0 + a), phys.K0 * np.exp(b)
+
+
+def inflow_at(phys: Physics, xi, y):
+    """Left-side inflow velocity q_in at heights y (the base of Eq.
+    e_recharge_of_param for field model 1)."""
+    if phys.field_model == 1:
+        return phys.q0 * (1.0 + 0.5 * xi[2]) + 0.0 * y
+    qf = 1.0 + 0.1 * xi[2] + 0.0 * y
+    if xi.shape[0] >= 6:
+        qf = qf + 0.05 * xi[5] * np.cos(np.pi * y)
+    return phys.q0 * qf
+
+
 def fields(grid: Grid, phys: Physics, xi, logk=None) -> Fields:
     """field_model 0 (the configs' smooth fields):
     phi = phi0 (1 + 0.1 xi1 cos(pi x/2) sin(pi y) [+ 0.05 xi4 cos(pi x) sin(2 pi y)])
@@ -142,27 +177,8 @@ def fields(grid: Grid, phys: Physics, xi, logk=None) -> Fields:
     xi = np.asarray(xi)
     x, y = cell_centres(grid, phys)
     X, Y = np.meshgrid(x, y)
-    if phys.field_model == 1:
-        Yp = Y - phys.Ly
-        C0 = np.where(Yp < -0.8, 1.2 * (1.0 + 0.2 * xi[0]), 1.0 + 0.0 * xi[0])
-        C1 = 1.0 + 0.15 * (xi[1] * np.cos(np.pi * X / 2) - xi[1] * np.sin(2 * np.pi * Yp)
-                           + xi[0] * np.cos(2 * np.pi * X))
-        C2 = 1.0 + 0.2 * (xi[0] * np.sin(64 * np.pi * X) + xi[1] * np.sin(32 * np.pi * Yp))
-        phi = phys.phi0 * C0 * C1 * C2
-        K = phys.kappa_kc * phi ** 3 / (1.0 - phi ** 2)
-        if logk is not None:
-            K = K * np.exp(logk)
-        return Fields(phi=phi, K=K, qin=phys.q0 * (1.0 + 0.5 * xi[2]) + 0.0 * y)
-    a = 0.1 * xi[0] * np.cos(np.pi * X / 2) * np.sin(np.pi * Y)
-    b = 0.5 * xi[1] * np.sin(np.pi * X / 2) * np.cos(np.pi * Y)
-    qf = 1.0 + 0.1 * xi[2] + 0.0 * y
-    if xi.shape[0] >= 6:
-        a = a + 0.05 * xi[3] * np.cos(np.pi * X) * np.sin(2 * np.pi * Y)
-        b = b + 0.05 * xi[4] * np.sin(np.pi * X) * np.cos(2 * np.pi * Y)
-        qf = qf + 0.05 * xi[5] * np.cos(np.pi * y)
-    if logk is not None:
-        b = b + logk
-    return Fields(phi=phys.phi0 * (1.0 + a), K=phys.K0 * np.exp(b), qin=phys.q0 * qf)
+    phi, K = field_at(phys, xi, X, Y, logk)
+    return Fields(phi=phi, K=K, qin=inflow_at(phys, xi, y))
 
 
 # ----------------------------------------------------------------------------

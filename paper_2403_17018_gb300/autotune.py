@@ -4,7 +4,8 @@ For each MLMC level it times short batched solves (a few implicit Euler
 steps at the level's own time step) for every candidate schedule — V-cycles
 per defect-correction iteration, pre/post smoothing sweeps and the largest
 grid handed to the shared-memory V-cycle kernel; then, for the winner, the
-operator reuse factor (jac_lag) — and, for
+operator reuse factor (jac_lag), then the residual kernel's tile height
+(res_rows) — and, for
 the level's batch size, several batch splits, then keeps the schedule with
 the highest solves per second. Results are cached in a JSON file keyed by
 GPU name, level grid, precision and batch so that later runs reuse them.
@@ -26,7 +27,7 @@ if ROOT not in sys.path:
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuning", "schedules.json")
 CANDIDATES = {"vcycles": (1, 2, 3), "nu": ((1, 1), (2, 2), (3, 3)), "small_cells": (0, 128, 512),
-              "jac_lag": (0, 10, 30)}
+              "jac_lag": (0, 10, 30), "res_rows": (0, 2, 4, 16)}
 
 
 def _key(gpu, level, precision, batch, nx0, ny0):
@@ -76,10 +77,10 @@ def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2),
     xi = torch.from_numpy(xi_batch(level, 0, batch, n_xi=n_xi)).cuda()
     table = []
 
-    def timed(vc, n1, n2, sc, lag, split):
+    def timed(vc, n1, n2, sc, lag, split, rr=0):
         cfg = hb.default_config(nlevels=level + 1, precision=prec, vcycles=vc, nu1=n1, nu2=n2,
-                                mg_small_cells=sc, jac_lag=lag, nt0=k, T=tau0 * k, n_xi=n_xi,
-                                **extra)
+                                mg_small_cells=sc, jac_lag=lag, res_rows=rr, nt0=k, T=tau0 * k,
+                                n_xi=n_xi, **extra)
         ctx = hb.Context(cfg)
         sub = batch // split
         parts = [xi[i * sub:(i + 1) * sub].contiguous() for i in range(split)]
@@ -94,7 +95,7 @@ def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2),
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / reps
         row = {"vcycles": vc, "nu1": n1, "nu2": n2, "mg_small_cells": sc, "jac_lag": lag,
-               "split": split, "solves_per_s": batch / dt, "failed": bad}
+               "res_rows": rr, "split": split, "solves_per_s": batch / dt, "failed": bad}
         table.append(row)
         if log:
             log(row)
@@ -115,6 +116,11 @@ def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2),
         if lag:
             timed(best["vcycles"], best["nu1"], best["nu2"], best["mg_small_cells"], lag,
                   best["split"])
+    best = best_of(table)
+    for rr in CANDIDATES.get("res_rows", (0,)):
+        if rr:
+            timed(best["vcycles"], best["nu1"], best["nu2"], best["mg_small_cells"],
+                  best["jac_lag"], best["split"], rr)
     return best_of(table), table
 
 

@@ -45,10 +45,25 @@ class HenryConfig(ctypes.Structure):
                 ("newton_stag_tol", ctypes.c_double), ("mg_fusion", ctypes.c_int),
                 ("mg_cluster_cells", ctypes.c_int), ("mg_small_cells", ctypes.c_int),
                 ("jac_lag", ctypes.c_int), ("field_model", ctypes.c_int),
-                ("krylov_iters", ctypes.c_int), ("adjoint_rtol", ctypes.c_double)]
+                ("krylov_iters", ctypes.c_int), ("adjoint_rtol", ctypes.c_double),
+                ("res_rows", ctypes.c_int)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
+
+
+class HenrySchedule(ctypes.Structure):
+    """Multigrid schedule of one MLMC level (henry_schedule)."""
+    _fields_ = [(n, ctypes.c_int) for n in ("vcycles", "nu1", "nu2", "mg_small_cells", "jac_lag",
+                                             "res_rows")]
+
+
+class HenryLevelBatch(ctypes.Structure):
+    """One level's pairs for henry_sample_levels (henry_level_batch)."""
+    _fields_ = [("level", ctypes.c_int), ("B", ctypes.c_int), ("xi", ctypes.c_void_p),
+                ("q_fine", ctypes.c_void_p), ("q_coarse", ctypes.c_void_p),
+                ("c_fine", ctypes.c_void_p), ("c_coarse", ctypes.c_void_p),
+                ("status", ctypes.c_void_p)]
 
 
 class LevelStats(ctypes.Structure):
@@ -84,6 +99,8 @@ def load():
         "henry_solve": (I, [P, I, V, V, I, V, V, V, V, V, V]),
         "henry_sample_pairs": (I, [P, I, V, I, V, V, V, V, V, V]),
         "henry_solve_series": (I, [P, I, V, V, I, I, V, V, V, V]),
+        "henry_set_schedule": (I, [P, I, ctypes.POINTER(HenrySchedule)]),
+        "henry_sample_levels": (I, [P, ctypes.POINTER(HenryLevelBatch), I, V]),
         "mlmc_level_stats": (I, [P, I, V, V, I, V, ctypes.POINTER(LevelStats), V]),
         "mlmc_field_stats": (I, [P, I, V, V, I, V, V, V, V, V, V, V]),
         "mlmc_field_exceedance": (I, [P, I, V, I, V, D, V, V]),
@@ -258,6 +275,39 @@ class Context:
             self._h, level, _ptr(xi, torch.float64, (B, self.cfg.n_xi), "xi"), B, _ptr(qf),
             _ptr(qc), _ptr(cf), _ptr(cc), _ptr(st), _stream(stream)))
         return qf, qc, cf, cc, st
+
+    def set_schedule(self, level, vcycles, nu1, nu2, mg_small_cells=512, jac_lag=0, res_rows=0,
+                     **_):
+        """henry_set_schedule: the multigrid schedule of one MLMC level."""
+        sc = HenrySchedule(vcycles, nu1, nu2, mg_small_cells, jac_lag, res_rows)
+        _check(self.lib.henry_set_schedule(self._h, level, ctypes.byref(sc)))
+
+    def sample_levels(self, xis, want_c=False, stream=None):
+        """henry_sample_levels: the pairs of several levels at once, one graph
+        launch per coarse time step. xis: {level: xi [B, n_xi]}. Returns
+        {level: (q_fine, q_coarse or None, c_fine, c_coarse, status)}."""
+        import torch
+        arr = (HenryLevelBatch * len(xis))()
+        out, keep = {}, []
+        for i, (level, xi) in enumerate(sorted(xis.items())):
+            B = xi.shape[0]
+            dev = xi.device
+            li = self.level_info(level)
+            qf = torch.empty((B, NQ), dtype=torch.float64, device=dev)
+            qc = torch.empty((B, NQ), dtype=torch.float64, device=dev) if level > 0 else None
+            cf = torch.empty((B, li.ny, li.nx), dtype=torch.float64, device=dev) if want_c else None
+            cc = None
+            if want_c and level > 0:
+                lc = self.level_info(level - 1)
+                cc = torch.empty((B, lc.ny, lc.nx), dtype=torch.float64, device=dev)
+            st = torch.empty((B,), dtype=torch.int32, device=dev)
+            p = lambda t, name=None, **kw: _ptr(t, **kw)
+            arr[i] = HenryLevelBatch(level, B, _ptr(xi, torch.float64, (B, self.cfg.n_xi), "xi"),
+                                     p(qf), p(qc), p(cf), p(cc), p(st))
+            out[level] = (qf, qc, cf, cc, st)
+            keep.append(xi)
+        _check(self.lib.henry_sample_levels(self._h, arr, len(xis), _stream(stream)))
+        return out
 
     def level_stats(self, level, q_fine, q_coarse, status, stats: LevelStats, stream=None):
         """mlmc_level_stats (synchronous): merges the batch into `stats`."""

@@ -32,6 +32,10 @@ using henry::Solver;
 
 struct henry_ctx {
   henry_config cfg;
+  // per MLMC level l: the context's config with level l's schedule
+  // (henry_set_schedule); used by the fine solver of level l and by the
+  // coarse half (level l-1) of the pairs of level l
+  std::vector<henry_config> level_cfg;
   int device = 0;
   // solvers per level: [0] fine role, [1] coarse role (level l-1 of a pair)
   std::vector<std::unique_ptr<Solver>> role[2];
@@ -44,6 +48,14 @@ struct henry_ctx {
   double* stats_dev = nullptr;         // 1 + 4*NQ doubles
   double* stats_host = nullptr;        // pinned
   unsigned long long* ctr = nullptr;   // launches outside the solvers
+  // henry_sample_levels: the graph of one coarse time step (every solver's
+  // chain of implicit steps as a parallel branch), its key (solvers,
+  // batches, steps, workspace generations) and the capture streams/events
+  cudaGraph_t multi_graph = nullptr;
+  cudaGraphExec_t multi_exec = nullptr;
+  std::vector<long long> multi_key;
+  std::vector<cudaStream_t> multi_streams;
+  std::vector<cudaEvent_t> multi_events;
 };
 
 namespace {
@@ -74,9 +86,19 @@ Solver* get_solver(henry_ctx* ctx, int level, int role) {
   if (!v[level]) {
     int nx, ny, nt;
     level_dims(ctx->cfg, level, &nx, &ny, &nt);
-    v[level].reset(new Solver(ctx->cfg, nx, ny, nt));
+    // role 1 solves level l-1 for the pairs of level l: that level's schedule
+    const henry_config& c = ctx->level_cfg[role == 0 ? level : level + 1];
+    v[level].reset(new Solver(c, nx, ny, nt));
   }
   return v[level].get();
+}
+
+void drop_multi_graph(henry_ctx* ctx) {
+  if (ctx->multi_exec) cudaGraphExecDestroy(ctx->multi_exec);
+  if (ctx->multi_graph) cudaGraphDestroy(ctx->multi_graph);
+  ctx->multi_exec = nullptr;
+  ctx->multi_graph = nullptr;
+  ctx->multi_key.clear();
 }
 
 int validate(const henry_config* c) {
@@ -100,6 +122,7 @@ int validate(const henry_config* c) {
     return fail(HENRY_E_INVALID, "krylov_iters = 1 is rejected (BiCGStab breakdown); use 0 or >= 2");
   if (!(c->adjoint_rtol > 0.0) || !(c->adjoint_rtol < 1e-3))
     return fail(HENRY_E_INVALID, "adjoint_rtol must be in (0, 1e-3)");
+  if (c->res_rows < 0 || c->res_rows > 64) return fail(HENRY_E_INVALID, "res_rows must be in 0..64");
   for (int l = 0; l < c->nlevels; ++l) {
     std::vector<henry::Geom> g;
     if (!henry::build_hierarchy(c->nx0 << l, c->ny0 << l, c->Lx, c->Ly, g))
@@ -160,6 +183,7 @@ int henry_create_levels(const henry_config* cfg, henry_ctx** out) {
   henry_ctx* ctx = new (std::nothrow) henry_ctx;
   if (!ctx) return fail(HENRY_E_NOMEM, "host allocation failed");
   ctx->cfg = *cfg;
+  ctx->level_cfg.assign(cfg->nlevels, *cfg);
   ctx->role[0].resize(cfg->nlevels);
   ctx->role[1].resize(cfg->nlevels);
   ctx->pair_stream.assign(cfg->nlevels, nullptr);
@@ -185,6 +209,9 @@ int henry_create_levels(const henry_config* cfg, henry_ctx** out) {
 void henry_destroy(henry_ctx* ctx) {
   if (!ctx) return;
   cudaDeviceSynchronize();
+  drop_multi_graph(ctx);
+  for (cudaStream_t st : ctx->multi_streams) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : ctx->multi_events) cudaEventDestroy(ev);
   for (auto& v : ctx->role) v.clear();
   for (size_t l = 0; l < ctx->pair_stream.size(); ++l) {
     if (ctx->pair_stream[l]) cudaStreamDestroy(ctx->pair_stream[l]);
@@ -271,6 +298,139 @@ int henry_sample_pairs(henry_ctx* ctx, int level, const double* xi, int B, doubl
   if (rc) return rc;
   CKR(cudaStreamWaitEvent(s, ctx->pair_join[level], 0));
   return henry::or_status(ctx->pair_status[level], status, B, ctx->ctr, s);
+}
+
+int henry_set_schedule(henry_ctx* ctx, int level, const henry_schedule* sc) {
+  if (!ctx || !sc) return fail(HENRY_E_INVALID, "NULL argument");
+  if (level < 0 || level >= ctx->cfg.nlevels) return fail(HENRY_E_INVALID, "bad level");
+  henry_config c = ctx->cfg;
+  c.vcycles = sc->vcycles;
+  c.nu1 = sc->nu1;
+  c.nu2 = sc->nu2;
+  c.mg_small_cells = sc->mg_small_cells;
+  c.jac_lag = sc->jac_lag;
+  c.res_rows = sc->res_rows;
+  const int rc = validate(&c);
+  if (rc) return rc;
+  CKR(cudaSetDevice(ctx->device));
+  CKR(cudaDeviceSynchronize());
+  drop_multi_graph(ctx);
+  ctx->level_cfg[level] = c;
+  ctx->role[0][level].reset();
+  if (level > 0) ctx->role[1][level - 1].reset();
+  return HENRY_OK;
+}
+
+int henry_sample_levels(henry_ctx* ctx, const henry_level_batch* batches, int n, void* stream) {
+  if (!ctx || !batches) return fail(HENRY_E_INVALID, "NULL argument");
+  if (n < 1 || n > ctx->cfg.nlevels) return fail(HENRY_E_INVALID, "n must be in 1..nlevels");
+  std::vector<int> seen(ctx->cfg.nlevels, 0);
+  for (int i = 0; i < n; ++i) {
+    const henry_level_batch& b = batches[i];
+    if (b.level < 0 || b.level >= ctx->cfg.nlevels) return fail(HENRY_E_INVALID, "bad level");
+    if (seen[b.level]++) return fail(HENRY_E_INVALID, "a level appears twice");
+    if (b.B < 0 || b.B > HENRY_MAX_BATCH) return fail(HENRY_E_INVALID, "B must be in 0..65535");
+    if (b.B == 0) continue;
+    if (!b.xi || !b.q_fine || !b.status) return fail(HENRY_E_INVALID, "xi, q_fine and status are required");
+    if (b.level == 0 && (b.q_coarse || b.c_coarse))
+      return fail(HENRY_E_INVALID, "level 0 has no coarse solve: q_coarse and c_coarse must be NULL");
+    if (b.level > 0 && !b.q_coarse) return fail(HENRY_E_INVALID, "q_coarse is required for level > 0");
+  }
+  CKR(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (ctx->cfg.loop_mode == HENRY_LOOP_HOST) {
+    // host-side Newton loops: the pairs one level after another
+    for (int i = 0; i < n; ++i) {
+      const henry_level_batch& b = batches[i];
+      const int rc = henry_sample_pairs(ctx, b.level, b.xi, b.B, b.q_fine, b.q_coarse, b.c_fine,
+                                        b.c_coarse, b.status, stream);
+      if (rc) return rc;
+    }
+    return HENRY_OK;
+  }
+  // the chains of implicit steps: per coarse step, level l advances 2^l steps
+  struct Chain { Solver* sv; int B; int steps; };
+  std::vector<Chain> chains;
+  for (int i = 0; i < n; ++i) {
+    const henry_level_batch& b = batches[i];
+    if (b.B == 0) continue;
+    chains.push_back({get_solver(ctx, b.level, 0), b.B, 1 << b.level});
+    if (b.level > 0) chains.push_back({get_solver(ctx, b.level - 1, 1), b.B, 1 << (b.level - 1)});
+  }
+  if (chains.empty()) return HENRY_OK;
+  // fields and initial states (these may grow workspaces)
+  for (int i = 0, k = 0; i < n; ++i) {
+    const henry_level_batch& b = batches[i];
+    if (b.B == 0) continue;
+    int rc = chains[k++].sv->begin(b.xi, nullptr, b.B, s);
+    if (!rc && b.level > 0) rc = chains[k++].sv->begin(b.xi, nullptr, b.B, s);
+    if (rc) return rc;
+  }
+  std::vector<long long> key;
+  for (const Chain& c : chains) {
+    key.push_back((long long)(intptr_t)c.sv);
+    key.push_back(c.B);
+    key.push_back(c.steps);
+    key.push_back((long long)c.sv->generation());
+  }
+  if (key != ctx->multi_key) {
+    drop_multi_graph(ctx);
+    while (ctx->multi_streams.size() < chains.size() + 2) {
+      cudaStream_t st;
+      CKR(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+      ctx->multi_streams.push_back(st);
+    }
+    while (ctx->multi_events.size() < chains.size() + 1) {
+      cudaEvent_t ev;
+      CKR(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      ctx->multi_events.push_back(ev);
+    }
+    cudaStream_t cs = ctx->multi_streams[0], bs = ctx->multi_streams[1];
+    cudaGraph_t g;
+    CKR(cudaGraphCreate(&g, 0));
+    std::vector<henry::StepBody> bodies;
+    int rc = HENRY_OK;
+    cudaError_t e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      e = cudaEventRecord(ctx->multi_events[0], cs);
+      for (size_t i = 0; i < chains.size() && e == cudaSuccess && !rc; ++i) {
+        cudaStream_t si = ctx->multi_streams[i + 2];
+        e = cudaStreamWaitEvent(si, ctx->multi_events[0], 0);
+        if (e == cudaSuccess) rc = chains[i].sv->capture_steps(g, si, chains[i].B, chains[i].steps, bodies);
+        if (e == cudaSuccess && !rc) e = cudaEventRecord(ctx->multi_events[i + 1], si);
+        if (e == cudaSuccess && !rc) e = cudaStreamWaitEvent(cs, ctx->multi_events[i + 1], 0);
+      }
+      cudaGraph_t gout = g;
+      const cudaError_t e2 = cudaStreamEndCapture(cs, &gout);
+      if (e == cudaSuccess) e = e2;
+    }
+    for (size_t k = 0; k < bodies.size() && e == cudaSuccess && !rc; ++k) {
+      int B = 0;
+      for (const Chain& c : chains)
+        if (c.sv == bodies[k].solver) B = c.B;
+      rc = bodies[k].solver->capture_body(bodies[k], B, bs);
+    }
+    if (e == cudaSuccess && !rc) e = cudaGraphInstantiate(&ctx->multi_exec, g, 0);
+    if (e != cudaSuccess || rc) {
+      cudaGraphDestroy(g);
+      ctx->multi_exec = nullptr;
+      if (rc) return rc;
+      return fail(HENRY_E_CUDA, std::string("henry_sample_levels graph: ") + cudaGetErrorString(e));
+    }
+    ctx->multi_graph = g;
+    ctx->multi_key = key;
+  }
+  for (int k = 0; k < ctx->cfg.nt0; ++k) CKR(cudaGraphLaunch(ctx->multi_exec, s));
+  for (int i = 0, k = 0; i < n; ++i) {
+    const henry_level_batch& b = batches[i];
+    if (b.B == 0) continue;
+    int rc = chains[k++].sv->finish(b.B, b.q_fine, b.c_fine, nullptr, b.status, nullptr, 0, s);
+    if (!rc && b.level > 0)
+      rc = chains[k++].sv->finish(b.B, b.q_coarse, b.c_coarse, nullptr, b.status, nullptr, 1, s);
+    if (rc) return rc;
+  }
+  return HENRY_OK;
 }
 
 int henry_adjoint(henry_ctx* ctx, int level, const double* xi, const double* logk, int B,

@@ -39,12 +39,16 @@ struct ResTile {
   int ntx, nty;     // tiles per sample in x and y
 };
 
-__host__ inline ResTile make_res_tile(int nx, int ny) {
+// rmax: most rows a thread walks (more rows per thread: fewer blocks, fewer
+// tile-edge recomputations of the south face; fewer: more parallelism for
+// small batches). 0 selects the default, 8.
+__host__ inline ResTile make_res_tile(int nx, int ny, int rmax = 0) {
   ResTile t;
+  if (rmax <= 0) rmax = 8;
   t.TX = nx < kBlock ? nx : kBlock;
   t.GR = kBlock / t.TX;
   int rows = (ny + t.GR - 1) / t.GR;        // rows per thread if one tile covered all
-  t.R = rows < 8 ? rows : 8;
+  t.R = rows < rmax ? rows : rmax;
   t.ntx = (nx + t.TX - 1) / t.TX;
   t.nty = (ny + t.GR * t.R - 1) / (t.GR * t.R);
   return t;

@@ -217,6 +217,16 @@ __global__ void k_begin_step(unsigned long long* ctr, Geom G, int B, double* __r
   }
 }
 
+// Condition of the operator-rebuild block of a defect-correction iteration
+// (graph loop with operator reuse): true when some sample asked for new
+// operators (count published by k_check). When none did, the rebuild
+// kernels, which would all skip every sample, are not launched.
+__global__ void k_set_rebuild(unsigned long long* ctr, const int* __restrict__ n_refresh,
+                              cudaGraphConditionalHandle h) {
+  HENRY_COUNT_LAUNCH(ctr);
+  if (threadIdx.x == 0) cudaGraphSetConditional(h, *n_refresh > 0 ? 1u : 0u);
+}
+
 __global__ void k_end_step(unsigned long long* ctr, int* __restrict__ step) {
   HENRY_COUNT_LAUNCH(ctr);
   if (threadIdx.x == 0) *step += 1;
@@ -430,7 +440,9 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, ResTile tl
 // of the enclosing CUDA graph. With refresh (operator reuse factor lag > 0)
 // it also decides whether the next iteration rebuilds the Jacobian and the
 // multigrid operators: always after the step's initial residual, later only
-// when the last iteration reduced the residual by less than a factor lag.
+// when the last iteration reduced the residual by less than a factor lag;
+// acc[2] counts those samples and the last block publishes the count in
+// n_active[1] (k_set_rebuild turns it into the condition of the rebuild).
 template <bool SET_COND>
 __global__ void k_check(unsigned long long* ctr, int B, int nchunk, int ncell,
                         const double* __restrict__ partial, double scale, double rtol,
@@ -442,9 +454,9 @@ __global__ void k_check(unsigned long long* ctr, int B, int nchunk, int ncell,
                         cudaGraphConditionalHandle h, int* __restrict__ refresh, int lag,
                         double stag_rel = 0.0) {
   HENRY_COUNT_LAUNCH(ctr);
-  __shared__ int cnt;
+  __shared__ int cnt, rcnt;
   __shared__ bool last;
-  if (threadIdx.x == 0) cnt = 0;
+  if (threadIdx.x == 0) cnt = rcnt = 0;
   __syncthreads();
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int b = blockIdx.x * (blockDim.x >> 5) + w;
@@ -472,13 +484,18 @@ __global__ void k_check(unsigned long long* ctr, int B, int nchunk, int ncell,
         it_step[b] = it + 1;
         iters[b] += 1;
         atomicAdd(&cnt, 1);
-        if (refresh) refresh[b] = (it == 0 || r * lag > prev) ? 1 : 0;
+        if (refresh) {
+          const int rf = (it == 0 || r * lag > prev) ? 1 : 0;
+          refresh[b] = rf;
+          if (rf) atomicAdd(&rcnt, 1);
+        }
       }
     }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     if (cnt) atomicAdd(&acc[0], (unsigned int)cnt);
+    if (rcnt) atomicAdd(&acc[2], (unsigned int)rcnt);
     __threadfence();
     last = atomicAdd(&acc[1], 1u) == gridDim.x - 1;
   }
@@ -486,6 +503,7 @@ __global__ void k_check(unsigned long long* ctr, int B, int nchunk, int ncell,
   if (last && threadIdx.x == 0) {
     __threadfence();
     const unsigned int total = atomicExch(&acc[0], 0u);
+    n_active[1] = (int)atomicExch(&acc[2], 0u);
     acc[1] = 0u;
     *n_active = (int)total;
     if (SET_COND) cudaGraphSetConditional(h, total > 0 ? 1u : 0u);

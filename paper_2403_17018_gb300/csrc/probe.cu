@@ -8,11 +8,11 @@ namespace henry {
 
 constexpr int kProbeBlocks = 152 * 8;
 constexpr int kProbeBlock = 256;
-constexpr int kProbeChains = 8;
+constexpr int kProbeChains = 16;
 constexpr int kProbeInner = 512;
 
-// Eight independent dependency chains per thread keep the FP64 pipe busy
-// (the latency of one FMA is hidden by the other seven); the multiplier and
+// Sixteen independent dependency chains per thread keep the FP64 pipe busy
+// (the latency of one FMA is hidden by the other fifteen); the multiplier and
 // addend keep every value bounded, and the sum is stored so that nothing is
 // eliminated.
 __global__ void __launch_bounds__(kProbeBlock) k_probe_fp64(int reps, double* __restrict__ out) {
@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(kProbeBlock) k_probe_fp64(int reps, double* __
   for (int k = 0; k < kProbeChains; ++k) a[k] = 1.0 + 1e-3 * (t + k);
   const double m = 0.999999, c = 1e-6;
   for (int r = 0; r < reps; ++r) {
-#pragma unroll 16
+#pragma unroll 8
     for (int i = 0; i < kProbeInner; ++i) {
 #pragma unroll
       for (int k = 0; k < kProbeChains; ++k) a[k] = fma(a[k], m, c);

@@ -76,7 +76,7 @@ Solver::Solver(const henry_config& cfg, int nx, int ny, int nt) : cfg_(cfg), nt_
   build_hierarchy(nx, ny, cfg.Lx, cfg.Ly, geoms_);
   levels_.resize(geoms_.size());
   for (size_t k = 0; k < geoms_.size(); ++k) levels_[k].g = geoms_[k];
-  tile_ = make_res_tile(geoms_.back().nx, geoms_.back().ny);
+  tile_ = make_res_tile(geoms_.back().nx, geoms_.back().ny, cfg.res_rows);
   nchunk_ = tile_.ntx * tile_.nty;
   ks_ = 0;
   kc_ = 0;
@@ -205,8 +205,8 @@ int Solver::ensure(int B, cudaStream_t s) {
   const size_t o_its = take(Bz * 4);
   const size_t o_st = take(Bz * 4);
   const size_t o_it = take(Bz * 4);
-  const size_t o_na = take(4);
-  const size_t o_acc = take(8);
+  const size_t o_na = take(8);     // active count, rebuild count
+  const size_t o_acc = take(16);   // k_check's accumulators
   // BiCGStab vectors r, rh, p, v, t, xk ([B][2][ncell] of the finest level),
   // per-sample scalars and dot partials (only with krylov_iters > 0)
   const size_t n2 = (size_t)2 * F.ncell();
@@ -218,7 +218,7 @@ int Solver::ensure(int B, cudaStream_t s) {
   const size_t o_kp = take(cfg_.krylov_iters ? 2 * Bz * kry_nchunk_ * 8 : 0);
   const size_t o_ctr = take(8);
   CK(cudaMalloc(&arena_, off));
-  CK(cudaHostAlloc((void**)&n_active_host_, sizeof(int), cudaHostAllocDefault));
+  CK(cudaHostAlloc((void**)&n_active_host_, 2 * sizeof(int), cudaHostAllocDefault));
   char* a = (char*)arena_;
   for (size_t k = 0; k < levels_.size(); ++k) {
     MGLevel& L = levels_[k];
@@ -260,6 +260,7 @@ int Solver::ensure(int B, cudaStream_t s) {
   CK(cudaMemset(arena_, 0, off));
   CK(cudaMemcpy(counter_, &count, sizeof(count), cudaMemcpyHostToDevice));
   cap_ = B;
+  ++generation_;
   (void)s;
   return HENRY_OK;
 }
@@ -439,12 +440,12 @@ void Solver::enqueue_bicgstab(int B, cudaStream_t s) {
   upd(4);                                              // x = xk
 }
 
-// Multigrid operators at the current iterate, V-cycles, state update.
+// Multigrid operators at the current iterate, for the samples that asked
+// for them (all samples without operator reuse).
 template <typename T>
-void Solver::enqueue_iteration(int B, cudaStream_t s) {
+void Solver::enqueue_rebuild(int B, cudaStream_t s) {
   const int* refresh = cfg_.jac_lag ? refresh_ : nullptr;
   if (refresh) {
-    // operators at the current iterate, for the samples that asked for them
     MGLevel& F = levels_.back();
     k_resjac<T, false><<<dim3(nchunk_, B), kBlock, 0, s>>>(
         counter_, phys_, F.g, F.g.hx * F.g.hy / tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx,
@@ -452,6 +453,12 @@ void Solver::enqueue_iteration(int B, cudaStream_t s) {
   }
   enqueue_coarse_ops<T>(B, s, refresh);
   enqueue_lu<T>(B, s, refresh);
+}
+
+// Linear solve of the defect correction (V-cycles or BiCGStab) and the
+// state update.
+template <typename T>
+void Solver::enqueue_solve_update(int B, cudaStream_t s) {
   if (cfg_.krylov_iters)
     enqueue_bicgstab<T>(B, s);
   else
@@ -462,7 +469,14 @@ void Solver::enqueue_iteration(int B, cudaStream_t s) {
 }
 
 template <typename T>
-void Solver::enqueue_resjac_check(int B, cudaStream_t s, bool set_cond) {
+void Solver::enqueue_iteration(int B, cudaStream_t s) {
+  enqueue_rebuild<T>(B, s);
+  enqueue_solve_update<T>(B, s);
+}
+
+template <typename T>
+void Solver::enqueue_resjac_check(int B, cudaStream_t s, bool set_cond,
+                                  unsigned long long cond) {
   MGLevel& F = levels_.back();
   const Geom& G = F.g;
   if (cfg_.jac_lag)   // residual only; the next iteration rebuilds operators where needed
@@ -483,7 +497,7 @@ void Solver::enqueue_resjac_check(int B, cudaStream_t s, bool set_cond) {
                                         cfg_.newton_rtol, cfg_.newton_atol, cfg_.newton_maxit,
                                         active_, it_step_, res0_, res_last_, status_w_, iters_w_,
                                         n_active_, check_acc_, stag_tol,
-                                        (cudaGraphConditionalHandle)cond_handle_, refresh,
+                                        (cudaGraphConditionalHandle)cond, refresh,
                                         cfg_.jac_lag);
   else
     k_check<false><<<gb, kBlock, 0, s>>>(counter_, B, nchunk_, G.ncell(), partial_, scale,
@@ -493,8 +507,109 @@ void Solver::enqueue_resjac_check(int B, cudaStream_t s, bool set_cond) {
                                          cfg_.jac_lag);
 }
 
-// One implicit Euler step as a CUDA graph: begin, residual + check, then a
-// device-side while loop over defect-correction iterations.
+// The nodes of one implicit Euler step on stream cs, which is capturing into
+// graph g: begin step, FP64 residual + convergence check, a conditional
+// while node whose body (one defect-correction iteration and the next
+// check) is recorded in `bodies` and captured by capture_body() once the
+// capture of g has ended, then the end of the step. Each step has its own
+// conditional handle, set by its own checks.
+template <typename T>
+int Solver::capture_step_t(cudaGraph_t g, cudaStream_t cs, int B, std::vector<StepBody>& bodies) {
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+  MGLevel& F = levels_.back();
+  k_begin_step<<<grid1((int64_t)B * F.g.ncell()), kBlock, 0, cs>>>(
+      counter_, F.g, B, F.p, F.c, p_prev_, c_old_, status_w_, active_, it_step_, step_,
+      cfg_.guess_extrapolation, cfg_.field_model == 1 ? qin0_ : nullptr, qin_, tau_);
+  enqueue_resjac_check<T>(B, cs, true, (unsigned long long)h);
+  cudaStreamCaptureStatus st;
+  cudaGraph_t cg;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(cs, &st, nullptr, &cg, &deps, nullptr, &nd));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t wn;
+  CK(cudaGraphAddNode(&wn, cg, deps, nullptr, nd, &cp));
+  bodies.push_back(StepBody{this, cp.conditional.phGraph_out[0], (unsigned long long)h});
+  CK(cudaStreamUpdateCaptureDependencies(cs, &wn, nullptr, 1, cudaStreamSetCaptureDependencies));
+  k_end_step<<<1, 32, 0, cs>>>(counter_, step_);
+  CK(cudaGetLastError());
+  return HENRY_OK;
+}
+
+// The body of a step's while node: one defect-correction iteration and the
+// next check. With operator reuse the rebuild kernels sit in a conditional
+// IF node (captured after the body) set by k_set_rebuild, so iterations in
+// which no sample rebuilds its operators launch none of them.
+template <typename T>
+int Solver::capture_body_t(const StepBody& sb, int B, cudaStream_t bs) {
+  cudaGraph_t body = sb.body;
+  CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  cudaGraph_t rebuild = nullptr;
+  if (cfg_.jac_lag) {
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, body, 0, 0);
+    if (e == cudaSuccess) {
+      k_set_rebuild<<<1, 32, 0, bs>>>(counter_, n_active_ + 1, h);
+      cudaStreamCaptureStatus st;
+      cudaGraph_t cg;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      e = cudaStreamGetCaptureInfo(bs, &st, nullptr, &cg, &deps, nullptr, &nd);
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeIf;
+      cp.conditional.size = 1;
+      cudaGraphNode_t in;
+      if (e == cudaSuccess) e = cudaGraphAddNode(&in, cg, deps, nullptr, nd, &cp);
+      if (e == cudaSuccess) {
+        rebuild = cp.conditional.phGraph_out[0];
+        e = cudaStreamUpdateCaptureDependencies(bs, &in, nullptr, 1, cudaStreamSetCaptureDependencies);
+      }
+    }
+    if (e != cudaSuccess) {
+      cudaStreamEndCapture(bs, &body);
+      set_last_error(std::string("rebuild condition: ") + cudaGetErrorString(e));
+      return HENRY_E_CUDA;
+    }
+  } else {
+    enqueue_rebuild<T>(B, bs);
+  }
+  enqueue_solve_update<T>(B, bs);
+  enqueue_resjac_check<T>(B, bs, true, sb.cond);
+  CK(cudaStreamEndCapture(bs, &body));
+  if (rebuild) {
+    CK(cudaStreamBeginCaptureToGraph(bs, rebuild, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    enqueue_rebuild<T>(B, bs);
+    CK(cudaStreamEndCapture(bs, &rebuild));
+  }
+  return HENRY_OK;
+}
+
+int Solver::capture_steps(cudaGraph_t g, cudaStream_t cs, int B, int nsteps,
+                          std::vector<StepBody>& bodies) {
+  for (int k = 0; k < nsteps; ++k) {
+    const int rc = tsize_ == sizeof(float) ? capture_step_t<float>(g, cs, B, bodies)
+                                           : capture_step_t<double>(g, cs, B, bodies);
+    if (rc) return rc;
+  }
+  return HENRY_OK;
+}
+
+int Solver::capture_body(const StepBody& sb, int B, cudaStream_t bs) {
+  return tsize_ == sizeof(float) ? capture_body_t<float>(sb, B, bs)
+                                 : capture_body_t<double>(sb, B, bs);
+}
+
+// One implicit Euler step as a CUDA graph (capture_step + its body),
+// rebuilt when B changes: one graph launch per step, no host
+// synchronisation.
 template <typename T>
 int Solver::step_graph(int B, cudaStream_t s) {
   if (graph_B_ != B) {
@@ -507,35 +622,15 @@ int Solver::step_graph(int B, cudaStream_t s) {
     CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
     cudaGraph_t g;
     CK(cudaGraphCreate(&g, 0));
-    cudaGraphConditionalHandle h;
-    CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
-    cond_handle_ = (unsigned long long)h;
+    std::vector<StepBody> bodies;
     CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    MGLevel& F = levels_.back();
-    k_begin_step<<<grid1((int64_t)B * F.g.ncell()), kBlock, 0, cs>>>(
-        counter_, F.g, B, F.p, F.c, p_prev_, c_old_, status_w_, active_, it_step_, step_,
-        cfg_.guess_extrapolation, cfg_.field_model == 1 ? qin0_ : nullptr, qin_, tau_);
-    enqueue_resjac_check<T>(B, cs, true);
-    cudaStreamCaptureStatus st;
-    cudaGraph_t cg;
-    const cudaGraphNode_t* deps = nullptr;
-    size_t nd = 0;
-    CK(cudaStreamGetCaptureInfo(cs, &st, nullptr, &cg, &deps, nullptr, &nd));
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t wn;
-    CK(cudaGraphAddNode(&wn, cg, deps, nullptr, nd, &cp));
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    CK(cudaStreamUpdateCaptureDependencies(cs, &wn, nullptr, 1, cudaStreamSetCaptureDependencies));
-    k_end_step<<<1, 32, 0, cs>>>(counter_, step_);
-    CK(cudaStreamEndCapture(cs, &g));
-    CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    enqueue_iteration<T>(B, bs);
-    enqueue_resjac_check<T>(B, bs, true);
-    CK(cudaStreamEndCapture(bs, &body));
+    int rc = capture_step_t<T>(g, cs, B, bodies);
+    cudaGraph_t gout = g;
+    const cudaError_t ee = cudaStreamEndCapture(cs, &gout);
+    if (rc) return rc;
+    CK(ee);
+    for (const StepBody& sb : bodies)
+      if ((rc = capture_body_t<T>(sb, B, bs))) return rc;
     CK(cudaGraphInstantiate(&step_exec_, g, 0));
     step_graph_ = g;
     graph_B_ = B;
@@ -594,10 +689,12 @@ int Solver::step_t(int B, cudaStream_t s) {
       cfg_.guess_extrapolation, cfg_.field_model == 1 ? qin0_ : nullptr, qin_, tau_);
   for (;;) {
     enqueue_resjac_check<T>(B, s, false);
-    CK(cudaMemcpyAsync(n_active_host_, n_active_, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(n_active_host_, n_active_, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (*n_active_host_ == 0) break;
-    enqueue_iteration<T>(B, s);
+    if (n_active_host_[0] == 0) break;
+    // with operator reuse, the rebuild is skipped when no sample asked for it
+    if (!cfg_.jac_lag || n_active_host_[1] > 0) enqueue_rebuild<T>(B, s);
+    enqueue_solve_update<T>(B, s);
   }
   k_end_step<<<1, 32, 0, s>>>(counter_, step_);
   return HENRY_OK;
@@ -619,6 +716,19 @@ int Solver::run_t(const double* xi, const double* logk, int B, double* q, double
                                  nullptr, nullptr, nout * kNQ);
     }
   }
+  return finish(B, q, c_out, p_out, status, iters, status_or, s);
+}
+
+int Solver::begin(const double* xi, const double* logk, int B, cudaStream_t s) {
+  if (B == 0) return HENRY_OK;
+  int rc = ensure(B, s);
+  if (rc) return rc;
+  last_B_ = B;
+  return tsize_ == sizeof(float) ? setup_t<float>(xi, logk, B, s) : setup_t<double>(xi, logk, B, s);
+}
+
+int Solver::finish(int B, double* q, double* c_out, double* p_out, int* status, int* iters,
+                   int status_or, cudaStream_t s) {
   MGLevel& F = levels_.back();
   const Geom& G = F.g;
   k_qoi<<<B, kBlock, 0, s>>>(counter_, phys_, G, B, F.p, F.c, F.phi, q, c_out, p_out, kNQ);

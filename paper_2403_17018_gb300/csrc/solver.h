@@ -38,6 +38,16 @@ struct MGLevel {
 // Returns false if the coarsest grid has more than 32 cells or an odd nx.
 bool build_hierarchy(int nx, int ny, double Lx, double Ly, std::vector<Geom>& out);
 
+class Solver;
+
+// The body graph of one step's conditional while node, captured after the
+// capture of the enclosing graph has ended.
+struct StepBody {
+  Solver* solver;
+  cudaGraph_t body;
+  unsigned long long cond;   // cudaGraphConditionalHandle of the node
+};
+
 class Solver {
  public:
   Solver(const henry_config& cfg, int nx, int ny, int nt);
@@ -56,6 +66,18 @@ class Solver {
   // Discrete adjoint of QoI `qoi` (0 Q_S, 2 toe); see henry_adjoint.
   int adjoint(const double* xi, const double* logk, int B, int qoi, int ckpt_every, double* q,
               double* dq_dxi, double* dq_dlogk, int* status, cudaStream_t s);
+  // A solve split for callers that drive the time steps themselves (one
+  // graph for the steps of several solvers): begin() evaluates the fields
+  // and the initial state, capture_steps() records `nsteps` implicit steps
+  // on a stream that is capturing into graph g (bodies to be captured with
+  // capture_body() after that capture ends), finish() computes the QoIs and
+  // copies (or ORs) the status.
+  int begin(const double* xi, const double* logk, int B, cudaStream_t s);
+  int capture_steps(cudaGraph_t g, cudaStream_t cs, int B, int nsteps,
+                    std::vector<StepBody>& bodies);
+  int capture_body(const StepBody& sb, int B, cudaStream_t bs);
+  int finish(int B, double* q, double* c_out, double* p_out, int* status, int* iters,
+             int status_or, cudaStream_t s);
   // Fields only (henry_fields).
   int fields(const double* xi, const double* logk, int B, double* phi, double* K, double* qin,
              cudaStream_t s);
@@ -68,6 +90,9 @@ class Solver {
   int time_kernel(int which, int reps, cudaStream_t s, void* flush, int64_t flush_bytes,
                   double* avg_ms, double* bytes, double* flops);
   int batch() const { return last_B_; }
+  // Incremented whenever the workspace is reallocated (graphs recorded on
+  // the old workspace must be rebuilt).
+  unsigned long long generation() const { return generation_; }
   // Copy an internal array (see henry_debug_copy); returns HENRY_* code.
   int debug_copy(int mg_level, int what, void* dst, int64_t bytes) const;
 
@@ -83,8 +108,14 @@ class Solver {
   template <typename T> void enqueue_precond(int B, cudaStream_t s);
   template <typename T> void enqueue_bicgstab(int B, cudaStream_t s);
   template <typename T> void enqueue_iteration(int B, cudaStream_t s);
+  template <typename T> void enqueue_rebuild(int B, cudaStream_t s);
+  template <typename T> void enqueue_solve_update(int B, cudaStream_t s);
   template <typename T> void enqueue_vcycle(int k, int B, cudaStream_t s);
-  template <typename T> void enqueue_resjac_check(int B, cudaStream_t s, bool set_cond);
+  template <typename T> void enqueue_resjac_check(int B, cudaStream_t s, bool set_cond,
+                                                  unsigned long long cond = 0);
+  template <typename T> int capture_step_t(cudaGraph_t g, cudaStream_t cs, int B,
+                                           std::vector<StepBody>& bodies);
+  template <typename T> int capture_body_t(const StepBody& sb, int B, cudaStream_t bs);
   template <typename T> int step_graph(int B, cudaStream_t s);
   template <typename T> void launch_timed(int which, int B, cudaStream_t s);
   template <typename T> void launch_small(int B, int ncycles, cudaStream_t s);
@@ -104,6 +135,7 @@ class Solver {
   std::vector<Geom> geoms_;   // 0 = coarsest
   std::vector<MGLevel> levels_;
   int cap_ = 0;               // allocated batch capacity
+  unsigned long long generation_ = 0;
   int last_B_ = 0;            // batch of the last solve
   void* arena_ = nullptr;
   // finest-level / per-sample arrays
@@ -122,7 +154,7 @@ class Solver {
   int* it_step_ = nullptr;
   int* status_w_ = nullptr;
   int* iters_w_ = nullptr;
-  int* n_active_ = nullptr;     // device
+  int* n_active_ = nullptr;     // device: active samples, samples rebuilding operators
   void* kry_v_[6] = {};           // BiCGStab vectors r, rh, p, v, t, xk (krylov_iters > 0)
   double* kry_S_ = nullptr;       // per-sample BiCGStab scalars [B][kKryS]
   double* kry_part_ = nullptr;    // dot-product partials [2][B][kry_nchunk_]
@@ -141,7 +173,6 @@ class Solver {
   cudaGraphExec_t step_exec_ = nullptr;
   cudaGraph_t step_graph_ = nullptr;
   int graph_B_ = -1;
-  unsigned long long cond_handle_ = 0;
   // adjoint workspace (allocated on the first henry_adjoint call)
   void* adj_arena_ = nullptr;
   int adj_B_ = 0, adj_nckpt_ = 0, adj_seg_ = 0, adj_nchunk_ = 0;

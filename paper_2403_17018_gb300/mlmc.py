@@ -149,8 +149,8 @@ class GpuSampler:
                 self.ctxs[l] = shared
             else:
                 kw = cfg.as_dict()
-                kw.update({k: sc[k] for k in ("vcycles", "nu1", "nu2", "mg_small_cells", "jac_lag")
-                           if k in sc})
+                kw.update({k: sc[k] for k in ("vcycles", "nu1", "nu2", "mg_small_cells", "jac_lag",
+                                              "res_rows") if k in sc})
                 self.ctxs[l] = hb.Context(hb.default_config(**kw))
         self.streams = {l: torch.cuda.Stream() for l in range(cfg.nlevels)}
 
@@ -393,7 +393,8 @@ def tuned_run(levels=6, eps=1e-3, n_xi=6, precision="fp32mg", vcycles=3, tune=Tr
     res.update({"precision": precision, "n_gpus": world, "tuning_s": tune_s,
                 "concurrent_levels": concurrent,
                 "schedules": {l: {k: v for k, v in sc.items() if k in ("vcycles", "nu1", "nu2",
-                                                                      "mg_small_cells", "jac_lag")}
+                                                                      "mg_small_cells", "jac_lag",
+                                                                      "res_rows")}
                               for l, sc in (schedules or {}).items()}})
     return res
 
