@@ -151,7 +151,22 @@ typedef struct henry_config {
                            1..64; 0 (default): 8. A schedule knob for the
                            autotuner: it trades blocks per sample against
                            recomputed faces at tile edges */
+  int discretisation;   /* HENRY_DISC_CELL (default) or HENRY_DISC_VERTEX:
+                           the vertex-centred variant of section 2.3 (box
+                           method with partial upwinding; see
+                           henry_residual_jacobian_vc). With the vertex
+                           variant henry_solve, henry_sample_pairs and
+                           henry_sample_levels return nodal fields c_out,
+                           p_out of shape [B][ny_l + 1][nx_l] (the unknown
+                           nodes i = 0..nx_l-1; x = Lx is Dirichlet);
+                           henry_adjoint, henry_solve_series, henry_fields
+                           and henry_time_kernel return HENRY_E_UNSUPPORTED */
 } henry_config;
+
+#define HENRY_DISC_CELL 0        /* cell-centred, full upwind (default)      */
+#define HENRY_DISC_VERTEX 1      /* vertex-centred, exponentially fitted
+                                    partial upwind, the paper's Dirichlet
+                                    boundaries                               */
 
 typedef struct henry_ctx henry_ctx; /* opaque: owns device workspaces */
 
@@ -368,6 +383,34 @@ int henry_residual_jacobian_noalloc(const henry_config* cfg, int nx, int ny, dou
                                     const double* phi, const double* K, const double* qin,
                                     const double* p, const double* c, const double* c_old,
                                     double* R, double* J, void* stream);
+
+/* The residual of one implicit Euler step of the vertex-centred variant
+ * (section 2.3: vertex-centred finite volumes, partial upwinding of the
+ * convective terms) and, optionally, its exact Jacobian, for B states on
+ * the nodes of an nx x ny cell grid. Context-free; for tests and tools.
+ * Scheme (this library's reading; the paper refers to ug4 for it): node
+ * boxes clipped to the domain; the random field of `xi` (field model and
+ * n_xi of cfg) evaluated at integration points -- phi at the quarter-cell
+ * centres of each box for its storage, K and phi at the midpoints of the
+ * two half segments of each box face for its transmissibility and
+ * diffusive conductance; two-point Darcy fluxes with the mean density in
+ * the gravity and diffusion terms; advected rho and rho c weighted by
+ * w = (1 + alpha(Pe) sgn Q) / 2, alpha(Pe) = coth(Pe/2) - 2/Pe (exponential
+ * fitting, Allen-Southwell / Il'in), Pe = |Q| / (diffusive conductance);
+ * boundaries of section 2.1: x = Lx Dirichlet p = rho1 g (Ly - y), c = 1
+ * (not unknowns), x = 0 inflow rho0 q_in and c = 0, its salt row being
+ * (V phi0 rho0 / tau) c; top and bottom closed.
+ *   xi              device [B][n_xi]
+ *   p, c, c_old     device [B][ny+1][nx]: nodes i = 0..nx-1, j = 0..ny;
+ *                   p is the full pressure
+ *   R               device [B][2][ny+1][nx] out: R_p then R_c
+ *   J               device [B][20][ny+1][nx] out or NULL: blocks P, W, E,
+ *                   S, N of d R_P / d u_Q as in henry_residual_jacobian
+ * nx must be even and >= 2, ny >= 1, 0 <= B <= HENRY_MAX_BATCH. Allocates
+ * its scratch (stream-ordered). Errors: HENRY_E_INVALID, HENRY_E_CUDA. */
+int henry_residual_jacobian_vc(const henry_config* cfg, int nx, int ny, double tau, int B,
+                               const double* xi, const double* p, const double* c,
+                               const double* c_old, double* R, double* J, void* stream);
 
 /* Random fields of the level-l grid for B samples (cell centres):
  *   phi = phi0 (1 + 0.1 xi1 cos(pi x/2) sin(pi y) [+ 0.05 xi4 cos(pi x) sin(2 pi y)])

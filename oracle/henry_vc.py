@@ -258,7 +258,11 @@ def newton_step(grid, phys, vf, p, c, c_old, maxit=30, tol_c=1e-12, tol_p_rel=1e
 
 
 def solve(grid, phys, xi, c0=None, p0=None, keep_states=False):
-    """Implicit Euler time loop (field model 0, no recharge time factor)."""
+    """Implicit Euler time loop from c = 0 (or c0). With the paper's field
+    model the inflow of step n carries (1 + sin(pi t / 40)) at t = n tau, as
+    in oracle.henry.solve."""
+    import dataclasses
+    import math
     vf = vfields(grid, phys, xi)
     p, c = initial_state(grid, phys)
     if c0 is not None:
@@ -267,8 +271,12 @@ def solve(grid, phys, xi, c0=None, p0=None, keep_states=False):
         p = np.array(p0, dtype=float)
     its = []
     states = [(p.copy(), c.copy())] if keep_states else None
-    for _ in range(grid.nt):
-        p, c, it = newton_step(grid, phys, vf, p, c, c.copy())
+    for n in range(grid.nt):
+        vn = vf
+        if phys.field_model == 1:
+            t = (n + 1) * grid.tau
+            vn = dataclasses.replace(vf, qin=vf.qin * (1.0 + math.sin(math.pi * t / 40.0)))
+        p, c, it = newton_step(grid, phys, vn, p, c, c.copy())
         its.append(it)
         if keep_states:
             states.append((p.copy(), c.copy()))

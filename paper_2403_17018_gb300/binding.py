@@ -23,6 +23,8 @@ PREC_FP64 = 0
 PREC_FP32_MG = 1
 LOOP_HOST = 0
 LOOP_GRAPH = 1
+DISC_CELL = 0
+DISC_VERTEX = 1
 S_MAXIT, S_NONFINITE, S_BADINPUT = 1, 2, 4
 ERRORS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "out of device memory",
           -4: "device wait timed out", -5: "unsupported grid"}
@@ -46,7 +48,7 @@ class HenryConfig(ctypes.Structure):
                 ("mg_cluster_cells", ctypes.c_int), ("mg_small_cells", ctypes.c_int),
                 ("jac_lag", ctypes.c_int), ("field_model", ctypes.c_int),
                 ("krylov_iters", ctypes.c_int), ("adjoint_rtol", ctypes.c_double),
-                ("res_rows", ctypes.c_int)]
+                ("res_rows", ctypes.c_int), ("discretisation", ctypes.c_int)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
@@ -106,6 +108,7 @@ def load():
         "mlmc_field_exceedance": (I, [P, I, V, I, V, D, V, V]),
         "henry_residual_jacobian": (I, [cfgp, I, I, D, I, V, V, V, V, V, V, V, V, V]),
         "henry_residual_jacobian_noalloc": (I, [cfgp, I, I, D, I, V, V, V, V, V, V, V, V, V]),
+        "henry_residual_jacobian_vc": (I, [cfgp, I, I, D, I, V, V, V, V, V, V, V]),
         "henry_fields": (I, [P, I, V, V, I, V, V, V, V]),
         "henry_adjoint": (I, [P, I, V, V, I, I, I, V, V, V, V, V]),
         "henry_level_info": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
@@ -203,6 +206,12 @@ class Context:
         _check(self.lib.henry_level_info(self._h, level, *[ctypes.byref(x) for x in v]))
         return LevelInfo(*[x.value for x in v])
 
+    def field_shape(self, level):
+        """Shape of one sample's c / p output at `level`: (ny, nx) cells, or
+        (ny + 1, nx) unknown nodes with the vertex-centred variant."""
+        li = self.level_info(level)
+        return (li.ny + 1, li.nx) if self.cfg.discretisation == DISC_VERTEX else (li.ny, li.nx)
+
     def debug_copy(self, level, role, mg_level, what, nbytes):
         """henry_debug_copy into a host numpy byte buffer."""
         buf = np.zeros(nbytes, dtype=np.uint8)
@@ -233,8 +242,10 @@ class Context:
         dev = xi.device
         q = torch.empty((B, NQ), dtype=torch.float64, device=dev)
         st = torch.empty((B,), dtype=torch.int32, device=dev)
-        c = torch.empty((B, li.ny, li.nx), dtype=torch.float64, device=dev) if want_c else None
-        p = torch.empty((B, li.ny, li.nx), dtype=torch.float64, device=dev) if want_p else None
+        c = torch.empty((B,) + self.field_shape(level), dtype=torch.float64, device=dev) \
+            if want_c else None
+        p = torch.empty((B,) + self.field_shape(level), dtype=torch.float64, device=dev) \
+            if want_p else None
         it = torch.empty((B,), dtype=torch.int32, device=dev) if want_iters else None
         _check(self.lib.henry_solve(
             self._h, level, _ptr(xi, torch.float64, (B, self.cfg.n_xi), "xi"),
@@ -265,11 +276,11 @@ class Context:
         li = self.level_info(level)
         qf = torch.empty((B, NQ), dtype=torch.float64, device=dev)
         qc = torch.empty((B, NQ), dtype=torch.float64, device=dev) if level > 0 else None
-        cf = torch.empty((B, li.ny, li.nx), dtype=torch.float64, device=dev) if want_c else None
+        cf = torch.empty((B,) + self.field_shape(level), dtype=torch.float64, device=dev) \
+            if want_c else None
         cc = None
         if want_c and level > 0:
-            lc = self.level_info(level - 1)
-            cc = torch.empty((B, lc.ny, lc.nx), dtype=torch.float64, device=dev)
+            cc = torch.empty((B,) + self.field_shape(level - 1), dtype=torch.float64, device=dev)
         st = torch.empty((B,), dtype=torch.int32, device=dev)
         _check(self.lib.henry_sample_pairs(
             self._h, level, _ptr(xi, torch.float64, (B, self.cfg.n_xi), "xi"), B, _ptr(qf),
@@ -295,11 +306,12 @@ class Context:
             li = self.level_info(level)
             qf = torch.empty((B, NQ), dtype=torch.float64, device=dev)
             qc = torch.empty((B, NQ), dtype=torch.float64, device=dev) if level > 0 else None
-            cf = torch.empty((B, li.ny, li.nx), dtype=torch.float64, device=dev) if want_c else None
+            cf = torch.empty((B,) + self.field_shape(level), dtype=torch.float64, device=dev) \
+                if want_c else None
             cc = None
             if want_c and level > 0:
-                lc = self.level_info(level - 1)
-                cc = torch.empty((B, lc.ny, lc.nx), dtype=torch.float64, device=dev)
+                cc = torch.empty((B,) + self.field_shape(level - 1), dtype=torch.float64,
+                                 device=dev)
             st = torch.empty((B,), dtype=torch.int32, device=dev)
             p = lambda t, name=None, **kw: _ptr(t, **kw)
             arr[i] = HenryLevelBatch(level, B, _ptr(xi, torch.float64, (B, self.cfg.n_xi), "xi"),
@@ -403,6 +415,22 @@ def residual_jacobian(cfg: HenryConfig, tau, phi, K, qin, p, c, c_old, want_J=Tr
         _ptr(K, f64, (B, ny, nx), "K"), _ptr(qin, f64, (B, ny), "qin"), _ptr(p, f64, None, "p"),
         _ptr(c, f64, (B, ny, nx), "c"), _ptr(c_old, f64, (B, ny, nx), "c_old"), _ptr(R), _ptr(J),
         _stream(stream)))
+    return R, J
+
+
+def residual_jacobian_vc(cfg: HenryConfig, tau, xi, p, c, c_old, want_J=True, stream=None):
+    """henry_residual_jacobian_vc: R [B,2,ny+1,nx] and J [B,20,ny+1,nx] (or
+    None) of the vertex-centred variant; p, c, c_old [B, ny+1, nx] at the
+    unknown nodes (nx, ny: cells of the grid)."""
+    import torch
+    B, ny1, nx = p.shape
+    R = torch.empty((B, 2, ny1, nx), dtype=torch.float64, device=p.device)
+    J = torch.empty((B, 20, ny1, nx), dtype=torch.float64, device=p.device) if want_J else None
+    f64 = torch.float64
+    _check(load().henry_residual_jacobian_vc(
+        ctypes.byref(cfg), nx, ny1 - 1, float(tau), B, _ptr(xi, f64, (B, cfg.n_xi), "xi"),
+        _ptr(p, f64, (B, ny1, nx), "p"), _ptr(c, f64, (B, ny1, nx), "c"),
+        _ptr(c_old, f64, (B, ny1, nx), "c_old"), _ptr(R), _ptr(J), _stream(stream)))
     return R, J
 
 

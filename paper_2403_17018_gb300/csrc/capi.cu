@@ -9,6 +9,7 @@
 
 #include "../../include/henry.h"
 #include "solver.h"
+#include "vc.h"
 
 namespace henry {
 cudaError_t launch_level_stats(unsigned long long* ctr, int B, const double* qf, const double* qc,
@@ -39,6 +40,7 @@ struct henry_ctx {
   int device = 0;
   // solvers per level: [0] fine role, [1] coarse role (level l-1 of a pair)
   std::vector<std::unique_ptr<Solver>> role[2];
+  std::vector<std::unique_ptr<henry::VcSolver>> vc_role[2];   // discretisation = vertex
   // per level: stream, events and status buffer of the concurrently run
   // coarse half of a pair (created on first use)
   std::vector<cudaStream_t> pair_stream;
@@ -93,6 +95,19 @@ Solver* get_solver(henry_ctx* ctx, int level, int role) {
   return v[level].get();
 }
 
+henry::VcSolver* get_vc_solver(henry_ctx* ctx, int level, int role) {
+  auto& v = ctx->vc_role[role];
+  if (!v[level]) {
+    int nx, ny, nt;
+    level_dims(ctx->cfg, level, &nx, &ny, &nt);
+    const henry_config& c = ctx->level_cfg[role == 0 ? level : level + 1];
+    v[level].reset(new henry::VcSolver(c, nx, ny, nt));
+  }
+  return v[level].get();
+}
+
+bool is_vertex(const henry_ctx* ctx) { return ctx->cfg.discretisation == HENRY_DISC_VERTEX; }
+
 void drop_multi_graph(henry_ctx* ctx) {
   if (ctx->multi_exec) cudaGraphExecDestroy(ctx->multi_exec);
   if (ctx->multi_graph) cudaGraphDestroy(ctx->multi_graph);
@@ -123,6 +138,10 @@ int validate(const henry_config* c) {
   if (!(c->adjoint_rtol > 0.0) || !(c->adjoint_rtol < 1e-3))
     return fail(HENRY_E_INVALID, "adjoint_rtol must be in (0, 1e-3)");
   if (c->res_rows < 0 || c->res_rows > 64) return fail(HENRY_E_INVALID, "res_rows must be in 0..64");
+  if (c->discretisation != HENRY_DISC_CELL && c->discretisation != HENRY_DISC_VERTEX)
+    return fail(HENRY_E_INVALID, "discretisation must be HENRY_DISC_CELL or HENRY_DISC_VERTEX");
+  if (c->discretisation == HENRY_DISC_VERTEX && (c->nx0 % 2 || c->ny0 < 1))
+    return fail(HENRY_E_INVALID, "the vertex-centred variant needs an even nx0");
   for (int l = 0; l < c->nlevels; ++l) {
     std::vector<henry::Geom> g;
     if (!henry::build_hierarchy(c->nx0 << l, c->ny0 << l, c->Lx, c->Ly, g))
@@ -186,6 +205,8 @@ int henry_create_levels(const henry_config* cfg, henry_ctx** out) {
   ctx->level_cfg.assign(cfg->nlevels, *cfg);
   ctx->role[0].resize(cfg->nlevels);
   ctx->role[1].resize(cfg->nlevels);
+  ctx->vc_role[0].resize(cfg->nlevels);
+  ctx->vc_role[1].resize(cfg->nlevels);
   ctx->pair_stream.assign(cfg->nlevels, nullptr);
   ctx->pair_fork.assign(cfg->nlevels, nullptr);
   ctx->pair_join.assign(cfg->nlevels, nullptr);
@@ -213,6 +234,7 @@ void henry_destroy(henry_ctx* ctx) {
   for (cudaStream_t st : ctx->multi_streams) cudaStreamDestroy(st);
   for (cudaEvent_t ev : ctx->multi_events) cudaEventDestroy(ev);
   for (auto& v : ctx->role) v.clear();
+  for (auto& v : ctx->vc_role) v.clear();
   for (size_t l = 0; l < ctx->pair_stream.size(); ++l) {
     if (ctx->pair_stream[l]) cudaStreamDestroy(ctx->pair_stream[l]);
     if (ctx->pair_fork[l]) cudaEventDestroy(ctx->pair_fork[l]);
@@ -241,6 +263,11 @@ int henry_solve(henry_ctx* ctx, int level, const double* xi, const double* logk,
   if (B == 0) return HENRY_OK;
   if (!xi || !q || !status) return fail(HENRY_E_INVALID, "xi, q and status are required");
   CKR(cudaSetDevice(ctx->device));
+  if (is_vertex(ctx)) {
+    if (logk) return fail(HENRY_E_UNSUPPORTED, "the vertex-centred variant takes no log-K field");
+    return get_vc_solver(ctx, level, 0)->run(xi, B, q, c_out, p_out, status, iters, 0,
+                                             (cudaStream_t)stream);
+  }
   return get_solver(ctx, level, 0)->run(xi, logk, B, q, c_out, p_out, status, iters, 0,
                                         (cudaStream_t)stream);
 }
@@ -254,6 +281,7 @@ int henry_solve_series(henry_ctx* ctx, int level, const double* xi, const double
   if (B == 0) return HENRY_OK;
   if (!xi || !q_series || !q || !status)
     return fail(HENRY_E_INVALID, "xi, q_series, q and status are required");
+  if (is_vertex(ctx)) return fail(HENRY_E_UNSUPPORTED, "no QoI series for the vertex-centred variant");
   CKR(cudaSetDevice(ctx->device));
   return get_solver(ctx, level, 0)->run_series(xi, logk, B, every, q_series, q, status,
                                                (cudaStream_t)stream);
@@ -272,6 +300,12 @@ int henry_sample_pairs(henry_ctx* ctx, int level, const double* xi, int B, doubl
   if (!xi || !q_fine || !status) return fail(HENRY_E_INVALID, "xi, q_fine and status are required");
   CKR(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
+  if (is_vertex(ctx)) {   // the two halves one after the other on `stream`
+    int rc = get_vc_solver(ctx, level, 0)->run(xi, B, q_fine, c_fine, nullptr, status, nullptr, 0, s);
+    if (rc || level == 0) return rc;
+    return get_vc_solver(ctx, level - 1, 1)->run(xi, B, q_coarse, c_coarse, nullptr, status,
+                                                 nullptr, 1, s);
+  }
   if (level == 0)
     return get_solver(ctx, 0, 0)->run(xi, nullptr, B, q_fine, c_fine, nullptr, status, nullptr, 0, s);
   // the coarse half runs concurrently on a stream forked from the caller's
@@ -338,7 +372,7 @@ int henry_sample_levels(henry_ctx* ctx, const henry_level_batch* batches, int n,
   }
   CKR(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
-  if (ctx->cfg.loop_mode == HENRY_LOOP_HOST) {
+  if (ctx->cfg.loop_mode == HENRY_LOOP_HOST || is_vertex(ctx)) {
     // host-side Newton loops: the pairs one level after another
     for (int i = 0; i < n; ++i) {
       const henry_level_batch& b = batches[i];
@@ -442,6 +476,7 @@ int henry_adjoint(henry_ctx* ctx, int level, const double* xi, const double* log
   if (qoi_id != 0 && qoi_id != 2) return fail(HENRY_E_INVALID, "qoi_id must be 0 (Q_S) or 2 (toe)");
   if (B == 0) return HENRY_OK;
   if (!xi || !q || !dq_dxi || !status) return fail(HENRY_E_INVALID, "xi, q, dq_dxi, status required");
+  if (is_vertex(ctx)) return fail(HENRY_E_UNSUPPORTED, "no adjoint for the vertex-centred variant");
   CKR(cudaSetDevice(ctx->device));
   return get_solver(ctx, level, 0)->adjoint(xi, logk, B, qoi_id, ckpt_every, q, dq_dxi, dq_dlogk,
                                             status, (cudaStream_t)stream);
@@ -454,6 +489,7 @@ int henry_fields(henry_ctx* ctx, int level, const double* xi, const double* logk
   if (B < 0 || B > HENRY_MAX_BATCH) return fail(HENRY_E_INVALID, "B must be in 0..65535");
   if (B == 0) return HENRY_OK;
   if (!xi || !phi || !K || !qin) return fail(HENRY_E_INVALID, "NULL argument");
+  if (is_vertex(ctx)) return fail(HENRY_E_UNSUPPORTED, "cell fields only (cell-centred variant)");
   CKR(cudaSetDevice(ctx->device));
   return get_solver(ctx, level, 0)->fields(xi, logk, B, phi, K, qin, (cudaStream_t)stream);
 }
@@ -544,6 +580,29 @@ int henry_residual_jacobian(const henry_config* cfg, int nx, int ny, double tau,
   return HENRY_OK;
 }
 
+int henry_residual_jacobian_vc(const henry_config* cfg, int nx, int ny, double tau, int B,
+                               const double* xi, const double* p, const double* c,
+                               const double* c_old, double* R, double* J, void* stream) {
+  if (!cfg) return fail(HENRY_E_INVALID, "config is NULL");
+  if (nx < 2 || nx % 2 || ny < 1 || B < 0 || B > HENRY_MAX_BATCH || !(tau > 0))
+    return fail(HENRY_E_INVALID, "bad sizes (even nx >= 2, ny >= 1, 0 <= B <= 65535, tau > 0)");
+  if (cfg->n_xi != 3 && cfg->n_xi != 6) return fail(HENRY_E_INVALID, "n_xi must be 3 or 6");
+  if (B == 0) return HENRY_OK;
+  if (!xi || !p || !c || !c_old || !R) return fail(HENRY_E_INVALID, "NULL argument");
+  henry::Phys P{cfg->rho0, cfg->rho1 - cfg->rho0, cfg->mu, cfg->g, cfg->D, cfg->K0, cfg->phi0,
+                cfg->q0, cfg->Lx, cfg->Ly};
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)B * nx * (ny + 1), rows = (size_t)B * (ny + 1);
+  double* scratch = nullptr;
+  CKR(cudaMallocAsync((void**)&scratch, sizeof(double) * (7 * n + 2 * rows), s));
+  cudaError_t e = henry::launch_vc_residual_jacobian(P, nx, ny, cfg->field_model, cfg->n_xi, tau, B,
+                                                     xi, p, c, c_old, R, J, scratch, s);
+  cudaError_t e2 = cudaFreeAsync(scratch, s);
+  CKR(e);
+  CKR(e2);
+  return HENRY_OK;
+}
+
 int henry_debug_copy(henry_ctx* ctx, int level, int role, int mg_level, int what, void* dst,
                      int64_t bytes) {
   if (!ctx || level < 0 || level >= ctx->cfg.nlevels || role < 0 || role > 1)
@@ -562,6 +621,7 @@ int henry_time_kernel(henry_ctx* ctx, int level, int role, int which, int reps, 
   if (!ctx || level < 0 || level >= ctx->cfg.nlevels || role < 0 || role > 1 || !avg_ms ||
       !bytes || !flops)
     return fail(HENRY_E_INVALID, "bad argument");
+  if (is_vertex(ctx)) return fail(HENRY_E_UNSUPPORTED, "kernel timing of the cell-centred solver only");
   const auto& s = ctx->role[role][level];
   if (!s) return fail(HENRY_E_INVALID, "no solver has run for this level and role");
   CKR(cudaSetDevice(ctx->device));
@@ -589,6 +649,9 @@ int64_t henry_launch_count(const henry_ctx* ctx) {
   cudaDeviceSynchronize();
   if (ctx->ctr && cudaMemcpy(&v, ctx->ctr, sizeof(v), cudaMemcpyDeviceToHost) == cudaSuccess) total += v;
   for (const auto& r : ctx->role)
+    for (const auto& s : r)
+      if (s) total += s->launches();
+  for (const auto& r : ctx->vc_role)
     for (const auto& s : r)
       if (s) total += s->launches();
   return (int64_t)total;

@@ -265,6 +265,49 @@ __device__ __forceinline__ void gather_cell(const Geom& G, int i, int j, const d
   if (in.hasN) { in.pN = p[id + nx]; in.cN = c[id + nx]; in.tN = ty[id]; in.dN = dy[id]; }
 }
 
+// Random fields at the point (x, y) (frame y in [0, Ly]) for one sample's
+// random vector z (see henry.h, henry_fields): porosity and permeability,
+// with the log-K perturbation lk when has_lk. model 1: the paper's
+// two-layer porosity (Eq. poro_2levels, in its frame y_p = y - Ly) and
+// Kozeny-Carman K with kappa = K0 (1 - phi0^2) / phi0^3 (Eq.
+// e_perm_Kozeny_Carman); model 0: the smooth fields of 3 or 6 variables.
+__device__ __forceinline__ void field_at(const Phys& P, int model, int n_xi, const double* z,
+                                         double x, double y, bool has_lk, double lk, double& phi,
+                                         double& K) {
+  const double pi = 3.14159265358979323846;
+  if (model == 1) {
+    const double yp = y - P.Ly;
+    const double c0 = yp < -0.8 ? 1.2 * (1.0 + 0.2 * z[0]) : 1.0;
+    const double c1 = 1.0 + 0.15 * (z[1] * cos(pi * x / 2) - z[1] * sin(2 * pi * yp) +
+                                    z[0] * cos(2 * pi * x));
+    const double c2 = 1.0 + 0.2 * (z[0] * sin(64 * pi * x) + z[1] * sin(32 * pi * yp));
+    phi = P.phi0 * c0 * c1 * c2;
+    const double kappa = P.K0 * (1.0 - P.phi0 * P.phi0) / (P.phi0 * P.phi0 * P.phi0);
+    K = kappa * (phi * phi * phi) / (1.0 - phi * phi);
+    if (has_lk) K *= exp(lk);
+    return;
+  }
+  double a = 0.1 * z[0] * cos(0.5 * pi * x) * sin(pi * y);
+  double e = 0.5 * z[1] * sin(0.5 * pi * x) * cos(pi * y);
+  if (n_xi >= 6) {
+    a += 0.05 * z[3] * cos(pi * x) * sin(2.0 * pi * y);
+    e += 0.05 * z[4] * sin(pi * x) * cos(2.0 * pi * y);
+  }
+  if (has_lk) e += lk;
+  phi = P.phi0 * (1.0 + a);
+  K = P.K0 * exp(e);
+}
+
+// Left-side inflow velocity at height y (model 1: the base of Eq.
+// e_recharge_of_param, its time factor applied per step).
+__device__ __forceinline__ double inflow_at(const Phys& P, int model, int n_xi, const double* z,
+                                            double y) {
+  if (model == 1) return P.q0 * (1.0 + 0.5 * z[2]);
+  double qf = 1.0 + 0.1 * z[2];
+  if (n_xi >= 6) qf += 0.05 * z[5] * cos(3.14159265358979323846 * y);
+  return P.q0 * qf;
+}
+
 // Face constants of cell (i, j): east face (if any) and north face (if any).
 __device__ __forceinline__ void face_constants(const Phys& P, const Geom& G, int i, int j,
                                                const double* __restrict__ phi,

@@ -64,9 +64,10 @@ __device__ __forceinline__ void store_operator(T* __restrict__ Jb, int ncell, co
 // set-up kernels (once per solve)
 // ---------------------------------------------------------------------------
 
-// Random fields at cell centres (workload stand-in for the paper's Eq.
-// poro_2levels; see henry.h for the formulas) and the inflow per row.
-__global__ void k_fields(unsigned long long* ctr, Phys P, Geom G, int B, int n_xi, int model,
+// Random fields at cell centres (field_at: the configs' smooth fields, or
+// the paper's Eq. poro_2levels; see henry.h for the formulas) and the
+// inflow per row.
+static __global__ void k_fields(unsigned long long* ctr, Phys P, Geom G, int B, int n_xi, int model,
                          const double* __restrict__ xi, const double* __restrict__ logk,
                          double* __restrict__ phi, double* __restrict__ K, double* __restrict__ qin,
                          int* __restrict__ status) {
@@ -79,54 +80,21 @@ __global__ void k_fields(unsigned long long* ctr, Phys P, Geom G, int B, int n_x
   const int j = cell / G.nx, i = cell - j * G.nx;
   const double x = (i + 0.5) * G.hx, y = (j + 0.5) * G.hy;
   const double* z = xi + (int64_t)b * n_xi;
-  const double pi = 3.14159265358979323846;
-  if (model == 1) {
-    // Eq. poro_2levels in the paper's frame y_p = y - Ly: two layers split
-    // at y_p = -0.8, a smooth and a high-frequency (64 pi x, 32 pi y) factor;
-    // K from Eq. e_perm_Kozeny_Carman with kappa_KC = K0 (1 - phi0^2) / phi0^3
-    // (the mean porosity gives K0); q_in base of Eq. e_recharge_of_param
-    // (its time factor is applied per step by k_begin_step)
-    const double yp = y - P.Ly;
-    const double c0 = yp < -0.8 ? 1.2 * (1.0 + 0.2 * z[0]) : 1.0;
-    const double c1 = 1.0 + 0.15 * (z[1] * cos(pi * x / 2) - z[1] * sin(2 * pi * yp) +
-                                    z[0] * cos(2 * pi * x));
-    const double c2 = 1.0 + 0.2 * (z[0] * sin(64 * pi * x) + z[1] * sin(32 * pi * yp));
-    const double ph = P.phi0 * c0 * c1 * c2;
-    const double kappa = P.K0 * (1.0 - P.phi0 * P.phi0) / (P.phi0 * P.phi0 * P.phi0);
-    double k = kappa * (ph * ph * ph) / (1.0 - ph * ph);
-    if (logk) k *= exp(logk[idx]);
-    phi[idx] = ph;
-    K[idx] = k;
-    if (i == 0) qin[(int64_t)b * G.ny + j] = P.q0 * (1.0 + 0.5 * z[2]);
-    if (cell == 0) {
-      bool ok = true;
-      for (int m = 0; m < n_xi; ++m) ok = ok && isfinite(z[m]);
-      status[b] = ok ? 0 : kStatusBadInput;
-    }
-    return;
-  }
-  double a = 0.1 * z[0] * cos(0.5 * pi * x) * sin(pi * y);
-  double e = 0.5 * z[1] * sin(0.5 * pi * x) * cos(pi * y);
-  double qf = 1.0 + 0.1 * z[2];
-  if (n_xi >= 6) {
-    a += 0.05 * z[3] * cos(pi * x) * sin(2.0 * pi * y);
-    e += 0.05 * z[4] * sin(pi * x) * cos(2.0 * pi * y);
-    qf += 0.05 * z[5] * cos(pi * y);
-  }
-  if (logk) e += logk[idx];
-  phi[idx] = P.phi0 * (1.0 + a);
-  K[idx] = P.K0 * exp(e);
-  if (i == 0) qin[(int64_t)b * G.ny + j] = P.q0 * qf;
+  double ph, k;
+  field_at(P, model, n_xi, z, x, y, logk != nullptr, logk ? logk[idx] : 0.0, ph, k);
+  phi[idx] = ph;
+  K[idx] = k;
+  if (i == 0) qin[(int64_t)b * G.ny + j] = inflow_at(P, model, n_xi, z, y);
   if (cell == 0) {
     bool ok = true;
-    for (int k = 0; k < n_xi; ++k) ok = ok && isfinite(z[k]);
+    for (int m = 0; m < n_xi; ++m) ok = ok && isfinite(z[m]);
     status[b] = ok ? 0 : kStatusBadInput;
   }
 }
 
 // Coarse-grid fields for the rediscretised multigrid operators: arithmetic
 // mean of the four children.
-__global__ void k_coarsen_fields(unsigned long long* ctr, Geom Gf, Geom Gc, int B,
+static __global__ void k_coarsen_fields(unsigned long long* ctr, Geom Gf, Geom Gc, int B,
                                  const double* __restrict__ phif, const double* __restrict__ Kf,
                                  double* __restrict__ phic, double* __restrict__ Kc) {
   HENRY_COUNT_LAUNCH(ctr);
@@ -141,7 +109,7 @@ __global__ void k_coarsen_fields(unsigned long long* ctr, Geom Gf, Geom Gc, int 
   Kc[idx] = 0.25 * (Kf[f0] + Kf[f0 + 1] + Kf[f0 + Gf.nx] + Kf[f0 + Gf.nx + 1]);
 }
 
-__global__ void k_face_consts(unsigned long long* ctr, Phys P, Geom G, int B,
+static __global__ void k_face_consts(unsigned long long* ctr, Phys P, Geom G, int B,
                               const double* __restrict__ phi, const double* __restrict__ K,
                               double* __restrict__ tx, double* __restrict__ dx,
                               double* __restrict__ ty, double* __restrict__ dy) {
@@ -158,7 +126,7 @@ __global__ void k_face_consts(unsigned long long* ctr, Phys P, Geom G, int B,
 
 // Initial state c = 0; the Newton guess for p is seawater hydrostatics,
 // stored as the reduced pressure p' = p - rho0 g (Ly - y).
-__global__ void k_init_state(unsigned long long* ctr, Phys P, Geom G, int B, double* __restrict__ p,
+static __global__ void k_init_state(unsigned long long* ctr, Phys P, Geom G, int B, double* __restrict__ p,
                              double* __restrict__ c, int* __restrict__ iters,
                              int* __restrict__ step) {
   HENRY_COUNT_LAUNCH(ctr);
@@ -184,7 +152,7 @@ __global__ void k_init_state(unsigned long long* ctr, Phys P, Geom G, int B, dou
 // linearly in time, u = 2 u^{n-1} - u^{n-2}, with c clamped to [0, 1]
 // (p_prev keeps p^{n-2}, c_old c^{n-2} on entry). `step` counts completed
 // steps (k_end_step increments it).
-__global__ void k_begin_step(unsigned long long* ctr, Geom G, int B, double* __restrict__ p,
+static __global__ void k_begin_step(unsigned long long* ctr, Geom G, int B, double* __restrict__ p,
                              double* __restrict__ c, double* __restrict__ p_prev,
                              double* __restrict__ c_old, const int* __restrict__ status,
                              int* __restrict__ active, int* __restrict__ it_step,
@@ -221,13 +189,13 @@ __global__ void k_begin_step(unsigned long long* ctr, Geom G, int B, double* __r
 // (graph loop with operator reuse): true when some sample asked for new
 // operators (count published by k_check). When none did, the rebuild
 // kernels, which would all skip every sample, are not launched.
-__global__ void k_set_rebuild(unsigned long long* ctr, const int* __restrict__ n_refresh,
+static __global__ void k_set_rebuild(unsigned long long* ctr, const int* __restrict__ n_refresh,
                               cudaGraphConditionalHandle h) {
   HENRY_COUNT_LAUNCH(ctr);
   if (threadIdx.x == 0) cudaGraphSetConditional(h, *n_refresh > 0 ? 1u : 0u);
 }
 
-__global__ void k_end_step(unsigned long long* ctr, int* __restrict__ step) {
+static __global__ void k_end_step(unsigned long long* ctr, int* __restrict__ step) {
   HENRY_COUNT_LAUNCH(ctr);
   if (threadIdx.x == 0) *step += 1;
 }
@@ -516,7 +484,7 @@ __global__ void k_check(unsigned long long* ctr, int B, int nchunk, int ncell,
 // children; at the right side these are the boundary fluxes). Linearising
 // every level about the same flux field keeps the upwind decisions of the
 // coarse operators consistent with the finest one.
-__global__ void k_restrict_state(unsigned long long* ctr, Geom Gf, Geom Gc, int B,
+static __global__ void k_restrict_state(unsigned long long* ctr, Geom Gf, Geom Gc, int B,
                                  const int* __restrict__ active, const double* __restrict__ cf,
                                  const double* __restrict__ qxf, const double* __restrict__ qyf,
                                  double* __restrict__ cc, double* __restrict__ qxc,
@@ -1068,7 +1036,7 @@ __device__ __forceinline__ double bilinear(const Geom& G, const double* c, doubl
          tx * ty * c[id + G.nx + 1];
 }
 
-__global__ void __launch_bounds__(kBlock)
+static __global__ void __launch_bounds__(kBlock)
 k_qoi(unsigned long long* ctr, Phys P, Geom G, int B, const double* __restrict__ p,
       const double* __restrict__ c, const double* __restrict__ phi, double* __restrict__ q,
       double* __restrict__ c_out, double* __restrict__ p_out, int qstride) {
@@ -1130,7 +1098,7 @@ k_qoi(unsigned long long* ctr, Phys P, Geom G, int B, const double* __restrict__
 }
 
 // p -> p' = p - rho0 g (Ly - y) for the natural-layout entry point.
-__global__ void k_reduce_pressure(Phys P, Geom G, int B, const double* __restrict__ p,
+static __global__ void k_reduce_pressure(Phys P, Geom G, int B, const double* __restrict__ p,
                                   double* __restrict__ pr) {
   const int64_t n = (int64_t)B * G.ncell();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1322,7 +1290,7 @@ k_kry_dot(unsigned long long* ctr, int n2, int B, const int* __restrict__ active
 // (alpha / omega), rho = rho_new; stage 1: alpha = rho / (rh, v); stage 2:
 // omega = (t, s) / (t, t). A zero denominator gives a zero coefficient (the
 // outer defect correction, whose residual is the FP64 one, carries on).
-__global__ void k_kry_scalars(unsigned long long* ctr, int B, int nchunk, int stage,
+static __global__ void k_kry_scalars(unsigned long long* ctr, int B, int nchunk, int stage,
                               const int* __restrict__ active, const double* __restrict__ partial,
                               double* __restrict__ S) {
   HENRY_COUNT_LAUNCH(ctr);
@@ -1407,7 +1375,7 @@ k_kry_update(unsigned long long* ctr, int n2, int B, int op, const int* __restri
 
 // rhs = dQ/du^r (only c enters the QoI), lam = 0. qoi 0: Q_S = int c rho
 // (integrand derivative rho0 + 2 drho c), qoi 2: toe = int c (Lx - x).
-__global__ void k_adj_seed(unsigned long long* ctr, Phys P, Geom G, int B, int qoi,
+static __global__ void k_adj_seed(unsigned long long* ctr, Phys P, Geom G, int B, int qoi,
                            const double* __restrict__ c, double* __restrict__ rhs,
                            double* __restrict__ lam) {
   HENRY_COUNT_LAUNCH(ctr);
@@ -1564,7 +1532,7 @@ __global__ void k_adj_update(unsigned long long* ctr, Geom G, int B, const int* 
 // right side's flux is proportional to K_P, its and the left side's
 // diffusion to phi_P. Each cell evaluates its four faces itself (no
 // atomics); p is the reduced pressure.
-__global__ void k_adj_sens(unsigned long long* ctr, Phys P, Geom G, double tau, double qfac, int B,
+static __global__ void k_adj_sens(unsigned long long* ctr, Phys P, Geom G, double tau, double qfac, int B,
                            const double* __restrict__ p, const double* __restrict__ c,
                            const double* __restrict__ c_old, const double* __restrict__ phi,
                            const double* __restrict__ K, const double* __restrict__ tx,
@@ -1636,7 +1604,7 @@ __global__ void k_adj_sens(unsigned long long* ctr, Phys P, Geom G, double tau, 
 // rhs for step n-1: -(dR^n/du^{n-1})^T lam^n; R^n sees u^{n-1} through
 // c_old only: dR_p/dc_old = -V phi drho / tau, dR_c/dc_old = -V phi
 // (rho(c_old) + drho c_old) / tau.
-__global__ void k_adj_prev_rhs(unsigned long long* ctr, Phys P, Geom G, double tau, int B,
+static __global__ void k_adj_prev_rhs(unsigned long long* ctr, Phys P, Geom G, double tau, int B,
                                const double* __restrict__ phi, const double* __restrict__ c_old,
                                const double* __restrict__ lam, double* __restrict__ rhs) {
   HENRY_COUNT_LAUNCH(ctr);
@@ -1653,7 +1621,7 @@ __global__ void k_adj_prev_rhs(unsigned long long* ctr, Phys P, Geom G, double t
 
 // dQ/dxi from the per-cell and per-row sensitivities (fields of k_fields);
 // one block per sample.
-__global__ void __launch_bounds__(kBlock)
+static __global__ void __launch_bounds__(kBlock)
 k_adj_contract(unsigned long long* ctr, Phys P, Geom G, int B, int n_xi, int model,
                const double* __restrict__ xi, const double* __restrict__ gK,
                const double* __restrict__ gphi, const double* __restrict__ gq,
