@@ -45,7 +45,7 @@ extern "C" {
 #define HENRY_E_INVALID (-1)     /* bad argument (NULL, size, level, config)  */
 #define HENRY_E_CUDA (-2)        /* a CUDA runtime call failed                */
 #define HENRY_E_NOMEM (-3)       /* device allocation failed                  */
-#define HENRY_E_TIMEOUT (-4)     /* a bounded device wait gave up             */
+/* (-4 is not used: no entry point waits on the device with a time limit) */
 #define HENRY_E_UNSUPPORTED (-5) /* grid cannot be coarsened to <= 32 cells  */
 
 /* Largest batch B of one call of the entry points that launch one grid row

@@ -27,7 +27,7 @@ DISC_CELL = 0
 DISC_VERTEX = 1
 S_MAXIT, S_NONFINITE, S_BADINPUT = 1, 2, 4
 ERRORS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "out of device memory",
-          -4: "device wait timed out", -5: "unsupported grid"}
+          -5: "unsupported grid"}
 
 
 class HenryError(RuntimeError):

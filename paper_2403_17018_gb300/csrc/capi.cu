@@ -663,7 +663,6 @@ const char* henry_strerror(int code) {
     case HENRY_E_INVALID: return "invalid argument";
     case HENRY_E_CUDA: return "CUDA error";
     case HENRY_E_NOMEM: return "out of device memory";
-    case HENRY_E_TIMEOUT: return "device wait timed out";
     case HENRY_E_UNSUPPORTED: return "unsupported grid";
     default: return "unknown error";
   }
