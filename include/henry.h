@@ -448,7 +448,9 @@ int henry_debug_copy(henry_ctx* ctx, int level, int role, int mg_level, int what
  * `reps` times on `stream`, after one untimed launch; the solver must have
  * run a solve before (the replay uses that solve's batch).
  * which: 0 red half-sweep of the block Gauss-Seidel smoother on the finest
- * multigrid level; 1 the FP64 residual + Jacobian kernel of the finest level.
+ * multigrid level; 1 the FP64 residual + Jacobian kernel of the finest level;
+ * 2 the residual-only evaluation of that kernel (iterations that reuse
+ * their operators).
  * flush, flush_bytes: optional device buffer (NULL, 0 for none). When
  * given, every timed launch is preceded by a write of flush_bytes bytes to
  * it (larger than the L2 cache: each launch starts cold) and is timed by its
@@ -457,7 +459,8 @@ int henry_debug_copy(henry_ctx* ctx, int level, int role, int mg_level, int what
  * Outputs the average duration of one launch [ms], its algorithmic DRAM
  * bytes (the method's per-cell figures: smoother 26 values of the multigrid
  * type per updated cell -- operator 20, b 2, x read 2 and written 2;
- * residual + Jacobian 56 B + 20 values per cell) and its FP64 + FP32
+ * residual + Jacobian 56 B + 20 values per cell, residual only 56 B) and
+ * its FP64 + FP32
  * floating point operations (FMA = 2). Synchronises the stream. The replay
  * changes the workspace (not the caller's outputs). */
 int henry_time_kernel(henry_ctx* ctx, int level, int role, int which, int reps, void* flush,

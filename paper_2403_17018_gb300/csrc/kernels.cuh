@@ -146,7 +146,8 @@ static __global__ void k_init_state(unsigned long long* ctr, Phys P, Geom G, int
 // ---------------------------------------------------------------------------
 // per time step
 // ---------------------------------------------------------------------------
-// Start of an implicit Euler step: c_old = c^{n-1}. With `extrapolate`, from
+// Start of an implicit Euler step: c_old = c^{n-1} (with mo / so given, also
+// the old-time storage terms of k_resid). With `extrapolate`, from
 // the third step on (both u^{n-1} and u^{n-2} are solutions; the first
 // step's pressure guess is not) the Newton initial guess is extrapolated
 // linearly in time, u = 2 u^{n-1} - u^{n-2}, with c clamped to [0, 1]
@@ -158,7 +159,9 @@ static __global__ void k_begin_step(unsigned long long* ctr, Geom G, int B, doub
                              int* __restrict__ active, int* __restrict__ it_step,
                              const int* __restrict__ step, int extrapolate,
                              const double* __restrict__ qin0, double* __restrict__ qin,
-                             double tau) {
+                             double tau, const double* __restrict__ phi = nullptr,
+                             double vtau = 0.0, double rho0 = 0.0, double drho = 0.0,
+                             double* __restrict__ mo = nullptr, double* __restrict__ so = nullptr) {
   HENRY_COUNT_LAUNCH(ctr);
   const int64_t n = (int64_t)B * G.ncell();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -178,6 +181,14 @@ static __global__ void k_begin_step(unsigned long long* ctr, Geom G, int B, doub
   }
   c_old[idx] = cn;
   p_prev[idx] = pn;
+  if (mo) {
+    // storage of the old time level, fixed for the whole step: (V phi / tau)
+    // rho(c_old) and (V phi / tau) rho(c_old) c_old (k_resid)
+    const double vt = vtau * phi[idx];
+    const double m = vt * (rho0 + drho * cn);
+    mo[idx] = m;
+    so[idx] = m * cn;
+  }
   const int b = (int)(idx / G.ncell());
   if (idx - (int64_t)b * G.ncell() == 0) {
     active[b] = (status[b] & (kStatusNonfinite | kStatusBadInput)) ? 0 : 1;
@@ -393,6 +404,152 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, ResTile tl
     const double s = block_sum(v, shr);
     if (threadIdx.x == 0) partial[(int64_t)b * gridDim.x + blockIdx.x] = s;
   }
+}
+
+// FP64 residual of the finest grid alone, for the defect-correction
+// iterations that keep their operators (operator reuse): the same discrete
+// residual as k_resjac, arranged to spend fewer FP64 instructions, the
+// limiting resource on GB300 (about 41 per cell instead of 58):
+//  * the old-time storage terms (V phi/tau) rho(c_old) and (V phi/tau)
+//    rho(c_old) c_old come from k_begin_step (mo, so), so the storage part
+//    is a = (V phi/tau) rho, R_p = a - mo, R_c = a c - so;
+//  * rho and rho c of a cell are formed once and carried down the thread's
+//    rows (the north neighbour's become the next row's own);
+//  * a face's mean density and its gravity term share the sum c_L + c_U;
+//  * the west face is the east face of the neighbouring lane (warp shuffle,
+//    no shared memory, no block barrier); lanes at a warp or tile edge
+//    evaluate it themselves, with the same operations.
+// Writes b = -Dinv R with the stored Dinv, x = 0, the face fluxes qx, qy
+// and one partial sum of R_p^2 + R_c^2 per block; same tiling as k_resjac.
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+k_resid(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, ResTile tl,
+        const double* __restrict__ p, const double* __restrict__ c,
+        const double* __restrict__ mo, const double* __restrict__ so,
+        const double* __restrict__ phi, const double* __restrict__ K,
+        const double* __restrict__ tx, const double* __restrict__ dx,
+        const double* __restrict__ ty, const double* __restrict__ dy,
+        const double* __restrict__ qin, const int* __restrict__ active, const T* __restrict__ J,
+        T* __restrict__ bvec, T* __restrict__ xvec, double* __restrict__ partial,
+        double* __restrict__ qx, double* __restrict__ qy) {
+  HENRY_COUNT_LAUNCH(ctr);
+  __shared__ double shr[kBlock / 32];
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  const int nx = G.nx, ny = G.ny, ncell = G.ncell(), half = G.half();
+  const int t = threadIdx.x, lane = t & 31;
+  const int col = t % tl.TX, rg = t / tl.TX;
+  const int bx = blockIdx.x % tl.ntx, by = blockIdx.x / tl.ntx;
+  const int i = bx * tl.TX + col;
+  const int j0 = by * tl.GR * tl.R + rg * tl.R;
+  const bool thr = rg < tl.GR && i < nx;
+  const bool west_from_lane = col > 0 && lane > 0;
+  const int64_t o = (int64_t)b * ncell;
+  const double* pb_ = p + o;
+  const double* cb_ = c + o;
+  const double hd = 0.5 * P.drho;             // rho_bar = rho0 + hd (c_L + c_U)
+  const double hdg = hd * P.g * G.hy;          // gravity term of a vertical face: hdg (c_L + c_U)
+  const double A = G.hy;
+  const double dcoL = 2.0 * A * P.D / G.hx;
+  const double tRf = 2.0 * A / (P.mu * G.hx);
+  // one face L -> U: mass and salt flux (rho and rho c of both sides given)
+  auto face = [&](double pL, double cL, double rL, double rcL, double pU, double cU, double rU,
+                  double rcU, double tf, double dco, bool vert, double& q, double& Fm,
+                  double& Fs) {
+    const double sc = cL + cU;
+    const double rbar = fma(hd, sc, P.rho0);
+    const double dp = pU - pL;
+    q = -tf * (vert ? fma(hdg, sc, dp) : dp);
+    const bool up = q >= 0.0;
+    Fm = q * (up ? rL : rU);
+    Fs = fma(q, up ? rcL : rcU, -(dco * rbar) * (cU - cL));
+    (void)rL; (void)rU;
+  };
+  double v = 0.0;
+  double pP = 0.0, cP = 0.0, rP = 0.0, rcP = 0.0, FmS = 0.0, FsS = 0.0;
+  if (thr && j0 < ny) {
+    pP = pb_[j0 * nx + i];
+    cP = cb_[j0 * nx + i];
+    rP = fma(P.drho, cP, P.rho0);
+    rcP = rP * cP;
+    if (j0 > 0) {   // south face of the first row
+      const int id = (j0 - 1) * nx + i;
+      const double pS = pb_[id], cS = cb_[id];
+      const double rS = fma(P.drho, cS, P.rho0);
+      double q;
+      face(pS, cS, rS, rS * cS, pP, cP, rP, rcP, ty[o + id], dy[o + id], true, q, FmS, FsS);
+    }
+  }
+  for (int r = 0; r < tl.R; ++r) {
+    const int j = j0 + r;
+    const bool cv = thr && j < ny;
+    const int id = j * nx + i;
+    double FmE = 0.0, FsE = 0.0, qE = 0.0;
+    double pN = 0.0, cN = 0.0, rN = 0.0, rcN = 0.0;
+    if (cv) {
+      if (i < nx - 1) {
+        const double pE = pb_[id + 1], cE = cb_[id + 1];
+        const double rE = fma(P.drho, cE, P.rho0);
+        face(pP, cP, rP, rcP, pE, cE, rE, rE * cE, tx[o + id], dx[o + id], false, qE, FmE, FsE);
+      } else {
+        const double pbd = P.drho * P.g * (P.Ly - (j + 0.5) * G.hy);
+        right_face<float, false, false>(P, pP, cP, tRf * K[o + id], dcoL * phi[o + id], pbd, qE,
+                                        FmE, FsE, nullptr);
+      }
+    }
+    // west face: the east face of the neighbouring lane (every lane shuffles)
+    const double FmL = __shfl_up_sync(0xffffffffu, FmE, 1);
+    const double FsL = __shfl_up_sync(0xffffffffu, FsE, 1);
+    if (cv) {
+      double FmW = 0.0, FsW = 0.0;
+      if (i > 0) {
+        if (west_from_lane) {
+          FmW = FmL;
+          FsW = FsL;
+        } else {
+          const double pW = pb_[id - 1], cW = cb_[id - 1];
+          const double rW = fma(P.drho, cW, P.rho0);
+          double q;
+          face(pW, cW, rW, rW * cW, pP, cP, rP, rcP, tx[o + id - 1], dx[o + id - 1], false, q, FmW,
+               FsW);
+        }
+      }
+      double FmN = 0.0, FsN = 0.0, qN = 0.0;
+      if (j < ny - 1) {
+        pN = pb_[id + nx];
+        cN = cb_[id + nx];
+        rN = fma(P.drho, cN, P.rho0);
+        rcN = rN * cN;
+        face(pP, cP, rP, rcP, pN, cN, rN, rcN, ty[o + id], dy[o + id], true, qN, FmN, FsN);
+      }
+      const double a = (vtau * phi[o + id]) * rP;
+      double Rp = (a - mo[o + id]) + FmE + FmN - FmW - FmS;
+      double Rc = fma(a, cP, -so[o + id]) + FsE + FsN - FsW - FsS;
+      if (i == 0) {   // left side: fresh-water inflow, diffusion to c = 0 at hx/2
+        Rp += -A * P.rho0 * qin[(int64_t)b * ny + j];
+        Rc += (dcoL * phi[o + id]) * (0.5 * (rP + P.rho0)) * cP;
+      }
+      const int cs = cs_pos(i, j, nx, half);
+      const int64_t ob = (int64_t)b * 2 * ncell;
+      const T* Jb = J + (int64_t)b * kJP * ncell + cs;
+      const T mp = (T)(-Rp), mc = (T)(-Rc);
+      bvec[ob + cs] = Jb[0] * mp + Jb[(int64_t)ncell] * mc;
+      bvec[ob + ncell + cs] = Jb[(int64_t)2 * ncell] * mp + Jb[(int64_t)3 * ncell] * mc;
+      xvec[ob + cs] = (T)0;
+      xvec[ob + ncell + cs] = (T)0;
+      qx[o + id] = qE;
+      qy[o + id] = qN;
+      v = fma(Rp, Rp, fma(Rc, Rc, v));
+      FmS = FmN;
+      FsS = FsN;
+      pP = pN;
+      cP = cN;
+      rP = rN;
+      rcP = rcN;
+    }
+  }
+  const double s = block_sum(v, shr);
+  if (threadIdx.x == 0) partial[(int64_t)b * gridDim.x + blockIdx.x] = s;
 }
 
 // Per-sample convergence decision after k_resjac, one warp per sample:

@@ -192,6 +192,8 @@ int Solver::ensure(int B, cudaStream_t s) {
   const Geom& F = levels_.back().g;
   const size_t o_cold = take((size_t)F.ncell() * Bz * 8);
   const size_t o_pprev = take((size_t)F.ncell() * Bz * 8);
+  const size_t o_mo = take((size_t)F.ncell() * Bz * 8);
+  const size_t o_so = take((size_t)F.ncell() * Bz * 8);
   const size_t o_step = take(8);
   const size_t o_qin = take((size_t)F.ny * Bz * 8);
   const size_t o_qin0 = take((size_t)F.ny * Bz * 8);
@@ -238,6 +240,8 @@ int Solver::ensure(int B, cudaStream_t s) {
   }
   c_old_ = (double*)(a + o_cold);
   p_prev_ = (double*)(a + o_pprev);
+  mo_ = (double*)(a + o_mo);
+  so_ = (double*)(a + o_so);
   step_ = (int*)(a + o_step);
   qin_ = (double*)(a + o_qin);
   qin0_ = (double*)(a + o_qin0);
@@ -480,9 +484,9 @@ void Solver::enqueue_resjac_check(int B, cudaStream_t s, bool set_cond,
   MGLevel& F = levels_.back();
   const Geom& G = F.g;
   if (cfg_.jac_lag)   // residual only; the next iteration rebuilds operators where needed
-    k_resjac<T, false, false><<<dim3(nchunk_, B), kBlock, 0, s>>>(
-        counter_, phys_, G, G.hx * G.hy / tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx,
-        F.ty, F.dy, qin_, active_, (T*)F.J, (T*)F.b, (T*)F.x, partial_, F.qx, F.qy, nullptr);
+    k_resid<T><<<dim3(nchunk_, B), kBlock, 0, s>>>(
+        counter_, phys_, G, G.hx * G.hy / tau_, B, tile_, F.p, F.c, mo_, so_, F.phi, F.K, F.tx,
+        F.dx, F.ty, F.dy, qin_, active_, (const T*)F.J, (T*)F.b, (T*)F.x, partial_, F.qx, F.qy);
   else
     k_resjac<T, false><<<dim3(nchunk_, B), kBlock, 0, s>>>(
         counter_, phys_, G, G.hx * G.hy / tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx,
@@ -520,7 +524,8 @@ int Solver::capture_step_t(cudaGraph_t g, cudaStream_t cs, int B, std::vector<St
   MGLevel& F = levels_.back();
   k_begin_step<<<grid1((int64_t)B * F.g.ncell()), kBlock, 0, cs>>>(
       counter_, F.g, B, F.p, F.c, p_prev_, c_old_, status_w_, active_, it_step_, step_,
-      cfg_.guess_extrapolation, cfg_.field_model == 1 ? qin0_ : nullptr, qin_, tau_);
+      cfg_.guess_extrapolation, cfg_.field_model == 1 ? qin0_ : nullptr, qin_, tau_, F.phi,
+      F.g.hx * F.g.hy / tau_, phys_.rho0, phys_.drho, mo_, so_);
   enqueue_resjac_check<T>(B, cs, true, (unsigned long long)h);
   cudaStreamCaptureStatus st;
   cudaGraph_t cg;
@@ -686,7 +691,8 @@ int Solver::step_t(int B, cudaStream_t s) {
   const Geom& G = F.g;
   k_begin_step<<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(
       counter_, G, B, F.p, F.c, p_prev_, c_old_, status_w_, active_, it_step_, step_,
-      cfg_.guess_extrapolation, cfg_.field_model == 1 ? qin0_ : nullptr, qin_, tau_);
+      cfg_.guess_extrapolation, cfg_.field_model == 1 ? qin0_ : nullptr, qin_, tau_, F.phi,
+      G.hx * G.hy / tau_, phys_.rho0, phys_.drho, mo_, so_);
   for (;;) {
     enqueue_resjac_check<T>(B, s, false);
     CK(cudaMemcpyAsync(n_active_host_, n_active_, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -744,6 +750,11 @@ void Solver::launch_timed(int which, int B, cudaStream_t s) {
   if (which == 0) {
     k_smooth<T><<<grid1((int64_t)B * F.g.half()), kBlock, 0, s>>>(
         counter_, F.g, B, 0, active_, (const T*)F.J, (const T*)F.b, (T*)F.x);
+  } else if (which == 2) {
+    k_resid<T><<<dim3(nchunk_, B), kBlock, 0, s>>>(
+        counter_, phys_, F.g, F.g.hx * F.g.hy / tau_, B, tile_, F.p, F.c, mo_, so_, F.phi, F.K,
+        F.tx, F.dx, F.ty, F.dy, qin_, active_, (const T*)F.J, (T*)F.b, (T*)F.x, partial_, F.qx,
+        F.qy);
   } else {
     k_resjac<T, false><<<dim3(nchunk_, B), kBlock, 0, s>>>(
         counter_, phys_, F.g, F.g.hx * F.g.hy / tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx, F.ty, F.dy,
@@ -760,6 +771,7 @@ void Solver::launch_timed(int which, int B, cudaStream_t s) {
 //    values instead of 20, so the kernel moves 22 values: the figure above
 //    credits it with the unscaled operator's bytes. FP ops: 16 FMA per
 //    update (32 FLOP).
+//  residual only (which = 2): 56 B per cell, 46 FP64 operations.
 //  residual + Jacobian, per cell: p, c, c_old, phi, K read (40 B), R written
 //    (16 B), J written (20 values of type T): 136 B (FP32 J) or 216 B. FP
 //    ops counted from the face-based code: 2 faces x 15 (flux) + 16
@@ -772,7 +784,7 @@ void Solver::launch_timed(int which, int B, cudaStream_t s) {
 // timed by its own event pair and the flush is not counted.
 int Solver::time_kernel(int which, int reps, cudaStream_t s, void* flush, int64_t flush_bytes,
                         double* avg_ms, double* bytes, double* flops) {
-  if (which < 0 || which > 1 || reps < 1 || reps > 100000 || last_B_ < 1 || flush_bytes < 0 ||
+  if (which < 0 || which > 2 || reps < 1 || reps > 100000 || last_B_ < 1 || flush_bytes < 0 ||
       (flush_bytes > 0 && !flush))
     return HENRY_E_INVALID;
   const int B = last_B_;
@@ -826,6 +838,10 @@ int Solver::time_kernel(int which, int reps, cudaStream_t s, void* flush, int64_
     const double cells = (double)B * G.half();
     *bytes = cells * 26.0 * T;
     *flops = cells * 32.0;
+  } else if (which == 2) {   // residual only: 40 B read, R written (16 B)
+    const double cells = (double)B * G.ncell();
+    *bytes = cells * 56.0;
+    *flops = cells * 46.0;
   } else {
     const double cells = (double)B * G.ncell();
     *bytes = cells * (40.0 + 16.0 + 20.0 * T);

@@ -141,6 +141,8 @@ class Solver {
   // finest-level / per-sample arrays
   double* c_old_ = nullptr;
   double* p_prev_ = nullptr;    // p of the previous step (initial-guess extrapolation)
+  double* mo_ = nullptr;        // old-time storage terms of the step (k_resid)
+  double* so_ = nullptr;
   int* step_ = nullptr;         // completed steps of the current solve (device)
   double* qin_ = nullptr;
   double* qin0_ = nullptr;     // inflow base of the paper field model (time factor per step)

@@ -1,8 +1,9 @@
 """Small, self-contained case for ncu captures of the hot kernels.
 
 Runs one batched solve of one MLMC level for a few implicit Euler steps,
-then replays the finest-level smoother half-sweep and the residual +
-Jacobian kernel a few times (henry_time_kernel) and prints their timings.
+then replays the finest-level smoother half-sweep, the residual +
+Jacobian kernel and the residual-only evaluation a few times
+(henry_time_kernel) and prints their timings.
 
   python -m paper_2403_17018_gb300.profile_case --level 3 --batch 16 --steps 2
 """
@@ -63,8 +64,8 @@ def main(argv=None):
            "status_bad": int((out["status"] != 0).sum().item())}
     # replays of the finest-level kernels, each inside an NVTX range named
     # after it so that ncu can select exactly these launches
-    # (--nvtx --nvtx-include "smooth_half_sweep/")
-    for which, name in ((0, "smooth_half_sweep"), (1, "resjac")):
+    # (--nvtx --nvtx-include "smooth_half_sweep/", "resjac/", "resid/")
+    for which, name in ((0, "smooth_half_sweep"), (1, "resjac"), (2, "resid")):
         torch.cuda.nvtx.range_push(name)
         ms, by, fl = ctx.time_kernel(a.level, 0, which, reps=a.reps)
         torch.cuda.nvtx.range_pop()

@@ -92,3 +92,20 @@ def test_residual_tile_height_keeps_parity(res_rows):
     p_o, c_o, _ = oracle_solve(cfg, 1, xi[0].cpu().numpy())
     assert np.max(np.abs(out["c"][0].cpu().numpy() - c_o)) <= 1e-9
     assert np.max(np.abs(out["p"][0].cpu().numpy() - p_o)) <= 1e-9 * np.max(np.abs(p_o))
+
+
+@pytest.mark.parametrize("precision", [hb.PREC_FP64, hb.PREC_FP32_MG])
+def test_bench_schedule_at_full_size_matches_the_oracle(precision):
+    """Level 3 at full size (256x128, 16 samples) with the schedule the
+    benchmark tunes for it (V(2,2) x3, shared-memory V-cycle up to 512 cells,
+    operator reuse 30: the residual-only kernel decides convergence) and the
+    shipped tolerances: 8 steps of 225 s, one sample against the oracle."""
+    cfg = hb.default_config(nlevels=4, nt0=1, T=1800.0, precision=precision, vcycles=3,
+                            mg_small_cells=512, jac_lag=30)
+    ctx = hb.Context(cfg)
+    xi = xi_cuda(3, 0, 16)
+    out = ctx.solve(3, xi, want_c=True, want_p=True)
+    assert out["status"].cpu().numpy().tolist() == [0] * 16
+    p_o, c_o, _ = oracle_solve(cfg, 3, xi[11].cpu().numpy())
+    assert np.max(np.abs(out["c"][11].cpu().numpy() - c_o)) <= 1e-9
+    assert np.max(np.abs(out["p"][11].cpu().numpy() - p_o)) <= 1e-9 * np.max(np.abs(p_o))

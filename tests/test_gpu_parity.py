@@ -165,10 +165,15 @@ def test_level1_pairs_match_oracle(precision):
         assert np.allclose(qc[b].cpu().numpy(), q0, rtol=1e-9, atol=1e-9)
 
 
-def test_ragged_grid_matches_oracle():
+@pytest.mark.parametrize("jac_lag,res_rows", [(0, 0), (10, 0), (10, 3)])
+def test_ragged_grid_matches_oracle(jac_lag, res_rows):
     """24x12 cells (coarsest multigrid grid 6x3, odd ny), 5 steps: blocks of
-    256 threads end mid-sample and mid-row."""
-    cfg = tight_config(nx0=24, ny0=12, nt0=5, T=5 * 1800.0, nlevels=1)
+    256 threads end mid-sample and mid-row; with operator reuse the
+    residual-only kernel runs, whose warps here span two row groups of 24
+    columns (its west faces come from the neighbouring lane only inside a
+    row group)."""
+    cfg = tight_config(nx0=24, ny0=12, nt0=5, T=5 * 1800.0, nlevels=1, jac_lag=jac_lag,
+                       res_rows=res_rows)
     ctx = hb.Context(cfg)
     assert ctx.level_info(0).n_mg == 3
     xi = xi_cuda(0, 9, 5)
