@@ -309,6 +309,10 @@ __device__ __forceinline__ double inflow_at(const Phys& P, int model, int n_xi, 
 }
 
 // Face constants of cell (i, j): east face (if any) and north face (if any).
+// The last column's east slots hold the right side's coefficients, 2 A K_P
+// / (mu hx) and 2 A phi_P D / hx (the Dirichlet side at hx/2), for kernels
+// that treat the right side as one more face (k_resid); the others compute
+// them from K and phi and read tx, dx only where an east neighbour exists.
 __device__ __forceinline__ void face_constants(const Phys& P, const Geom& G, int i, int j,
                                                const double* __restrict__ phi,
                                                const double* __restrict__ K, double& tx, double& dx,
@@ -321,6 +325,9 @@ __device__ __forceinline__ void face_constants(const Phys& P, const Geom& G, int
     const double ff = 2.0 * f1 * f2 / (f1 + f2);
     tx = G.hy * Kf / (P.mu * G.hx);
     dx = G.hy * ff * P.D / G.hx;
+  } else {
+    tx = (2.0 * G.hy / (P.mu * G.hx)) * K[id];
+    dx = (2.0 * G.hy * P.D / G.hx) * phi[id];
   }
   if (j < G.ny - 1) {
     const double k1 = K[id], k2 = K[id + G.nx], f1 = phi[id], f2 = phi[id + G.nx];

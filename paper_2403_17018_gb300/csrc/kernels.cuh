@@ -161,7 +161,8 @@ static __global__ void k_begin_step(unsigned long long* ctr, Geom G, int B, doub
                              const double* __restrict__ qin0, double* __restrict__ qin,
                              double tau, const double* __restrict__ phi = nullptr,
                              double vtau = 0.0, double rho0 = 0.0, double drho = 0.0,
-                             double* __restrict__ mo = nullptr, double* __restrict__ so = nullptr) {
+                             double* __restrict__ mo = nullptr, double* __restrict__ so = nullptr,
+                             double* __restrict__ vt_out = nullptr) {
   HENRY_COUNT_LAUNCH(ctr);
   const int64_t n = (int64_t)B * G.ncell();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -188,6 +189,7 @@ static __global__ void k_begin_step(unsigned long long* ctr, Geom G, int B, doub
     const double m = vt * (rho0 + drho * cn);
     mo[idx] = m;
     so[idx] = m * cn;
+    vt_out[idx] = vt;
   }
   const int b = (int)(idx / G.ncell());
   if (idx - (int64_t)b * G.ncell() == 0) {
@@ -408,51 +410,62 @@ k_resjac(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, ResTile tl
 
 // FP64 residual of the finest grid alone, for the defect-correction
 // iterations that keep their operators (operator reuse): the same discrete
-// residual as k_resjac, arranged to spend fewer FP64 instructions, the
-// limiting resource on GB300 (about 41 per cell instead of 58):
-//  * the old-time storage terms (V phi/tau) rho(c_old) and (V phi/tau)
-//    rho(c_old) c_old come from k_begin_step (mo, so), so the storage part
-//    is a = (V phi/tau) rho, R_p = a - mo, R_c = a c - so;
-//  * rho and rho c of a cell are formed once and carried down the thread's
-//    rows (the north neighbour's become the next row's own);
-//  * a face's mean density and its gravity term share the sum c_L + c_U;
-//  * the west face is the east face of the neighbouring lane (warp shuffle,
-//    no shared memory, no block barrier); lanes at a warp or tile edge
-//    evaluate it themselves, with the same operations.
+// residual as k_resjac, arranged for GB300's narrow FP64 pipe, where every
+// FP64 warp instruction costs the same pipe time whether one lane or 32
+// are active (so the kernel avoids divergent FP64 work):
+//  * per-cell constants: vt = V phi / tau and the old-time storage terms
+//    mo = vt rho(c_old), so = mo c_old from k_begin_step, so the storage part
+//    is a = vt rho, R_p = a - mo, R_c = a c - so;
+//  * rho and rho c of a cell are formed once: the east neighbour's come from
+//    the next lane (shuffle), the north neighbour's become the next row's;
+//  * the west face is the east face of the previous lane; across a warp
+//    edge both the neighbour's state and the face travel through shared
+//    memory (two block barriers per row); only tile edges recompute;
+//  * the right side is one more face, to the Dirichlet values (p_b, c = 1),
+//    with the coefficients face_constants keeps in the last column;
+//  * a face's mean density and its gravity term share c_L + c_U.
 // Writes b = -Dinv R with the stored Dinv, x = 0, the face fluxes qx, qy
 // and one partial sum of R_p^2 + R_c^2 per block; same tiling as k_resjac.
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
-k_resid(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, ResTile tl,
+k_resid(unsigned long long* ctr, Phys P, Geom G, int B, ResTile tl,
         const double* __restrict__ p, const double* __restrict__ c,
-        const double* __restrict__ mo, const double* __restrict__ so,
-        const double* __restrict__ phi, const double* __restrict__ K,
+        const double* __restrict__ vt, const double* __restrict__ mo,
+        const double* __restrict__ so, const double* __restrict__ phi,
         const double* __restrict__ tx, const double* __restrict__ dx,
         const double* __restrict__ ty, const double* __restrict__ dy,
         const double* __restrict__ qin, const int* __restrict__ active, const T* __restrict__ J,
         T* __restrict__ bvec, T* __restrict__ xvec, double* __restrict__ partial,
         double* __restrict__ qx, double* __restrict__ qy) {
   HENRY_COUNT_LAUNCH(ctr);
-  __shared__ double shr[kBlock / 32];
+  constexpr int kW = kBlock / 32;
+  __shared__ double shS[4][kW];    // lane 0's p, c, rho, rho c for the previous warp's lane 31
+  __shared__ double shF[2][kW];    // lane 31's east-face fluxes for the next warp's lane 0
+  __shared__ double shr[kW];
   const int b = blockIdx.y;
   if (!active[b]) return;
   const int nx = G.nx, ny = G.ny, ncell = G.ncell(), half = G.half();
-  const int t = threadIdx.x, lane = t & 31;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int col = t % tl.TX, rg = t / tl.TX;
   const int bx = blockIdx.x % tl.ntx, by = blockIdx.x / tl.ntx;
   const int i = bx * tl.TX + col;
   const int j0 = by * tl.GR * tl.R + rg * tl.R;
   const bool thr = rg < tl.GR && i < nx;
-  const bool west_from_lane = col > 0 && lane > 0;
+  // where the east neighbour's state and the west face come from
+  const bool east_in = thr && col < tl.TX - 1 && i < nx - 1;   // a thread of this tile
+  const bool east_lane = east_in && lane < 31;
+  const bool east_smem = east_in && lane == 31;
+  const bool east_load = thr && col == tl.TX - 1 && i < nx - 1;  // tile edge
+  const bool west_in = thr && col > 0;
+  const bool west_lane = west_in && lane > 0;
+  const bool west_smem = west_in && lane == 0;
+  const bool west_load = thr && col == 0 && i > 0;               // tile edge
   const int64_t o = (int64_t)b * ncell;
   const double* pb_ = p + o;
   const double* cb_ = c + o;
-  const double hd = 0.5 * P.drho;             // rho_bar = rho0 + hd (c_L + c_U)
+  const double hd = 0.5 * P.drho;              // rho_bar = rho0 + hd (c_L + c_U)
   const double hdg = hd * P.g * G.hy;          // gravity term of a vertical face: hdg (c_L + c_U)
-  const double A = G.hy;
-  const double dcoL = 2.0 * A * P.D / G.hx;
-  const double tRf = 2.0 * A / (P.mu * G.hx);
-  // one face L -> U: mass and salt flux (rho and rho c of both sides given)
+  // one face L -> U: mass and salt flux from both sides' p, c, rho, rho c
   auto face = [&](double pL, double cL, double rL, double rcL, double pU, double cU, double rU,
                   double rcU, double tf, double dco, bool vert, double& q, double& Fm,
                   double& Fs) {
@@ -463,71 +476,80 @@ k_resid(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, ResTile tl,
     const bool up = q >= 0.0;
     Fm = q * (up ? rL : rU);
     Fs = fma(q, up ? rcL : rcU, -(dco * rbar) * (cU - cL));
-    (void)rL; (void)rU;
   };
   double v = 0.0;
   double pP = 0.0, cP = 0.0, rP = 0.0, rcP = 0.0, FmS = 0.0, FsS = 0.0;
   if (thr && j0 < ny) {
     pP = pb_[j0 * nx + i];
     cP = cb_[j0 * nx + i];
-    rP = fma(P.drho, cP, P.rho0);
-    rcP = rP * cP;
-    if (j0 > 0) {   // south face of the first row
-      const int id = (j0 - 1) * nx + i;
-      const double pS = pb_[id], cS = cb_[id];
-      const double rS = fma(P.drho, cS, P.rho0);
-      double q;
-      face(pS, cS, rS, rS * cS, pP, cP, rP, rcP, ty[o + id], dy[o + id], true, q, FmS, FsS);
-    }
+  }
+  rP = fma(P.drho, cP, P.rho0);
+  rcP = rP * cP;
+  if (thr && j0 < ny && j0 > 0) {   // south face of the first row (every thread of a row group)
+    const int id = (j0 - 1) * nx + i;
+    const double pS = pb_[id], cS = cb_[id];
+    const double rS = fma(P.drho, cS, P.rho0);
+    double q;
+    face(pS, cS, rS, rS * cS, pP, cP, rP, rcP, ty[o + id], dy[o + id], true, q, FmS, FsS);
   }
   for (int r = 0; r < tl.R; ++r) {
     const int j = j0 + r;
     const bool cv = thr && j < ny;
     const int id = j * nx + i;
-    double FmE = 0.0, FsE = 0.0, qE = 0.0;
-    double pN = 0.0, cN = 0.0, rN = 0.0, rcN = 0.0;
-    if (cv) {
-      if (i < nx - 1) {
-        const double pE = pb_[id + 1], cE = cb_[id + 1];
-        const double rE = fma(P.drho, cE, P.rho0);
-        face(pP, cP, rP, rcP, pE, cE, rE, rE * cE, tx[o + id], dx[o + id], false, qE, FmE, FsE);
-      } else {
-        const double pbd = P.drho * P.g * (P.Ly - (j + 0.5) * G.hy);
-        right_face<float, false, false>(P, pP, cP, tRf * K[o + id], dcoL * phi[o + id], pbd, qE,
-                                        FmE, FsE, nullptr);
+    // east neighbour: the next lane's state, across a warp edge through
+    // shared memory, at a tile edge from memory, at the right side the
+    // seawater values
+    if (lane == 0) { shS[0][w] = pP; shS[1][w] = cP; shS[2][w] = rP; shS[3][w] = rcP; }
+    double pE = __shfl_down_sync(0xffffffffu, pP, 1);
+    double cE = __shfl_down_sync(0xffffffffu, cP, 1);
+    double rE = __shfl_down_sync(0xffffffffu, rP, 1);
+    double rcE = __shfl_down_sync(0xffffffffu, rcP, 1);
+    __syncthreads();
+    if (east_smem) { pE = shS[0][w + 1]; cE = shS[1][w + 1]; rE = shS[2][w + 1]; rcE = shS[3][w + 1]; }
+    if (!east_lane && !east_smem) {
+      if (east_load && cv) {
+        pE = pb_[id + 1];
+        cE = cb_[id + 1];
+      } else {   // the right side: reduced seawater pressure at this row, c = 1
+        pE = P.drho * P.g * (P.Ly - (j + 0.5) * G.hy);
+        cE = 1.0;
       }
+      rE = fma(P.drho, cE, P.rho0);
+      rcE = rE * cE;
     }
-    // west face: the east face of the neighbouring lane (every lane shuffles)
-    const double FmL = __shfl_up_sync(0xffffffffu, FmE, 1);
-    const double FsL = __shfl_up_sync(0xffffffffu, FsE, 1);
+    double FmE = 0.0, FsE = 0.0, qE = 0.0;
+    if (cv) face(pP, cP, rP, rcP, pE, cE, rE, rcE, tx[o + id], dx[o + id], false, qE, FmE, FsE);
+    // west face: the previous lane's east face (across a warp edge through
+    // shared memory; recomputed at a tile edge)
+    if (lane == 31) { shF[0][w] = FmE; shF[1][w] = FsE; }
+    double FmW = __shfl_up_sync(0xffffffffu, FmE, 1);
+    double FsW = __shfl_up_sync(0xffffffffu, FsE, 1);
+    __syncthreads();
+    if (west_smem) { FmW = shF[0][w - 1]; FsW = shF[1][w - 1]; }
+    if (!west_in) { FmW = 0.0; FsW = 0.0; }
+    if (west_load && cv) {
+      const double pW = pb_[id - 1], cW = cb_[id - 1];
+      const double rW = fma(P.drho, cW, P.rho0);
+      double q;
+      face(pW, cW, rW, rW * cW, pP, cP, rP, rcP, tx[o + id - 1], dx[o + id - 1], false, q, FmW,
+           FsW);
+    }
+    double pN = 0.0, cN = 0.0;
+    double FmN = 0.0, FsN = 0.0, qN = 0.0;
+    if (cv && j < ny - 1) {
+      pN = pb_[id + nx];
+      cN = cb_[id + nx];
+    }
+    const double rN = fma(P.drho, cN, P.rho0);
+    const double rcN = rN * cN;
+    if (cv && j < ny - 1) face(pP, cP, rP, rcP, pN, cN, rN, rcN, ty[o + id], dy[o + id], true, qN, FmN, FsN);
     if (cv) {
-      double FmW = 0.0, FsW = 0.0;
-      if (i > 0) {
-        if (west_from_lane) {
-          FmW = FmL;
-          FsW = FsL;
-        } else {
-          const double pW = pb_[id - 1], cW = cb_[id - 1];
-          const double rW = fma(P.drho, cW, P.rho0);
-          double q;
-          face(pW, cW, rW, rW * cW, pP, cP, rP, rcP, tx[o + id - 1], dx[o + id - 1], false, q, FmW,
-               FsW);
-        }
-      }
-      double FmN = 0.0, FsN = 0.0, qN = 0.0;
-      if (j < ny - 1) {
-        pN = pb_[id + nx];
-        cN = cb_[id + nx];
-        rN = fma(P.drho, cN, P.rho0);
-        rcN = rN * cN;
-        face(pP, cP, rP, rcP, pN, cN, rN, rcN, ty[o + id], dy[o + id], true, qN, FmN, FsN);
-      }
-      const double a = (vtau * phi[o + id]) * rP;
+      const double a = vt[o + id] * rP;
       double Rp = (a - mo[o + id]) + FmE + FmN - FmW - FmS;
       double Rc = fma(a, cP, -so[o + id]) + FsE + FsN - FsW - FsS;
       if (i == 0) {   // left side: fresh-water inflow, diffusion to c = 0 at hx/2
-        Rp += -A * P.rho0 * qin[(int64_t)b * ny + j];
-        Rc += (dcoL * phi[o + id]) * (0.5 * (rP + P.rho0)) * cP;
+        Rp += -G.hy * P.rho0 * qin[(int64_t)b * ny + j];
+        Rc += ((2.0 * G.hy * P.D / G.hx) * phi[o + id]) * (0.5 * (rP + P.rho0)) * cP;
       }
       const int cs = cs_pos(i, j, nx, half);
       const int64_t ob = (int64_t)b * 2 * ncell;
@@ -540,13 +562,13 @@ k_resid(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, ResTile tl,
       qx[o + id] = qE;
       qy[o + id] = qN;
       v = fma(Rp, Rp, fma(Rc, Rc, v));
-      FmS = FmN;
-      FsS = FsN;
-      pP = pN;
-      cP = cN;
-      rP = rN;
-      rcP = rcN;
     }
+    FmS = FmN;
+    FsS = FsN;
+    pP = pN;
+    cP = cN;
+    rP = rN;
+    rcP = rcN;
   }
   const double s = block_sum(v, shr);
   if (threadIdx.x == 0) partial[(int64_t)b * gridDim.x + blockIdx.x] = s;

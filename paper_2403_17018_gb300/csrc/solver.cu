@@ -194,6 +194,7 @@ int Solver::ensure(int B, cudaStream_t s) {
   const size_t o_pprev = take((size_t)F.ncell() * Bz * 8);
   const size_t o_mo = take((size_t)F.ncell() * Bz * 8);
   const size_t o_so = take((size_t)F.ncell() * Bz * 8);
+  const size_t o_vt = take((size_t)F.ncell() * Bz * 8);
   const size_t o_step = take(8);
   const size_t o_qin = take((size_t)F.ny * Bz * 8);
   const size_t o_qin0 = take((size_t)F.ny * Bz * 8);
@@ -242,6 +243,7 @@ int Solver::ensure(int B, cudaStream_t s) {
   p_prev_ = (double*)(a + o_pprev);
   mo_ = (double*)(a + o_mo);
   so_ = (double*)(a + o_so);
+  vt_ = (double*)(a + o_vt);
   step_ = (int*)(a + o_step);
   qin_ = (double*)(a + o_qin);
   qin0_ = (double*)(a + o_qin0);
@@ -485,8 +487,8 @@ void Solver::enqueue_resjac_check(int B, cudaStream_t s, bool set_cond,
   const Geom& G = F.g;
   if (cfg_.jac_lag)   // residual only; the next iteration rebuilds operators where needed
     k_resid<T><<<dim3(nchunk_, B), kBlock, 0, s>>>(
-        counter_, phys_, G, G.hx * G.hy / tau_, B, tile_, F.p, F.c, mo_, so_, F.phi, F.K, F.tx,
-        F.dx, F.ty, F.dy, qin_, active_, (const T*)F.J, (T*)F.b, (T*)F.x, partial_, F.qx, F.qy);
+        counter_, phys_, G, B, tile_, F.p, F.c, vt_, mo_, so_, F.phi, F.tx, F.dx, F.ty, F.dy,
+        qin_, active_, (const T*)F.J, (T*)F.b, (T*)F.x, partial_, F.qx, F.qy);
   else
     k_resjac<T, false><<<dim3(nchunk_, B), kBlock, 0, s>>>(
         counter_, phys_, G, G.hx * G.hy / tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx,
@@ -525,7 +527,7 @@ int Solver::capture_step_t(cudaGraph_t g, cudaStream_t cs, int B, std::vector<St
   k_begin_step<<<grid1((int64_t)B * F.g.ncell()), kBlock, 0, cs>>>(
       counter_, F.g, B, F.p, F.c, p_prev_, c_old_, status_w_, active_, it_step_, step_,
       cfg_.guess_extrapolation, cfg_.field_model == 1 ? qin0_ : nullptr, qin_, tau_, F.phi,
-      F.g.hx * F.g.hy / tau_, phys_.rho0, phys_.drho, mo_, so_);
+      F.g.hx * F.g.hy / tau_, phys_.rho0, phys_.drho, mo_, so_, vt_);
   enqueue_resjac_check<T>(B, cs, true, (unsigned long long)h);
   cudaStreamCaptureStatus st;
   cudaGraph_t cg;
@@ -692,7 +694,7 @@ int Solver::step_t(int B, cudaStream_t s) {
   k_begin_step<<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(
       counter_, G, B, F.p, F.c, p_prev_, c_old_, status_w_, active_, it_step_, step_,
       cfg_.guess_extrapolation, cfg_.field_model == 1 ? qin0_ : nullptr, qin_, tau_, F.phi,
-      G.hx * G.hy / tau_, phys_.rho0, phys_.drho, mo_, so_);
+      G.hx * G.hy / tau_, phys_.rho0, phys_.drho, mo_, so_, vt_);
   for (;;) {
     enqueue_resjac_check<T>(B, s, false);
     CK(cudaMemcpyAsync(n_active_host_, n_active_, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -752,9 +754,8 @@ void Solver::launch_timed(int which, int B, cudaStream_t s) {
         counter_, F.g, B, 0, active_, (const T*)F.J, (const T*)F.b, (T*)F.x);
   } else if (which == 2) {
     k_resid<T><<<dim3(nchunk_, B), kBlock, 0, s>>>(
-        counter_, phys_, F.g, F.g.hx * F.g.hy / tau_, B, tile_, F.p, F.c, mo_, so_, F.phi, F.K,
-        F.tx, F.dx, F.ty, F.dy, qin_, active_, (const T*)F.J, (T*)F.b, (T*)F.x, partial_, F.qx,
-        F.qy);
+        counter_, phys_, F.g, B, tile_, F.p, F.c, vt_, mo_, so_, F.phi, F.tx, F.dx, F.ty, F.dy,
+        qin_, active_, (const T*)F.J, (T*)F.b, (T*)F.x, partial_, F.qx, F.qy);
   } else {
     k_resjac<T, false><<<dim3(nchunk_, B), kBlock, 0, s>>>(
         counter_, phys_, F.g, F.g.hx * F.g.hy / tau_, B, tile_, F.p, F.c, c_old_, F.phi, F.K, F.tx, F.dx, F.ty, F.dy,

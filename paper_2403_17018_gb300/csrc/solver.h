@@ -143,6 +143,7 @@ class Solver {
   double* p_prev_ = nullptr;    // p of the previous step (initial-guess extrapolation)
   double* mo_ = nullptr;        // old-time storage terms of the step (k_resid)
   double* so_ = nullptr;
+  double* vt_ = nullptr;        // V phi / tau per cell (k_resid)
   int* step_ = nullptr;         // completed steps of the current solve (device)
   double* qin_ = nullptr;
   double* qin0_ = nullptr;     // inflow base of the paper field model (time factor per step)
