@@ -60,6 +60,9 @@ extern "C" {
 #define HENRY_S_MAXIT 1          /* some time step hit newton_maxit          */
 #define HENRY_S_NONFINITE 2      /* a residual norm became NaN or Inf        */
 #define HENRY_S_BADINPUT 4       /* xi was not finite                        */
+#define HENRY_S_STALL 8          /* a kernel's bounded wait for its own bulk
+                                    copies into shared memory gave up; the
+                                    sample is dropped from later work       */
 
 /* ---- quantities of interest (q[] outputs, HENRY_NQ per sample) --------- */
 #define HENRY_NQ 22
@@ -161,6 +164,15 @@ typedef struct henry_config {
                            nodes i = 0..nx_l-1; x = Lx is Dirichlet);
                            henry_adjoint, henry_solve_series, henry_fields
                            and henry_time_kernel return HENRY_E_UNSUPPORTED */
+  int mg_tb_cells;      /* largest multigrid level (cells per sample) above
+                           the shared-memory kernel whose V-cycle legs run
+                           temporally blocked: the nu1 pre-sweeps and the
+                           residual restriction in one launch, the
+                           prolongation and the nu2 post-sweeps in another,
+                           a tile of cells plus a halo per block (needs
+                           nu1, nu2 >= 1; results bitwise those of one launch
+                           per operation). 0 (default): one launch per
+                           operation. A schedule knob for the autotuner */
 } henry_config;
 
 #define HENRY_DISC_CELL 0        /* cell-centred, full upwind (default)      */
@@ -240,7 +252,7 @@ int henry_sample_pairs(henry_ctx* ctx, int level, const double* xi, int B,
 /* Multigrid schedule of one MLMC level (the autotuner's knobs; meanings as
  * the henry_config fields of the same names). */
 typedef struct henry_schedule {
-  int vcycles, nu1, nu2, mg_small_cells, jac_lag, res_rows;
+  int vcycles, nu1, nu2, mg_small_cells, jac_lag, res_rows, mg_tb_cells;
 } henry_schedule;
 
 /* Give MLMC level `level` its own schedule: the fine solves of level l

@@ -25,7 +25,7 @@ LOOP_HOST = 0
 LOOP_GRAPH = 1
 DISC_CELL = 0
 DISC_VERTEX = 1
-S_MAXIT, S_NONFINITE, S_BADINPUT = 1, 2, 4
+S_MAXIT, S_NONFINITE, S_BADINPUT, S_STALL = 1, 2, 4, 8
 ERRORS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "out of device memory",
           -5: "unsupported grid"}
 
@@ -48,7 +48,8 @@ class HenryConfig(ctypes.Structure):
                 ("mg_cluster_cells", ctypes.c_int), ("mg_small_cells", ctypes.c_int),
                 ("jac_lag", ctypes.c_int), ("field_model", ctypes.c_int),
                 ("krylov_iters", ctypes.c_int), ("adjoint_rtol", ctypes.c_double),
-                ("res_rows", ctypes.c_int), ("discretisation", ctypes.c_int)]
+                ("res_rows", ctypes.c_int), ("discretisation", ctypes.c_int),
+                ("mg_tb_cells", ctypes.c_int)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
@@ -57,7 +58,7 @@ class HenryConfig(ctypes.Structure):
 class HenrySchedule(ctypes.Structure):
     """Multigrid schedule of one MLMC level (henry_schedule)."""
     _fields_ = [(n, ctypes.c_int) for n in ("vcycles", "nu1", "nu2", "mg_small_cells", "jac_lag",
-                                             "res_rows")]
+                                             "res_rows", "mg_tb_cells")]
 
 
 class HenryLevelBatch(ctypes.Structure):
@@ -288,9 +289,9 @@ class Context:
         return qf, qc, cf, cc, st
 
     def set_schedule(self, level, vcycles, nu1, nu2, mg_small_cells=512, jac_lag=0, res_rows=0,
-                     **_):
+                     mg_tb_cells=0, **_):
         """henry_set_schedule: the multigrid schedule of one MLMC level."""
-        sc = HenrySchedule(vcycles, nu1, nu2, mg_small_cells, jac_lag, res_rows)
+        sc = HenrySchedule(vcycles, nu1, nu2, mg_small_cells, jac_lag, res_rows, mg_tb_cells)
         _check(self.lib.henry_set_schedule(self._h, level, ctypes.byref(sc)))
 
     def sample_levels(self, xis, want_c=False, stream=None):

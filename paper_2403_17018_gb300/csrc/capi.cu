@@ -138,6 +138,7 @@ int validate(const henry_config* c) {
   if (!(c->adjoint_rtol > 0.0) || !(c->adjoint_rtol < 1e-3))
     return fail(HENRY_E_INVALID, "adjoint_rtol must be in (0, 1e-3)");
   if (c->res_rows < 0 || c->res_rows > 64) return fail(HENRY_E_INVALID, "res_rows must be in 0..64");
+  if (c->mg_tb_cells < 0) return fail(HENRY_E_INVALID, "mg_tb_cells must be >= 0");
   if (c->discretisation != HENRY_DISC_CELL && c->discretisation != HENRY_DISC_VERTEX)
     return fail(HENRY_E_INVALID, "discretisation must be HENRY_DISC_CELL or HENRY_DISC_VERTEX");
   if (c->discretisation == HENRY_DISC_VERTEX && (c->nx0 % 2 || c->ny0 < 1))
@@ -191,6 +192,7 @@ int henry_default_config(henry_config* c) {
   c->field_model = 0;
   c->krylov_iters = 0;
   c->adjoint_rtol = 1e-14;
+  c->mg_tb_cells = 0;
   return HENRY_OK;
 }
 
@@ -344,6 +346,7 @@ int henry_set_schedule(henry_ctx* ctx, int level, const henry_schedule* sc) {
   c.mg_small_cells = sc->mg_small_cells;
   c.jac_lag = sc->jac_lag;
   c.res_rows = sc->res_rows;
+  c.mg_tb_cells = sc->mg_tb_cells;
   const int rc = validate(&c);
   if (rc) return rc;
   CKR(cudaSetDevice(ctx->device));

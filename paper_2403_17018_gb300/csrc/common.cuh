@@ -10,6 +10,7 @@ constexpr int kNQ = 22;
 constexpr int kStatusMaxit = 1;
 constexpr int kStatusNonfinite = 2;
 constexpr int kStatusBadInput = 4;
+constexpr int kStatusStall = 8;      // a bounded wait for an asynchronous copy gave up
 constexpr int kBlock = 256;
 constexpr int kMaxCoarseUnknowns = 64;
 
@@ -18,6 +19,71 @@ constexpr int kMaxCoarseUnknowns = 64;
     if (ctr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)                 \
       atomicAdd((unsigned long long*)(ctr), 1ULL);                                     \
   } while (0)
+
+// ---------------------------------------------------------------------------
+// One-dimensional bulk copies from global to shared memory by the TMA unit
+// (cp.async.bulk), completing on an mbarrier in shared memory. A copy needs
+// both addresses and its size to be multiples of 16 bytes (bulk_ok); callers
+// copy anything else with plain loads. Waits are bounded by the global
+// timer so that a copy that never lands cannot hang the block.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kBulkWaitNs = 200000000ull;   // 0.2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool bulk_ok(const void* dst, const void* src, size_t bytes) {
+  return bytes > 0 && ((((uintptr_t)dst) | ((uintptr_t)src) | (uintptr_t)bytes) & 15) == 0;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One arrival that also raises the barrier's expected transaction bytes.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile(
+      "{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(
+          smem_u32(bar)),
+      "r"(bytes)
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for phase `parity` of the barrier; false when kBulkWaitNs passed first.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > kBulkWaitNs) return false;
+  return true;
+}
 
 // Block sum of a double, result valid in thread 0. Fixed order.
 __device__ __forceinline__ double block_sum(double v, double* sh) {

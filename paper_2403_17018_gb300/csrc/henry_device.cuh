@@ -50,6 +50,35 @@ struct Geom {
   __host__ __device__ int half() const { return (nx * ny) >> 1; }
 };
 
+// Tiling of the temporally blocked multigrid legs (see k_tb_down, k_tb_up).
+constexpr int kTbBlock = 512;
+constexpr int kTbTileX = 64, kTbTileY = 32;   // interior cells of a tile, at most
+
+struct TbTile {
+  int TX, TY;    // interior cells per tile (even)
+  int ntx, nty;  // tiles per sample
+  int H;         // halo rows (the halo columns are H rounded up to even)
+  int EX, EY;    // largest extended tile, for the shared-memory size
+};
+
+// Tiles of at most tx x ty cells (both even) with a halo of 2 nu + extra.
+inline TbTile make_tb_tile(const Geom& G, int nu, int extra, int tx, int ty) {
+  TbTile t;
+  t.TX = tx < G.nx ? tx : G.nx;
+  t.TY = ty < G.ny ? ty : G.ny;
+  t.ntx = (G.nx + t.TX - 1) / t.TX;
+  t.nty = (G.ny + t.TY - 1) / t.TY;
+  t.H = 2 * nu + extra;
+  const int hx = (t.H + 1) & ~1;
+  t.EX = t.TX + 2 * hx < G.nx ? t.TX + 2 * hx : G.nx;
+  t.EY = t.TY + 2 * t.H < G.ny ? t.TY + 2 * t.H : G.ny;
+  return t;
+}
+
+inline size_t tb_smem_bytes(const TbTile& t, size_t tsize) {
+  return (size_t)2 * t.EX * t.EY * tsize;
+}
+
 // Colour-split position of cell (i, j) inside one plane: red cells
 // ((i + j) even) first, then black, each in row-major order of (j, i/2).
 // Requires nx even.

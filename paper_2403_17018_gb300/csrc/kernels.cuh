@@ -193,7 +193,7 @@ static __global__ void k_begin_step(unsigned long long* ctr, Geom G, int B, doub
   }
   const int b = (int)(idx / G.ncell());
   if (idx - (int64_t)b * G.ncell() == 0) {
-    active[b] = (status[b] & (kStatusNonfinite | kStatusBadInput)) ? 0 : 1;
+    active[b] = (status[b] & (kStatusNonfinite | kStatusBadInput | kStatusStall)) ? 0 : 1;
     it_step[b] = 0;
   }
 }
@@ -718,74 +718,117 @@ k_jac(unsigned long long* ctr, Phys P, Geom G, double vtau, int B, const int* __
   store_operator<T>(Jb, ncell, Jc, d);
 }
 
-// Dense LU with partial pivoting of the coarsest system (Gaussian
-// elimination, section 2.3), one warp per sample, rows spread over lanes.
-// Unknown order 2*cell + var, cell natural. FP64 whatever T is. Shared
-// memory: warps_per_block * n * (n + 1) doubles (dynamic).
+// Explicit inverse of the coarsest system (the direct coarse solve of the
+// multigrid, section 2.3), one block per sample: in-place Gauss-Jordan
+// elimination with partial pivoting by rows. Per pivot k, three phases
+// separated by barriers: warp 0 picks the pivot row and records the
+// multipliers of column k, the pivot row is swapped in and divided by the
+// pivot, and every other element is updated by its own thread. The column
+// interchanges that undo the row pivots (last pivot first) are folded into
+// the output index. Unknown order 2*cell + var, cell natural; the inverse is
+// stored transposed, Ainv^T[v][u] at v*n + u, so that the coarse solve
+// x = Ainv b reads it with lanes over u. The arithmetic is the multigrid
+// type T (the coarse solve is part of the preconditioner): one n^3
+// elimination per operator rebuild turns each coarse solve into one
+// parallel matrix-vector product instead of 2n dependent substitution
+// steps. Shared memory (dynamic): coarse_inv_smem_bytes<T>(n).
 template <typename T>
-__global__ void k_coarse_lu(unsigned long long* ctr, Geom G, int B, const int* __restrict__ active,
-                            const T* __restrict__ J, double* __restrict__ LU, int* __restrict__ piv,
-                            const int* __restrict__ refresh) {
+__host__ __device__ inline size_t coarse_inv_smem_bytes(int n) {
+  return ((size_t)n * (n + 1) + n + 2) * sizeof(T) + 2 * (size_t)n * sizeof(int);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+k_coarse_inv(unsigned long long* ctr, Geom G, int B, const int* __restrict__ active,
+             const T* __restrict__ J, T* __restrict__ AinvT, const int* __restrict__ refresh) {
   HENRY_COUNT_LAUNCH(ctr);
-  extern __shared__ double lu_sh[];
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  const int b = blockIdx.x * (blockDim.x >> 5) + w;
-  if (b >= B || !active[b] || (refresh && !refresh[b])) return;
+  extern __shared__ __align__(16) unsigned char inv_sh[];
+  const int b = blockIdx.x;
+  if (!active[b] || (refresh && !refresh[b])) return;
   const int nc = G.ncell(), n = 2 * nc, half = G.half(), ld = n + 1;
-  double* A = lu_sh + (size_t)w * n * ld;
+  T* A = (T*)inv_sh;
+  T* fcol = A + n * ld;                 // multipliers of column k, after the swap
+  T* rinv_sh = fcol + n;                // 1 / pivot
+  int* pv = (int*)(rinv_sh + 2);        // pivot row of each step
+  int* qcol = pv + n;                   // output column -> eliminated column
+  const int l = threadIdx.x & 31;
   const T* Jb = J + (int64_t)b * kJP * nc;
-  for (int e = l; e < n * ld; e += 32) A[e] = 0.0;
-  __syncwarp();
-  for (int cell = l; cell < nc; cell += 32) {
+  for (int e = threadIdx.x; e < n * ld; e += blockDim.x) A[e] = (T)0;
+  __syncthreads();
+  for (int cell = threadIdx.x; cell < nc; cell += blockDim.x) {
     const int j = cell / G.nx, i = cell - j * G.nx;
     const int cs = cs_pos(i, j, G.nx, half);
     const int nb[5] = {cell, i > 0 ? cell - 1 : -1, i < G.nx - 1 ? cell + 1 : -1,
                        j > 0 ? cell - G.nx : -1, j < G.ny - 1 ? cell + G.nx : -1};
     // the scaled system: identity diagonal blocks, At off the diagonal
-    A[(2 * cell) * ld + 2 * cell] = 1.0;
-    A[(2 * cell + 1) * ld + 2 * cell + 1] = 1.0;
+    A[(2 * cell) * ld + 2 * cell] = (T)1;
+    A[(2 * cell + 1) * ld + 2 * cell + 1] = (T)1;
     for (int q = 1; q < 5; ++q) {
       if (nb[q] < 0) continue;
       for (int e = 0; e < 2; ++e)
         for (int v = 0; v < 2; ++v)
-          A[(2 * cell + e) * ld + 2 * nb[q] + v] = (double)Jb[(int64_t)(4 * q + 2 * e + v) * nc + cs];
+          A[(2 * cell + e) * ld + 2 * nb[q] + v] = Jb[(int64_t)(4 * q + 2 * e + v) * nc + cs];
     }
   }
-  __syncwarp();
-  int* pv = piv + (int64_t)b * kMaxCoarseUnknowns;
+  __syncthreads();
   for (int k = 0; k < n; ++k) {
-    // pivot: largest |A[r][k]|, r >= k, lowest index on ties
-    double bv = -1.0;
-    int br = k;
-    for (int r = k + l; r < n; r += 32) {
-      const double v = fabs(A[r * ld + k]);
-      if (v > bv) { bv = v; br = r; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_down_sync(0xffffffffu, bv, o);
-      const int orr = __shfl_down_sync(0xffffffffu, br, o);
-      if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
-    }
-    br = __shfl_sync(0xffffffffu, br, 0);
-    if (l == 0) pv[k] = br;
-    if (br != k)
-      for (int col = l; col < n; col += 32) {
-        const double t = A[k * ld + col];
-        A[k * ld + col] = A[br * ld + col];
-        A[br * ld + col] = t;
+    if (threadIdx.x < 32) {
+      // pivot: largest |A[r][k]|, r >= k, lowest index on ties
+      T bv = (T)-1;
+      int br = k;
+      for (int r = k + l; r < n; r += 32) {
+        const T v = fabs(A[r * ld + k]);
+        if (v > bv) { bv = v; br = r; }
       }
-    __syncwarp();
-    const double d = A[k * ld + k];
-    for (int row = k + 1 + l; row < n; row += 32) {
-      const double m = d != 0.0 ? A[row * ld + k] / d : 0.0;
-      A[row * ld + k] = m;
-      for (int col = k + 1; col < n; ++col) A[row * ld + col] -= m * A[k * ld + col];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_down_sync(0xffffffffu, bv, o);
+        const int orr = __shfl_down_sync(0xffffffffu, br, o);
+        if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
+      }
+      br = __shfl_sync(0xffffffffu, br, 0);
+      // column k of the rows after the swap of rows k and br
+      for (int r = l; r < n; r += 32) fcol[r] = r == k ? (T)0 : A[(r == br ? k : r) * ld + k];
+      if (l == 0) {
+        const T d = A[br * ld + k];
+        pv[k] = br;
+        rinv_sh[0] = d != (T)0 ? (T)1 / d : (T)0;
+      }
     }
-    __syncwarp();
+    __syncthreads();
+    const int br = pv[k];
+    const T rinv = rinv_sh[0];
+    for (int col = threadIdx.x; col < n; col += blockDim.x) {
+      // swap rows k and br; the new pivot row divided by the pivot, its own
+      // column becoming 1 / pivot
+      const T a = A[br * ld + col];
+      if (br != k) A[br * ld + col] = A[k * ld + col];
+      A[k * ld + col] = (col == k ? (T)1 : a) * rinv;
+    }
+    __syncthreads();
+    // every other row: subtract f times the pivot row, its column k
+    // becoming -f / pivot
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int row = e / n, col = e - row * n;
+      if (row == k) continue;
+      const T v = col == k ? (T)0 : A[row * ld + col];
+      A[row * ld + col] = fma(-fcol[row], A[k * ld + col], v);
+    }
+    __syncthreads();
   }
-  double* L = LU + (int64_t)b * kMaxCoarseUnknowns * kMaxCoarseUnknowns;
-  for (int e = l; e < n * n; e += 32) L[e] = A[(e / n) * ld + (e % n)];
+  // column c of the inverse is column q(c) of the eliminated matrix, with
+  // the interchanges (k, pv[k]) applied to c for k = 0, 1, ..., n-1
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    int x = c;
+    for (int k = 0; k < n; ++k) x = x == k ? pv[k] : (x == pv[k] ? k : x);
+    qcol[c] = x;
+  }
+  __syncthreads();
+  T* out = AinvT + (int64_t)b * kMaxCoarseUnknowns * kMaxCoarseUnknowns;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int v = e / n, u = e - v * n;
+    out[e] = A[u * ld + qcol[v]];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -794,101 +837,85 @@ __global__ void k_coarse_lu(unsigned long long* ctr, Geom G, int B, const int* _
 // global-memory bases, and by k_vcycle_small, with shared-memory copies.
 // ---------------------------------------------------------------------------
 
-// Point-block Gauss-Seidel update of the cell at colour-split position
-// `pos` of colour `colour`, on the row-scaled system: x_P = bt_P - sum_Q
-// At_PQ x_Q (= D_P^{-1} (b_P - sum_Q A_PQ x_Q)). Each product is subtracted
-// on its own so that it compiles to one FMA (the FP64 form of this kernel
-// is bound by GB300's FP64 pipe).
-template <typename T>
-__device__ __forceinline__ void smooth_cell(const Geom& G, int colour, int pos,
-                                            const T* __restrict__ J, const T* __restrict__ b,
-                                            T* __restrict__ x) {
-  const int half = G.half(), ncell = G.ncell(), hx2 = G.nx >> 1;
-  const int j = pos / hx2, k = pos - j * hx2;
-  const int i = 2 * k + ((j + colour) & 1);
-  const int own = colour * half + pos;
-  const int oth = (1 - colour) * half;
-  const T* Jb = J + own;
-  const T* xp = x + oth;
-  const T* xc = x + ncell + oth;
-  T rp = b[own], rc = b[ncell + own];
+// Point-block Gauss-Seidel update of cell (i, j) on the row-scaled system:
+// x_P = bt_P - sum_Q At_PQ x_Q (= D_P^{-1} (b_P - sum_Q A_PQ x_Q)). Jb points
+// at the cell's colour-split position of plane 0 (planes ncell apart);
+// nb(i', j', vp, vc) reads a neighbour's two unknowns, so that the batched,
+// shared-memory and temporally blocked smoothers all perform the same
+// operations in the same order (their results are bitwise equal). Each
+// product is subtracted on its own so that it compiles to one FMA (the FP64
+// form of the smoother is bound by GB300's FP64 pipe).
+template <typename T, typename NB>
+__device__ __forceinline__ void gs_point(int i, int j, int nx, int ny, int ncell,
+                                         const T* __restrict__ Jb, T bp, T bc, NB nb, T& xp,
+                                         T& xc) {
+  T rp = bp, rc = bc;
+  T vp, vc;
   if (i > 0) {
-    const int q = j * hx2 + ((i - 1) >> 1);
-    const T vp = xp[q], vc = xc[q];
+    nb(i - 1, j, vp, vc);
     rp -= Jb[4 * ncell] * vp;
     rp -= Jb[5 * ncell] * vc;
     rc -= Jb[6 * ncell] * vp;
     rc -= Jb[7 * ncell] * vc;
   }
-  if (i < G.nx - 1) {
-    const int q = j * hx2 + ((i + 1) >> 1);
-    const T vp = xp[q], vc = xc[q];
+  if (i < nx - 1) {
+    nb(i + 1, j, vp, vc);
     rp -= Jb[8 * ncell] * vp;
     rp -= Jb[9 * ncell] * vc;
     rc -= Jb[10 * ncell] * vp;
     rc -= Jb[11 * ncell] * vc;
   }
   if (j > 0) {
-    const int q = (j - 1) * hx2 + (i >> 1);
-    const T vp = xp[q], vc = xc[q];
+    nb(i, j - 1, vp, vc);
     rp -= Jb[12 * ncell] * vp;
     rp -= Jb[13 * ncell] * vc;
     rc -= Jb[14 * ncell] * vp;
     rc -= Jb[15 * ncell] * vc;
   }
-  if (j < G.ny - 1) {
-    const int q = (j + 1) * hx2 + (i >> 1);
-    const T vp = xp[q], vc = xc[q];
+  if (j < ny - 1) {
+    nb(i, j + 1, vp, vc);
     rp -= Jb[16 * ncell] * vp;
     rp -= Jb[17 * ncell] * vc;
     rc -= Jb[18 * ncell] * vp;
     rc -= Jb[19 * ncell] * vc;
   }
-  x[own] = rp;
-  x[ncell + own] = rc;
+  xp = rp;
+  xc = rc;
 }
 
 // Unscaled residual b - A x at cell (i, j) from the row-scaled system:
-// D_P (bt_P - x_P - sum_Q At_PQ x_Q).
-template <typename T>
-__device__ __forceinline__ void residual_cell(const Geom& G, int i, int j, const T* __restrict__ Jb,
-                                              const T* __restrict__ b, const T* __restrict__ x,
-                                              T& rp, T& rc) {
-  const int ncell = G.ncell(), half = G.half(), nx = G.nx;
-  const int cs = cs_pos(i, j, nx, half);
-  const T* Jc = Jb + cs;
-  const T* xp = x;
-  const T* xc = x + ncell;
-  rp = b[cs] - xp[cs];
-  rc = b[ncell + cs] - xc[cs];
+// D_P (bt_P - x_P - sum_Q At_PQ x_Q); Jc, nb as in gs_point, (x0p, x0c) the
+// cell's own unknowns.
+template <typename T, typename NB>
+__device__ __forceinline__ void resid_point(int i, int j, int nx, int ny, int ncell,
+                                            const T* __restrict__ Jc, T bp, T bc, T x0p, T x0c,
+                                            NB nb, T& rp, T& rc) {
+  rp = bp - x0p;
+  rc = bc - x0c;
   T vp, vc;
   if (i > 0) {
-    const int q = cs_pos(i - 1, j, nx, half);
-    vp = xp[q]; vc = xc[q];
+    nb(i - 1, j, vp, vc);
     rp -= Jc[4 * ncell] * vp;
     rp -= Jc[5 * ncell] * vc;
     rc -= Jc[6 * ncell] * vp;
     rc -= Jc[7 * ncell] * vc;
   }
   if (i < nx - 1) {
-    const int q = cs_pos(i + 1, j, nx, half);
-    vp = xp[q]; vc = xc[q];
+    nb(i + 1, j, vp, vc);
     rp -= Jc[8 * ncell] * vp;
     rp -= Jc[9 * ncell] * vc;
     rc -= Jc[10 * ncell] * vp;
     rc -= Jc[11 * ncell] * vc;
   }
   if (j > 0) {
-    const int q = cs_pos(i, j - 1, nx, half);
-    vp = xp[q]; vc = xc[q];
+    nb(i, j - 1, vp, vc);
     rp -= Jc[12 * ncell] * vp;
     rp -= Jc[13 * ncell] * vc;
     rc -= Jc[14 * ncell] * vp;
     rc -= Jc[15 * ncell] * vc;
   }
-  if (j < G.ny - 1) {
-    const int q = cs_pos(i, j + 1, nx, half);
-    vp = xp[q]; vc = xc[q];
+  if (j < ny - 1) {
+    nb(i, j + 1, vp, vc);
     rp -= Jc[16 * ncell] * vp;
     rp -= Jc[17 * ncell] * vc;
     rc -= Jc[18 * ncell] * vp;
@@ -897,6 +924,52 @@ __device__ __forceinline__ void residual_cell(const Geom& G, int i, int j, const
   const T sp = rp, sc = rc;
   rp = Jc[20 * ncell] * sp + Jc[21 * ncell] * sc;
   rc = Jc[22 * ncell] * sp + Jc[23 * ncell] * sc;
+}
+
+// Reader of a sample's unknowns in the colour-split layout.
+template <typename T>
+struct CsReader {
+  const T* x;
+  int ncell, hx2, half, nx;
+  __device__ __forceinline__ void operator()(int i, int j, T& vp, T& vc) const {
+    const int q = cs_pos(i, j, nx, half);
+    vp = x[q];
+    vc = x[ncell + q];
+  }
+};
+
+// Point-block Gauss-Seidel update of the cell at colour-split position
+// `pos` of colour `colour` on one sample's arrays (colour-split layout).
+template <typename T>
+__device__ __forceinline__ void smooth_cell(const Geom& G, int colour, int pos,
+                                            const T* __restrict__ J, const T* __restrict__ b,
+                                            T* __restrict__ x) {
+  const int half = G.half(), ncell = G.ncell(), hx2 = G.nx >> 1;
+  const int j = pos / hx2, k = pos - j * hx2;
+  const int i = 2 * k + ((j + colour) & 1);
+  const int own = colour * half + pos;
+  const T* xo = x + (1 - colour) * half;   // the other colour's half of each plane
+  T xp, xc;
+  gs_point<T>(i, j, G.nx, G.ny, ncell, J + own, b[own], b[ncell + own],
+              [&](int ii, int jj, T& vp, T& vc) {
+                const int q = jj * hx2 + (ii >> 1);
+                vp = xo[q];
+                vc = xo[ncell + q];
+              },
+              xp, xc);
+  x[own] = xp;
+  x[ncell + own] = xc;
+}
+
+// Unscaled residual b - A x at cell (i, j) (colour-split layout).
+template <typename T>
+__device__ __forceinline__ void residual_cell(const Geom& G, int i, int j, const T* __restrict__ Jb,
+                                              const T* __restrict__ b, const T* __restrict__ x,
+                                              T& rp, T& rc) {
+  const int ncell = G.ncell(), half = G.half(), nx = G.nx;
+  const int cs = cs_pos(i, j, nx, half);
+  resid_point<T>(i, j, nx, G.ny, ncell, Jb + cs, b[cs], b[ncell + cs], x[cs], x[ncell + cs],
+                 CsReader<T>{x, ncell, nx >> 1, half, nx}, rp, rc);
 }
 
 // Coarse cell `cell` of level k-1: b_c = sum over the four children of
@@ -938,6 +1011,23 @@ __device__ __forceinline__ int black_cell(const Geom& G, int pos) {
   return j * G.nx + 2 * k + ((j + 1) & 1);
 }
 
+// Bilinear correction (vp, vc) of fine cell (i, j) from the coarse
+// unknowns xc (colour-split layout of Gc).
+template <typename T>
+__device__ __forceinline__ void prolong_value(const Geom& Gc, int i, int j,
+                                              const T* __restrict__ xc, T& vp, T& vc) {
+  const int I = i >> 1, J = j >> 1;
+  int I2 = I + ((i & 1) ? 1 : -1), J2 = J + ((j & 1) ? 1 : -1);
+  I2 = I2 < 0 ? 0 : (I2 >= Gc.nx ? Gc.nx - 1 : I2);
+  J2 = J2 < 0 ? 0 : (J2 >= Gc.ny ? Gc.ny - 1 : J2);
+  const int ncc = Gc.ncell(), hc = Gc.half();
+  const int a0 = cs_pos(I, J, Gc.nx, hc), a1 = cs_pos(I2, J, Gc.nx, hc);
+  const int a2 = cs_pos(I, J2, Gc.nx, hc), a3 = cs_pos(I2, J2, Gc.nx, hc);
+  const T w0 = (T)0.5625, w1 = (T)0.1875, w3 = (T)0.0625;
+  vp = w0 * xc[a0] + w1 * (xc[a1] + xc[a2]) + w3 * xc[a3];
+  vc = w0 * xc[ncc + a0] + w1 * (xc[ncc + a1] + xc[ncc + a2]) + w3 * xc[ncc + a3];
+}
+
 // Fine cell `cell` of level k: x_f += P x_c, cell-centred bilinear
 // interpolation (9/16, 3/16, 3/16, 1/16), constant extrapolation at the
 // domain boundary. When post-smoothing follows, only black cells are
@@ -948,58 +1038,33 @@ template <typename T>
 __device__ __forceinline__ void prolong_cell(const Geom& Gc, const Geom& Gf, int cell,
                                              const T* __restrict__ xc, T* __restrict__ xf) {
   const int j = cell / Gf.nx, i = cell - j * Gf.nx;
-  const int I = i >> 1, J = j >> 1;
-  int I2 = I + ((i & 1) ? 1 : -1), J2 = J + ((j & 1) ? 1 : -1);
-  I2 = I2 < 0 ? 0 : (I2 >= Gc.nx ? Gc.nx - 1 : I2);
-  J2 = J2 < 0 ? 0 : (J2 >= Gc.ny ? Gc.ny - 1 : J2);
-  const int ncc = Gc.ncell(), hc = Gc.half(), ncf = Gf.ncell();
-  const int a0 = cs_pos(I, J, Gc.nx, hc), a1 = cs_pos(I2, J, Gc.nx, hc);
-  const int a2 = cs_pos(I, J2, Gc.nx, hc), a3 = cs_pos(I2, J2, Gc.nx, hc);
-  const T w0 = (T)0.5625, w1 = (T)0.1875, w3 = (T)0.0625;
-  const T vp = w0 * xc[a0] + w1 * (xc[a1] + xc[a2]) + w3 * xc[a3];
-  const T vc = w0 * xc[ncc + a0] + w1 * (xc[ncc + a1] + xc[ncc + a2]) + w3 * xc[ncc + a3];
-  const int cs = cs_pos(i, j, Gf.nx, Gf.half());
+  T vp, vc;
+  prolong_value<T>(Gc, i, j, xc, vp, vc);
+  const int cs = cs_pos(i, j, Gf.nx, Gf.half()), ncf = Gf.ncell();
   xf[cs] += vp;
   xf[ncf + cs] += vc;
 }
 
-// Coarsest-grid solve with the stored LU factors (row-major n x n, pivots)
-// by one warp; y is an n-vector of scratch in shared memory.
+// Coarsest-grid solve x = Ainv b with the stored transposed inverse (see
+// k_coarse_inv) by one warp, lanes over unknowns; y is an n-vector of
+// scratch in shared memory.
 template <typename T>
-__device__ __forceinline__ void coarse_solve_warp(const Geom& G, const double* __restrict__ A,
-                                                  const int* __restrict__ pv,
-                                                  const T* __restrict__ b, T* __restrict__ x,
-                                                  double* y, int l) {
+__device__ __forceinline__ void coarse_solve_warp(const Geom& G, const T* __restrict__ AinvT,
+                                                  const T* __restrict__ b, T* __restrict__ x, T* y,
+                                                  int l) {
   const int nc = G.ncell(), n = 2 * nc, half = G.half();
   for (int u = l; u < n; u += 32) {
     const int cell = u >> 1, v = u & 1;
     const int j = cell / G.nx, i = cell - j * G.nx;
-    y[u] = (double)b[v * nc + cs_pos(i, j, G.nx, half)];
+    y[u] = b[v * nc + cs_pos(i, j, G.nx, half)];
   }
   __syncwarp();
-  if (l == 0)
-    for (int k = 0; k < n; ++k) {
-      const int r = pv[k];
-      if (r != k) { const double t = y[k]; y[k] = y[r]; y[r] = t; }
-    }
-  __syncwarp();
-  for (int k = 0; k < n; ++k) {  // forward, unit lower
-    const double yk = y[k];
-    __syncwarp();
-    for (int r = k + 1 + l; r < n; r += 32) y[r] -= A[r * n + k] * yk;
-    __syncwarp();
-  }
-  for (int k = n - 1; k >= 0; --k) {  // backward
-    if (l == 0) y[k] = y[k] / A[k * n + k];
-    __syncwarp();
-    const double yk = y[k];
-    for (int r = l; r < k; r += 32) y[r] -= A[r * n + k] * yk;
-    __syncwarp();
-  }
   for (int u = l; u < n; u += 32) {
-    const int cell = u >> 1, v = u & 1;
+    T acc = (T)0;
+    for (int v = 0; v < n; ++v) acc = fma(AinvT[v * n + u], y[v], acc);
+    const int cell = u >> 1, var = u & 1;
     const int j = cell / G.nx, i = cell - j * G.nx;
-    x[v * nc + cs_pos(i, j, G.nx, half)] = (T)y[u];
+    x[var * nc + cs_pos(i, j, G.nx, half)] = acc;
   }
 }
 
@@ -1008,16 +1073,16 @@ __device__ __forceinline__ void coarse_solve_warp(const Geom& G, const double* _
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_coarse_solve(unsigned long long* ctr, Geom G, int B, const int* __restrict__ active,
-                               const double* __restrict__ LU, const int* __restrict__ piv,
-                               const T* __restrict__ bvec, T* __restrict__ xvec) {
+                               const T* __restrict__ AinvT, const T* __restrict__ bvec,
+                               T* __restrict__ xvec) {
   HENRY_COUNT_LAUNCH(ctr);
-  __shared__ double ysh[kBlock / 32][kMaxCoarseUnknowns];
+  __shared__ T ysh[kBlock / 32][kMaxCoarseUnknowns];
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int b = blockIdx.x * (blockDim.x >> 5) + w;
   if (b >= B || !active[b]) return;
   const int64_t ob = (int64_t)b * 2 * G.ncell();
-  coarse_solve_warp<T>(G, LU + (int64_t)b * kMaxCoarseUnknowns * kMaxCoarseUnknowns,
-                       piv + (int64_t)b * kMaxCoarseUnknowns, bvec + ob, xvec + ob, ysh[w], l);
+  coarse_solve_warp<T>(G, AinvT + (int64_t)b * kMaxCoarseUnknowns * kMaxCoarseUnknowns, bvec + ob,
+                       xvec + ob, ysh[w], l);
 }
 
 // One red (colour 0) or black (colour 1) half-sweep of point-block
@@ -1076,9 +1141,13 @@ k_prolong(unsigned long long* ctr, Geom Gc, Geom Gf, int B, const int* __restric
 // ---------------------------------------------------------------------------
 // fused V-cycles on the small multigrid levels 0..ks (at most kSmallCells
 // cells per sample on level ks): one block per sample; J, b and x of these
-// levels and the coarsest LU factors are staged in shared memory and every
+// levels and the coarsest inverse are staged in shared memory and every
 // phase of the cycle is separated by __syncthreads(). Level ks takes b from
 // and returns x to global memory (x_ks is read as the initial guess).
+// Each staged array is one contiguous run per sample, so the staging is a
+// handful of TMA bulk copies issued by one thread (plain loads only for a
+// run that is not 16-byte aligned); the first 16 bytes of the dynamic shared
+// memory hold their mbarrier.
 // ---------------------------------------------------------------------------
 constexpr int kSmallCells = 512;   // largest level the shared-memory kernel accepts
 constexpr int kMaxLevels = 12;
@@ -1097,15 +1166,14 @@ __host__ __device__ inline size_t small_smem_bytes(const SmallMG<T>& M) {
   size_t cells = 0;
   for (int k = 0; k <= M.ks; ++k) cells += (size_t)M.g[k].ncell();
   const int n = 2 * M.g[0].ncell();
-  return cells * (kJP + 4) * sizeof(T) + (size_t)n * n * sizeof(double) + n * sizeof(double) +
-         n * sizeof(int) + 64;
+  return 16 + cells * (kJP + 4) * sizeof(T) + (size_t)n * n * sizeof(T) + n * sizeof(T) + 64;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 k_vcycle_small(unsigned long long* ctr, SmallMG<T> M, int B, const int* __restrict__ active,
-               const double* __restrict__ LU, const int* __restrict__ piv, int nu1, int nu2,
-               int ncycles) {
+               const T* __restrict__ AinvT, int nu1, int nu2, int ncycles,
+               int* __restrict__ status) {
   HENRY_COUNT_LAUNCH(ctr);
   extern __shared__ __align__(16) unsigned char smem[];
   const int bs = blockIdx.x;
@@ -1114,7 +1182,8 @@ k_vcycle_small(unsigned long long* ctr, SmallMG<T> M, int B, const int* __restri
   T* J[kMaxLevels];
   T* bv[kMaxLevels];
   T* xv[kMaxLevels];
-  T* p = (T*)smem;
+  uint64_t* bar = (uint64_t*)smem;
+  T* p = (T*)(smem + 16);
   for (int k = 0; k <= ks; ++k) {
     const int nc = M.g[k].ncell();
     J[k] = p; p += kJP * nc;
@@ -1122,25 +1191,45 @@ k_vcycle_small(unsigned long long* ctr, SmallMG<T> M, int B, const int* __restri
     xv[k] = p; p += 2 * nc;
   }
   const int n = 2 * M.g[0].ncell();
-  double* A = (double*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
-  double* y = A + n * n;
-  int* pv = (int*)(y + n);
-  // stage J of all small levels, b and x of the top one, the LU factors
-  for (int k = 0; k <= ks; ++k) {
-    const int nc = M.g[k].ncell();
-    const T* src = M.J[k] + (int64_t)bs * kJP * nc;
-    for (int e = threadIdx.x; e < kJP * nc; e += blockDim.x) J[k][e] = src[e];
-  }
-  {
+  T* A = (T*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+  T* y = A + n * n;
+  // stage J of all small levels, b and x of the top one and the coarsest
+  // inverse: each is one run (destination, source, bytes), sizes multiples of 4
+  auto runs = [&](auto&& f) {
+    for (int k = 0; k <= ks; ++k) {
+      const int nc = M.g[k].ncell();
+      f(J[k], M.J[k] + (int64_t)bs * kJP * nc, (unsigned)(kJP * nc * sizeof(T)));
+    }
     const int nc = M.g[ks].ncell();
-    const T* sb = M.b[ks] + (int64_t)bs * 2 * nc;
-    const T* sx = M.x[ks] + (int64_t)bs * 2 * nc;
-    for (int e = threadIdx.x; e < 2 * nc; e += blockDim.x) { bv[ks][e] = sb[e]; xv[ks][e] = sx[e]; }
+    f(bv[ks], M.b[ks] + (int64_t)bs * 2 * nc, (unsigned)(2 * nc * sizeof(T)));
+    f(xv[ks], M.x[ks] + (int64_t)bs * 2 * nc, (unsigned)(2 * nc * sizeof(T)));
+    f(A, AinvT + (int64_t)bs * kMaxCoarseUnknowns * kMaxCoarseUnknowns,
+      (unsigned)(n * n * sizeof(T)));
+  };
+  unsigned tx = 0;
+  runs([&](void* d, const void* src, unsigned bytes) { tx += bulk_ok(d, src, bytes) ? bytes : 0u; });
+  if (threadIdx.x == 0 && tx > 0) {
+    mbar_init(bar, 1);
+    mbar_arrive_expect_tx(bar, tx);
+    runs([&](void* d, const void* src, unsigned bytes) {
+      if (bulk_ok(d, src, bytes)) bulk_g2s(d, src, bytes, bar);
+    });
   }
-  const double* Ag = LU + (int64_t)bs * kMaxCoarseUnknowns * kMaxCoarseUnknowns;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = Ag[e];
-  for (int e = threadIdx.x; e < n; e += blockDim.x) pv[e] = piv[(int64_t)bs * kMaxCoarseUnknowns + e];
-  __syncthreads();
+  runs([&](void* d, const void* src, unsigned bytes) {
+    if (bulk_ok(d, src, bytes))
+      return;
+    uint32_t* dw = (uint32_t*)d;
+    const uint32_t* sw = (const uint32_t*)src;
+    for (unsigned e = threadIdx.x; e < bytes / 4; e += blockDim.x) dw[e] = sw[e];
+  });
+  __syncthreads();              // the barrier is initialised before anyone waits on it
+  if (tx > 0 && !__syncthreads_and(mbar_wait_bounded(bar, 0))) {
+    // a copy did not land in time: flag the sample, give copies still in
+    // flight one more bounded wait, and leave x_ks untouched
+    if (threadIdx.x == 0) status[bs] |= kStatusStall;
+    mbar_wait_bounded(bar, 0);
+    return;
+  }
   for (int cyc = 0; cyc < ncycles; ++cyc) {
     for (int k = ks; k >= 1; --k) {
       const Geom& G = M.g[k];
@@ -1155,7 +1244,7 @@ k_vcycle_small(unsigned long long* ctr, SmallMG<T> M, int B, const int* __restri
                          xv[k - 1], nu1 > 0);
       __syncthreads();
     }
-    if (threadIdx.x < 32) coarse_solve_warp<T>(M.g[0], A, pv, bv[0], xv[0], y, threadIdx.x);
+    if (threadIdx.x < 32) coarse_solve_warp<T>(M.g[0], A, bv[0], xv[0], y, threadIdx.x);
     __syncthreads();
     for (int k = 1; k <= ks; ++k) {
       const Geom& G = M.g[k];
@@ -1303,11 +1392,11 @@ constexpr int kMaxCluster = 8;
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 k_vcycle_cluster(unsigned long long* ctr, SmallMG<T> M, int B, const int* __restrict__ active,
-                 const double* __restrict__ LU, const int* __restrict__ piv, int nu1, int nu2,
+                 const T* __restrict__ AinvT, int nu1, int nu2,
                  int ncycles, int CL) {
   HENRY_COUNT_LAUNCH(ctr);
   namespace cg = cooperative_groups;
-  __shared__ double ysh[kMaxCoarseUnknowns];
+  __shared__ T ysh[kMaxCoarseUnknowns];
   const int b = blockIdx.x / CL;
   const int rank = blockIdx.x - b * CL;
   if (b >= B || !active[b]) return;           // uniform over the cluster
@@ -1327,8 +1416,7 @@ k_vcycle_cluster(unsigned long long* ctr, SmallMG<T> M, int B, const int* __rest
     bv[k] = M.b[k] + (int64_t)b * 2 * nc;
     xv[k] = M.x[k] + (int64_t)b * 2 * nc;
   }
-  const double* A = LU + (int64_t)b * kMaxCoarseUnknowns * kMaxCoarseUnknowns;
-  const int* pv = piv + (int64_t)b * kMaxCoarseUnknowns;
+  const T* A = AinvT + (int64_t)b * kMaxCoarseUnknowns * kMaxCoarseUnknowns;
   for (int cyc = 0; cyc < ncycles; ++cyc) {
     for (int k = kc; k >= 1; --k) {
       const Geom& G = M.g[k];
@@ -1342,7 +1430,7 @@ k_vcycle_cluster(unsigned long long* ctr, SmallMG<T> M, int B, const int* __rest
                          xv[k - 1], nu1 > 0);
       sync();
     }
-    if (rank == 0 && threadIdx.x < 32) coarse_solve_warp<T>(M.g[0], A, pv, bv[0], xv[0], ysh, threadIdx.x);
+    if (rank == 0 && threadIdx.x < 32) coarse_solve_warp<T>(M.g[0], A, bv[0], xv[0], ysh, threadIdx.x);
     sync();
     for (int k = 1; k <= kc; ++k) {
       const Geom& G = M.g[k];

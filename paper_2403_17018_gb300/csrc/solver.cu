@@ -3,11 +3,13 @@
 
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <utility>
 
 #include "kernels.cuh"
+#include "tb.cuh"
 
 namespace henry {
 
@@ -33,7 +35,7 @@ __global__ void k_activate(unsigned long long* ctr, int B, const int* __restrict
   HENRY_COUNT_LAUNCH(ctr);
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b < B) {
-    active[b] = (status[b] & (kStatusNonfinite | kStatusBadInput)) ? 0 : 1;
+    active[b] = (status[b] & (kStatusNonfinite | kStatusBadInput | kStatusStall)) ? 0 : 1;
     it_step[b] = 0;
   }
 }
@@ -87,6 +89,18 @@ Solver::Solver(const henry_config& cfg, int nx, int ny, int nt) : cfg_(cfg), nt_
   const int per = geoms_[kc_].ncell() / 1024;
   cl_ = per < 1 ? 1 : (per > kMaxCluster ? kMaxCluster : per);
   if (!cfg_.mg_fusion) ks_ = kc_ = 0;
+  // temporally blocked legs: batched levels (above the fused kernels) of at
+  // most mg_tb_cells cells, tiles of at most 64 x 32 cells
+  tb_.assign(geoms_.size(), 0);
+  tbd_.resize(geoms_.size());
+  tbu_.resize(geoms_.size());
+  for (size_t k = 1; k < geoms_.size(); ++k) {
+    const bool fused = (int)k <= ks_ || ((int)k <= kc_ && kc_ > ks_);
+    if (fused || cfg_.nu1 < 1 || cfg_.nu2 < 1 || geoms_[k].ncell() > cfg_.mg_tb_cells) continue;
+    tb_[k] = 1;
+    tbd_[k] = make_tb_tile(geoms_[k], cfg_.nu1, 1, kTbTileX, kTbTileY);
+    tbu_[k] = make_tb_tile(geoms_[k], cfg_.nu2, 0, kTbTileX, kTbTileY);
+  }
 }
 
 Solver::~Solver() { free_all(); }
@@ -135,20 +149,19 @@ int Solver::debug_copy(int mg_level, int what, void* dst, int64_t bytes) const {
   return HENRY_OK;
 }
 
-// The dynamic shared-memory limit of k_vcycle_small<T> is an attribute of
-// the function in the device's context, shared by every solver of the
-// process: it is only ever raised, to the largest size any solver needs,
-// and outside stream capture (from ensure()), so that no solver's graph
-// capture can meet a limit lowered by another solver.
-template <typename T>
-static cudaError_t raise_small_smem_limit(size_t smem) {
+// The dynamic shared-memory limit of a kernel is an attribute of the
+// function in the device's context, shared by every solver of the process:
+// it is only ever raised, to the largest size any solver needs, and outside
+// stream capture (from ensure()), so that no solver's graph capture can meet
+// a limit lowered by another solver.
+static cudaError_t raise_smem_limit(const void* fn, size_t smem) {
   static std::mutex mu;
-  static size_t cur = 0;
+  static std::map<const void*, size_t> cur;
   std::lock_guard<std::mutex> lock(mu);
-  if (smem <= cur) return cudaSuccess;
-  const cudaError_t e =
-      cudaFuncSetAttribute(k_vcycle_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) cur = smem;
+  size_t& c = cur[fn];
+  if (smem <= c || smem <= 48 * 1024) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) c = smem;
   return e;
 }
 
@@ -159,9 +172,17 @@ int Solver::ensure(int B, cudaStream_t s) {
     Mf.ks = Md.ks = ks_;
     for (int k = 0; k <= ks_; ++k) Mf.g[k] = Md.g[k] = geoms_[k];
     if (tsize_ == sizeof(float))
-      CK(raise_small_smem_limit<float>(small_smem_bytes(Mf)));
+      CK(raise_smem_limit((const void*)k_vcycle_small<float>, small_smem_bytes(Mf)));
     else
-      CK(raise_small_smem_limit<double>(small_smem_bytes(Md)));
+      CK(raise_smem_limit((const void*)k_vcycle_small<double>, small_smem_bytes(Md)));
+  }
+  for (size_t k = 1; k < levels_.size(); ++k) {
+    if (!tb_[k]) continue;
+    const bool f32 = tsize_ == sizeof(float);
+    CK(raise_smem_limit(f32 ? (const void*)k_tb_down<float> : (const void*)k_tb_down<double>,
+                        tb_smem_bytes(tbd_[k], tsize_)));
+    CK(raise_smem_limit(f32 ? (const void*)k_tb_up<float> : (const void*)k_tb_up<double>,
+                        tb_smem_bytes(tbu_[k], tsize_)));
   }
   if (B <= cap_) return HENRY_OK;
   unsigned long long count = 0;
@@ -171,13 +192,14 @@ int Solver::ensure(int B, cudaStream_t s) {
   const size_t Bz = (size_t)B;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
-  struct Off { size_t J, b, x, p, c, phi, K, tx, dx, ty, dy, qx, qy; };
+  struct Off { size_t J, b, x, x2, p, c, phi, K, tx, dx, ty, dy, qx, qy; };
   std::vector<Off> lo(levels_.size());
   for (size_t k = 0; k < levels_.size(); ++k) {
     const size_t n = (size_t)levels_[k].g.ncell() * Bz;
     lo[k].J = take(kJP * n * tsize_);
     lo[k].b = take(2 * n * tsize_);
     lo[k].x = take(2 * n * tsize_);
+    lo[k].x2 = take(tb_[k] ? 2 * n * tsize_ : 0);
     lo[k].p = take(n * 8);
     lo[k].c = take(n * 8);
     lo[k].phi = take(n * 8);
@@ -201,8 +223,7 @@ int Solver::ensure(int B, cudaStream_t s) {
   const size_t o_part = take((size_t)nchunk_ * Bz * 8);
   const size_t o_res0 = take(Bz * 8);
   const size_t o_resl = take(Bz * 8);
-  const size_t o_lu = take(Bz * kMaxCoarseUnknowns * kMaxCoarseUnknowns * 8);
-  const size_t o_piv = take(Bz * kMaxCoarseUnknowns * 4);
+  const size_t o_cinv = take(Bz * kMaxCoarseUnknowns * kMaxCoarseUnknowns * 8);
   const size_t o_act = take(Bz * 4);
   const size_t o_ref = take(Bz * 4);
   const size_t o_its = take(Bz * 4);
@@ -228,6 +249,7 @@ int Solver::ensure(int B, cudaStream_t s) {
     L.J = a + lo[k].J;
     L.b = a + lo[k].b;
     L.x = a + lo[k].x;
+    L.x2 = tb_[k] ? a + lo[k].x2 : nullptr;
     L.p = (double*)(a + lo[k].p);
     L.c = (double*)(a + lo[k].c);
     L.phi = (double*)(a + lo[k].phi);
@@ -250,8 +272,7 @@ int Solver::ensure(int B, cudaStream_t s) {
   partial_ = (double*)(a + o_part);
   res0_ = (double*)(a + o_res0);
   res_last_ = (double*)(a + o_resl);
-  lu_ = (double*)(a + o_lu);
-  piv_ = (int*)(a + o_piv);
+  cinv_ = a + o_cinv;
   active_ = (int*)(a + o_act);
   refresh_ = (int*)(a + o_ref);
   it_step_ = (int*)(a + o_its);
@@ -282,8 +303,8 @@ void Solver::launch_small(int B, int ncycles, cudaStream_t s) {
     M.x[k] = (T*)levels_[k].x;
   }
   const size_t smem = small_smem_bytes(M);
-  k_vcycle_small<T><<<B, kBlock, smem, s>>>(counter_, M, B, active_, lu_, piv_, cfg_.nu1, cfg_.nu2,
-                                            ncycles);
+  k_vcycle_small<T><<<B, kBlock, smem, s>>>(counter_, M, B, active_, (const T*)cinv_, cfg_.nu1, cfg_.nu2,
+                                            ncycles, status_w_);
 }
 
 template <typename T>
@@ -309,7 +330,7 @@ void Solver::launch_cluster(int B, int ncycles, cudaStream_t s) {
   lc.attrs = at;
   lc.numAttrs = 1;
   cudaLaunchKernelEx(&lc, k_vcycle_cluster<T>, counter_, M, B, (const int*)active_,
-                     (const double*)lu_, (const int*)piv_, cfg_.nu1, cfg_.nu2, ncycles, cl_);
+                     (const T*)cinv_, cfg_.nu1, cfg_.nu2, ncycles, cl_);
 }
 
 // Whole hierarchy fits the shared-memory kernel, or the cluster kernel, or
@@ -327,8 +348,23 @@ void Solver::enqueue_vcycle(int k, int B, cudaStream_t s) {
     return;
   }
   if (k == 0) {
-    k_coarse_solve<T><<<(B + 7) / 8, kBlock, 0, s>>>(counter_, G, B, active_, lu_, piv_,
+    k_coarse_solve<T><<<(B + 7) / 8, kBlock, 0, s>>>(counter_, G, B, active_, (const T*)cinv_,
                                                      (const T*)L.b, (T*)L.x);
+    return;
+  }
+  MGLevel& C = levels_[k - 1];
+  if (tb_[k]) {
+    // two launches: pre-sweeps + restriction (x -> x2), then the coarse
+    // levels, then prolongation + post-sweeps (x2 -> x)
+    const TbTile& td = tbd_[k];
+    const TbTile& tu = tbu_[k];
+    k_tb_down<T><<<dim3(td.ntx * td.nty, B), kTbBlock, tb_smem_bytes(td, sizeof(T)), s>>>(
+        counter_, G, C.g, B, active_, td, cfg_.nu1, (const T*)L.J, (const T*)L.b,
+        (const T*)L.x, (T*)L.x2, (const T*)C.J, (T*)C.b, (T*)C.x);
+    enqueue_vcycle<T>(k - 1, B, s);
+    k_tb_up<T><<<dim3(tu.ntx * tu.nty, B), kTbBlock, tb_smem_bytes(tu, sizeof(T)), s>>>(
+        counter_, C.g, G, B, active_, tu, cfg_.nu2, (const T*)C.x, (const T*)L.J, (const T*)L.b,
+        (const T*)L.x2, (T*)L.x);
     return;
   }
   const int gs = grid1((int64_t)B * G.half());
@@ -336,7 +372,6 @@ void Solver::enqueue_vcycle(int k, int B, cudaStream_t s) {
     for (int col = 0; col < 2; ++col)
       k_smooth<T><<<gs, kBlock, 0, s>>>(counter_, G, B, col, active_, (const T*)L.J,
                                        (const T*)L.b, (T*)L.x);
-  MGLevel& C = levels_[k - 1];
   k_resid_restrict<T><<<grid1((int64_t)B * C.g.ncell()), kBlock, 0, s>>>(
       counter_, G, C.g, B, active_, (const T*)L.J, (const T*)L.b, (const T*)L.x,
       (const T*)C.J, (T*)C.b, (T*)C.x, cfg_.nu1 > 0);
@@ -367,14 +402,11 @@ void Solver::enqueue_coarse_ops(int B, cudaStream_t s, const int* refresh) {
 }
 
 template <typename T>
-void Solver::enqueue_lu(int B, cudaStream_t s, const int* refresh) {
+void Solver::enqueue_coarse_inv(int B, cudaStream_t s, const int* refresh) {
   {
     const int n = 2 * levels_[0].g.ncell();
-    const size_t per_warp = (size_t)n * (n + 1) * sizeof(double);
-    int wpb = (int)(40960 / per_warp);
-    wpb = wpb < 1 ? 1 : (wpb > 8 ? 8 : wpb);
-    k_coarse_lu<T><<<(B + wpb - 1) / wpb, 32 * wpb, per_warp * wpb, s>>>(
-        counter_, levels_[0].g, B, active_, (const T*)levels_[0].J, lu_, piv_, refresh);
+    k_coarse_inv<T><<<B, kBlock, coarse_inv_smem_bytes<T>(n), s>>>(
+        counter_, levels_[0].g, B, active_, (const T*)levels_[0].J, (T*)cinv_, refresh);
   }
 }
 
@@ -458,7 +490,7 @@ void Solver::enqueue_rebuild(int B, cudaStream_t s) {
         F.dx, F.ty, F.dy, qin_, active_, (T*)F.J, (T*)F.b, (T*)F.x, partial_, F.qx, F.qy, refresh);
   }
   enqueue_coarse_ops<T>(B, s, refresh);
-  enqueue_lu<T>(B, s, refresh);
+  enqueue_coarse_inv<T>(B, s, refresh);
 }
 
 // Linear solve of the defect correction (V-cycles or BiCGStab) and the
@@ -999,7 +1031,7 @@ int Solver::adjoint_t(const double* xi, const double* logk, int B, int qoi, int 
             counter_, levels_[k].g, B, active_, (const T*)levels_[k].J, (T*)JT_[k]);
       // the multigrid cycles below read the transposed operators
       for (size_t k = 0; k < levels_.size(); ++k) std::swap(levels_[k].J, JT_[k]);
-      enqueue_lu<T>(B, s, nullptr);
+      enqueue_coarse_inv<T>(B, s, nullptr);
       CK(cudaMemsetAsync(lam_, 0, 2 * n * 8, s));
       for (;;) {
         k_adj_residual<T><<<dim3(adj_nchunk_, B), kBlock, 0, s>>>(

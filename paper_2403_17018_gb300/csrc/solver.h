@@ -21,6 +21,7 @@ struct MGLevel {
   void* J = nullptr;     // T [B][20][ncell], colour-split planes
   void* b = nullptr;     // T [B][2][ncell]
   void* x = nullptr;     // T [B][2][ncell]
+  void* x2 = nullptr;    // T [B][2][ncell], the other copy for temporally blocked legs
   double* p = nullptr;   // state at this level (finest: the solver's p)
   double* c = nullptr;
   double* phi = nullptr;
@@ -103,7 +104,7 @@ class Solver {
   template <typename T> int setup_t(const double* xi, const double* logk, int B, cudaStream_t s);
   template <typename T> int step_t(int B, cudaStream_t s);
   template <typename T> void enqueue_coarse_ops(int B, cudaStream_t s, const int* refresh);
-  template <typename T> void enqueue_lu(int B, cudaStream_t s, const int* refresh);
+  template <typename T> void enqueue_coarse_inv(int B, cudaStream_t s, const int* refresh);
   template <typename T> void enqueue_vcycles(int B, cudaStream_t s);
   template <typename T> void enqueue_precond(int B, cudaStream_t s);
   template <typename T> void enqueue_bicgstab(int B, cudaStream_t s);
@@ -150,8 +151,7 @@ class Solver {
   double* partial_ = nullptr;
   double* res0_ = nullptr;
   double* res_last_ = nullptr;
-  double* lu_ = nullptr;
-  int* piv_ = nullptr;
+  char* cinv_ = nullptr;      // transposed inverse of the coarsest operator (multigrid type)
   int* active_ = nullptr;
   int* refresh_ = nullptr;      // per sample: rebuild operators next iteration (jac_lag)
   int* it_step_ = nullptr;
@@ -172,6 +172,8 @@ class Solver {
   int ks_ = 0;                // top multigrid level handled by k_vcycle_small
   int kc_ = 0;                // top multigrid level handled by k_vcycle_cluster
   int cl_ = 1;                // blocks per cluster (one cluster per sample)
+  std::vector<char> tb_;      // per multigrid level: legs temporally blocked
+  std::vector<TbTile> tbd_, tbu_;   // tiles of the down (halo 2 nu1 + 1) and up legs
   // CUDA graph of one time step (HENRY_LOOP_GRAPH), rebuilt when B changes
   cudaGraphExec_t step_exec_ = nullptr;
   cudaGraph_t step_graph_ = nullptr;

@@ -1,0 +1,227 @@
+// Temporally blocked legs of the multigrid V-cycle (red-black point-block
+// Gauss-Seidel smoothing, section 2.3) on the batched levels.
+//
+// The per-operation path launches one kernel per half-sweep, one for the
+// residual restriction and one for the prolongation: 2 nu1 + 1 launches on
+// the way down a level and 2 nu2 + 1 on the way up, each a full pass over
+// the level. On the levels whose operators stay in L2 those launches are
+// latency-bound. Here each leg is one launch: a block owns a tile of one
+// sample's cells plus a halo, holds the tile's unknowns in shared memory
+// and performs all of the leg's half-sweeps on it, reading the operator
+// rows and right-hand sides from global memory (L2). A half-sweep can only
+// be trusted where every neighbour it read was trusted, so the trusted
+// region shrinks by one cell per half-sweep on every side that is not a
+// domain boundary; a halo of 2 nu cells (plus one for the residual of the
+// down leg) keeps the tile's interior exact. Each block writes back only
+// its interior, to a second buffer: a tile's halo is read before the leg
+// while the neighbouring tiles finish theirs, so every leg reads one copy
+// of the level's unknowns and writes the other (the down leg from the
+// level's x to its second buffer, the up leg back). The arithmetic per cell
+// is that of gs_point, resid_point and prolong_value in the same order, so
+// the results are bitwise those of the per-operation path.
+//
+// Shared layout of a tile: [var][colour][row][m], the colour-split order of
+// the global planes restricted to the tile (m = (i - ex0) / 2 with ex0
+// even), so that a warp's own cells and each of its neighbour reads are
+// consecutive words.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace henry {
+
+// The tile's extended region [ex0, ex1) x [ey0, ey1) and its interior.
+struct TbRegion {
+  int i0, i1, j0, j1;      // interior
+  int ex0, ex1, ey0, ey1;  // interior plus halo, clipped to the domain
+  int hEX, EY;             // half width (cells per colour and row), rows
+  __device__ __forceinline__ TbRegion(const Geom& G, const TbTile& t, int tile) {
+    const int ty = tile / t.ntx, tx = tile - ty * t.ntx;
+    i0 = tx * t.TX;
+    j0 = ty * t.TY;
+    i1 = i0 + t.TX < G.nx ? i0 + t.TX : G.nx;
+    j1 = j0 + t.TY < G.ny ? j0 + t.TY : G.ny;
+    const int hx = (t.H + 1) & ~1;
+    ex0 = i0 - hx > 0 ? i0 - hx : 0;
+    ex1 = i1 + hx < G.nx ? i1 + hx : G.nx;
+    ey0 = j0 - t.H > 0 ? j0 - t.H : 0;
+    ey1 = j1 + t.H < G.ny ? j1 + t.H : G.ny;
+    hEX = (ex1 - ex0) >> 1;
+    EY = ey1 - ey0;
+  }
+  // shared index of cell (i, j), variable v
+  __device__ __forceinline__ int at(int v, int i, int j) const {
+    return ((v * 2 + ((i + j) & 1)) * EY + (j - ey0)) * hEX + ((i - ex0) >> 1);
+  }
+};
+
+// One half-sweep of colour c over the cells of the tile that are trusted
+// after s half-sweeps (the extended region shrunk by s on every side that
+// is not a domain boundary).
+template <typename T>
+__device__ __forceinline__ void tb_half_sweep(const Geom& G, const TbRegion& R, int c, int s,
+                                              const T* __restrict__ Js, const T* __restrict__ bs,
+                                              T* xs) {
+  const int ncell = G.ncell(), half = G.half(), hx2 = G.nx >> 1;
+  const int vx0 = R.ex0 == 0 ? 0 : R.ex0 + s, vx1 = R.ex1 == G.nx ? G.nx : R.ex1 - s;
+  const int vy0 = R.ey0 == 0 ? 0 : R.ey0 + s, vy1 = R.ey1 == G.ny ? G.ny : R.ey1 - s;
+  const int items = (vy1 - vy0) * R.hEX;
+  auto nb = [&](int ii, int jj, T& vp, T& vc) {
+    vp = xs[R.at(0, ii, jj)];
+    vc = xs[R.at(1, ii, jj)];
+  };
+  for (int e = threadIdx.x; e < items; e += blockDim.x) {
+    const int r = e / R.hEX, m = e - r * R.hEX;
+    const int j = vy0 + r;
+    const int i = R.ex0 + 2 * m + ((c + j) & 1);
+    if (i < vx0 || i >= vx1) continue;
+    const int cs = c * half + j * hx2 + (i >> 1);
+    T xp, xc;
+    gs_point<T>(i, j, G.nx, G.ny, ncell, Js + cs, bs[cs], bs[ncell + cs], nb, xp, xc);
+    xs[R.at(0, i, j)] = xp;
+    xs[R.at(1, i, j)] = xc;
+  }
+}
+
+// Copy the tile's interior unknowns back to the sample's global planes.
+template <typename T>
+__device__ __forceinline__ void tb_store_interior(const Geom& G, const TbRegion& R,
+                                                  const T* xs, T* __restrict__ xg) {
+  const int ncell = G.ncell(), half = G.half(), hx2 = G.nx >> 1;
+  const int hw = (R.i1 - R.i0) >> 1, rows = R.j1 - R.j0;
+  const int items = 2 * rows * hw;
+  for (int e = threadIdx.x; e < items; e += blockDim.x) {
+    const int c = e / (rows * hw);
+    const int rr = e - c * rows * hw;
+    const int r = rr / hw, m = rr - r * hw;
+    const int j = R.j0 + r;
+    const int i = R.i0 + 2 * m + ((c + j) & 1);
+    const int cs = c * half + j * hx2 + (i >> 1);
+    xg[cs] = xs[R.at(0, i, j)];
+    xg[ncell + cs] = xs[R.at(1, i, j)];
+  }
+}
+
+// Down leg of level G: nu1 red-black sweeps on (J, b, x) starting from
+// xin, the result to xout, then the finite-volume restriction of the
+// residual to level Gc (b_c scaled by the coarse Dinv, x_c = 0), as
+// restrict_cell. nu1 >= 1; the tile's halo is 2 nu1 + 1. Grid (tiles, B),
+// kTbBlock threads.
+template <typename T>
+__global__ void __launch_bounds__(kTbBlock)
+k_tb_down(unsigned long long* ctr, Geom G, Geom Gc, int B, const int* __restrict__ active,
+          TbTile t, int nu1, const T* __restrict__ J, const T* __restrict__ bvec,
+          const T* __restrict__ xin, T* __restrict__ xout, const T* __restrict__ Jc,
+          T* __restrict__ bc, T* __restrict__ xc) {
+  HENRY_COUNT_LAUNCH(ctr);
+  extern __shared__ __align__(16) unsigned char tb_sh[];
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  T* xs = (T*)tb_sh;
+  const TbRegion R(G, t, blockIdx.x);
+  const int ncell = G.ncell(), half = G.half(), hx2 = G.nx >> 1;
+  const T* Js = J + (int64_t)b * kJP * ncell;
+  const T* bs = bvec + (int64_t)b * 2 * ncell;
+  const T* xg = xin + (int64_t)b * 2 * ncell;
+  {
+    const int items = 2 * R.EY * R.hEX;
+    for (int e = threadIdx.x; e < items; e += blockDim.x) {
+      const int c = e / (R.EY * R.hEX);
+      const int rr = e - c * R.EY * R.hEX;
+      const int r = rr / R.hEX, m = rr - r * R.hEX;
+      const int j = R.ey0 + r;
+      const int cs = c * half + j * hx2 + (R.ex0 >> 1) + m;
+      xs[(c * R.EY + r) * R.hEX + m] = xg[cs];
+      xs[((2 + c) * R.EY + r) * R.hEX + m] = xg[ncell + cs];
+    }
+  }
+  __syncthreads();
+  for (int s = 1; s <= 2 * nu1; ++s) {
+    tb_half_sweep<T>(G, R, (s - 1) & 1, s, Js, bs, xs);
+    __syncthreads();
+  }
+  tb_store_interior<T>(G, R, xs, xout + (int64_t)b * 2 * ncell);
+  // restriction: the coarse cells whose children are this tile's interior;
+  // after a black half-sweep only the red children carry a residual
+  const int ncc = Gc.ncell();
+  const int cw = (R.i1 - R.i0) >> 1, ch = (R.j1 - R.j0) >> 1;
+  const T* Jcs = Jc + (int64_t)b * kJP * ncc;
+  T* bcs = bc + (int64_t)b * 2 * ncc;
+  T* xcs = xc + (int64_t)b * 2 * ncc;
+  auto nb = [&](int ii, int jj, T& vp, T& vc) {
+    vp = xs[R.at(0, ii, jj)];
+    vc = xs[R.at(1, ii, jj)];
+  };
+  for (int e = threadIdx.x; e < cw * ch; e += blockDim.x) {
+    const int rj = e / cw;
+    const int I = (R.i0 >> 1) + (e - rj * cw), Jr = (R.j0 >> 1) + rj;
+    T sp = 0, sc = 0;
+#pragma unroll
+    for (int c4 = 0; c4 < 4; ++c4) {
+      if (c4 == 1 || c4 == 2) continue;
+      const int i = 2 * I + (c4 & 1), j = 2 * Jr + (c4 >> 1);
+      const int cs = cs_pos(i, j, G.nx, half);
+      T rp, rc;
+      resid_point<T>(i, j, G.nx, G.ny, ncell, Js + cs, bs[cs], bs[ncell + cs], xs[R.at(0, i, j)],
+                     xs[R.at(1, i, j)], nb, rp, rc);
+      sp += rp;
+      sc += rc;
+    }
+    const int csc = cs_pos(I, Jr, Gc.nx, Gc.half());
+    const T* d = Jcs + csc;
+    bcs[csc] = d[0] * sp + d[ncc] * sc;
+    bcs[ncc + csc] = d[2 * ncc] * sp + d[3 * ncc] * sc;
+    xcs[csc] = (T)0;
+    xcs[ncc + csc] = (T)0;
+  }
+}
+
+// Up leg of level G: xin + P x_c on the black cells (the red half-sweep
+// that follows rewrites every red value without reading it), then nu2
+// red-black sweeps, the result to xout. nu2 >= 1; the tile's halo is
+// 2 nu2. Grid (tiles, B), kTbBlock threads.
+template <typename T>
+__global__ void __launch_bounds__(kTbBlock)
+k_tb_up(unsigned long long* ctr, Geom Gc, Geom G, int B, const int* __restrict__ active,
+        TbTile t, int nu2, const T* __restrict__ xc, const T* __restrict__ J,
+        const T* __restrict__ bvec, const T* __restrict__ xin, T* __restrict__ xout) {
+  HENRY_COUNT_LAUNCH(ctr);
+  extern __shared__ __align__(16) unsigned char tb_sh[];
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  T* xs = (T*)tb_sh;
+  const TbRegion R(G, t, blockIdx.x);
+  const int ncell = G.ncell(), half = G.half(), hx2 = G.nx >> 1;
+  const T* Js = J + (int64_t)b * kJP * ncell;
+  const T* bs = bvec + (int64_t)b * 2 * ncell;
+  const T* xg = xin + (int64_t)b * 2 * ncell;
+  const T* xcs = xc + (int64_t)b * 2 * Gc.ncell();
+  {
+    const int items = 2 * R.EY * R.hEX;
+    for (int e = threadIdx.x; e < items; e += blockDim.x) {
+      const int c = e / (R.EY * R.hEX);
+      const int rr = e - c * R.EY * R.hEX;
+      const int r = rr / R.hEX, m = rr - r * R.hEX;
+      const int j = R.ey0 + r;
+      const int cs = c * half + j * hx2 + (R.ex0 >> 1) + m;
+      T xp = xg[cs], xv = xg[ncell + cs];
+      if (c == 1) {
+        const int i = R.ex0 + 2 * m + ((1 + j) & 1);
+        T vp, vc;
+        prolong_value<T>(Gc, i, j, xcs, vp, vc);
+        xp += vp;
+        xv += vc;
+      }
+      xs[(c * R.EY + r) * R.hEX + m] = xp;
+      xs[((2 + c) * R.EY + r) * R.hEX + m] = xv;
+    }
+  }
+  __syncthreads();
+  for (int s = 1; s <= 2 * nu2; ++s) {
+    tb_half_sweep<T>(G, R, (s - 1) & 1, s, Js, bs, xs);
+    __syncthreads();
+  }
+  tb_store_interior<T>(G, R, xs, xout + (int64_t)b * 2 * ncell);
+}
+
+}  // namespace henry

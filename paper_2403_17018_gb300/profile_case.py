@@ -34,6 +34,8 @@ def main(argv=None):
     ap.add_argument("--small-cells", type=int, default=512,
                     help="largest multigrid level (cells per sample) run by the shared-memory "
                          "V-cycle kernel; 0 disables it")
+    ap.add_argument("--tb-cells", type=int, default=0,
+                    help="largest batched multigrid level run with temporally blocked legs")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--loop", choices=["graph", "host"], default="graph",
                     help="host: plain launches with a host convergence check (visible to ncu "
@@ -52,14 +54,22 @@ def main(argv=None):
     k = max(1, a.steps // f)
     cfg = hb.default_config(nlevels=a.level + 1, precision=prec, vcycles=a.vcycles,
                             nu1=a.nu[0], nu2=a.nu[1], mg_small_cells=a.small_cells,
-                            jac_lag=a.jac_lag, nt0=k, T=1800.0 * k,
+                            jac_lag=a.jac_lag, mg_tb_cells=a.tb_cells, nt0=k, T=1800.0 * k,
                             loop_mode=hb.LOOP_HOST if a.loop == "host" else hb.LOOP_GRAPH)
     ctx = hb.Context(cfg)
     xi = torch.from_numpy(xi_batch(a.level, 0, a.batch)).cuda()
     out = ctx.solve(a.level, xi, want_iters=True)
     torch.cuda.synchronize()
+    # the whole solve once more, timed on the device (the first one built
+    # the workspaces and graphs)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    ctx.solve(a.level, xi)
+    ev[1].record()
+    torch.cuda.synchronize()
     res = {"level": a.level, "batch": a.batch, "steps": ctx.level_info(a.level).nt,
-           "full_steps": nt_full, "precision": a.precision,
+           "full_steps": nt_full, "precision": a.precision, "tb_cells": a.tb_cells,
+           "solve_ms": ev[0].elapsed_time(ev[1]),
            "iters": out["iters"].float().mean().item(),
            "status_bad": int((out["status"] != 0).sum().item())}
     # replays of the finest-level kernels, each inside an NVTX range named
