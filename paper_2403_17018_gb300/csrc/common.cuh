@@ -85,6 +85,40 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
   return true;
 }
 
+// Stage the runs that runs(f) enumerates as f(destination in shared memory,
+// source in global memory, bytes; every size a multiple of 4) with the
+// whole block: one thread issues a TMA bulk copy for each 16-byte aligned
+// run, all threads copy the others with plain loads; bar is an mbarrier in
+// shared memory. Returns true once everything has landed. When a copy does
+// not land within the bounded wait, sets kStatusStall in status[b], gives
+// the copies in flight one more bounded wait and returns false (uniformly
+// over the block: the caller returns).
+template <typename Runs>
+__device__ __forceinline__ bool stage_runs(uint64_t* bar, Runs runs, int* status, int b) {
+  unsigned tx = 0;
+  runs([&](void* d, const void* src, unsigned bytes) { tx += bulk_ok(d, src, bytes) ? bytes : 0u; });
+  if (threadIdx.x == 0 && tx > 0) {
+    mbar_init(bar, 1);
+    mbar_arrive_expect_tx(bar, tx);
+    runs([&](void* d, const void* src, unsigned bytes) {
+      if (bulk_ok(d, src, bytes)) bulk_g2s(d, src, bytes, bar);
+    });
+  }
+  runs([&](void* d, const void* src, unsigned bytes) {
+    if (bulk_ok(d, src, bytes)) return;
+    uint32_t* dw = (uint32_t*)d;
+    const uint32_t* sw = (const uint32_t*)src;
+    for (unsigned e = threadIdx.x; e < bytes / 4; e += blockDim.x) dw[e] = sw[e];
+  });
+  __syncthreads();              // the barrier is initialised before anyone waits on it
+  if (tx > 0 && !__syncthreads_and(mbar_wait_bounded(bar, 0))) {
+    if (threadIdx.x == 0) status[b] |= kStatusStall;
+    mbar_wait_bounded(bar, 0);
+    return false;
+  }
+  return true;
+}
+
 // Block sum of a double, result valid in thread 0. Fixed order.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
 #pragma unroll

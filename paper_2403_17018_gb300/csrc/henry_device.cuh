@@ -54,15 +54,23 @@ struct Geom {
 constexpr int kTbBlock = 512;
 constexpr int kTbTileX = 64, kTbTileY = 32;   // interior cells of a tile, at most
 
+constexpr size_t kMaxSmemOptin = 232448;        // 227 KB per block
+
 struct TbTile {
   int TX, TY;    // interior cells per tile (even)
   int ntx, nty;  // tiles per sample
   int H;         // halo rows (the halo columns are H rounded up to even)
   int EX, EY;    // largest extended tile, for the shared-memory size
+  int staged;    // 1: one tile per sample whose operator planes, right-hand
+                 // side and unknowns all fit in shared memory
+  size_t smem;   // dynamic shared memory of the launch
 };
 
-// Tiles of at most tx x ty cells (both even) with a halo of 2 nu + extra.
-inline TbTile make_tb_tile(const Geom& G, int nu, int extra, int tx, int ty) {
+// Tiles of at most tx x ty cells (both even) with a halo of 2 nu + extra;
+// nplanes operator planes (from plane 4) are staged when the whole sample
+// is one tile and fits.
+inline TbTile make_tb_tile(const Geom& G, int nu, int extra, int tx, int ty, int nplanes,
+                           size_t tsize) {
   TbTile t;
   t.TX = tx < G.nx ? tx : G.nx;
   t.TY = ty < G.ny ? ty : G.ny;
@@ -72,11 +80,10 @@ inline TbTile make_tb_tile(const Geom& G, int nu, int extra, int tx, int ty) {
   const int hx = (t.H + 1) & ~1;
   t.EX = t.TX + 2 * hx < G.nx ? t.TX + 2 * hx : G.nx;
   t.EY = t.TY + 2 * t.H < G.ny ? t.TY + 2 * t.H : G.ny;
+  const size_t staged = 16 + (size_t)(nplanes + 4) * G.ncell() * tsize;
+  t.staged = t.ntx == 1 && t.nty == 1 && staged <= kMaxSmemOptin;
+  t.smem = t.staged ? staged : (size_t)2 * t.EX * t.EY * tsize;
   return t;
-}
-
-inline size_t tb_smem_bytes(const TbTile& t, size_t tsize) {
-  return (size_t)2 * t.EX * t.EY * tsize;
 }
 
 // Colour-split position of cell (i, j) inside one plane: red cells

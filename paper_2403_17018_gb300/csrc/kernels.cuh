@@ -845,39 +845,41 @@ k_coarse_inv(unsigned long long* ctr, Geom G, int B, const int* __restrict__ act
 // operations in the same order (their results are bitwise equal). Each
 // product is subtracted on its own so that it compiles to one FMA (the FP64
 // form of the smoother is bound by GB300's FP64 pipe).
-template <typename T, typename NB>
+template <typename T, int P0 = 0, typename NB>
 __device__ __forceinline__ void gs_point(int i, int j, int nx, int ny, int ncell,
                                          const T* __restrict__ Jb, T bp, T bc, NB nb, T& xp,
                                          T& xc) {
+  // Jb points at plane P0 (a copy that starts at plane P0 > 0, e.g. in
+  // shared memory); plane q is at (q - P0) * ncell
   T rp = bp, rc = bc;
   T vp, vc;
   if (i > 0) {
     nb(i - 1, j, vp, vc);
-    rp -= Jb[4 * ncell] * vp;
-    rp -= Jb[5 * ncell] * vc;
-    rc -= Jb[6 * ncell] * vp;
-    rc -= Jb[7 * ncell] * vc;
+    rp -= Jb[(4 - P0) * ncell] * vp;
+    rp -= Jb[(5 - P0) * ncell] * vc;
+    rc -= Jb[(6 - P0) * ncell] * vp;
+    rc -= Jb[(7 - P0) * ncell] * vc;
   }
   if (i < nx - 1) {
     nb(i + 1, j, vp, vc);
-    rp -= Jb[8 * ncell] * vp;
-    rp -= Jb[9 * ncell] * vc;
-    rc -= Jb[10 * ncell] * vp;
-    rc -= Jb[11 * ncell] * vc;
+    rp -= Jb[(8 - P0) * ncell] * vp;
+    rp -= Jb[(9 - P0) * ncell] * vc;
+    rc -= Jb[(10 - P0) * ncell] * vp;
+    rc -= Jb[(11 - P0) * ncell] * vc;
   }
   if (j > 0) {
     nb(i, j - 1, vp, vc);
-    rp -= Jb[12 * ncell] * vp;
-    rp -= Jb[13 * ncell] * vc;
-    rc -= Jb[14 * ncell] * vp;
-    rc -= Jb[15 * ncell] * vc;
+    rp -= Jb[(12 - P0) * ncell] * vp;
+    rp -= Jb[(13 - P0) * ncell] * vc;
+    rc -= Jb[(14 - P0) * ncell] * vp;
+    rc -= Jb[(15 - P0) * ncell] * vc;
   }
   if (j < ny - 1) {
     nb(i, j + 1, vp, vc);
-    rp -= Jb[16 * ncell] * vp;
-    rp -= Jb[17 * ncell] * vc;
-    rc -= Jb[18 * ncell] * vp;
-    rc -= Jb[19 * ncell] * vc;
+    rp -= Jb[(16 - P0) * ncell] * vp;
+    rp -= Jb[(17 - P0) * ncell] * vc;
+    rc -= Jb[(18 - P0) * ncell] * vp;
+    rc -= Jb[(19 - P0) * ncell] * vc;
   }
   xp = rp;
   xc = rc;
@@ -886,7 +888,7 @@ __device__ __forceinline__ void gs_point(int i, int j, int nx, int ny, int ncell
 // Unscaled residual b - A x at cell (i, j) from the row-scaled system:
 // D_P (bt_P - x_P - sum_Q At_PQ x_Q); Jc, nb as in gs_point, (x0p, x0c) the
 // cell's own unknowns.
-template <typename T, typename NB>
+template <typename T, int P0 = 0, typename NB>
 __device__ __forceinline__ void resid_point(int i, int j, int nx, int ny, int ncell,
                                             const T* __restrict__ Jc, T bp, T bc, T x0p, T x0c,
                                             NB nb, T& rp, T& rc) {
@@ -895,35 +897,35 @@ __device__ __forceinline__ void resid_point(int i, int j, int nx, int ny, int nc
   T vp, vc;
   if (i > 0) {
     nb(i - 1, j, vp, vc);
-    rp -= Jc[4 * ncell] * vp;
-    rp -= Jc[5 * ncell] * vc;
-    rc -= Jc[6 * ncell] * vp;
-    rc -= Jc[7 * ncell] * vc;
+    rp -= Jc[(4 - P0) * ncell] * vp;
+    rp -= Jc[(5 - P0) * ncell] * vc;
+    rc -= Jc[(6 - P0) * ncell] * vp;
+    rc -= Jc[(7 - P0) * ncell] * vc;
   }
   if (i < nx - 1) {
     nb(i + 1, j, vp, vc);
-    rp -= Jc[8 * ncell] * vp;
-    rp -= Jc[9 * ncell] * vc;
-    rc -= Jc[10 * ncell] * vp;
-    rc -= Jc[11 * ncell] * vc;
+    rp -= Jc[(8 - P0) * ncell] * vp;
+    rp -= Jc[(9 - P0) * ncell] * vc;
+    rc -= Jc[(10 - P0) * ncell] * vp;
+    rc -= Jc[(11 - P0) * ncell] * vc;
   }
   if (j > 0) {
     nb(i, j - 1, vp, vc);
-    rp -= Jc[12 * ncell] * vp;
-    rp -= Jc[13 * ncell] * vc;
-    rc -= Jc[14 * ncell] * vp;
-    rc -= Jc[15 * ncell] * vc;
+    rp -= Jc[(12 - P0) * ncell] * vp;
+    rp -= Jc[(13 - P0) * ncell] * vc;
+    rc -= Jc[(14 - P0) * ncell] * vp;
+    rc -= Jc[(15 - P0) * ncell] * vc;
   }
   if (j < ny - 1) {
     nb(i, j + 1, vp, vc);
-    rp -= Jc[16 * ncell] * vp;
-    rp -= Jc[17 * ncell] * vc;
-    rc -= Jc[18 * ncell] * vp;
-    rc -= Jc[19 * ncell] * vc;
+    rp -= Jc[(16 - P0) * ncell] * vp;
+    rp -= Jc[(17 - P0) * ncell] * vc;
+    rc -= Jc[(18 - P0) * ncell] * vp;
+    rc -= Jc[(19 - P0) * ncell] * vc;
   }
   const T sp = rp, sc = rc;
-  rp = Jc[20 * ncell] * sp + Jc[21 * ncell] * sc;
-  rc = Jc[22 * ncell] * sp + Jc[23 * ncell] * sc;
+  rp = Jc[(20 - P0) * ncell] * sp + Jc[(21 - P0) * ncell] * sc;
+  rc = Jc[(22 - P0) * ncell] * sp + Jc[(23 - P0) * ncell] * sc;
 }
 
 // Reader of a sample's unknowns in the colour-split layout.
@@ -939,8 +941,9 @@ struct CsReader {
 };
 
 // Point-block Gauss-Seidel update of the cell at colour-split position
-// `pos` of colour `colour` on one sample's arrays (colour-split layout).
-template <typename T>
+// `pos` of colour `colour` on one sample's arrays (colour-split layout; J
+// from plane P0 on).
+template <typename T, int P0 = 0>
 __device__ __forceinline__ void smooth_cell(const Geom& G, int colour, int pos,
                                             const T* __restrict__ J, const T* __restrict__ b,
                                             T* __restrict__ x) {
@@ -950,7 +953,7 @@ __device__ __forceinline__ void smooth_cell(const Geom& G, int colour, int pos,
   const int own = colour * half + pos;
   const T* xo = x + (1 - colour) * half;   // the other colour's half of each plane
   T xp, xc;
-  gs_point<T>(i, j, G.nx, G.ny, ncell, J + own, b[own], b[ncell + own],
+  gs_point<T, P0>(i, j, G.nx, G.ny, ncell, J + own, b[own], b[ncell + own],
               [&](int ii, int jj, T& vp, T& vc) {
                 const int q = jj * hx2 + (ii >> 1);
                 vp = xo[q];
@@ -961,14 +964,15 @@ __device__ __forceinline__ void smooth_cell(const Geom& G, int colour, int pos,
   x[ncell + own] = xc;
 }
 
-// Unscaled residual b - A x at cell (i, j) (colour-split layout).
-template <typename T>
+// Unscaled residual b - A x at cell (i, j) (colour-split layout; Jb from
+// plane P0 on).
+template <typename T, int P0 = 0>
 __device__ __forceinline__ void residual_cell(const Geom& G, int i, int j, const T* __restrict__ Jb,
                                               const T* __restrict__ b, const T* __restrict__ x,
                                               T& rp, T& rc) {
   const int ncell = G.ncell(), half = G.half(), nx = G.nx;
   const int cs = cs_pos(i, j, nx, half);
-  resid_point<T>(i, j, nx, G.ny, ncell, Jb + cs, b[cs], b[ncell + cs], x[cs], x[ncell + cs],
+  resid_point<T, P0>(i, j, nx, G.ny, ncell, Jb + cs, b[cs], b[ncell + cs], x[cs], x[ncell + cs],
                  CsReader<T>{x, ncell, nx >> 1, half, nx}, rp, rc);
 }
 
@@ -978,7 +982,7 @@ __device__ __forceinline__ void residual_cell(const Geom& G, int i, int j, const
 // level k was a black half-sweep, which leaves the residual of every black
 // cell zero up to rounding, so only the two red children (i + j even) are
 // evaluated.
-template <typename T>
+template <typename T, int P0 = 0>
 __device__ __forceinline__ void restrict_cell(const Geom& Gf, const Geom& Gc, int cell,
                                               const T* __restrict__ Jf, const T* __restrict__ bf,
                                               const T* __restrict__ xf, const T* __restrict__ Jc,
@@ -992,7 +996,7 @@ __device__ __forceinline__ void restrict_cell(const Geom& Gf, const Geom& Gc, in
     if (red_only && (c4 == 1 || c4 == 2)) continue;
     const int i = 2 * I + (c4 & 1), j = 2 * J + (c4 >> 1);
     T rp, rc;
-    residual_cell(Gf, i, j, Jf, bf, xf, rp, rc);
+    residual_cell<T, P0>(Gf, i, j, Jf, bf, xf, rp, rc);
     sp += rp;
     sc += rc;
   }
@@ -1206,30 +1210,8 @@ k_vcycle_small(unsigned long long* ctr, SmallMG<T> M, int B, const int* __restri
     f(A, AinvT + (int64_t)bs * kMaxCoarseUnknowns * kMaxCoarseUnknowns,
       (unsigned)(n * n * sizeof(T)));
   };
-  unsigned tx = 0;
-  runs([&](void* d, const void* src, unsigned bytes) { tx += bulk_ok(d, src, bytes) ? bytes : 0u; });
-  if (threadIdx.x == 0 && tx > 0) {
-    mbar_init(bar, 1);
-    mbar_arrive_expect_tx(bar, tx);
-    runs([&](void* d, const void* src, unsigned bytes) {
-      if (bulk_ok(d, src, bytes)) bulk_g2s(d, src, bytes, bar);
-    });
-  }
-  runs([&](void* d, const void* src, unsigned bytes) {
-    if (bulk_ok(d, src, bytes))
-      return;
-    uint32_t* dw = (uint32_t*)d;
-    const uint32_t* sw = (const uint32_t*)src;
-    for (unsigned e = threadIdx.x; e < bytes / 4; e += blockDim.x) dw[e] = sw[e];
-  });
-  __syncthreads();              // the barrier is initialised before anyone waits on it
-  if (tx > 0 && !__syncthreads_and(mbar_wait_bounded(bar, 0))) {
-    // a copy did not land in time: flag the sample, give copies still in
-    // flight one more bounded wait, and leave x_ks untouched
-    if (threadIdx.x == 0) status[bs] |= kStatusStall;
-    mbar_wait_bounded(bar, 0);
-    return;
-  }
+  // a copy that did not land in time leaves x_ks untouched (sample flagged)
+  if (!stage_runs(bar, runs, status, bs)) return;
   for (int cyc = 0; cyc < ncycles; ++cyc) {
     for (int k = ks; k >= 1; --k) {
       const Geom& G = M.g[k];

@@ -98,8 +98,8 @@ Solver::Solver(const henry_config& cfg, int nx, int ny, int nt) : cfg_(cfg), nt_
     const bool fused = (int)k <= ks_ || ((int)k <= kc_ && kc_ > ks_);
     if (fused || cfg_.nu1 < 1 || cfg_.nu2 < 1 || geoms_[k].ncell() > cfg_.mg_tb_cells) continue;
     tb_[k] = 1;
-    tbd_[k] = make_tb_tile(geoms_[k], cfg_.nu1, 1, kTbTileX, kTbTileY);
-    tbu_[k] = make_tb_tile(geoms_[k], cfg_.nu2, 0, kTbTileX, kTbTileY);
+    tbd_[k] = make_tb_tile(geoms_[k], cfg_.nu1, 1, kTbTileX, kTbTileY, 20, tsize_);
+    tbu_[k] = make_tb_tile(geoms_[k], cfg_.nu2, 0, kTbTileX, kTbTileY, 16, tsize_);
   }
 }
 
@@ -179,10 +179,14 @@ int Solver::ensure(int B, cudaStream_t s) {
   for (size_t k = 1; k < levels_.size(); ++k) {
     if (!tb_[k]) continue;
     const bool f32 = tsize_ == sizeof(float);
-    CK(raise_smem_limit(f32 ? (const void*)k_tb_down<float> : (const void*)k_tb_down<double>,
-                        tb_smem_bytes(tbd_[k], tsize_)));
-    CK(raise_smem_limit(f32 ? (const void*)k_tb_up<float> : (const void*)k_tb_up<double>,
-                        tb_smem_bytes(tbu_[k], tsize_)));
+    const TbTile& d = tbd_[k];
+    const TbTile& u = tbu_[k];
+    const void* fd = f32 ? (d.staged ? (const void*)k_tb_down<float, true> : (const void*)k_tb_down<float, false>)
+                         : (d.staged ? (const void*)k_tb_down<double, true> : (const void*)k_tb_down<double, false>);
+    const void* fu = f32 ? (u.staged ? (const void*)k_tb_up<float, true> : (const void*)k_tb_up<float, false>)
+                         : (u.staged ? (const void*)k_tb_up<double, true> : (const void*)k_tb_up<double, false>);
+    CK(raise_smem_limit(fd, d.smem));
+    CK(raise_smem_limit(fu, u.smem));
   }
   if (B <= cap_) return HENRY_OK;
   unsigned long long count = 0;
@@ -358,13 +362,15 @@ void Solver::enqueue_vcycle(int k, int B, cudaStream_t s) {
     // levels, then prolongation + post-sweeps (x2 -> x)
     const TbTile& td = tbd_[k];
     const TbTile& tu = tbu_[k];
-    k_tb_down<T><<<dim3(td.ntx * td.nty, B), kTbBlock, tb_smem_bytes(td, sizeof(T)), s>>>(
+    auto down = td.staged ? k_tb_down<T, true> : k_tb_down<T, false>;
+    auto up = tu.staged ? k_tb_up<T, true> : k_tb_up<T, false>;
+    down<<<dim3(td.ntx * td.nty, B), kTbBlock, td.smem, s>>>(
         counter_, G, C.g, B, active_, td, cfg_.nu1, (const T*)L.J, (const T*)L.b,
-        (const T*)L.x, (T*)L.x2, (const T*)C.J, (T*)C.b, (T*)C.x);
+        (const T*)L.x, (T*)L.x2, (const T*)C.J, (T*)C.b, (T*)C.x, status_w_);
     enqueue_vcycle<T>(k - 1, B, s);
-    k_tb_up<T><<<dim3(tu.ntx * tu.nty, B), kTbBlock, tb_smem_bytes(tu, sizeof(T)), s>>>(
+    up<<<dim3(tu.ntx * tu.nty, B), kTbBlock, tu.smem, s>>>(
         counter_, C.g, G, B, active_, tu, cfg_.nu2, (const T*)C.x, (const T*)L.J, (const T*)L.b,
-        (const T*)L.x2, (T*)L.x);
+        (const T*)L.x2, (T*)L.x, status_w_);
     return;
   }
   const int gs = grid1((int64_t)B * G.half());

@@ -58,7 +58,7 @@ struct TbRegion {
 // One half-sweep of colour c over the cells of the tile that are trusted
 // after s half-sweeps (the extended region shrunk by s on every side that
 // is not a domain boundary).
-template <typename T>
+template <typename T, int P0>
 __device__ __forceinline__ void tb_half_sweep(const Geom& G, const TbRegion& R, int c, int s,
                                               const T* __restrict__ Js, const T* __restrict__ bs,
                                               T* xs) {
@@ -77,7 +77,7 @@ __device__ __forceinline__ void tb_half_sweep(const Geom& G, const TbRegion& R, 
     if (i < vx0 || i >= vx1) continue;
     const int cs = c * half + j * hx2 + (i >> 1);
     T xp, xc;
-    gs_point<T>(i, j, G.nx, G.ny, ncell, Js + cs, bs[cs], bs[ncell + cs], nb, xp, xc);
+    gs_point<T, P0>(i, j, G.nx, G.ny, ncell, Js + cs, bs[cs], bs[ncell + cs], nb, xp, xc);
     xs[R.at(0, i, j)] = xp;
     xs[R.at(1, i, j)] = xc;
   }
@@ -102,52 +102,97 @@ __device__ __forceinline__ void tb_store_interior(const Geom& G, const TbRegion&
   }
 }
 
+// Load the extended tile's unknowns from the sample's global planes
+// (consecutive threads read consecutive words of one colour's row run);
+// with PROLONG, black cells get x_f + P x_c (the red half-sweep that follows
+// rewrites every red value without reading it).
+template <typename T, bool PROLONG>
+__device__ __forceinline__ void tb_load(const Geom& G, const TbRegion& R, const T* __restrict__ xg,
+                                        const Geom& Gc, const T* __restrict__ xcs, T* xs) {
+  const int ncell = G.ncell(), half = G.half(), hx2 = G.nx >> 1;
+  const int items = 2 * R.EY * R.hEX;
+  for (int e = threadIdx.x; e < items; e += blockDim.x) {
+    const int c = e / (R.EY * R.hEX);
+    const int rr = e - c * R.EY * R.hEX;
+    const int r = rr / R.hEX, m = rr - r * R.hEX;
+    const int j = R.ey0 + r;
+    const int cs = c * half + j * hx2 + (R.ex0 >> 1) + m;
+    T xp = xg[cs], xv = xg[ncell + cs];
+    if (PROLONG && c == 1) {
+      const int i = R.ex0 + 2 * m + ((1 + j) & 1);
+      T vp, vc;
+      prolong_value<T>(Gc, i, j, xcs, vp, vc);
+      xp += vp;
+      xv += vc;
+    }
+    xs[(c * R.EY + r) * R.hEX + m] = xp;
+    xs[((2 + c) * R.EY + r) * R.hEX + m] = xv;
+  }
+}
+
 // Down leg of level G: nu1 red-black sweeps on (J, b, x) starting from
 // xin, the result to xout, then the finite-volume restriction of the
 // residual to level Gc (b_c scaled by the coarse Dinv, x_c = 0), as
 // restrict_cell. nu1 >= 1; the tile's halo is 2 nu1 + 1. Grid (tiles, B),
-// kTbBlock threads.
-template <typename T>
+// kTbBlock threads. STAGED (one tile per sample): operator planes 4..23,
+// b and x are first copied to shared memory by TMA bulk copies, in the
+// sample's global colour-split layout, and every operation runs out of
+// shared memory with the per-cell routines of the per-operation kernels; a
+// copy that does not land within the bounded wait flags status[b]
+// (kStatusStall) and leaves the sample.
+template <typename T, bool STAGED>
 __global__ void __launch_bounds__(kTbBlock)
 k_tb_down(unsigned long long* ctr, Geom G, Geom Gc, int B, const int* __restrict__ active,
           TbTile t, int nu1, const T* __restrict__ J, const T* __restrict__ bvec,
           const T* __restrict__ xin, T* __restrict__ xout, const T* __restrict__ Jc,
-          T* __restrict__ bc, T* __restrict__ xc) {
+          T* __restrict__ bc, T* __restrict__ xc, int* __restrict__ status) {
   HENRY_COUNT_LAUNCH(ctr);
   extern __shared__ __align__(16) unsigned char tb_sh[];
   const int b = blockIdx.y;
   if (!active[b]) return;
-  T* xs = (T*)tb_sh;
-  const TbRegion R(G, t, blockIdx.x);
-  const int ncell = G.ncell(), half = G.half(), hx2 = G.nx >> 1;
+  const int ncell = G.ncell(), half = G.half(), ncc = Gc.ncell();
   const T* Js = J + (int64_t)b * kJP * ncell;
   const T* bs = bvec + (int64_t)b * 2 * ncell;
   const T* xg = xin + (int64_t)b * 2 * ncell;
-  {
-    const int items = 2 * R.EY * R.hEX;
-    for (int e = threadIdx.x; e < items; e += blockDim.x) {
-      const int c = e / (R.EY * R.hEX);
-      const int rr = e - c * R.EY * R.hEX;
-      const int r = rr / R.hEX, m = rr - r * R.hEX;
-      const int j = R.ey0 + r;
-      const int cs = c * half + j * hx2 + (R.ex0 >> 1) + m;
-      xs[(c * R.EY + r) * R.hEX + m] = xg[cs];
-      xs[((2 + c) * R.EY + r) * R.hEX + m] = xg[ncell + cs];
-    }
-  }
-  __syncthreads();
-  for (int s = 1; s <= 2 * nu1; ++s) {
-    tb_half_sweep<T>(G, R, (s - 1) & 1, s, Js, bs, xs);
-    __syncthreads();
-  }
-  tb_store_interior<T>(G, R, xs, xout + (int64_t)b * 2 * ncell);
-  // restriction: the coarse cells whose children are this tile's interior;
-  // after a black half-sweep only the red children carry a residual
-  const int ncc = Gc.ncell();
-  const int cw = (R.i1 - R.i0) >> 1, ch = (R.j1 - R.j0) >> 1;
+  T* xo = xout + (int64_t)b * 2 * ncell;
   const T* Jcs = Jc + (int64_t)b * kJP * ncc;
   T* bcs = bc + (int64_t)b * 2 * ncc;
   T* xcs = xc + (int64_t)b * 2 * ncc;
+  if (STAGED) {
+    // the whole sample in shared memory, in its global layout: the
+    // per-cell routines of the per-operation kernels apply unchanged
+    uint64_t* bar = (uint64_t*)tb_sh;
+    T* Jst = (T*)(tb_sh + 16);           // planes 4..23
+    T* bst = Jst + 20 * ncell;
+    T* xs = bst + 2 * ncell;
+    auto runs = [&](auto&& f) {
+      f(Jst, Js + 4 * ncell, (unsigned)(20 * ncell * sizeof(T)));
+      f(bst, bs, (unsigned)(2 * ncell * sizeof(T)));
+      f(xs, xg, (unsigned)(2 * ncell * sizeof(T)));
+    };
+    if (!stage_runs(bar, runs, status, b)) return;
+    for (int s = 0; s < 2 * nu1; ++s) {
+      for (int pos = threadIdx.x; pos < half; pos += blockDim.x)
+        smooth_cell<T, 4>(G, s & 1, pos, Jst, bst, xs);
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < 2 * ncell; e += blockDim.x) xo[e] = xs[e];
+    for (int cell = threadIdx.x; cell < ncc; cell += blockDim.x)
+      restrict_cell<T, 4>(G, Gc, cell, Jst, bst, xs, Jcs, bcs, xcs, true);
+    return;
+  }
+  const TbRegion R(G, t, blockIdx.x);
+  T* xs = (T*)tb_sh;
+  tb_load<T, false>(G, R, xg, Gc, nullptr, xs);
+  __syncthreads();
+  for (int s = 1; s <= 2 * nu1; ++s) {
+    tb_half_sweep<T, 0>(G, R, (s - 1) & 1, s, Js, bs, xs);
+    __syncthreads();
+  }
+  tb_store_interior<T>(G, R, xs, xo);
+  // restriction: the coarse cells whose children are this tile's interior;
+  // after a black half-sweep only the red children carry a residual
+  const int cw = (R.i1 - R.i0) >> 1, ch = (R.j1 - R.j0) >> 1;
   auto nb = [&](int ii, int jj, T& vp, T& vc) {
     vp = xs[R.at(0, ii, jj)];
     vc = xs[R.at(1, ii, jj)];
@@ -179,49 +224,55 @@ k_tb_down(unsigned long long* ctr, Geom G, Geom Gc, int B, const int* __restrict
 // Up leg of level G: xin + P x_c on the black cells (the red half-sweep
 // that follows rewrites every red value without reading it), then nu2
 // red-black sweeps, the result to xout. nu2 >= 1; the tile's halo is
-// 2 nu2. Grid (tiles, B), kTbBlock threads.
-template <typename T>
+// 2 nu2. Grid (tiles, B), kTbBlock threads. STAGED as in k_tb_down, with
+// operator planes 4..19.
+template <typename T, bool STAGED>
 __global__ void __launch_bounds__(kTbBlock)
 k_tb_up(unsigned long long* ctr, Geom Gc, Geom G, int B, const int* __restrict__ active,
         TbTile t, int nu2, const T* __restrict__ xc, const T* __restrict__ J,
-        const T* __restrict__ bvec, const T* __restrict__ xin, T* __restrict__ xout) {
+        const T* __restrict__ bvec, const T* __restrict__ xin, T* __restrict__ xout,
+        int* __restrict__ status) {
   HENRY_COUNT_LAUNCH(ctr);
   extern __shared__ __align__(16) unsigned char tb_sh[];
   const int b = blockIdx.y;
   if (!active[b]) return;
-  T* xs = (T*)tb_sh;
-  const TbRegion R(G, t, blockIdx.x);
-  const int ncell = G.ncell(), half = G.half(), hx2 = G.nx >> 1;
+  const int ncell = G.ncell(), half = G.half();
   const T* Js = J + (int64_t)b * kJP * ncell;
   const T* bs = bvec + (int64_t)b * 2 * ncell;
   const T* xg = xin + (int64_t)b * 2 * ncell;
+  T* xo = xout + (int64_t)b * 2 * ncell;
   const T* xcs = xc + (int64_t)b * 2 * Gc.ncell();
-  {
-    const int items = 2 * R.EY * R.hEX;
-    for (int e = threadIdx.x; e < items; e += blockDim.x) {
-      const int c = e / (R.EY * R.hEX);
-      const int rr = e - c * R.EY * R.hEX;
-      const int r = rr / R.hEX, m = rr - r * R.hEX;
-      const int j = R.ey0 + r;
-      const int cs = c * half + j * hx2 + (R.ex0 >> 1) + m;
-      T xp = xg[cs], xv = xg[ncell + cs];
-      if (c == 1) {
-        const int i = R.ex0 + 2 * m + ((1 + j) & 1);
-        T vp, vc;
-        prolong_value<T>(Gc, i, j, xcs, vp, vc);
-        xp += vp;
-        xv += vc;
-      }
-      xs[(c * R.EY + r) * R.hEX + m] = xp;
-      xs[((2 + c) * R.EY + r) * R.hEX + m] = xv;
+  if (STAGED) {
+    uint64_t* bar = (uint64_t*)tb_sh;
+    T* Jst = (T*)(tb_sh + 16);           // planes 4..19
+    T* bst = Jst + 16 * ncell;
+    T* xs = bst + 2 * ncell;
+    auto runs = [&](auto&& f) {
+      f(Jst, Js + 4 * ncell, (unsigned)(16 * ncell * sizeof(T)));
+      f(bst, bs, (unsigned)(2 * ncell * sizeof(T)));
+      f(xs, xg, (unsigned)(2 * ncell * sizeof(T)));
+    };
+    if (!stage_runs(bar, runs, status, b)) return;
+    for (int pos = threadIdx.x; pos < half; pos += blockDim.x)
+      prolong_cell<T>(Gc, G, black_cell(G, pos), xcs, xs);
+    __syncthreads();
+    for (int s = 0; s < 2 * nu2; ++s) {
+      for (int pos = threadIdx.x; pos < half; pos += blockDim.x)
+        smooth_cell<T, 4>(G, s & 1, pos, Jst, bst, xs);
+      __syncthreads();
     }
+    for (int e = threadIdx.x; e < 2 * ncell; e += blockDim.x) xo[e] = xs[e];
+    return;
   }
+  const TbRegion R(G, t, blockIdx.x);
+  T* xs = (T*)tb_sh;
+  tb_load<T, true>(G, R, xg, Gc, xcs, xs);
   __syncthreads();
   for (int s = 1; s <= 2 * nu2; ++s) {
-    tb_half_sweep<T>(G, R, (s - 1) & 1, s, Js, bs, xs);
+    tb_half_sweep<T, 0>(G, R, (s - 1) & 1, s, Js, bs, xs);
     __syncthreads();
   }
-  tb_store_interior<T>(G, R, xs, xout + (int64_t)b * 2 * ncell);
+  tb_store_interior<T>(G, R, xs, xo);
 }
 
 }  // namespace henry
