@@ -260,15 +260,15 @@ class Workload:
 
 def tune_schedules(precision_name):
     """Autotuned schedule per level: V-cycles per iteration x smoothing sweeps
-    x shared-memory V-cycle threshold, then the operator reuse factor and the
-    residual tile height, each timed on one solve of the level over the whole
-    horizon. Kept in the autotuner's cache (by GPU, level, precision, batch),
+    x shared-memory V-cycle threshold, then the operator reuse factor, the
+    residual tile height and the temporally blocked legs, each timed on one
+    solve of the level over the whole horizon. Kept in the autotuner's cache (by GPU, level, precision, batch),
     so a second run on the same machine -- e.g. under a profiler -- reuses
     it; returns (schedules, seconds spent tuning)."""
     import torch
     from paper_2403_17018_gb300 import autotune as A
     A.CANDIDATES = {"vcycles": (2, 3), "nu": ((2, 2), (3, 3)), "small_cells": (0, 128, 512),
-                    "jac_lag": (0, 10, 30), "res_rows": (0, 2, 16)}
+                    "jac_lag": (0, 10, 30), "res_rows": (0, 2, 16), "tb_cells": (0, 2048)}
     t0 = time.perf_counter()
     gpu = torch.cuda.get_device_name(0)
     cache = A.load_cache()
@@ -285,7 +285,7 @@ def tune_schedules(precision_name):
 
 def sched_str(s):
     return (f"V({s['nu1']},{s['nu2']}) x{s['vcycles']} smem<={s['mg_small_cells']} "
-            f"lag={s['jac_lag']} rows={s.get('res_rows', 0)}")
+            f"lag={s['jac_lag']} rows={s.get('res_rows', 0)} tb<={s.get('mg_tb_cells', 0)}")
 
 
 def time_steps(wl, xis, K, W, barrier, flush, host=None):

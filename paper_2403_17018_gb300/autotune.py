@@ -27,7 +27,7 @@ if ROOT not in sys.path:
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuning", "schedules.json")
 CANDIDATES = {"vcycles": (1, 2, 3), "nu": ((1, 1), (2, 2), (3, 3)), "small_cells": (0, 128, 512),
-              "jac_lag": (0, 10, 30), "res_rows": (0, 2, 4, 16)}
+              "jac_lag": (0, 10, 30), "res_rows": (0, 2, 4, 16), "tb_cells": (0, 2048)}
 
 
 def _key(gpu, level, precision, batch, nx0, ny0):
@@ -77,10 +77,10 @@ def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2),
     xi = torch.from_numpy(xi_batch(level, 0, batch, n_xi=n_xi)).cuda()
     table = []
 
-    def timed(vc, n1, n2, sc, lag, split, rr=0):
+    def timed(vc, n1, n2, sc, lag, split, rr=0, tb=0):
         cfg = hb.default_config(nlevels=level + 1, precision=prec, vcycles=vc, nu1=n1, nu2=n2,
-                                mg_small_cells=sc, jac_lag=lag, res_rows=rr, nt0=k, T=tau0 * k,
-                                n_xi=n_xi, **extra)
+                                mg_small_cells=sc, jac_lag=lag, res_rows=rr, mg_tb_cells=tb,
+                                nt0=k, T=tau0 * k, n_xi=n_xi, **extra)
         ctx = hb.Context(cfg)
         sub = batch // split
         parts = [xi[i * sub:(i + 1) * sub].contiguous() for i in range(split)]
@@ -95,7 +95,8 @@ def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2),
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / reps
         row = {"vcycles": vc, "nu1": n1, "nu2": n2, "mg_small_cells": sc, "jac_lag": lag,
-               "res_rows": rr, "split": split, "solves_per_s": batch / dt, "failed": bad}
+               "res_rows": rr, "mg_tb_cells": tb, "split": split, "solves_per_s": batch / dt,
+               "failed": bad}
         table.append(row)
         if log:
             log(row)
@@ -121,6 +122,11 @@ def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2),
         if rr:
             timed(best["vcycles"], best["nu1"], best["nu2"], best["mg_small_cells"],
                   best["jac_lag"], best["split"], rr)
+    best = best_of(table)
+    for tb in CANDIDATES.get("tb_cells", (0,)):
+        if tb:
+            timed(best["vcycles"], best["nu1"], best["nu2"], best["mg_small_cells"],
+                  best["jac_lag"], best["split"], best["res_rows"], tb)
     return best_of(table), table
 
 

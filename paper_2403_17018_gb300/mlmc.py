@@ -150,7 +150,7 @@ class GpuSampler:
             else:
                 kw = cfg.as_dict()
                 kw.update({k: sc[k] for k in ("vcycles", "nu1", "nu2", "mg_small_cells", "jac_lag",
-                                              "res_rows") if k in sc})
+                                              "res_rows", "mg_tb_cells") if k in sc})
                 self.ctxs[l] = hb.Context(hb.default_config(**kw))
         self.streams = {l: torch.cuda.Stream() for l in range(cfg.nlevels)}
 
@@ -394,7 +394,7 @@ def tuned_run(levels=6, eps=1e-3, n_xi=6, precision="fp32mg", vcycles=3, tune=Tr
                 "concurrent_levels": concurrent,
                 "schedules": {l: {k: v for k, v in sc.items() if k in ("vcycles", "nu1", "nu2",
                                                                       "mg_small_cells", "jac_lag",
-                                                                      "res_rows")}
+                                                                      "res_rows", "mg_tb_cells")}
                               for l, sc in (schedules or {}).items()}})
     return res
 

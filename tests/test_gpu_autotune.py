@@ -1,6 +1,6 @@
 """The autotuner times candidate multigrid schedules on a short solve (then,
-for the winner, operator reuse factors and residual tile heights) and
-returns the fastest one that converged."""
+for the winner, operator reuse factors, residual tile heights and the
+temporally blocked legs) and returns the fastest one that converged."""
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -14,7 +14,7 @@ def test_tune_level_returns_a_converging_schedule(tmp_path):
     best, table = A.tune_level(0, 64, "fp32mg", steps=2, reps=1, splits=(1, 2))
     n = len(A.CANDIDATES["vcycles"]) * len(A.CANDIDATES["nu"]) * len(A.CANDIDATES["small_cells"])
     assert len(table) == n * 2 + len([g for g in A.CANDIDATES["jac_lag"] if g]) + len(
-        [r for r in A.CANDIDATES["res_rows"] if r])
+        [r for r in A.CANDIDATES["res_rows"] if r]) + len([t for t in A.CANDIDATES["tb_cells"] if t])
     assert {r["mg_small_cells"] for r in table} == set(A.CANDIDATES["small_cells"])
     assert best["failed"] == 0 and best["solves_per_s"] > 0
     assert best["solves_per_s"] == max(r["solves_per_s"] for r in table if r["failed"] == 0)
