@@ -51,7 +51,7 @@ struct Geom {
 };
 
 // Tiling of the temporally blocked multigrid legs (see k_tb_down, k_tb_up).
-constexpr int kTbBlock = 512;
+constexpr int kTbBlock = 1024;
 constexpr int kTbTileX = 64, kTbTileY = 32;   // interior cells of a tile, at most
 
 constexpr size_t kMaxSmemOptin = 232448;        // 227 KB per block
