@@ -454,7 +454,8 @@ def mlmc_wall_times():
     random variables, identical seeds, with FP32 multigrid and with FP64
     multigrid; schedules autotuned first (tuning time reported apart)."""
     from paper_2403_17018_gb300 import mlmc
-    cands = {"vcycles": (2, 3), "nu": ((2, 2),), "small_cells": (128, 512), "jac_lag": (0, 30)}
+    cands = {"vcycles": (2, 3), "nu": ((2, 2),), "small_cells": (128, 512), "jac_lag": (0, 30),
+             "tb_cells": (0, 2048)}
     out = {"config": "6 levels 32x16..1024x512, 6 random variables, RMSE 1e-3 on c at "
                      "(1.40,0.05), (1.65,0.25), (1.90,0.50), variance budget eps^2/2, "
                      "levels on concurrent streams"}

@@ -346,8 +346,9 @@ def tuned_schedules(levels, precision, n_xi, nx0=32, ny0=16, world=1, extra=None
     import torch
     from paper_2403_17018_gb300 import autotune as A
     A.CANDIDATES = dict(candidates or TUNE_CANDIDATES)
-    tag = "" if candidates is None else "|c" + hashlib.sha1(
-        json.dumps(candidates, sort_keys=True).encode()).hexdigest()[:8]
+    # the candidate set is part of the key: a schedule tuned over other
+    # candidates is not reused
+    tag = "|c" + hashlib.sha1(json.dumps(A.CANDIDATES, sort_keys=True).encode()).hexdigest()[:8]
     t0 = time.perf_counter()
     schedules = {}
     gpu = torch.cuda.get_device_name(0)
