@@ -388,11 +388,27 @@ int henry_sample_levels(henry_ctx* ctx, const henry_level_batch* batches, int n,
   // the chains of implicit steps: per coarse step, level l advances 2^l steps
   struct Chain { Solver* sv; int B; int steps; };
   std::vector<Chain> chains;
+  // scheduling priorities: the finest level's chain is the critical path of
+  // a coarse step (the most dependent steps, the smallest batch), so its
+  // kernels go first and the coarser levels' fill the SMs it leaves idle
+  int least = 0, greatest = 0;
+  CKR(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  int lmax = 0;
+  for (int i = 0; i < n; ++i)
+    if (batches[i].B > 0 && batches[i].level > lmax) lmax = batches[i].level;
+  auto prio = [&](int level) {
+    const int p = greatest + (lmax - level);   // greatest is the numerically lowest
+    return p > least ? least : p;
+  };
   for (int i = 0; i < n; ++i) {
     const henry_level_batch& b = batches[i];
     if (b.B == 0) continue;
     chains.push_back({get_solver(ctx, b.level, 0), b.B, 1 << b.level});
-    if (b.level > 0) chains.push_back({get_solver(ctx, b.level - 1, 1), b.B, 1 << (b.level - 1)});
+    chains.back().sv->set_priority(prio(b.level));
+    if (b.level > 0) {
+      chains.push_back({get_solver(ctx, b.level - 1, 1), b.B, 1 << (b.level - 1)});
+      chains.back().sv->set_priority(prio(b.level));
+    }
   }
   if (chains.empty()) return HENRY_OK;
   // fields and initial states (these may grow workspaces)
@@ -442,13 +458,41 @@ int henry_sample_levels(henry_ctx* ctx, const henry_level_batch* batches, int n,
       const cudaError_t e2 = cudaStreamEndCapture(cs, &gout);
       if (e == cudaSuccess) e = e2;
     }
+    // the step nodes of the top graph: each kernel's first argument is the
+    // launch counter of the solver that launched it
+    if (e == cudaSuccess && !rc) {
+      size_t nn = 0;
+      e = cudaGraphGetNodes(g, nullptr, &nn);
+      std::vector<cudaGraphNode_t> nodes(nn);
+      if (e == cudaSuccess && nn) e = cudaGraphGetNodes(g, nodes.data(), &nn);
+      for (size_t k = 0; k < nn && e == cudaSuccess; ++k) {
+        cudaGraphNodeType t;
+        e = cudaGraphNodeGetType(nodes[k], &t);
+        if (e != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp = {};
+        e = cudaGraphKernelNodeGetParams(nodes[k], &kp);
+        if (e != cudaSuccess || !kp.kernelParams) continue;
+        const unsigned long long* ctr = *(unsigned long long* const*)kp.kernelParams[0];
+        for (const Chain& c : chains)
+          if (c.sv->launch_counter() == ctr) {
+            e = Solver::set_node_priority(nodes[k], c.sv->priority());
+            break;
+          }
+      }
+    }
     for (size_t k = 0; k < bodies.size() && e == cudaSuccess && !rc; ++k) {
       int B = 0;
       for (const Chain& c : chains)
         if (c.sv == bodies[k].solver) B = c.B;
       rc = bodies[k].solver->capture_body(bodies[k], B, bs);
     }
-    if (e == cudaSuccess && !rc) e = cudaGraphInstantiate(&ctx->multi_exec, g, 0);
+    if (e == cudaSuccess && !rc) {
+      e = cudaGraphInstantiate(&ctx->multi_exec, g, cudaGraphInstantiateFlagUseNodePriority);
+      if (e != cudaSuccess) {   // priorities are a scheduling hint: run without them
+        cudaGetLastError();
+        e = cudaGraphInstantiate(&ctx->multi_exec, g, 0);
+      }
+    }
     if (e != cudaSuccess || rc) {
       cudaGraphDestroy(g);
       ctx->multi_exec = nullptr;

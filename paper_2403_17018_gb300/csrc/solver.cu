@@ -586,6 +586,28 @@ int Solver::capture_step_t(cudaGraph_t g, cudaStream_t cs, int B, std::vector<St
   return HENRY_OK;
 }
 
+cudaError_t Solver::set_node_priority(cudaGraphNode_t node, int p) {
+  cudaLaunchAttributeValue v = {};
+  v.priority = p;
+  return cudaGraphKernelNodeSetAttribute(node, cudaLaunchAttributePriority, &v);
+}
+
+// Give every kernel node of g (not descending into conditional nodes, whose
+// bodies are captured and prioritised on their own) the priority p.
+static cudaError_t prioritise_kernels(cudaGraph_t g, int p) {
+  size_t n = 0;
+  cudaError_t e = cudaGraphGetNodes(g, nullptr, &n);
+  if (e != cudaSuccess || n == 0) return e;
+  std::vector<cudaGraphNode_t> nodes(n);
+  e = cudaGraphGetNodes(g, nodes.data(), &n);
+  for (size_t k = 0; k < n && e == cudaSuccess; ++k) {
+    cudaGraphNodeType t;
+    e = cudaGraphNodeGetType(nodes[k], &t);
+    if (e == cudaSuccess && t == cudaGraphNodeTypeKernel) e = Solver::set_node_priority(nodes[k], p);
+  }
+  return e;
+}
+
 // The body of a step's while node: one defect-correction iteration and the
 // next check. With operator reuse the rebuild kernels sit in a conditional
 // IF node (captured after the body) set by k_set_rebuild, so iterations in
@@ -628,11 +650,13 @@ int Solver::capture_body_t(const StepBody& sb, int B, cudaStream_t bs) {
   enqueue_solve_update<T>(B, bs);
   enqueue_resjac_check<T>(B, bs, true, sb.cond);
   CK(cudaStreamEndCapture(bs, &body));
+  if (prio_) CK(prioritise_kernels(body, prio_));
   if (rebuild) {
     CK(cudaStreamBeginCaptureToGraph(bs, rebuild, nullptr, nullptr, 0,
                                      cudaStreamCaptureModeThreadLocal));
     enqueue_rebuild<T>(B, bs);
     CK(cudaStreamEndCapture(bs, &rebuild));
+    if (prio_) CK(prioritise_kernels(rebuild, prio_));
   }
   return HENRY_OK;
 }

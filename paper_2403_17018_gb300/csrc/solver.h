@@ -94,6 +94,13 @@ class Solver {
   // Incremented whenever the workspace is reallocated (graphs recorded on
   // the old workspace must be rebuilt).
   unsigned long long generation() const { return generation_; }
+  // Scheduling priority given to the kernel nodes of graphs this solver
+  // captures (the stream-priority scale; 0 leaves them unset), and the
+  // helper that applies it to every kernel node of a captured graph.
+  void set_priority(int p) { prio_ = p; }
+  int priority() const { return prio_; }
+  const unsigned long long* launch_counter() const { return counter_; }
+  static cudaError_t set_node_priority(cudaGraphNode_t node, int p);
   // Copy an internal array (see henry_debug_copy); returns HENRY_* code.
   int debug_copy(int mg_level, int what, void* dst, int64_t bytes) const;
 
@@ -167,6 +174,7 @@ class Solver {
   unsigned int* check_acc_ = nullptr;  // k_check's block count / active count (2 words)
   int* n_active_host_ = nullptr;  // pinned
   unsigned long long* counter_ = nullptr;  // device launch counter
+  int prio_ = 0;
   int nchunk_ = 0;            // residual blocks per sample
   ResTile tile_{};            // tiling of the residual kernel
   int ks_ = 0;                // top multigrid level handled by k_vcycle_small
