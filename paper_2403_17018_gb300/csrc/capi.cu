@@ -45,6 +45,7 @@ struct henry_ctx {
   // coarse half of a pair (created on first use)
   std::vector<cudaStream_t> pair_stream;
   std::vector<cudaEvent_t> pair_fork, pair_join;
+  std::vector<int> pair_prio;        // priority each pair_stream was created with
   std::vector<int*> pair_status;
   std::vector<int> pair_status_cap;
   double* stats_dev = nullptr;         // 1 + 4*NQ doubles
@@ -212,6 +213,7 @@ int henry_create_levels(const henry_config* cfg, henry_ctx** out) {
   ctx->pair_stream.assign(cfg->nlevels, nullptr);
   ctx->pair_fork.assign(cfg->nlevels, nullptr);
   ctx->pair_join.assign(cfg->nlevels, nullptr);
+  ctx->pair_prio.assign(cfg->nlevels, 0);
   ctx->pair_status.assign(cfg->nlevels, nullptr);
   ctx->pair_status_cap.assign(cfg->nlevels, 0);
   cudaError_t e = cudaGetDevice(&ctx->device);
@@ -310,11 +312,22 @@ int henry_sample_pairs(henry_ctx* ctx, int level, const double* xi, int B, doubl
   }
   if (level == 0)
     return get_solver(ctx, 0, 0)->run(xi, nullptr, B, q_fine, c_fine, nullptr, status, nullptr, 0, s);
-  // the coarse half runs concurrently on a stream forked from the caller's
+  // the coarse half runs concurrently on a stream forked from the caller's,
+  // with the caller's stream priority
+  int prio = 0;
+  CKR(cudaStreamGetPriority(s, &prio));
+  if (ctx->pair_stream[level] && ctx->pair_prio[level] != prio) {
+    CKR(cudaStreamSynchronize(ctx->pair_stream[level]));
+    CKR(cudaStreamDestroy(ctx->pair_stream[level]));
+    ctx->pair_stream[level] = nullptr;
+  }
   if (!ctx->pair_stream[level]) {
-    CKR(cudaStreamCreateWithFlags(&ctx->pair_stream[level], cudaStreamNonBlocking));
-    CKR(cudaEventCreateWithFlags(&ctx->pair_fork[level], cudaEventDisableTiming));
-    CKR(cudaEventCreateWithFlags(&ctx->pair_join[level], cudaEventDisableTiming));
+    CKR(cudaStreamCreateWithPriority(&ctx->pair_stream[level], cudaStreamNonBlocking, prio));
+    ctx->pair_prio[level] = prio;
+    if (!ctx->pair_fork[level]) {
+      CKR(cudaEventCreateWithFlags(&ctx->pair_fork[level], cudaEventDisableTiming));
+      CKR(cudaEventCreateWithFlags(&ctx->pair_join[level], cudaEventDisableTiming));
+    }
   }
   if (ctx->pair_status_cap[level] < B) {
     CKR(cudaStreamSynchronize(ctx->pair_stream[level]));

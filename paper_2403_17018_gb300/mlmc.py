@@ -152,7 +152,12 @@ class GpuSampler:
                 kw.update({k: sc[k] for k in ("vcycles", "nu1", "nu2", "mg_small_cells", "jac_lag",
                                               "res_rows", "mg_tb_cells") if k in sc})
                 self.ctxs[l] = hb.Context(hb.default_config(**kw))
-        self.streams = {l: torch.cuda.Stream() for l in range(cfg.nlevels)}
+        # one stream per level; the finest levels' pairs are the long chains
+        # (most steps, fewest samples), so their streams get the higher
+        # scheduling priority and the coarser levels fill the SMs left idle
+        least, greatest = torch.cuda.Stream.priority_range()
+        self.streams = {l: torch.cuda.Stream(priority=min(least, greatest + cfg.nlevels - 1 - l))
+                        for l in range(cfg.nlevels)}
 
     def _slice(self, first, count):
         lo = first + (count * self.rank) // self.world
