@@ -92,7 +92,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 // shared memory. Returns true once everything has landed. When a copy does
 // not land within the bounded wait, sets kStatusStall in status[b], gives
 // the copies in flight one more bounded wait and returns false (uniformly
-// over the block: the caller returns).
+// over the block: the caller returns; a block of a cluster first agrees
+// with the others, see cluster_stage).
 template <typename Runs>
 __device__ __forceinline__ bool stage_runs(uint64_t* bar, Runs runs, int* status, int b) {
   unsigned tx = 0;

@@ -63,7 +63,8 @@ struct TbTile {
   int EX, EY;    // largest extended tile, for the shared-memory size
   int staged;    // 1: one tile per sample whose operator planes, right-hand
                  // side and unknowns all fit in shared memory
-  size_t smem;   // dynamic shared memory of the launch
+  int cl;        // > 1: staged in strips by a cluster of cl blocks per sample
+  size_t smem;   // dynamic shared memory of the launch (per block)
 };
 
 // Tiles of at most tx x ty cells (both even) with a halo of 2 nu + extra;
@@ -82,7 +83,18 @@ inline TbTile make_tb_tile(const Geom& G, int nu, int extra, int tx, int ty, int
   t.EY = t.TY + 2 * t.H < G.ny ? t.TY + 2 * t.H : G.ny;
   const size_t staged = 16 + (size_t)(nplanes + 4) * G.ncell() * tsize;
   t.staged = t.ntx == 1 && t.nty == 1 && staged <= kMaxSmemOptin;
+  t.cl = 0;
   t.smem = t.staged ? staged : (size_t)2 * t.EX * t.EY * tsize;
+  // otherwise strips of an even number of rows, one block each, in a
+  // cluster of at most 8 blocks (the portable cluster size)
+  for (int cl = 2; !t.staged && cl <= 8; cl *= 2) {
+    const size_t strip = 16 + (size_t)(nplanes + 4) * (G.ncell() / cl) * tsize;
+    if (G.ny % (2 * cl) == 0 && (G.nx >> 1) % 2 == 0 && strip <= kMaxSmemOptin) {
+      t.cl = cl;
+      t.smem = strip;
+      break;
+    }
+  }
   return t;
 }
 

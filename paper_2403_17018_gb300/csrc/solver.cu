@@ -181,12 +181,38 @@ int Solver::ensure(int B, cudaStream_t s) {
     const bool f32 = tsize_ == sizeof(float);
     const TbTile& d = tbd_[k];
     const TbTile& u = tbu_[k];
-    const void* fd = f32 ? (d.staged ? (const void*)k_tb_down<float, true> : (const void*)k_tb_down<float, false>)
-                         : (d.staged ? (const void*)k_tb_down<double, true> : (const void*)k_tb_down<double, false>);
-    const void* fu = f32 ? (u.staged ? (const void*)k_tb_up<float, true> : (const void*)k_tb_up<float, false>)
-                         : (u.staged ? (const void*)k_tb_up<double, true> : (const void*)k_tb_up<double, false>);
+    const void* fd =
+        d.cl ? (f32 ? (const void*)k_tbc_down<float> : (const void*)k_tbc_down<double>)
+        : f32 ? (d.staged ? (const void*)k_tb_down<float, true> : (const void*)k_tb_down<float, false>)
+              : (d.staged ? (const void*)k_tb_down<double, true> : (const void*)k_tb_down<double, false>);
+    const void* fu =
+        u.cl ? (f32 ? (const void*)k_tbc_up<float> : (const void*)k_tbc_up<double>)
+        : f32 ? (u.staged ? (const void*)k_tb_up<float, true> : (const void*)k_tb_up<float, false>)
+              : (u.staged ? (const void*)k_tb_up<double, true> : (const void*)k_tb_up<double, false>);
     CK(raise_smem_limit(fd, d.smem));
     CK(raise_smem_limit(fu, u.smem));
+    // a cluster shape that cannot be resident on this GPU: one launch per
+    // operation on this level instead
+    for (const TbTile* t : {&d, &u}) {
+      if (!t->cl) continue;
+      cudaLaunchConfig_t lc = {};
+      lc.gridDim = dim3((unsigned)t->cl);
+      lc.blockDim = dim3(kTbBlock);
+      lc.dynamicSmemBytes = t->smem;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = t->cl;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      lc.attrs = at;
+      lc.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, t == &d ? fd : fu, &lc) != cudaSuccess ||
+          nclusters < 1) {
+        cudaGetLastError();
+        tb_[k] = 0;
+      }
+    }
   }
   if (B <= cap_) return HENRY_OK;
   unsigned long long count = 0;
@@ -362,15 +388,44 @@ void Solver::enqueue_vcycle(int k, int B, cudaStream_t s) {
     // levels, then prolongation + post-sweeps (x2 -> x)
     const TbTile& td = tbd_[k];
     const TbTile& tu = tbu_[k];
-    auto down = td.staged ? k_tb_down<T, true> : k_tb_down<T, false>;
-    auto up = tu.staged ? k_tb_up<T, true> : k_tb_up<T, false>;
-    down<<<dim3(td.ntx * td.nty, B), kTbBlock, td.smem, s>>>(
-        counter_, G, C.g, B, active_, td, cfg_.nu1, (const T*)L.J, (const T*)L.b,
-        (const T*)L.x, (T*)L.x2, (const T*)C.J, (T*)C.b, (T*)C.x, status_w_);
+    auto cluster_cfg = [&](const TbTile& t, cudaLaunchConfig_t& lc, cudaLaunchAttribute* at) {
+      lc = {};
+      lc.gridDim = dim3((unsigned)(B * t.cl));
+      lc.blockDim = dim3(kTbBlock);
+      lc.dynamicSmemBytes = t.smem;
+      lc.stream = s;
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = t.cl;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      lc.attrs = at;
+      lc.numAttrs = 1;
+    };
+    cudaLaunchConfig_t lc;
+    cudaLaunchAttribute at[1];
+    if (td.cl) {
+      cluster_cfg(td, lc, at);
+      cudaLaunchKernelEx(&lc, k_tbc_down<T>, counter_, G, C.g, B, (const int*)active_, cfg_.nu1,
+                         td.cl, (const T*)L.J, (const T*)L.b, (const T*)L.x, (T*)L.x2,
+                         (const T*)C.J, (T*)C.b, (T*)C.x, status_w_);
+    } else {
+      auto down = td.staged ? k_tb_down<T, true> : k_tb_down<T, false>;
+      down<<<dim3(td.ntx * td.nty, B), kTbBlock, td.smem, s>>>(
+          counter_, G, C.g, B, active_, td, cfg_.nu1, (const T*)L.J, (const T*)L.b,
+          (const T*)L.x, (T*)L.x2, (const T*)C.J, (T*)C.b, (T*)C.x, status_w_);
+    }
     enqueue_vcycle<T>(k - 1, B, s);
-    up<<<dim3(tu.ntx * tu.nty, B), kTbBlock, tu.smem, s>>>(
-        counter_, C.g, G, B, active_, tu, cfg_.nu2, (const T*)C.x, (const T*)L.J, (const T*)L.b,
-        (const T*)L.x2, (T*)L.x, status_w_);
+    if (tu.cl) {
+      cluster_cfg(tu, lc, at);
+      cudaLaunchKernelEx(&lc, k_tbc_up<T>, counter_, C.g, G, B, (const int*)active_, cfg_.nu2,
+                         tu.cl, (const T*)C.x, (const T*)L.J, (const T*)L.b, (const T*)L.x2,
+                         (T*)L.x, status_w_);
+    } else {
+      auto up = tu.staged ? k_tb_up<T, true> : k_tb_up<T, false>;
+      up<<<dim3(tu.ntx * tu.nty, B), kTbBlock, tu.smem, s>>>(
+          counter_, C.g, G, B, active_, tu, cfg_.nu2, (const T*)C.x, (const T*)L.J, (const T*)L.b,
+          (const T*)L.x2, (T*)L.x, status_w_);
+    }
     return;
   }
   const int gs = grid1((int64_t)B * G.half());

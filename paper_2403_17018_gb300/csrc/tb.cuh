@@ -275,4 +275,201 @@ k_tb_up(unsigned long long* ctr, Geom Gc, Geom G, int B, const int* __restrict__
   tb_store_interior<T>(G, R, xs, xo);
 }
 
+// Clustered staged legs: a level whose sample does not fit one block's
+// shared memory is split into CL strips of R = ny / CL rows (R even), one
+// block of a thread-block cluster per strip. Each block stages its strip's
+// operator planes (4..23 down, 4..19 up), b and x by TMA bulk copies, in the
+// strip's own colour-split layout [plane][colour][row][m] (every run of a
+// colour's rows is contiguous in the global planes); the unknowns of the row
+// above and below the strip are read from the neighbouring blocks' shared
+// memory (distributed shared memory), and every phase ends with a hardware
+// cluster barrier, whose release/acquire order makes a phase's writes
+// visible to the next phase's remote reads. Per cell the operations are
+// those of gs_point, resid_point and prolong_value in the same order, so the
+// results are bitwise those of the per-operation path. Grid B * CL, clusters
+// of CL blocks, kTbBlock threads.
+template <typename T>
+struct StripX {
+  const T* lo;   // the block below (rows j0 - 1), or null
+  const T* me;
+  const T* hi;   // the block above (row j0 + R), or null
+  int j0, R, hs, hx2;
+  __device__ __forceinline__ void operator()(int i, int j, T& vp, T& vc) const {
+    const T* X = me;
+    int r = j - j0;
+    if (r < 0) { X = lo; r = R - 1; }
+    else if (r >= R) { X = hi; r = 0; }
+    const int idx = ((i + j) & 1) * hs + r * hx2 + (i >> 1);
+    vp = X[idx];
+    vc = X[2 * hs + idx];
+  }
+};
+
+// Stage with the whole cluster: true when every block's copies landed (the
+// decision is the same in every block of the cluster).
+template <typename Runs>
+__device__ __forceinline__ bool cluster_stage(uint64_t* bar, int* flag, Runs runs, int* status,
+                                              int b) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const bool ok = stage_runs(bar, runs, status, b);
+  if (threadIdx.x == 0) flag[0] = ok ? 1 : 0;
+  cl.sync();
+  if (threadIdx.x == 0) {
+    int all = 1;
+    for (unsigned r = 0; r < cl.num_blocks(); ++r) all &= *cl.map_shared_rank(flag, r);
+    flag[1] = all;
+  }
+  cl.sync();   // every block has read every flag before any block may leave
+  return flag[1] != 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTbBlock)
+k_tbc_down(unsigned long long* ctr, Geom G, Geom Gc, int B, const int* __restrict__ active,
+           int nu1, int CL, const T* __restrict__ J, const T* __restrict__ bvec,
+           const T* __restrict__ xin, T* __restrict__ xout, const T* __restrict__ Jc,
+           T* __restrict__ bc, T* __restrict__ xc, int* __restrict__ status) {
+  HENRY_COUNT_LAUNCH(ctr);
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char tb_sh[];
+  const int b = blockIdx.x / CL, rank = blockIdx.x - b * CL;
+  if (!active[b]) return;                      // uniform over the cluster
+  const int ncell = G.ncell(), half = G.half(), hx2 = G.nx >> 1;
+  const int R = G.ny / CL, j0 = rank * R, hs = R * hx2;
+  uint64_t* bar = (uint64_t*)tb_sh;
+  int* flag = (int*)(tb_sh + 8);
+  T* Jst = (T*)(tb_sh + 16);                   // planes 4..23, [plane][colour][row][m]
+  T* bst = Jst + 40 * hs;
+  T* xs = bst + 4 * hs;
+  const T* Js = J + (int64_t)b * kJP * ncell;
+  const T* bs = bvec + (int64_t)b * 2 * ncell;
+  const T* xg = xin + (int64_t)b * 2 * ncell;
+  auto runs = [&](auto&& f) {
+    for (int q = 4; q < 24; ++q)
+      for (int c = 0; c < 2; ++c)
+        f(Jst + ((q - 4) * 2 + c) * hs, Js + (int64_t)q * ncell + c * half + j0 * hx2,
+          (unsigned)(hs * sizeof(T)));
+    for (int v = 0; v < 2; ++v)
+      for (int c = 0; c < 2; ++c) {
+        f(bst + (v * 2 + c) * hs, bs + v * ncell + c * half + j0 * hx2, (unsigned)(hs * sizeof(T)));
+        f(xs + (v * 2 + c) * hs, xg + v * ncell + c * half + j0 * hx2, (unsigned)(hs * sizeof(T)));
+      }
+  };
+  if (!cluster_stage(bar, flag, runs, status, b)) return;
+  const StripX<T> nb{rank > 0 ? cl.map_shared_rank(xs, rank - 1) : nullptr, xs,
+                     rank < CL - 1 ? cl.map_shared_rank(xs, rank + 1) : nullptr, j0, R, hs, hx2};
+  for (int s = 0; s < 2 * nu1; ++s) {
+    const int c = s & 1;
+    for (int pos = threadIdx.x; pos < hs; pos += blockDim.x) {
+      const int r = pos / hx2, m = pos - r * hx2, j = j0 + r;
+      const int i = 2 * m + ((c + j) & 1), own = c * hs + pos;
+      T xp, xv;
+      gs_point<T, 4>(i, j, G.nx, G.ny, 2 * hs, Jst + own, bst[own], bst[2 * hs + own], nb, xp, xv);
+      xs[own] = xp;
+      xs[2 * hs + own] = xv;
+    }
+    cl.sync();
+  }
+  T* xo = xout + (int64_t)b * 2 * ncell;
+  for (int e = threadIdx.x; e < 4 * hs; e += blockDim.x) {
+    const int vc = e / hs, k = e - vc * hs;       // vc = v * 2 + c
+    xo[(vc >> 1) * ncell + (vc & 1) * half + j0 * hx2 + k] = xs[e];
+  }
+  // restriction of the coarse rows j0/2 .. (j0 + R)/2 - 1 (red children)
+  const int ncc = Gc.ncell();
+  const T* Jcs = Jc + (int64_t)b * kJP * ncc;
+  T* bcs = bc + (int64_t)b * 2 * ncc;
+  T* xcs = xc + (int64_t)b * 2 * ncc;
+  for (int e = threadIdx.x; e < hx2 * (R >> 1); e += blockDim.x) {
+    const int rj = e / hx2;
+    const int I = e - rj * hx2, Jr = (j0 >> 1) + rj;
+    T sp = 0, sc = 0;
+#pragma unroll
+    for (int c4 = 0; c4 < 4; ++c4) {
+      if (c4 == 1 || c4 == 2) continue;
+      const int i = 2 * I + (c4 & 1), j = 2 * Jr + (c4 >> 1);
+      const int own = ((i + j) & 1) * hs + (j - j0) * hx2 + (i >> 1);
+      T rp, rc;
+      resid_point<T, 4>(i, j, G.nx, G.ny, 2 * hs, Jst + own, bst[own], bst[2 * hs + own], xs[own],
+                        xs[2 * hs + own], nb, rp, rc);
+      sp += rp;
+      sc += rc;
+    }
+    const int csc = cs_pos(I, Jr, Gc.nx, Gc.half());
+    const T* d = Jcs + csc;
+    bcs[csc] = d[0] * sp + d[ncc] * sc;
+    bcs[ncc + csc] = d[2 * ncc] * sp + d[3 * ncc] * sc;
+    xcs[csc] = (T)0;
+    xcs[ncc + csc] = (T)0;
+  }
+  cl.sync();   // no block leaves while another may still read its unknowns
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTbBlock)
+k_tbc_up(unsigned long long* ctr, Geom Gc, Geom G, int B, const int* __restrict__ active, int nu2,
+         int CL, const T* __restrict__ xc, const T* __restrict__ J, const T* __restrict__ bvec,
+         const T* __restrict__ xin, T* __restrict__ xout, int* __restrict__ status) {
+  HENRY_COUNT_LAUNCH(ctr);
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char tb_sh[];
+  const int b = blockIdx.x / CL, rank = blockIdx.x - b * CL;
+  if (!active[b]) return;                      // uniform over the cluster
+  const int ncell = G.ncell(), half = G.half(), hx2 = G.nx >> 1;
+  const int R = G.ny / CL, j0 = rank * R, hs = R * hx2;
+  uint64_t* bar = (uint64_t*)tb_sh;
+  int* flag = (int*)(tb_sh + 8);
+  T* Jst = (T*)(tb_sh + 16);                   // planes 4..19
+  T* bst = Jst + 32 * hs;
+  T* xs = bst + 4 * hs;
+  const T* Js = J + (int64_t)b * kJP * ncell;
+  const T* bs = bvec + (int64_t)b * 2 * ncell;
+  const T* xg = xin + (int64_t)b * 2 * ncell;
+  const T* xcs = xc + (int64_t)b * 2 * Gc.ncell();
+  auto runs = [&](auto&& f) {
+    for (int q = 4; q < 20; ++q)
+      for (int c = 0; c < 2; ++c)
+        f(Jst + ((q - 4) * 2 + c) * hs, Js + (int64_t)q * ncell + c * half + j0 * hx2,
+          (unsigned)(hs * sizeof(T)));
+    for (int v = 0; v < 2; ++v)
+      for (int c = 0; c < 2; ++c) {
+        f(bst + (v * 2 + c) * hs, bs + v * ncell + c * half + j0 * hx2, (unsigned)(hs * sizeof(T)));
+        f(xs + (v * 2 + c) * hs, xg + v * ncell + c * half + j0 * hx2, (unsigned)(hs * sizeof(T)));
+      }
+  };
+  if (!cluster_stage(bar, flag, runs, status, b)) return;
+  // prolongation onto the strip's black cells
+  for (int pos = threadIdx.x; pos < hs; pos += blockDim.x) {
+    const int r = pos / hx2, m = pos - r * hx2, j = j0 + r;
+    const int i = 2 * m + ((1 + j) & 1);
+    T vp, vc;
+    prolong_value<T>(Gc, i, j, xcs, vp, vc);
+    xs[hs + pos] += vp;
+    xs[3 * hs + pos] += vc;
+  }
+  cl.sync();
+  const StripX<T> nb{rank > 0 ? cl.map_shared_rank(xs, rank - 1) : nullptr, xs,
+                     rank < CL - 1 ? cl.map_shared_rank(xs, rank + 1) : nullptr, j0, R, hs, hx2};
+  for (int s = 0; s < 2 * nu2; ++s) {
+    const int c = s & 1;
+    for (int pos = threadIdx.x; pos < hs; pos += blockDim.x) {
+      const int r = pos / hx2, m = pos - r * hx2, j = j0 + r;
+      const int i = 2 * m + ((c + j) & 1), own = c * hs + pos;
+      T xp, xv;
+      gs_point<T, 4>(i, j, G.nx, G.ny, 2 * hs, Jst + own, bst[own], bst[2 * hs + own], nb, xp, xv);
+      xs[own] = xp;
+      xs[2 * hs + own] = xv;
+    }
+    cl.sync();   // the last one also keeps every block until no remote read is left
+  }
+  T* xo = xout + (int64_t)b * 2 * ncell;
+  for (int e = threadIdx.x; e < 4 * hs; e += blockDim.x) {
+    const int vc = e / hs, k = e - vc * hs;
+    xo[(vc >> 1) * ncell + (vc & 1) * half + j0 * hx2 + k] = xs[e];
+  }
+}
+
 }  // namespace henry
