@@ -106,7 +106,13 @@ typedef struct henry_config {
   int newton_maxit;    /* iteration cap per step -> HENRY_S_MAXIT           */
   int nu1, nu2;        /* red-black block Gauss-Seidel sweeps pre / post    */
   int vcycles;         /* V-cycles per defect-correction iteration          */
-  int guess_extrapolation; /* 1: Newton guess 2u^{n-1} - u^{n-2} from step 3 */
+  int guess_extrapolation; /* Newton's initial guess for u^{n+1}: 0 u^n;
+                              1 2u^n - u^{n-1} from the third step; 2
+                              (default) 3u^n - 3u^{n-1} + u^{n-2} from the
+                              fourth step (linear at the third); c clamped
+                              to [0, 1]. Changes the iterations, not the
+                              converged solution (the vertex-centred variant
+                              takes 2 as 1) */
   double newton_stag_tol;  /* also converged when r <= this and the last
                               iteration reduced r by less than half (the
                               FP64 rounding floor, which grows with

@@ -162,7 +162,9 @@ static __global__ void k_begin_step(unsigned long long* ctr, Geom G, int B, doub
                              double tau, const double* __restrict__ phi = nullptr,
                              double vtau = 0.0, double rho0 = 0.0, double drho = 0.0,
                              double* __restrict__ mo = nullptr, double* __restrict__ so = nullptr,
-                             double* __restrict__ vt_out = nullptr) {
+                             double* __restrict__ vt_out = nullptr,
+                             double* __restrict__ p_prev2 = nullptr,
+                             double* __restrict__ c_old2 = nullptr) {
   HENRY_COUNT_LAUNCH(ctr);
   const int64_t n = (int64_t)B * G.ncell();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -174,11 +176,23 @@ static __global__ void k_begin_step(unsigned long long* ctr, Geom G, int B, doub
     const double t = (*step + 1) * tau;
     qin[idx] = qin0[idx] * (1.0 + sin(pi * t / 40.0));
   }
+  // Newton's initial guess for u^(n+1): u^n (extrapolate 0), the linear
+  // extrapolation 2u^n - u^(n-1) (1, from the third step), or the quadratic
+  // one 3u^n - 3u^(n-1) + u^(n-2) (2, from the fourth step; the second
+  // previous state is kept in p_prev2 / c_old2); c clamped to [0, 1]
   const double cn = c[idx], pn = p[idx];
-  if (extrapolate && *step > 1) {
-    const double c2 = c_old[idx], p2 = p_prev[idx];
+  const double c2 = c_old[idx], p2 = p_prev[idx];
+  if (extrapolate == 2 && c_old2 && *step > 2) {
+    const double c3 = c_old2[idx], p3 = p_prev2[idx];
+    c[idx] = fmin(fmax(3.0 * (cn - c2) + c3, 0.0), 1.0);
+    p[idx] = 3.0 * (pn - p2) + p3;
+  } else if (extrapolate && *step > 1) {
     c[idx] = fmin(fmax(2.0 * cn - c2, 0.0), 1.0);
     p[idx] = 2.0 * pn - p2;
+  }
+  if (c_old2) {
+    c_old2[idx] = c2;
+    p_prev2[idx] = p2;
   }
   c_old[idx] = cn;
   p_prev[idx] = pn;

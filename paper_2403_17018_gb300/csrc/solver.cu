@@ -244,6 +244,9 @@ int Solver::ensure(int B, cudaStream_t s) {
   const Geom& F = levels_.back().g;
   const size_t o_cold = take((size_t)F.ncell() * Bz * 8);
   const size_t o_pprev = take((size_t)F.ncell() * Bz * 8);
+  const size_t q2 = cfg_.guess_extrapolation == 2 ? (size_t)F.ncell() * Bz * 8 : 0;
+  const size_t o_pprev2 = take(q2);
+  const size_t o_cold2 = take(q2);
   const size_t o_mo = take((size_t)F.ncell() * Bz * 8);
   const size_t o_so = take((size_t)F.ncell() * Bz * 8);
   const size_t o_vt = take((size_t)F.ncell() * Bz * 8);
@@ -293,6 +296,8 @@ int Solver::ensure(int B, cudaStream_t s) {
   }
   c_old_ = (double*)(a + o_cold);
   p_prev_ = (double*)(a + o_pprev);
+  p_prev2_ = q2 ? (double*)(a + o_pprev2) : nullptr;
+  c_old2_ = q2 ? (double*)(a + o_cold2) : nullptr;
   mo_ = (double*)(a + o_mo);
   so_ = (double*)(a + o_so);
   vt_ = (double*)(a + o_vt);
@@ -620,7 +625,7 @@ int Solver::capture_step_t(cudaGraph_t g, cudaStream_t cs, int B, std::vector<St
   k_begin_step<<<grid1((int64_t)B * F.g.ncell()), kBlock, 0, cs>>>(
       counter_, F.g, B, F.p, F.c, p_prev_, c_old_, status_w_, active_, it_step_, step_,
       cfg_.guess_extrapolation, cfg_.field_model == 1 ? qin0_ : nullptr, qin_, tau_, F.phi,
-      F.g.hx * F.g.hy / tau_, phys_.rho0, phys_.drho, mo_, so_, vt_);
+      F.g.hx * F.g.hy / tau_, phys_.rho0, phys_.drho, mo_, so_, vt_, p_prev2_, c_old2_);
   enqueue_resjac_check<T>(B, cs, true, (unsigned long long)h);
   cudaStreamCaptureStatus st;
   cudaGraph_t cg;
@@ -811,7 +816,7 @@ int Solver::step_t(int B, cudaStream_t s) {
   k_begin_step<<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(
       counter_, G, B, F.p, F.c, p_prev_, c_old_, status_w_, active_, it_step_, step_,
       cfg_.guess_extrapolation, cfg_.field_model == 1 ? qin0_ : nullptr, qin_, tau_, F.phi,
-      G.hx * G.hy / tau_, phys_.rho0, phys_.drho, mo_, so_, vt_);
+      G.hx * G.hy / tau_, phys_.rho0, phys_.drho, mo_, so_, vt_, p_prev2_, c_old2_);
   for (;;) {
     enqueue_resjac_check<T>(B, s, false);
     CK(cudaMemcpyAsync(n_active_host_, n_active_, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1002,7 +1007,7 @@ int Solver::ensure_adjoint(int B, int nckpt, int seglen) {
   const size_t n = (size_t)F.ncell() * B;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
-  const size_t o_ck = take((size_t)nckpt * 4 * n * 8);
+  const size_t o_ck = take((size_t)nckpt * ckpt_width() * n * 8);
   const size_t o_sg = take((size_t)(seglen + 1) * 2 * n * 8);
   const size_t o_j64 = take(20 * n * 8);
   const size_t o_lam = take(2 * n * 8);
@@ -1049,19 +1054,24 @@ int Solver::adjoint_t(const double* xi, const double* logk, int B, int qoi, int 
   auto slot_step = [&](int m) { return m <= nfull ? m * kc : nt_; };
   int rc = ensure_adjoint(B, nck, kc);
   if (rc) return rc;
-  // a checkpoint holds u^m and u^{m-1} (the latter feeds the extrapolated
-  // Newton guess of the next step), so recomputed steps are bitwise the
-  // forward's; segment states keep u^n only
+  // a checkpoint holds u^m and the previous states that feed the
+  // extrapolated Newton guess of the next step (u^{m-1}, and u^{m-2} with
+  // the quadratic guess), so recomputed steps are bitwise the forward's;
+  // segment states keep u^n only
   auto save = [&](double* dst, bool full) -> int {
     CK(cudaMemcpyAsync(dst, F.p, n * 8, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(dst + n, F.c, n * 8, cudaMemcpyDeviceToDevice, s));
     if (full) {
       CK(cudaMemcpyAsync(dst + 2 * n, p_prev_, n * 8, cudaMemcpyDeviceToDevice, s));
       CK(cudaMemcpyAsync(dst + 3 * n, c_old_, n * 8, cudaMemcpyDeviceToDevice, s));
+      if (p_prev2_) {
+        CK(cudaMemcpyAsync(dst + 4 * n, p_prev2_, n * 8, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(dst + 5 * n, c_old2_, n * 8, cudaMemcpyDeviceToDevice, s));
+      }
     }
     return HENRY_OK;
   };
-  auto ck = [&](int m) { return ckpt_ + (size_t)m * 4 * n; };
+  auto ck = [&](int m) { return ckpt_ + (size_t)m * ckpt_width() * n; };
   // forward with checkpoints
   rc = setup_t<T>(xi, logk, B, s);
   if (rc) return rc;
@@ -1090,6 +1100,10 @@ int Solver::adjoint_t(const double* xi, const double* logk, int B, int qoi, int 
     CK(cudaMemcpyAsync(F.c, ck(m) + n, n * 8, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(p_prev_, ck(m) + 2 * n, n * 8, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(c_old_, ck(m) + 3 * n, n * 8, cudaMemcpyDeviceToDevice, s));
+    if (p_prev2_) {
+      CK(cudaMemcpyAsync(p_prev2_, ck(m) + 4 * n, n * 8, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(c_old2_, ck(m) + 5 * n, n * 8, cudaMemcpyDeviceToDevice, s));
+    }
     k_set_int<<<1, 32, 0, s>>>(counter_, step_, n0);
     if ((rc = save(seg_, false))) return rc;
     for (int st = n0 + 1; st <= n1; ++st) {
