@@ -106,13 +106,17 @@ typedef struct henry_config {
   int newton_maxit;    /* iteration cap per step -> HENRY_S_MAXIT           */
   int nu1, nu2;        /* red-black block Gauss-Seidel sweeps pre / post    */
   int vcycles;         /* V-cycles per defect-correction iteration          */
-  int guess_extrapolation; /* Newton's initial guess for u^{n+1}: 0 u^n;
-                              1 2u^n - u^{n-1} from the third step; 2
-                              (default) 3u^n - 3u^{n-1} + u^{n-2} from the
-                              fourth step (linear at the third); c clamped
+  int guess_extrapolation; /* Newton's initial guess for u^{n+1}: the
+                              polynomial extrapolation in time of order q
+                              through u^n, ..., u^{n-q} (q = 1: 2u^n -
+                              u^{n-1}; q = 2: 3u^n - 3u^{n-1} + u^{n-2}),
+                              q = min(guess_extrapolation, steps done - 1)
+                              so that the initial state is never used; 0
+                              starts from u^n. 0..6, default 4; c clamped
                               to [0, 1]. Changes the iterations, not the
-                              converged solution (the vertex-centred variant
-                              takes 2 as 1) */
+                              converged solution; the adjoint's checkpoints
+                              grow by two state components per order above
+                              1 (the vertex-centred variant uses q <= 1) */
   double newton_stag_tol;  /* also converged when r <= this and the last
                               iteration reduced r by less than half (the
                               FP64 rounding floor, which grows with

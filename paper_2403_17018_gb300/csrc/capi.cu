@@ -140,8 +140,8 @@ int validate(const henry_config* c) {
     return fail(HENRY_E_INVALID, "adjoint_rtol must be in (0, 1e-3)");
   if (c->res_rows < 0 || c->res_rows > 64) return fail(HENRY_E_INVALID, "res_rows must be in 0..64");
   if (c->mg_tb_cells < 0) return fail(HENRY_E_INVALID, "mg_tb_cells must be >= 0");
-  if (c->guess_extrapolation < 0 || c->guess_extrapolation > 2)
-    return fail(HENRY_E_INVALID, "guess_extrapolation must be 0, 1 or 2");
+  if (c->guess_extrapolation < 0 || c->guess_extrapolation > 1 + henry::kMaxGuessHist)
+    return fail(HENRY_E_INVALID, "guess_extrapolation must be in 0..6");
   if (c->discretisation != HENRY_DISC_CELL && c->discretisation != HENRY_DISC_VERTEX)
     return fail(HENRY_E_INVALID, "discretisation must be HENRY_DISC_CELL or HENRY_DISC_VERTEX");
   if (c->discretisation == HENRY_DISC_VERTEX && (c->nx0 % 2 || c->ny0 < 1))
@@ -186,7 +186,7 @@ int henry_default_config(henry_config* c) {
   c->nu1 = 2;
   c->nu2 = 2;
   c->vcycles = 3;
-  c->guess_extrapolation = 2;
+  c->guess_extrapolation = 4;
   c->newton_stag_tol = 1e-9;
   c->mg_fusion = 1;
   c->mg_cluster_cells = 0;

@@ -50,6 +50,15 @@ struct Geom {
   __host__ __device__ int half() const { return (nx * ny) >> 1; }
 };
 
+// Previous states beyond u^(n-1) for the extrapolated Newton guess of the
+// implicit steps (see k_begin_step): p[k], c[k] hold u^(n-2-k).
+constexpr int kMaxGuessHist = 5;   // guess orders up to 6
+struct GuessHist {
+  double* p[kMaxGuessHist];
+  double* c[kMaxGuessHist];
+  int depth;                       // arrays in use
+};
+
 // Tiling of the temporally blocked multigrid legs (see k_tb_down, k_tb_up).
 constexpr int kTbBlock = 1024;
 constexpr int kTbTileX = 64, kTbTileY = 32;   // interior cells of a tile, at most

@@ -162,9 +162,7 @@ static __global__ void k_begin_step(unsigned long long* ctr, Geom G, int B, doub
                              double tau, const double* __restrict__ phi = nullptr,
                              double vtau = 0.0, double rho0 = 0.0, double drho = 0.0,
                              double* __restrict__ mo = nullptr, double* __restrict__ so = nullptr,
-                             double* __restrict__ vt_out = nullptr,
-                             double* __restrict__ p_prev2 = nullptr,
-                             double* __restrict__ c_old2 = nullptr) {
+                             double* __restrict__ vt_out = nullptr, GuessHist hx = {}) {
   HENRY_COUNT_LAUNCH(ctr);
   const int64_t n = (int64_t)B * G.ncell();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -176,23 +174,38 @@ static __global__ void k_begin_step(unsigned long long* ctr, Geom G, int B, doub
     const double t = (*step + 1) * tau;
     qin[idx] = qin0[idx] * (1.0 + sin(pi * t / 40.0));
   }
-  // Newton's initial guess for u^(n+1): u^n (extrapolate 0), the linear
-  // extrapolation 2u^n - u^(n-1) (1, from the third step), or the quadratic
-  // one 3u^n - 3u^(n-1) + u^(n-2) (2, from the fourth step; the second
-  // previous state is kept in p_prev2 / c_old2); c clamped to [0, 1]
+  // Newton's initial guess for u^(n+1): the polynomial extrapolation in time
+  // of order q through u^n, u^(n-1), ..., u^(n-q), i.e.
+  //   u^(n+1) ~ sum_k (-1)^k C(q+1, k+1) u^(n-k)   (q = 1: 2u^n - u^(n-1)),
+  // with q = min(extrapolate, step - 1, 1 + hx.depth): the initial state u^0
+  // (before the first step's transient) is never used; c clamped to [0, 1].
+  // c_old / p_prev hold u^(n-1) on entry and u^n (the old time level of this
+  // step) on exit; hx holds u^(n-2) ... and is shifted by one step.
   const double cn = c[idx], pn = p[idx];
-  const double c2 = c_old[idx], p2 = p_prev[idx];
-  if (extrapolate == 2 && c_old2 && *step > 2) {
-    const double c3 = c_old2[idx], p3 = p_prev2[idx];
-    c[idx] = fmin(fmax(3.0 * (cn - c2) + c3, 0.0), 1.0);
-    p[idx] = 3.0 * (pn - p2) + p3;
-  } else if (extrapolate && *step > 1) {
-    c[idx] = fmin(fmax(2.0 * cn - c2, 0.0), 1.0);
-    p[idx] = 2.0 * pn - p2;
+  double hc[1 + kMaxGuessHist], hp[1 + kMaxGuessHist];
+  hc[0] = c_old[idx];
+  hp[0] = p_prev[idx];
+  for (int k = 0; k < hx.depth; ++k) {
+    hc[k + 1] = hx.c[k][idx];
+    hp[k + 1] = hx.p[k][idx];
   }
-  if (c_old2) {
-    c_old2[idx] = c2;
-    p_prev2[idx] = p2;
+  int q = extrapolate;
+  if (q > *step - 1) q = *step - 1;
+  if (q > 1 + hx.depth) q = 1 + hx.depth;
+  if (q >= 1) {
+    double w = q + 1.0;                 // C(q+1, 1)
+    double ec = w * cn, ep = w * pn;
+    for (int k = 1; k <= q; ++k) {
+      w = -w * (q + 1 - k) / (k + 1);   // (-1)^k C(q+1, k+1)
+      ec += w * hc[k - 1];
+      ep += w * hp[k - 1];
+    }
+    c[idx] = fmin(fmax(ec, 0.0), 1.0);
+    p[idx] = ep;
+  }
+  for (int k = hx.depth - 1; k >= 0; --k) {
+    hx.c[k][idx] = hc[k];
+    hx.p[k][idx] = hp[k];
   }
   c_old[idx] = cn;
   p_prev[idx] = pn;

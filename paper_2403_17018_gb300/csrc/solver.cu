@@ -244,9 +244,9 @@ int Solver::ensure(int B, cudaStream_t s) {
   const Geom& F = levels_.back().g;
   const size_t o_cold = take((size_t)F.ncell() * Bz * 8);
   const size_t o_pprev = take((size_t)F.ncell() * Bz * 8);
-  const size_t q2 = cfg_.guess_extrapolation == 2 ? (size_t)F.ncell() * Bz * 8 : 0;
-  const size_t o_pprev2 = take(q2);
-  const size_t o_cold2 = take(q2);
+  size_t o_hist[2 * kMaxGuessHist];
+  for (int k = 0; k < 2 * kMaxGuessHist; ++k)
+    o_hist[k] = take(k / 2 < guess_depth() ? (size_t)F.ncell() * Bz * 8 : 0);
   const size_t o_mo = take((size_t)F.ncell() * Bz * 8);
   const size_t o_so = take((size_t)F.ncell() * Bz * 8);
   const size_t o_vt = take((size_t)F.ncell() * Bz * 8);
@@ -296,8 +296,12 @@ int Solver::ensure(int B, cudaStream_t s) {
   }
   c_old_ = (double*)(a + o_cold);
   p_prev_ = (double*)(a + o_pprev);
-  p_prev2_ = q2 ? (double*)(a + o_pprev2) : nullptr;
-  c_old2_ = q2 ? (double*)(a + o_cold2) : nullptr;
+  hx_ = {};
+  hx_.depth = guess_depth();
+  for (int k = 0; k < hx_.depth; ++k) {
+    hx_.p[k] = (double*)(a + o_hist[2 * k]);
+    hx_.c[k] = (double*)(a + o_hist[2 * k + 1]);
+  }
   mo_ = (double*)(a + o_mo);
   so_ = (double*)(a + o_so);
   vt_ = (double*)(a + o_vt);
@@ -625,7 +629,7 @@ int Solver::capture_step_t(cudaGraph_t g, cudaStream_t cs, int B, std::vector<St
   k_begin_step<<<grid1((int64_t)B * F.g.ncell()), kBlock, 0, cs>>>(
       counter_, F.g, B, F.p, F.c, p_prev_, c_old_, status_w_, active_, it_step_, step_,
       cfg_.guess_extrapolation, cfg_.field_model == 1 ? qin0_ : nullptr, qin_, tau_, F.phi,
-      F.g.hx * F.g.hy / tau_, phys_.rho0, phys_.drho, mo_, so_, vt_, p_prev2_, c_old2_);
+      F.g.hx * F.g.hy / tau_, phys_.rho0, phys_.drho, mo_, so_, vt_, hx_);
   enqueue_resjac_check<T>(B, cs, true, (unsigned long long)h);
   cudaStreamCaptureStatus st;
   cudaGraph_t cg;
@@ -816,7 +820,7 @@ int Solver::step_t(int B, cudaStream_t s) {
   k_begin_step<<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(
       counter_, G, B, F.p, F.c, p_prev_, c_old_, status_w_, active_, it_step_, step_,
       cfg_.guess_extrapolation, cfg_.field_model == 1 ? qin0_ : nullptr, qin_, tau_, F.phi,
-      G.hx * G.hy / tau_, phys_.rho0, phys_.drho, mo_, so_, vt_, p_prev2_, c_old2_);
+      G.hx * G.hy / tau_, phys_.rho0, phys_.drho, mo_, so_, vt_, hx_);
   for (;;) {
     enqueue_resjac_check<T>(B, s, false);
     CK(cudaMemcpyAsync(n_active_host_, n_active_, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1055,8 +1059,9 @@ int Solver::adjoint_t(const double* xi, const double* logk, int B, int qoi, int 
   int rc = ensure_adjoint(B, nck, kc);
   if (rc) return rc;
   // a checkpoint holds u^m and the previous states that feed the
-  // extrapolated Newton guess of the next step (u^{m-1}, and u^{m-2} with
-  // the quadratic guess), so recomputed steps are bitwise the forward's;
+  // extrapolated Newton guess of the next step (u^{m-1}, and u^{m-2} ...
+  // for guesses of higher order), so recomputed steps are bitwise the
+  // forward's;
   // segment states keep u^n only
   auto save = [&](double* dst, bool full) -> int {
     CK(cudaMemcpyAsync(dst, F.p, n * 8, cudaMemcpyDeviceToDevice, s));
@@ -1064,9 +1069,9 @@ int Solver::adjoint_t(const double* xi, const double* logk, int B, int qoi, int 
     if (full) {
       CK(cudaMemcpyAsync(dst + 2 * n, p_prev_, n * 8, cudaMemcpyDeviceToDevice, s));
       CK(cudaMemcpyAsync(dst + 3 * n, c_old_, n * 8, cudaMemcpyDeviceToDevice, s));
-      if (p_prev2_) {
-        CK(cudaMemcpyAsync(dst + 4 * n, p_prev2_, n * 8, cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemcpyAsync(dst + 5 * n, c_old2_, n * 8, cudaMemcpyDeviceToDevice, s));
+      for (int k = 0; k < hx_.depth; ++k) {
+        CK(cudaMemcpyAsync(dst + (4 + 2 * k) * n, hx_.p[k], n * 8, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(dst + (5 + 2 * k) * n, hx_.c[k], n * 8, cudaMemcpyDeviceToDevice, s));
       }
     }
     return HENRY_OK;
@@ -1100,9 +1105,9 @@ int Solver::adjoint_t(const double* xi, const double* logk, int B, int qoi, int 
     CK(cudaMemcpyAsync(F.c, ck(m) + n, n * 8, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(p_prev_, ck(m) + 2 * n, n * 8, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(c_old_, ck(m) + 3 * n, n * 8, cudaMemcpyDeviceToDevice, s));
-    if (p_prev2_) {
-      CK(cudaMemcpyAsync(p_prev2_, ck(m) + 4 * n, n * 8, cudaMemcpyDeviceToDevice, s));
-      CK(cudaMemcpyAsync(c_old2_, ck(m) + 5 * n, n * 8, cudaMemcpyDeviceToDevice, s));
+    for (int k = 0; k < hx_.depth; ++k) {
+      CK(cudaMemcpyAsync(hx_.p[k], ck(m) + (4 + 2 * k) * n, n * 8, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(hx_.c[k], ck(m) + (5 + 2 * k) * n, n * 8, cudaMemcpyDeviceToDevice, s));
     }
     k_set_int<<<1, 32, 0, s>>>(counter_, step_, n0);
     if ((rc = save(seg_, false))) return rc;

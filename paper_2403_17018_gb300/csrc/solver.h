@@ -149,11 +149,15 @@ class Solver {
   // finest-level / per-sample arrays
   double* c_old_ = nullptr;
   double* p_prev_ = nullptr;    // p of the previous step (initial-guess extrapolation)
-  double* p_prev2_ = nullptr;   // p and c two steps back (quadratic extrapolation only)
-  double* c_old2_ = nullptr;
-  // state components per adjoint checkpoint: u, u^{n-1} and, with the
-  // quadratic Newton guess, u^{n-2}
-  size_t ckpt_width() const { return cfg_.guess_extrapolation == 2 ? 6 : 4; }
+  GuessHist hx_ = {};           // u^(n-2), ... for guesses of order >= 2
+  // previous states the Newton guess reads beyond u^(n-1)
+  int guess_depth() const {
+    const int d = cfg_.guess_extrapolation - 1;
+    return d < 0 ? 0 : (d > kMaxGuessHist ? kMaxGuessHist : d);
+  }
+  // state components per adjoint checkpoint: u, u^(n-1) and the older
+  // states of the guess
+  size_t ckpt_width() const { return 4 + 2 * (size_t)guess_depth(); }
   double* mo_ = nullptr;        // old-time storage terms of the step (k_resid)
   double* so_ = nullptr;
   double* vt_ = nullptr;        // V phi / tau per cell (k_resid)
