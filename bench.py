@@ -268,7 +268,8 @@ def tune_schedules(precision_name):
     import torch
     from paper_2403_17018_gb300 import autotune as A
     A.CANDIDATES = {"vcycles": (3, 4), "nu": ((2, 2), (3, 3)), "small_cells": (128, 512),
-                    "jac_lag": (0, 10, 30), "res_rows": (0, 2, 16), "tb_cells": (0, 2048)}
+                    "jac_lag": (0, 10, 30), "res_rows": (0, 2, 16), "tb_cells": (0, 2048),
+                    "keep_lags": (30, 100)}
     t0 = time.perf_counter()
     gpu = torch.cuda.get_device_name(0)
     cache = A.load_cache()
@@ -285,7 +286,8 @@ def tune_schedules(precision_name):
 
 def sched_str(s):
     return (f"V({s['nu1']},{s['nu2']}) x{s['vcycles']} smem<={s['mg_small_cells']} "
-            f"lag={s['jac_lag']} rows={s.get('res_rows', 0)} tb<={s.get('mg_tb_cells', 0)}")
+            f"lag={s['jac_lag']}{'+keep' if s.get('jac_keep') else ''} rows={s.get('res_rows', 0)} "
+            f"tb<={s.get('mg_tb_cells', 0)}")
 
 
 def time_steps(wl, xis, K, W, barrier, flush, host=None):
@@ -455,7 +457,7 @@ def mlmc_wall_times():
     multigrid; schedules autotuned first (tuning time reported apart)."""
     from paper_2403_17018_gb300 import mlmc
     cands = {"vcycles": (2, 3), "nu": ((2, 2),), "small_cells": (128, 512), "jac_lag": (0, 30),
-             "tb_cells": (0, 2048)}
+             "tb_cells": (0, 2048), "keep_lags": (30, 100)}
     out = {"config": "6 levels 32x16..1024x512, 6 random variables, RMSE 1e-3 on c at "
                      "(1.40,0.05), (1.65,0.25), (1.90,0.50), variance budget eps^2/2, "
                      "levels on concurrent streams"}

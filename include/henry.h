@@ -183,6 +183,14 @@ typedef struct henry_config {
                            nu1, nu2 >= 1; results bitwise those of one launch
                            per operation). 0 (default): one launch per
                            operation. A schedule knob for the autotuner */
+  int jac_keep;         /* with jac_lag > 0: 1 keeps the operators across
+                           time steps (rebuilt before the first iteration of a
+                           solve and after any iteration that reduced the
+                           residual by less than jac_lag), 0 (default)
+                           rebuilds them at the first iteration of every step.
+                           Changes the iterations, not the converged
+                           solution; henry_adjoint's forward always rebuilds
+                           per step. A schedule knob for the autotuner */
 } henry_config;
 
 #define HENRY_DISC_CELL 0        /* cell-centred, full upwind (default)      */
@@ -262,7 +270,7 @@ int henry_sample_pairs(henry_ctx* ctx, int level, const double* xi, int B,
 /* Multigrid schedule of one MLMC level (the autotuner's knobs; meanings as
  * the henry_config fields of the same names). */
 typedef struct henry_schedule {
-  int vcycles, nu1, nu2, mg_small_cells, jac_lag, res_rows, mg_tb_cells;
+  int vcycles, nu1, nu2, mg_small_cells, jac_lag, res_rows, mg_tb_cells, jac_keep;
 } henry_schedule;
 
 /* Give MLMC level `level` its own schedule: the fine solves of level l

@@ -6,8 +6,9 @@ V-cycles per defect-correction iteration, pre/post smoothing sweeps, the
 largest grid handed to the shared-memory V-cycle kernel and, for the level's
 batch size, several batch splits — under the largest operator reuse factor;
 then, for the winner, the other reuse factors (jac_lag), the residual
-kernel's tile height (res_rows) and the temporally blocked legs
-(mg_tb_cells), and keeps the schedule with the highest solves per second. Results are cached in a JSON file keyed by
+kernel's tile height (res_rows), the temporally blocked legs (mg_tb_cells)
+and operators kept across time steps (jac_keep, with the reuse factors in
+keep_lags), and keeps the schedule with the highest solves per second. Results are cached in a JSON file keyed by
 GPU name, level grid, precision and batch so that later runs reuse them.
 
   python -m paper_2403_17018_gb300.autotune --levels 4 --precision fp32mg
@@ -27,7 +28,8 @@ if ROOT not in sys.path:
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuning", "schedules.json")
 CANDIDATES = {"vcycles": (1, 2, 3), "nu": ((1, 1), (2, 2), (3, 3)), "small_cells": (0, 128, 512),
-              "jac_lag": (0, 10, 30), "res_rows": (0, 2, 4, 16), "tb_cells": (0, 2048)}
+              "jac_lag": (0, 10, 30), "res_rows": (0, 2, 4, 16), "tb_cells": (0, 2048),
+              "keep_lags": (30, 100)}
 
 
 def _key(gpu, level, precision, batch, nx0, ny0):
@@ -80,10 +82,10 @@ def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2),
     xi = torch.from_numpy(xi_batch(level, 0, batch, n_xi=n_xi)).cuda()
     table = []
 
-    def timed(vc, n1, n2, sc, lag, split, rr=0, tb=0):
+    def timed(vc, n1, n2, sc, lag, split, rr=0, tb=0, keep=0):
         cfg = hb.default_config(nlevels=level + 1, precision=prec, vcycles=vc, nu1=n1, nu2=n2,
                                 mg_small_cells=sc, jac_lag=lag, res_rows=rr, mg_tb_cells=tb,
-                                nt0=k, T=tau0 * k, n_xi=n_xi, **extra)
+                                jac_keep=keep, nt0=k, T=tau0 * k, n_xi=n_xi, **extra)
         ctx = hb.Context(cfg)
         sub = batch // split
         parts = [xi[i * sub:(i + 1) * sub].contiguous() for i in range(split)]
@@ -98,8 +100,8 @@ def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2),
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / reps
         row = {"vcycles": vc, "nu1": n1, "nu2": n2, "mg_small_cells": sc, "jac_lag": lag,
-               "res_rows": rr, "mg_tb_cells": tb, "split": split, "solves_per_s": batch / dt,
-               "failed": bad}
+               "res_rows": rr, "mg_tb_cells": tb, "jac_keep": keep, "split": split,
+               "solves_per_s": batch / dt, "failed": bad}
         table.append(row)
         if log:
             log(row)
@@ -137,6 +139,10 @@ def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2),
         if tb:
             timed(best["vcycles"], best["nu1"], best["nu2"], best["mg_small_cells"],
                   best["jac_lag"], best["split"], best["res_rows"], tb)
+    best = best_of(table)
+    for lag in CANDIDATES.get("keep_lags", ()):
+        timed(best["vcycles"], best["nu1"], best["nu2"], best["mg_small_cells"], lag,
+              best["split"], best["res_rows"], best["mg_tb_cells"], 1)
     return best_of(table), table
 
 

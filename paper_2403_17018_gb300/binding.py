@@ -49,7 +49,7 @@ class HenryConfig(ctypes.Structure):
                 ("jac_lag", ctypes.c_int), ("field_model", ctypes.c_int),
                 ("krylov_iters", ctypes.c_int), ("adjoint_rtol", ctypes.c_double),
                 ("res_rows", ctypes.c_int), ("discretisation", ctypes.c_int),
-                ("mg_tb_cells", ctypes.c_int)]
+                ("mg_tb_cells", ctypes.c_int), ("jac_keep", ctypes.c_int)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
@@ -58,7 +58,7 @@ class HenryConfig(ctypes.Structure):
 class HenrySchedule(ctypes.Structure):
     """Multigrid schedule of one MLMC level (henry_schedule)."""
     _fields_ = [(n, ctypes.c_int) for n in ("vcycles", "nu1", "nu2", "mg_small_cells", "jac_lag",
-                                             "res_rows", "mg_tb_cells")]
+                                             "res_rows", "mg_tb_cells", "jac_keep")]
 
 
 class HenryLevelBatch(ctypes.Structure):
@@ -289,9 +289,10 @@ class Context:
         return qf, qc, cf, cc, st
 
     def set_schedule(self, level, vcycles, nu1, nu2, mg_small_cells=512, jac_lag=0, res_rows=0,
-                     mg_tb_cells=0, **_):
+                     mg_tb_cells=0, jac_keep=0, **_):
         """henry_set_schedule: the multigrid schedule of one MLMC level."""
-        sc = HenrySchedule(vcycles, nu1, nu2, mg_small_cells, jac_lag, res_rows, mg_tb_cells)
+        sc = HenrySchedule(vcycles, nu1, nu2, mg_small_cells, jac_lag, res_rows, mg_tb_cells,
+                           jac_keep)
         _check(self.lib.henry_set_schedule(self._h, level, ctypes.byref(sc)))
 
     def sample_levels(self, xis, want_c=False, stream=None):

@@ -140,6 +140,7 @@ int validate(const henry_config* c) {
     return fail(HENRY_E_INVALID, "adjoint_rtol must be in (0, 1e-3)");
   if (c->res_rows < 0 || c->res_rows > 64) return fail(HENRY_E_INVALID, "res_rows must be in 0..64");
   if (c->mg_tb_cells < 0) return fail(HENRY_E_INVALID, "mg_tb_cells must be >= 0");
+  if (c->jac_keep != 0 && c->jac_keep != 1) return fail(HENRY_E_INVALID, "jac_keep must be 0 or 1");
   if (c->guess_extrapolation < 0 || c->guess_extrapolation > 1 + henry::kMaxGuessHist)
     return fail(HENRY_E_INVALID, "guess_extrapolation must be in 0..6");
   if (c->discretisation != HENRY_DISC_CELL && c->discretisation != HENRY_DISC_VERTEX)
@@ -196,6 +197,7 @@ int henry_default_config(henry_config* c) {
   c->krylov_iters = 0;
   c->adjoint_rtol = 1e-14;
   c->mg_tb_cells = 0;
+  c->jac_keep = 0;
   return HENRY_OK;
 }
 
@@ -362,6 +364,7 @@ int henry_set_schedule(henry_ctx* ctx, int level, const henry_schedule* sc) {
   c.jac_lag = sc->jac_lag;
   c.res_rows = sc->res_rows;
   c.mg_tb_cells = sc->mg_tb_cells;
+  c.jac_keep = sc->jac_keep;
   const int rc = validate(&c);
   if (rc) return rc;
   CKR(cudaSetDevice(ctx->device));

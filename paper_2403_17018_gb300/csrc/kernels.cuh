@@ -613,10 +613,12 @@ k_resid(unsigned long long* ctr, Phys P, Geom G, int B, ResTile tl,
 // acc for the next launch and, when SET_COND, sets the while-loop condition
 // of the enclosing CUDA graph. With refresh (operator reuse factor lag > 0)
 // it also decides whether the next iteration rebuilds the Jacobian and the
-// multigrid operators: always after the step's initial residual, later only
-// when the last iteration reduced the residual by less than a factor lag;
-// acc[2] counts those samples and the last block publishes the count in
-// n_active[1] (k_set_rebuild turns it into the condition of the rebuild).
+// multigrid operators: after the step's initial residual (with *keep != 0
+// only before the first iteration of the solve: the operators of the
+// previous step are kept), later when the last iteration reduced the
+// residual by less than a factor lag; acc[2] counts those samples and the
+// last block publishes the count in n_active[1] (k_set_rebuild turns it
+// into the condition of the rebuild).
 template <bool SET_COND>
 __global__ void k_check(unsigned long long* ctr, int B, int nchunk, int ncell,
                         const double* __restrict__ partial, double scale, double rtol,
@@ -626,7 +628,7 @@ __global__ void k_check(unsigned long long* ctr, int B, int nchunk, int ncell,
                         int* __restrict__ iters, int* __restrict__ n_active,
                         unsigned int* __restrict__ acc, double stag_tol,
                         cudaGraphConditionalHandle h, int* __restrict__ refresh, int lag,
-                        double stag_rel = 0.0) {
+                        double stag_rel = 0.0, const int* __restrict__ keep = nullptr) {
   HENRY_COUNT_LAUNCH(ctr);
   __shared__ int cnt, rcnt;
   __shared__ bool last;
@@ -655,11 +657,13 @@ __global__ void k_check(unsigned long long* ctr, int B, int nchunk, int ncell,
         status[b] |= kStatusMaxit;
         active[b] = 0;
       } else {
+        const bool first = iters[b] == 0;   // no operators built yet in this solve
         it_step[b] = it + 1;
         iters[b] += 1;
         atomicAdd(&cnt, 1);
         if (refresh) {
-          const int rf = (it == 0 || r * lag > prev) ? 1 : 0;
+          const bool kept = keep && *keep;
+          const int rf = (it == 0 ? (!kept || first) : r * lag > prev) ? 1 : 0;
           refresh[b] = rf;
           if (rf) atomicAdd(&rcnt, 1);
         }

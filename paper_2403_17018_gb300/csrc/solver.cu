@@ -263,6 +263,7 @@ int Solver::ensure(int B, cudaStream_t s) {
   const size_t o_st = take(Bz * 4);
   const size_t o_it = take(Bz * 4);
   const size_t o_na = take(8);     // active count, rebuild count
+  const size_t o_keep = take(8);   // operators kept across steps in this solve (k_check)
   const size_t o_acc = take(16);   // k_check's accumulators
   // BiCGStab vectors r, rh, p, v, t, xk ([B][2][ncell] of the finest level),
   // per-sample scalars and dot partials (only with krylov_iters > 0)
@@ -318,6 +319,7 @@ int Solver::ensure(int B, cudaStream_t s) {
   status_w_ = (int*)(a + o_st);
   iters_w_ = (int*)(a + o_it);
   n_active_ = (int*)(a + o_na);
+  keep_ = (int*)(a + o_keep);
   check_acc_ = (unsigned int*)(a + o_acc);
   for (int k = 0; k < 6; ++k) kry_v_[k] = a + o_kv[k];
   kry_S_ = (double*)(a + o_ks);
@@ -606,13 +608,13 @@ void Solver::enqueue_resjac_check(int B, cudaStream_t s, bool set_cond,
                                         active_, it_step_, res0_, res_last_, status_w_, iters_w_,
                                         n_active_, check_acc_, stag_tol,
                                         (cudaGraphConditionalHandle)cond, refresh,
-                                        cfg_.jac_lag);
+                                        cfg_.jac_lag, 0.0, keep_);
   else
     k_check<false><<<gb, kBlock, 0, s>>>(counter_, B, nchunk_, G.ncell(), partial_, scale,
                                          cfg_.newton_rtol, cfg_.newton_atol, cfg_.newton_maxit,
                                          active_, it_step_, res0_, res_last_, status_w_, iters_w_,
                                          n_active_, check_acc_, stag_tol, 0, refresh,
-                                         cfg_.jac_lag);
+                                         cfg_.jac_lag, 0.0, keep_);
 }
 
 // The nodes of one implicit Euler step on stream cs, which is capturing into
@@ -807,6 +809,7 @@ int Solver::setup_t(const double* xi, const double* logk, int B, cudaStream_t s)
   }
   k_init_state<<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(counter_, phys_, G, B, F.p, F.c,
                                                                 iters_w_, step_);
+  k_set_int<<<1, 32, 0, s>>>(counter_, keep_, cfg_.jac_keep);
   CK(cudaGetLastError());
   return HENRY_OK;
 }
@@ -1080,6 +1083,9 @@ int Solver::adjoint_t(const double* xi, const double* logk, int B, int qoi, int 
   // forward with checkpoints
   rc = setup_t<T>(xi, logk, B, s);
   if (rc) return rc;
+  // steps recomputed from a checkpoint must be bitwise the forward's, so
+  // every step of the adjoint's forward builds its own operators
+  k_set_int<<<1, 32, 0, s>>>(counter_, keep_, 0);
   if ((rc = save(ck(0), true))) return rc;
   for (int st = 1; st <= nt_; ++st) {
     if ((rc = step_t<T>(B, s))) return rc;

@@ -184,6 +184,7 @@ class Solver {
   int* n_active_host_ = nullptr;  // pinned
   unsigned long long* counter_ = nullptr;  // device launch counter
   int prio_ = 0;
+  int* keep_ = nullptr;       // device flag: operators kept across steps (k_check)
   int nchunk_ = 0;            // residual blocks per sample
   ResTile tile_{};            // tiling of the residual kernel
   int ks_ = 0;                // top multigrid level handled by k_vcycle_small

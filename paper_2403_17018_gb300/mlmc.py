@@ -150,7 +150,7 @@ class GpuSampler:
             else:
                 kw = cfg.as_dict()
                 kw.update({k: sc[k] for k in ("vcycles", "nu1", "nu2", "mg_small_cells", "jac_lag",
-                                              "res_rows", "mg_tb_cells") if k in sc})
+                                              "res_rows", "mg_tb_cells", "jac_keep") if k in sc})
                 self.ctxs[l] = hb.Context(hb.default_config(**kw))
         # one stream per level; the finest levels' pairs are the long chains
         # (most steps, fewest samples), so their streams get the higher
@@ -340,7 +340,7 @@ def run(sampler, L, eps, qois=(3, 4, 5), pilot=None, max_batch=None, var_budget_
 
 
 TUNE_CANDIDATES = {"vcycles": (3, 4), "nu": ((2, 2), (3, 3)), "small_cells": (128, 512),
-                   "jac_lag": (0, 10, 30), "tb_cells": (0, 2048)}
+                   "jac_lag": (0, 10, 30), "tb_cells": (0, 2048), "keep_lags": (30, 100)}
 
 
 def tuned_schedules(levels, precision, n_xi, nx0=32, ny0=16, world=1, extra=None,
@@ -400,7 +400,7 @@ def tuned_run(levels=6, eps=1e-3, n_xi=6, precision="fp32mg", vcycles=3, tune=Tr
                 "concurrent_levels": concurrent,
                 "schedules": {l: {k: v for k, v in sc.items() if k in ("vcycles", "nu1", "nu2",
                                                                       "mg_small_cells", "jac_lag",
-                                                                      "res_rows", "mg_tb_cells")}
+                                                                      "res_rows", "mg_tb_cells", "jac_keep")}
                               for l, sc in (schedules or {}).items()}})
     return res
 

@@ -44,7 +44,7 @@ def test_error_strings_and_invalid_config(lib):
     {"vcycles": 0}, {"nu1": -1}, {"precision": 2}, {"nlevels": 0}, {"krylov_iters": 1},
     {"adjoint_rtol": 0.0}, {"adjoint_rtol": 1e-2}, {"adjoint_rtol": float("nan")},
     {"res_rows": -1}, {"res_rows": 65}, {"discretisation": 2}, {"mg_tb_cells": -1},
-    {"guess_extrapolation": 7}, {"guess_extrapolation": -1},
+    {"guess_extrapolation": 7}, {"guess_extrapolation": -1}, {"jac_keep": 2},
 ])
 def test_config_validation_rejects_out_of_range_options(lib, kw):
     """henry_create_levels validates the whole config before touching the
