@@ -267,7 +267,7 @@ def tune_schedules(precision_name):
     it; returns (schedules, seconds spent tuning)."""
     import torch
     from paper_2403_17018_gb300 import autotune as A
-    A.CANDIDATES = {"vcycles": (3, 4), "nu": ((2, 2), (3, 3)), "small_cells": (128, 512),
+    A.CANDIDATES = {"vcycles": (2, 3, 4), "nu": ((2, 2), (3, 3)), "small_cells": (128, 512),
                     "jac_lag": (0, 10, 30), "res_rows": (0, 2, 16), "tb_cells": (0, 2048),
                     "keep_lags": (30, 100)}
     t0 = time.perf_counter()

@@ -4,12 +4,14 @@ For each MLMC level it times short batched solves (a few implicit Euler
 steps at the level's own time step) for every candidate cycle shape —
 V-cycles per defect-correction iteration, pre/post smoothing sweeps, the
 largest grid handed to the shared-memory V-cycle kernel and, for the level's
-batch size, several batch splits — under the largest operator reuse factor;
-then, for the winner, the other reuse factors (jac_lag), the residual
-kernel's tile height (res_rows), the temporally blocked legs (mg_tb_cells)
-and operators kept across time steps (jac_keep, with the reuse factors in
-keep_lags), and keeps the schedule with the highest solves per second. Results are cached in a JSON file keyed by
-GPU name, level grid, precision and batch so that later runs reuse them.
+batch size, several batch splits — under a reference operator reuse (the
+largest factor of keep_lags with the operators kept across time steps,
+jac_keep); then, for the winner, the other reuse variants (the factors of
+jac_lag, and of keep_lags with kept operators), the residual kernel's tile
+height (res_rows) and the temporally blocked legs (mg_tb_cells), and keeps
+the schedule with the highest solves per second. Results are cached in a
+JSON file keyed by GPU name, level grid, precision and batch so that later
+runs reuse them.
 
   python -m paper_2403_17018_gb300.autotune --levels 4 --precision fp32mg
 """
@@ -62,9 +64,10 @@ def best_schedule(level, precision, batch, gpu=None, nx0=32, ny0=16, path=CACHE)
 def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2), log=None, n_xi=3,
                cfg_extra=None):
     """Time every candidate cycle shape (V-cycles per iteration, sweeps,
-    shared-memory threshold, batch split) under the largest operator-reuse
-    factor, then the other reuse factors, residual tile heights and blocked
-    legs on the best one, each on about `steps` steps of level `level` at
+    shared-memory threshold, batch split) under the reference operator reuse
+    (the largest factor of keep_lags with kept operators, else the largest
+    jac_lag), then the other reuse variants, residual tile heights and
+    blocked legs on the best one, each on about `steps` steps of level `level` at
     the level's own time step (steps=None: the whole 43200 s horizon, whose
     early steps need more iterations than the later ones); returns the best
     {vcycles, nu1, nu2, mg_small_cells, jac_lag, res_rows, mg_tb_cells,
@@ -112,37 +115,35 @@ def tune_level(level, batch, precision="fp32mg", steps=4, reps=2, splits=(1, 2),
         ok = [r for r in rows if r["failed"] == 0] or rows
         return max(ok, key=lambda r: r["solves_per_s"])
 
-    # the cycle shapes are compared under the largest operator-reuse factor:
-    # reuse changes which shape wins (with a rebuild at every iteration more
-    # V-cycles per iteration amortise it; with reuse fewer are faster), and
-    # it is the usual winner; the other factors are then timed on the best
-    # shape
+    # the cycle shapes are compared under the reuse that usually wins: the
+    # largest factor of keep_lags with the operators kept across steps, or,
+    # without keep_lags, the largest jac_lag (reuse changes which shape
+    # wins: with a rebuild at every iteration more V-cycles per iteration
+    # amortise it, with reuse fewer are faster); the other reuse variants,
+    # tile heights and blocked legs are then timed on the best shape
     lags = tuple(CANDIDATES.get("jac_lag", (0,)))
-    lag0 = max(lags)
+    keep_lags = tuple(CANDIDATES.get("keep_lags", ()))
+    ref = (max(keep_lags), 1) if keep_lags else (max(lags), 0)
     for vc, (n1, n2), sc, split in itertools.product(
             CANDIDATES["vcycles"], CANDIDATES["nu"], CANDIDATES.get("small_cells", (512,)), splits):
         if batch % split:
             continue
-        timed(vc, n1, n2, sc, lag0, split)
+        timed(vc, n1, n2, sc, ref[0], split, keep=ref[1])
     best = best_of(table)
-    for lag in lags:
-        if lag != lag0:
+    for lag, keep in [(l, 0) for l in lags] + [(l, 1) for l in keep_lags]:
+        if (lag, keep) != ref:
             timed(best["vcycles"], best["nu1"], best["nu2"], best["mg_small_cells"], lag,
-                  best["split"])
+                  best["split"], keep=keep)
     best = best_of(table)
     for rr in CANDIDATES.get("res_rows", (0,)):
         if rr:
             timed(best["vcycles"], best["nu1"], best["nu2"], best["mg_small_cells"],
-                  best["jac_lag"], best["split"], rr)
+                  best["jac_lag"], best["split"], rr, keep=best["jac_keep"])
     best = best_of(table)
     for tb in CANDIDATES.get("tb_cells", (0,)):
         if tb:
             timed(best["vcycles"], best["nu1"], best["nu2"], best["mg_small_cells"],
-                  best["jac_lag"], best["split"], best["res_rows"], tb)
-    best = best_of(table)
-    for lag in CANDIDATES.get("keep_lags", ()):
-        timed(best["vcycles"], best["nu1"], best["nu2"], best["mg_small_cells"], lag,
-              best["split"], best["res_rows"], best["mg_tb_cells"], 1)
+                  best["jac_lag"], best["split"], best["res_rows"], tb, best["jac_keep"])
     return best_of(table), table
 
 

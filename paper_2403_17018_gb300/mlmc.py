@@ -339,7 +339,7 @@ def run(sampler, L, eps, qois=(3, 4, 5), pilot=None, max_batch=None, var_budget_
             "state": [lv.to_json() for lv in local]}
 
 
-TUNE_CANDIDATES = {"vcycles": (3, 4), "nu": ((2, 2), (3, 3)), "small_cells": (128, 512),
+TUNE_CANDIDATES = {"vcycles": (2, 3, 4), "nu": ((2, 2), (3, 3)), "small_cells": (128, 512),
                    "jac_lag": (0, 10, 30), "tb_cells": (0, 2048), "keep_lags": (30, 100)}
 
 

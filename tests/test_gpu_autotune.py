@@ -13,11 +13,10 @@ def test_tune_level_returns_a_converging_schedule(tmp_path):
     from paper_2403_17018_gb300 import autotune as A
     best, table = A.tune_level(0, 64, "fp32mg", steps=2, reps=1, splits=(1, 2))
     n = len(A.CANDIDATES["vcycles"]) * len(A.CANDIDATES["nu"]) * len(A.CANDIDATES["small_cells"])
-    assert len(table) == n * 2 + len(A.CANDIDATES["jac_lag"]) - 1 + len(
-        [r for r in A.CANDIDATES["res_rows"] if r]) + len([t for t in A.CANDIDATES["tb_cells"] if t]) + len(
-        A.CANDIDATES["keep_lags"])
-    lag0 = max(A.CANDIDATES["jac_lag"])
-    assert all(r["jac_lag"] == lag0 for r in table[:n * 2])
+    assert len(table) == n * 2 + len(A.CANDIDATES["jac_lag"]) + len(A.CANDIDATES["keep_lags"]) - 1 + len(
+        [r for r in A.CANDIDATES["res_rows"] if r]) + len([t for t in A.CANDIDATES["tb_cells"] if t])
+    lag0 = max(A.CANDIDATES["keep_lags"])
+    assert all(r["jac_lag"] == lag0 and r["jac_keep"] == 1 for r in table[:n * 2])
     assert {r["mg_small_cells"] for r in table} == set(A.CANDIDATES["small_cells"])
     assert best["failed"] == 0 and best["solves_per_s"] > 0
     assert best["solves_per_s"] == max(r["solves_per_s"] for r in table if r["failed"] == 0)
