@@ -34,6 +34,9 @@ def main(argv=None):
     ap.add_argument("--small-cells", type=int, default=512,
                     help="largest multigrid level (cells per sample) run by the shared-memory "
                          "V-cycle kernel; 0 disables it")
+    ap.add_argument("--jac-keep", type=int, default=0, choices=(0, 1),
+                    help="keep the operators across time steps (with --jac-lag > 0)")
+    ap.add_argument("--res-rows", type=int, default=0, help="residual kernel tile height")
     ap.add_argument("--tb-cells", type=int, default=0,
                     help="largest batched multigrid level run with temporally blocked legs")
     ap.add_argument("--reps", type=int, default=3)
@@ -54,7 +57,8 @@ def main(argv=None):
     k = max(1, a.steps // f)
     cfg = hb.default_config(nlevels=a.level + 1, precision=prec, vcycles=a.vcycles,
                             nu1=a.nu[0], nu2=a.nu[1], mg_small_cells=a.small_cells,
-                            jac_lag=a.jac_lag, mg_tb_cells=a.tb_cells, nt0=k, T=1800.0 * k,
+                            jac_lag=a.jac_lag, jac_keep=a.jac_keep, res_rows=a.res_rows,
+                            mg_tb_cells=a.tb_cells, nt0=k, T=1800.0 * k,
                             loop_mode=hb.LOOP_HOST if a.loop == "host" else hb.LOOP_GRAPH)
     ctx = hb.Context(cfg)
     xi = torch.from_numpy(xi_batch(a.level, 0, a.batch)).cuda()
