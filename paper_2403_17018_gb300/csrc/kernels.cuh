@@ -153,6 +153,7 @@ static __global__ void k_init_state(unsigned long long* ctr, Phys P, Geom G, int
 // linearly in time, u = 2 u^{n-1} - u^{n-2}, with c clamped to [0, 1]
 // (p_prev keeps p^{n-2}, c_old c^{n-2} on entry). `step` counts completed
 // steps (k_end_step increments it).
+template <int D = 0>   // history arrays in use (hx.depth)
 static __global__ void k_begin_step(unsigned long long* ctr, Geom G, int B, double* __restrict__ p,
                              double* __restrict__ c, double* __restrict__ p_prev,
                              double* __restrict__ c_old, const int* __restrict__ status,
@@ -182,20 +183,23 @@ static __global__ void k_begin_step(unsigned long long* ctr, Geom G, int B, doub
   // c_old / p_prev hold u^(n-1) on entry and u^n (the old time level of this
   // step) on exit; hx holds u^(n-2) ... and is shifted by one step.
   const double cn = c[idx], pn = p[idx];
-  double hc[1 + kMaxGuessHist], hp[1 + kMaxGuessHist];
+  double hc[1 + D], hp[1 + D];
   hc[0] = c_old[idx];
   hp[0] = p_prev[idx];
-  for (int k = 0; k < hx.depth; ++k) {
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
     hc[k + 1] = hx.c[k][idx];
     hp[k + 1] = hx.p[k][idx];
   }
   int q = extrapolate;
   if (q > *step - 1) q = *step - 1;
-  if (q > 1 + hx.depth) q = 1 + hx.depth;
+  if (q > 1 + D) q = 1 + D;
   if (q >= 1) {
     double w = q + 1.0;                 // C(q+1, 1)
     double ec = w * cn, ep = w * pn;
-    for (int k = 1; k <= q; ++k) {
+#pragma unroll
+    for (int k = 1; k <= 1 + D; ++k) {
+      if (k > q) break;
       w = -w * (q + 1 - k) / (k + 1);   // (-1)^k C(q+1, k+1)
       ec += w * hc[k - 1];
       ep += w * hp[k - 1];
@@ -203,7 +207,8 @@ static __global__ void k_begin_step(unsigned long long* ctr, Geom G, int B, doub
     c[idx] = fmin(fmax(ec, 0.0), 1.0);
     p[idx] = ep;
   }
-  for (int k = hx.depth - 1; k >= 0; --k) {
+#pragma unroll
+  for (int k = D - 1; k >= 0; --k) {
     hx.c[k][idx] = hc[k];
     hx.p[k][idx] = hp[k];
   }

@@ -628,10 +628,7 @@ int Solver::capture_step_t(cudaGraph_t g, cudaStream_t cs, int B, std::vector<St
   cudaGraphConditionalHandle h;
   CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
   MGLevel& F = levels_.back();
-  k_begin_step<<<grid1((int64_t)B * F.g.ncell()), kBlock, 0, cs>>>(
-      counter_, F.g, B, F.p, F.c, p_prev_, c_old_, status_w_, active_, it_step_, step_,
-      cfg_.guess_extrapolation, cfg_.field_model == 1 ? qin0_ : nullptr, qin_, tau_, F.phi,
-      F.g.hx * F.g.hy / tau_, phys_.rho0, phys_.drho, mo_, so_, vt_, hx_);
+  launch_begin_step(B, cs);
   enqueue_resjac_check<T>(B, cs, true, (unsigned long long)h);
   cudaStreamCaptureStatus st;
   cudaGraph_t cg;
@@ -814,16 +811,34 @@ int Solver::setup_t(const double* xi, const double* logk, int B, cudaStream_t s)
   return HENRY_OK;
 }
 
+// Begin every sample's step (k_begin_step, instantiated for the depth of
+// the Newton guess's history).
+void Solver::launch_begin_step(int B, cudaStream_t s) {
+  MGLevel& F = levels_.back();
+  const Geom& G = F.g;
+  auto go = [&](auto kern) {
+    kern<<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(
+        counter_, G, B, F.p, F.c, p_prev_, c_old_, status_w_, active_, it_step_, step_,
+        cfg_.guess_extrapolation, cfg_.field_model == 1 ? qin0_ : nullptr, qin_, tau_, F.phi,
+        G.hx * G.hy / tau_, phys_.rho0, phys_.drho, mo_, so_, vt_, hx_);
+  };
+  switch (hx_.depth) {
+    case 0: go(k_begin_step<0>); break;
+    case 1: go(k_begin_step<1>); break;
+    case 2: go(k_begin_step<2>); break;
+    case 3: go(k_begin_step<3>); break;
+    case 4: go(k_begin_step<4>); break;
+    default: go(k_begin_step<5>); break;
+  }
+}
+
 // One implicit Euler step of every sample (Newton defect correction).
 template <typename T>
 int Solver::step_t(int B, cudaStream_t s) {
   if (cfg_.loop_mode == HENRY_LOOP_GRAPH) return step_graph<T>(B, s);
   MGLevel& F = levels_.back();
   const Geom& G = F.g;
-  k_begin_step<<<grid1((int64_t)B * G.ncell()), kBlock, 0, s>>>(
-      counter_, G, B, F.p, F.c, p_prev_, c_old_, status_w_, active_, it_step_, step_,
-      cfg_.guess_extrapolation, cfg_.field_model == 1 ? qin0_ : nullptr, qin_, tau_, F.phi,
-      G.hx * G.hy / tau_, phys_.rho0, phys_.drho, mo_, so_, vt_, hx_);
+  launch_begin_step(B, s);
   for (;;) {
     enqueue_resjac_check<T>(B, s, false);
     CK(cudaMemcpyAsync(n_active_host_, n_active_, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));

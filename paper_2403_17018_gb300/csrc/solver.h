@@ -151,6 +151,7 @@ class Solver {
   double* p_prev_ = nullptr;    // p of the previous step (initial-guess extrapolation)
   GuessHist hx_ = {};           // u^(n-2), ... for guesses of order >= 2
   // previous states the Newton guess reads beyond u^(n-1)
+  void launch_begin_step(int B, cudaStream_t s);
   int guess_depth() const {
     const int d = cfg_.guess_extrapolation - 1;
     return d < 0 ? 0 : (d > kMaxGuessHist ? kMaxGuessHist : d);
