@@ -570,7 +570,8 @@ def cpu_baseline():
 
 def run_reference(args):
     """The oracle on every host core, on this workload's config and metric:
-    step k times level k mod 4 on every core (levels 0 and 1: whole solves;
+    warm-up step w runs level w mod 4 and timed step k level (W + k) mod 4
+    on every core (levels 0 and 1: whole solves;
     level 2: 12 steps, level 3: 2 steps, each from mid-horizon states of the
     level below prepared in the first warm-up step and scaled to the level's
     step count). value = pairs/s of the workload from the per-level solve
@@ -601,15 +602,24 @@ def run_reference(args):
         for w in range(W):
             for t in one_step(w % 4):
                 seen[w % 4].append(t)
+        # the timed steps continue the cycle of levels where the warm-up left
+        # it, so that warm-up and timed steps together cover every level
         timed = {l: [] for l in LEVELS}
         for k in range(K):
+            level = (W + k) % 4
             t0 = time.perf_counter()
-            timed[k % 4] += one_step(k % 4)
+            timed[level] += one_step(level)
             step_ms.append((time.perf_counter() - t0) * 1e3)
+        # a level that neither reached (fewer than four steps in all) is
+        # measured once more, outside the timed steps
+        for l in LEVELS:
+            if not timed[l] and not seen[l]:
+                seen[l] += one_step(l)
     solve_s = {l: (sum(timed[l]) / len(timed[l])) if timed[l] else sum(seen[l]) / len(seen[l])
                for l in LEVELS}
     value, pair = pair_rate(solve_s, cores)
-    sample = (f"numpy/scipy FP64 oracle, one process per core ({cores}); step k: level k mod 4 "
+    sample = (f"numpy/scipy FP64 oracle, one process per core ({cores}); warm-up step w: level "
+              f"w mod 4, timed step k: level (W + k) mod 4 "
               f"on every core (levels 0, 1 whole solves; level 2: 12 steps, level 3: 2 steps, "
               f"from mid-horizon states, scaled to 96 / 192 steps)")
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
