@@ -568,6 +568,17 @@ def cpu_baseline():
             "pair_seconds": {f"L{l}": round(pair[l], 4) for l in LEVELS}}
 
 
+def reference_levels(W, K):
+    """Levels of the reference arm's warm-up and timed steps: warm-up step w
+    runs level w mod 4, timed step k continues the cycle with level
+    (W + k) mod 4; the levels neither list reaches are measured once more
+    outside the timed steps (the third list)."""
+    warm = [w % 4 for w in range(W)]
+    timed = [(W + k) % 4 for k in range(K)]
+    extra = [l for l in LEVELS if l not in warm and l not in timed]
+    return warm, timed, extra
+
+
 def run_reference(args):
     """The oracle on every host core, on this workload's config and metric:
     warm-up step w runs level w mod 4 and timed step k level (W + k) mod 4
@@ -599,22 +610,16 @@ def run_reference(args):
                     for s in range(cores)]
             return [j.get()[1] for j in jobs]
 
-        for w in range(W):
-            for t in one_step(w % 4):
-                seen[w % 4].append(t)
-        # the timed steps continue the cycle of levels where the warm-up left
-        # it, so that warm-up and timed steps together cover every level
+        warm_levels, timed_levels, extra_levels = reference_levels(W, K)
+        for level in warm_levels:
+            seen[level] += one_step(level)
         timed = {l: [] for l in LEVELS}
-        for k in range(K):
-            level = (W + k) % 4
+        for level in timed_levels:
             t0 = time.perf_counter()
             timed[level] += one_step(level)
             step_ms.append((time.perf_counter() - t0) * 1e3)
-        # a level that neither reached (fewer than four steps in all) is
-        # measured once more, outside the timed steps
-        for l in LEVELS:
-            if not timed[l] and not seen[l]:
-                seen[l] += one_step(l)
+        for level in extra_levels:
+            seen[level] += one_step(level)
     solve_s = {l: (sum(timed[l]) / len(timed[l])) if timed[l] else sum(seen[l]) / len(seen[l])
                for l in LEVELS}
     value, pair = pair_rate(solve_s, cores)
